@@ -1,0 +1,884 @@
+/*
+ * hi_oracle.c -- plain, slow CPU oracle for the interpolation predictor +
+ * error-bounded linear quantizer of cuSZ-Hi (arXiv 2507.11165).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file: only the tests, the smoke check and the timed CPU baseline
+ * of the benchmark use it.  It shares no code, header, table or constant
+ * generator with the CUDA library.
+ *
+ * What it follows (paper sections):
+ *   Sec. 3.1, Eq. 1      -- the pointwise bound |x - x'| <= eps.
+ *   Sec. 3.2             -- anchor grid stored losslessly, hierarchical
+ *                           interpolation from large to small stride, one
+ *                           independent data block per thread block.
+ *   Sec. 5.1.1           -- (A+1)^d blocks that include their anchors,
+ *                           anchor stride A (16 in the paper), log2(A) levels.
+ *   Sec. 5.1.2           -- 1D interpolation passes along a dimension
+ *                           sequence; linear / quadratic / cubic splines.
+ *   Sec. 5.1.3           -- auto-tuning on uniformly sampled blocks (0.2 %)
+ *                           with per-level minimum aggregated error.
+ *   Sec. 5.2.1           -- one-byte quantization codes, outliers stored
+ *                           separately; Sec. 5.2.3: 128 is the zero symbol.
+ *   Sec. 6.1.4 (metrics) -- value-range-relative error bound.
+ *
+ * Readings where the paper is silent (the same list is kept with the design
+ * notes of the repository):
+ *   - stencil weights are the Lagrange midpoint weights: linear (1,1)/2,
+ *     cubic (-1,9,9,-1)/16, and the two one-sided quadratics (3,6,-1)/8 and
+ *     (-1,6,3)/8 near a block edge; a point with no right neighbour (only at
+ *     the global upper edge) is extrapolated linearly, (3b - a)/2, or copied;
+ *   - stencils never leave their block (blocks are independent);
+ *   - quantization radius R = 128: q in [-127,127] maps to code q+128,
+ *     code 0 marks an outlier;  t = (x-p)*r with r = fl(1/(2 eps)), q =
+ *     rint(t) (ties to even), x' = p + q*fl(2 eps);  outlier when
+ *     !(|t| < 127.5) or !(|x - x'| < eb_f), eb_f = largest float <= eps;
+ *   - value-range-relative bound: eps = eb * (max - min) over finite values,
+ *     eps = eb for a constant field;
+ *   - auto-tune error = sum of |x - p| with predictions taken from the
+ *     original (not reconstructed) values; ties go to the first config in
+ *     enumeration order (cubic before linear, lexicographic permutations).
+ *
+ * Arithmetic: float32, every operation written out in the order it is
+ * evaluated; build with -ffp-contract=off and without fast-math so no
+ * multiply-add is ever contracted.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL 1
+#define ORC_ENOMEM 2
+#define ORC_ETRAVERSAL 10 /* a stencil point was read before it was known  */
+#define ORC_EREVISIT 11   /* a point was predicted twice inside one block   */
+#define ORC_EMISSED 12    /* a point of a block was never predicted         */
+#define ORC_EFACE 13      /* two blocks disagree on a shared face point      */
+#define ORC_ECORRUPT 14   /* decompress input references a missing outlier  */
+
+#define ORC_LINEAR 0
+#define ORC_CUBIC 1
+#define ORC_RADIUS 128
+#define ORC_MAX_LEVELS 8
+
+/* ------------------------------------------------------------------------ */
+/* Geometry: blocks of (A+1)^d points sharing their faces (Sec. 5.1.1).     */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t n[3];  /* field dims, slowest -> fastest; a dim of size 1 is inactive */
+    int A;         /* anchor stride                                           */
+    int L;         /* number of interpolation levels, log2(A)                 */
+    int64_t nb[3]; /* blocks per dim                                          */
+    int64_t na[3]; /* anchors per dim                                         */
+    int64_t N;     /* number of points                                        */
+} geom;
+
+static int ilog2_exact(int A)
+{
+    int l = 0;
+    if (A < 2) return -1;
+    while ((1 << l) < A) l++;
+    return ((1 << l) == A) ? l : -1;
+}
+
+static int geom_init(geom* G, const int64_t dims[3], int A)
+{
+    int d;
+    G->A = A;
+    G->L = ilog2_exact(A);
+    if (G->L < 1 || G->L > 5) return ORC_EINVAL;
+    G->N = 1;
+    for (d = 0; d < 3; d++) {
+        if (dims[d] < 1) return ORC_EINVAL;
+        G->n[d] = dims[d];
+        G->N *= dims[d];
+        if (dims[d] == 1) {
+            G->nb[d] = 1;
+        } else {
+            G->nb[d] = (dims[d] - 1 + A - 1) / A; /* ceil((n-1)/A) */
+        }
+        G->na[d] = (dims[d] - 1) / A + 1;
+    }
+    return ORC_OK;
+}
+
+static int64_t gindex(const geom* G, int64_t g0, int64_t g1, int64_t g2)
+{
+    return (g0 * G->n[1] + g1) * G->n[2] + g2;
+}
+
+static int is_anchor(const geom* G, int64_t g0, int64_t g1, int64_t g2)
+{
+    return (g0 % G->A == 0) && (g1 % G->A == 0) && (g2 % G->A == 0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Error-bound constants (Eq. 1 and the value-range-relative bound).       */
+/* ------------------------------------------------------------------------ */
+int hi_oracle_eps(int eb_mode, double eb, const float* x, int64_t N, float* out5, double* eps_out)
+{
+    int64_t i;
+    int any = 0;
+    float vmin = INFINITY, vmax = -INFINITY;
+    double eps;
+    float eb_f, ebx2_f, r_f;
+
+    if (!(eb > 0.0) || !isfinite(eb) || (eb_mode != 0 && eb_mode != 1) || N < 0) return ORC_EINVAL;
+    for (i = 0; i < N; i++) {
+        float v = x[i];
+        if (!isfinite(v)) continue;
+        if (!any) {
+            vmin = v;
+            vmax = v;
+            any = 1;
+        } else {
+            if (v < vmin) vmin = v;
+            if (v > vmax) vmax = v;
+        }
+    }
+    if (!any) {
+        vmin = 0.0f;
+        vmax = 0.0f;
+    }
+    /* a signed zero is reported as +0 */
+    vmin = vmin + 0.0f;
+    vmax = vmax + 0.0f;
+
+    if (eb_mode == 0) {
+        eps = eb;
+    } else {
+        double range = (double)vmax - (double)vmin;
+        eps = (range > 0.0) ? eb * range : eb;
+    }
+    if (!(eps > 0.0) || !isfinite(eps)) return ORC_EINVAL;
+
+    /* eb_f: the largest float not above eps */
+    eb_f = (float)eps;
+    if ((double)eb_f > eps) eb_f = nextafterf(eb_f, 0.0f);
+    ebx2_f = (float)(2.0 * eps);
+    r_f = (float)(1.0 / (2.0 * eps));
+    if (!(eb_f > 0.0f) || !isfinite(ebx2_f) || !isfinite(r_f) || !(r_f > 0.0f)) return ORC_EINVAL;
+
+    out5[0] = eb_f;
+    out5[1] = ebx2_f;
+    out5[2] = r_f;
+    out5[3] = vmin;
+    out5[4] = vmax;
+    if (eps_out) *eps_out = eps;
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Prediction along one line (Sec. 5.1.2; weights: reading above).          */
+/* a = f(c-3s), b = f(c-s), u = f(c+s), v = f(c+3s)                         */
+/* ------------------------------------------------------------------------ */
+static float predict_line(int interp, int have_l3, int have_r, int have_r3, float a, float b, float u,
+                          float v)
+{
+    if (!have_r) {
+        /* global upper edge: no point at c+s */
+        if (have_l3) return (3.0f * b - a) * 0.5f;
+        return b;
+    }
+    if (interp == ORC_LINEAR) return (b + u) * 0.5f;
+    if (have_l3 && have_r3) return (9.0f * (b + u) - (a + v)) * 0.0625f;
+    if (have_r3) return ((3.0f * b + 6.0f * u) - v) * 0.125f;
+    if (have_l3) return ((6.0f * b + 3.0f * u) - a) * 0.125f;
+    return (b + u) * 0.5f;
+}
+
+/* Which stencil predict_line uses (for the traversal trace):
+ * 0 linear midpoint, 1 cubic 4-point, 2 quadratic without f(c-3s),
+ * 3 quadratic without f(c+3s), 4 linear extrapolation, 5 copy of f(c-s). */
+static int stencil_case(int interp, int have_l3, int have_r, int have_r3)
+{
+    if (!have_r) return have_l3 ? 4 : 5;
+    if (interp == ORC_LINEAR) return 0;
+    if (have_l3 && have_r3) return 1;
+    if (have_r3) return 2;
+    if (have_l3) return 3;
+    return 0;
+}
+
+/* Linear quantization of the prediction error (Sec. 5.2.1).  Returns the
+ * code (1..255, or 0 for an outlier) and stores the reconstructed value. */
+static int quantize(float x, float p, float eb_f, float ebx2_f, float r_f, float* xr_out)
+{
+    float t = (x - p) * r_f;
+    float qf, xr;
+    if (!(fabsf(t) < 127.5f)) {
+        *xr_out = x;
+        return 0;
+    }
+    qf = rintf(t);
+    xr = p + qf * ebx2_f;
+    if (!(fabsf(x - xr) < eb_f)) {
+        *xr_out = x;
+        return 0;
+    }
+    *xr_out = xr;
+    return (int)qf + ORC_RADIUS;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One block.                                                               */
+/* ------------------------------------------------------------------------ */
+enum { MODE_COMPRESS = 0, MODE_DECOMPRESS = 1, MODE_TUNE = 2 };
+
+typedef struct {
+    const geom* G;
+    int64_t o[3]; /* origin */
+    int e[3];     /* local extent per dim (0 for an inactive dim) */
+    int P;        /* local pitch: A+1 */
+    float* orig;  /* original values (compress, tune) */
+    float* rec;   /* reconstructed values */
+    uint8_t* known;
+    uint8_t* code;
+} block;
+
+static int lidx(const block* B, int c0, int c1, int c2)
+{
+    return (c0 * B->P + c1) * B->P + c2;
+}
+
+static void block_init(block* B, const geom* G, int64_t t0, int64_t t1, int64_t t2)
+{
+    int64_t t[3];
+    int d;
+    t[0] = t0;
+    t[1] = t1;
+    t[2] = t2;
+    B->G = G;
+    B->P = G->A + 1;
+    for (d = 0; d < 3; d++) {
+        B->o[d] = t[d] * G->A;
+        if (G->n[d] == 1) {
+            B->e[d] = 0;
+        } else {
+            int64_t rem = G->n[d] - 1 - B->o[d];
+            B->e[d] = (int)(rem < G->A ? rem : G->A);
+        }
+    }
+    memset(B->known, 0, (size_t)B->P * B->P * B->P);
+}
+
+typedef struct {
+    int mode;
+    float eb_f, ebx2_f, r_f;
+    /* decompress inputs */
+    const uint8_t* g_codes;
+    const float* g_outval; /* dense outlier values, indexed by point */
+    const uint8_t* g_outhas;
+    /* tune output */
+    double err;
+    /* optional traversal trace, indexed by point: level, dimension, stencil case */
+    int8_t* t_lvl;
+    int8_t* t_dir;
+    int8_t* t_case;
+    int status;
+} action;
+
+/* Every point c of the block with
+ *   c[d_p] = s mod 2s,  c[d_q] = 0 mod s (q < p),  c[d_q] = 0 mod 2s (q > p)
+ * is predicted in pass p of level l (stride s = 2^l) along d_p = order[p]. */
+static void run_level(block* B, int l, int interp, const uint8_t order[3], action* act)
+{
+    int s = 1 << l;
+    int p, q, d;
+    for (p = 0; p < 3; p++) {
+        int dp = order[p];
+        int start[3], step[3];
+        int c[3];
+        for (q = 0; q < 3; q++) {
+            d = order[q];
+            if (q == p) {
+                start[d] = s;
+                step[d] = 2 * s;
+            } else if (q < p) {
+                start[d] = 0;
+                step[d] = s;
+            } else {
+                start[d] = 0;
+                step[d] = 2 * s;
+            }
+        }
+        for (c[0] = start[0]; c[0] <= B->e[0]; c[0] += step[0])
+            for (c[1] = start[1]; c[1] <= B->e[1]; c[1] += step[1])
+                for (c[2] = start[2]; c[2] <= B->e[2]; c[2] += step[2]) {
+                    int li = lidx(B, c[0], c[1], c[2]);
+                    int cd = c[dp];
+                    int e = B->e[dp];
+                    int have_l3 = (cd - 3 * s) >= 0;
+                    int have_r = (cd + s) <= e;
+                    int have_r3 = (cd + 3 * s) <= e;
+                    int cm[3], cl[3];
+                    float a = 0.0f, b, u = 0.0f, v = 0.0f, pr;
+                    const float* src = (act->mode == MODE_TUNE) ? B->orig : B->rec;
+                    int lb, la = -1, lu = -1, lv = -1;
+
+                    if (B->known[li]) {
+                        act->status = ORC_EREVISIT;
+                        return;
+                    }
+                    memcpy(cm, c, sizeof cm);
+                    memcpy(cl, c, sizeof cl);
+                    cm[dp] = cd - s;
+                    lb = lidx(B, cm[0], cm[1], cm[2]);
+                    if (have_r) {
+                        cm[dp] = cd + s;
+                        lu = lidx(B, cm[0], cm[1], cm[2]);
+                    }
+                    if (have_l3) {
+                        cl[dp] = cd - 3 * s;
+                        la = lidx(B, cl[0], cl[1], cl[2]);
+                    }
+                    if (have_r3) {
+                        cl[dp] = cd + 3 * s;
+                        lv = lidx(B, cl[0], cl[1], cl[2]);
+                    }
+                    /* every stencil point must already be known */
+                    if (!B->known[lb] || (lu >= 0 && !B->known[lu]) || (la >= 0 && !B->known[la]) ||
+                        (lv >= 0 && !B->known[lv])) {
+                        act->status = ORC_ETRAVERSAL;
+                        return;
+                    }
+                    b = src[lb];
+                    if (lu >= 0) u = src[lu];
+                    if (la >= 0) a = src[la];
+                    if (lv >= 0) v = src[lv];
+                    pr = predict_line(interp, have_l3, have_r, have_r3, a, b, u, v);
+
+                    if (act->mode == MODE_COMPRESS) {
+                        float xr;
+                        int k = quantize(B->orig[li], pr, act->eb_f, act->ebx2_f, act->r_f, &xr);
+                        B->code[li] = (uint8_t)k;
+                        B->rec[li] = xr;
+                    } else if (act->mode == MODE_DECOMPRESS) {
+                        int64_t g = gindex(B->G, B->o[0] + c[0], B->o[1] + c[1], B->o[2] + c[2]);
+                        int k = act->g_codes[g];
+                        B->code[li] = (uint8_t)k;
+                        if (k == 0) {
+                            if (!act->g_outhas[g]) {
+                                act->status = ORC_ECORRUPT;
+                                return;
+                            }
+                            B->rec[li] = act->g_outval[g];
+                        } else {
+                            B->rec[li] = pr + (float)(k - ORC_RADIUS) * act->ebx2_f;
+                        }
+                    } else {
+                        float x = B->orig[li];
+                        act->err += (double)fabsf(x - pr);
+                    }
+                    if (act->t_lvl) {
+                        int64_t g = gindex(B->G, B->o[0] + c[0], B->o[1] + c[1], B->o[2] + c[2]);
+                        int kc = stencil_case(interp, have_l3, have_r, have_r3);
+                        if (act->t_lvl[g] >= 0 &&
+                            (act->t_lvl[g] != l || act->t_dir[g] != dp || act->t_case[g] != kc)) {
+                            act->status = ORC_EFACE;
+                            return;
+                        }
+                        act->t_lvl[g] = (int8_t)l;
+                        act->t_dir[g] = (int8_t)dp;
+                        act->t_case[g] = (int8_t)kc;
+                    }
+                    B->known[li] = 1;
+                }
+    }
+}
+
+/* Seed the anchors of a block; load originals if needed. */
+static void block_seed(block* B, const float* x, const float* anchors, int mode)
+{
+    const geom* G = B->G;
+    int c0, c1, c2;
+    for (c0 = 0; c0 <= B->e[0]; c0++)
+        for (c1 = 0; c1 <= B->e[1]; c1++)
+            for (c2 = 0; c2 <= B->e[2]; c2++) {
+                int li = lidx(B, c0, c1, c2);
+                int64_t g0 = B->o[0] + c0, g1 = B->o[1] + c1, g2 = B->o[2] + c2;
+                if (mode != MODE_DECOMPRESS) B->orig[li] = x[gindex(G, g0, g1, g2)];
+                if (is_anchor(G, g0, g1, g2)) {
+                    float av;
+                    if (mode == MODE_DECOMPRESS) {
+                        av = anchors[(g0 / G->A * G->na[1] + g1 / G->A) * G->na[2] + g2 / G->A];
+                    } else {
+                        av = x[gindex(G, g0, g1, g2)];
+                    }
+                    B->rec[li] = av;
+                    B->code[li] = ORC_RADIUS;
+                    B->known[li] = 1;
+                }
+            }
+}
+
+static int block_complete(const block* B)
+{
+    int c0, c1, c2;
+    for (c0 = 0; c0 <= B->e[0]; c0++)
+        for (c1 = 0; c1 <= B->e[1]; c1++)
+            for (c2 = 0; c2 <= B->e[2]; c2++)
+                if (!B->known[lidx(B, c0, c1, c2)]) return 0;
+    return 1;
+}
+
+static int check_levels(int L, const uint8_t* interp, const uint8_t* order)
+{
+    int l;
+    for (l = 0; l < L; l++) {
+        int seen = 0, q;
+        if (interp[l] != ORC_LINEAR && interp[l] != ORC_CUBIC) return ORC_EINVAL;
+        for (q = 0; q < 3; q++) {
+            if (order[3 * l + q] > 2) return ORC_EINVAL;
+            seen |= 1 << order[3 * l + q];
+        }
+        if (seen != 7) return ORC_EINVAL;
+    }
+    return ORC_OK;
+}
+
+/* Run every level of one block, from the coarsest to the finest. */
+static int block_run(block* B, const uint8_t* interp, const uint8_t* order, action* act)
+{
+    int l;
+    for (l = B->G->L - 1; l >= 0; l--) {
+        run_level(B, l, interp[l], order + 3 * l, act);
+        if (act->status) return act->status;
+    }
+    if (!block_complete(B)) return ORC_EMISSED;
+    return ORC_OK;
+}
+
+/* Write a finished block into the global arrays; a point written earlier
+ * by another block must carry identical bits. */
+static int block_store(const block* B, uint8_t* g_codes, float* g_rec, uint8_t* written)
+{
+    const geom* G = B->G;
+    int c0, c1, c2;
+    for (c0 = 0; c0 <= B->e[0]; c0++)
+        for (c1 = 0; c1 <= B->e[1]; c1++)
+            for (c2 = 0; c2 <= B->e[2]; c2++) {
+                int li = lidx(B, c0, c1, c2);
+                int64_t g = gindex(G, B->o[0] + c0, B->o[1] + c1, B->o[2] + c2);
+                if (written[g]) {
+                    if (g_codes && g_codes[g] != B->code[li]) return ORC_EFACE;
+                    if (memcmp(&g_rec[g], &B->rec[li], sizeof(float)) != 0) return ORC_EFACE;
+                } else {
+                    if (g_codes) g_codes[g] = B->code[li];
+                    g_rec[g] = B->rec[li];
+                    written[g] = 1;
+                }
+            }
+    return ORC_OK;
+}
+
+typedef struct {
+    float* orig;
+    float* rec;
+    uint8_t* known;
+    uint8_t* code;
+} block_mem;
+
+static int block_mem_alloc(block_mem* M, int A)
+{
+    size_t V = (size_t)(A + 1) * (A + 1) * (A + 1);
+    M->orig = (float*)malloc(V * sizeof(float));
+    M->rec = (float*)malloc(V * sizeof(float));
+    M->known = (uint8_t*)malloc(V);
+    M->code = (uint8_t*)malloc(V);
+    if (!M->orig || !M->rec || !M->known || !M->code) return ORC_ENOMEM;
+    return ORC_OK;
+}
+
+static void block_mem_free(block_mem* M)
+{
+    free(M->orig);
+    free(M->rec);
+    free(M->known);
+    free(M->code);
+}
+
+static void block_attach(block* B, block_mem* M)
+{
+    B->orig = M->orig;
+    B->rec = M->rec;
+    B->known = M->known;
+    B->code = M->code;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Compress.                                                                */
+/*   consts = {eb_f, ebx2_f, r_f}.                                          */
+/*   tiles / ntiles: optional list of linear block ids (row-major over the  */
+/*   block grid); NULL = every block.  Only the listed blocks are written.  */
+/*   Outputs (codes, recon: N entries; anchors: na0*na1*na2) are written    */
+/*   only at points of processed blocks.                                    */
+/* ------------------------------------------------------------------------ */
+int hi_oracle_compress(const int64_t dims[3], int A, const uint8_t* interp, const uint8_t* order,
+                       const float* consts, const float* x, const int64_t* tiles, int64_t ntiles,
+                       uint8_t* codes, float* anchors, float* recon)
+{
+    geom G;
+    block B;
+    block_mem M;
+    action act;
+    uint8_t* written;
+    int64_t k, nblocks;
+    int rc = geom_init(&G, dims, A);
+    if (rc) return rc;
+    rc = check_levels(G.L, interp, order);
+    if (rc) return rc;
+    nblocks = G.nb[0] * G.nb[1] * G.nb[2];
+    if (block_mem_alloc(&M, A)) {
+        block_mem_free(&M);
+        return ORC_ENOMEM;
+    }
+    written = (uint8_t*)calloc((size_t)G.N, 1);
+    if (!written) {
+        block_mem_free(&M);
+        return ORC_ENOMEM;
+    }
+    block_attach(&B, &M);
+    memset(&act, 0, sizeof act);
+    act.mode = MODE_COMPRESS;
+    act.eb_f = consts[0];
+    act.ebx2_f = consts[1];
+    act.r_f = consts[2];
+
+    for (k = 0; k < (tiles ? ntiles : nblocks); k++) {
+        int64_t t = tiles ? tiles[k] : k;
+        int64_t t0, t1, t2;
+        if (t < 0 || t >= nblocks) {
+            rc = ORC_EINVAL;
+            break;
+        }
+        t0 = t / (G.nb[1] * G.nb[2]);
+        t1 = (t / G.nb[2]) % G.nb[1];
+        t2 = t % G.nb[2];
+        block_init(&B, &G, t0, t1, t2);
+        block_seed(&B, x, NULL, MODE_COMPRESS);
+        rc = block_run(&B, interp, order, &act);
+        if (rc) break;
+        rc = block_store(&B, codes, recon, written);
+        if (rc) break;
+    }
+    if (!rc && anchors) {
+        /* anchors of processed points, verbatim (Sec. 3.2) */
+        int64_t a0, a1, a2;
+        for (a0 = 0; a0 < G.na[0]; a0++)
+            for (a1 = 0; a1 < G.na[1]; a1++)
+                for (a2 = 0; a2 < G.na[2]; a2++) {
+                    int64_t g = gindex(&G, a0 * A, a1 * A, a2 * A);
+                    if (written[g]) anchors[(a0 * G.na[1] + a1) * G.na[2] + a2] = x[g];
+                }
+    }
+    free(written);
+    block_mem_free(&M);
+    return rc;
+}
+
+/* Outliers and histogram from a complete code array: every non-anchor point
+ * with code 0 is an outlier (index ascending, value = original); the
+ * histogram counts the codes of the non-anchor points. */
+int hi_oracle_collect(const int64_t dims[3], int A, const float* x, const uint8_t* codes,
+                      uint32_t* out_idx, float* out_val, int64_t out_cap, int64_t* n_out, uint32_t* hist256)
+{
+    geom G;
+    int64_t g0, g1, g2, cnt = 0;
+    int rc = geom_init(&G, dims, A);
+    if (rc) return rc;
+    if (hist256) memset(hist256, 0, 256 * sizeof(uint32_t));
+    for (g0 = 0; g0 < G.n[0]; g0++)
+        for (g1 = 0; g1 < G.n[1]; g1++)
+            for (g2 = 0; g2 < G.n[2]; g2++) {
+                int64_t g = gindex(&G, g0, g1, g2);
+                if (is_anchor(&G, g0, g1, g2)) continue;
+                if (hist256) hist256[codes[g]]++;
+                if (codes[g] == 0) {
+                    if (cnt < out_cap) {
+                        out_idx[cnt] = (uint32_t)g;
+                        out_val[cnt] = x[g];
+                    }
+                    cnt++;
+                }
+            }
+    *n_out = cnt;
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Decompress: the same traversal; x' = p + (code-128)*fl(2 eps), or the    */
+/* stored outlier value when the code is 0.                                 */
+/* ------------------------------------------------------------------------ */
+int hi_oracle_decompress(const int64_t dims[3], int A, const uint8_t* interp, const uint8_t* order,
+                         float ebx2_f, const uint8_t* codes, const float* anchors, const uint32_t* out_idx,
+                         const float* out_val, int64_t n_out, const int64_t* tiles, int64_t ntiles, float* recon)
+{
+    geom G;
+    block B;
+    block_mem M;
+    action act;
+    uint8_t *written, *outhas;
+    float* outval;
+    int64_t k, nblocks;
+    int rc = geom_init(&G, dims, A);
+    if (rc) return rc;
+    rc = check_levels(G.L, interp, order);
+    if (rc) return rc;
+    nblocks = G.nb[0] * G.nb[1] * G.nb[2];
+    if (block_mem_alloc(&M, A)) {
+        block_mem_free(&M);
+        return ORC_ENOMEM;
+    }
+    written = (uint8_t*)calloc((size_t)G.N, 1);
+    outhas = (uint8_t*)calloc((size_t)G.N, 1);
+    outval = (float*)calloc((size_t)G.N, sizeof(float));
+    if (!written || !outhas || !outval) {
+        rc = ORC_ENOMEM;
+        goto done;
+    }
+    for (k = 0; k < n_out; k++) {
+        if ((int64_t)out_idx[k] >= G.N) {
+            rc = ORC_ECORRUPT;
+            goto done;
+        }
+        outhas[out_idx[k]] = 1;
+        outval[out_idx[k]] = out_val[k];
+    }
+    block_attach(&B, &M);
+    memset(&act, 0, sizeof act);
+    act.mode = MODE_DECOMPRESS;
+    act.ebx2_f = ebx2_f;
+    act.g_codes = codes;
+    act.g_outval = outval;
+    act.g_outhas = outhas;
+    for (k = 0; k < (tiles ? ntiles : nblocks); k++) {
+        int64_t t = tiles ? tiles[k] : k;
+        int64_t t0, t1, t2;
+        if (t < 0 || t >= nblocks) {
+            rc = ORC_EINVAL;
+            break;
+        }
+        t0 = t / (G.nb[1] * G.nb[2]);
+        t1 = (t / G.nb[2]) % G.nb[1];
+        t2 = t % G.nb[2];
+        block_init(&B, &G, t0, t1, t2);
+        block_seed(&B, NULL, anchors, MODE_DECOMPRESS);
+        rc = block_run(&B, interp, order, &act);
+        if (rc) break;
+        rc = block_store(&B, NULL, recon, written);
+        if (rc) break;
+    }
+done:
+    free(written);
+    free(outhas);
+    free(outval);
+    block_mem_free(&M);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Auto-tuning (Sec. 5.1.3).                                                */
+/* ------------------------------------------------------------------------ */
+
+/* Number of sampled blocks: 0.2 % of the points, in whole blocks. */
+int64_t hi_oracle_tune_samples(const int64_t dims[3], int A)
+{
+    geom G;
+    int64_t nblocks, vol = 1, m;
+    int d;
+    if (geom_init(&G, dims, A)) return -1;
+    nblocks = G.nb[0] * G.nb[1] * G.nb[2];
+    for (d = 0; d < 3; d++)
+        if (G.n[d] > 1) vol *= A;
+    m = (int64_t)floor(0.002 * (double)G.N / (double)vol + 0.5);
+    if (m < 1) m = 1;
+    if (m > nblocks) m = nblocks;
+    return m;
+}
+
+/* Candidate configurations of one level, in enumeration order: cubic before
+ * linear; within each, the permutations of the active dims in lexicographic
+ * order, inactive dims appended in ascending order.  Returns the count. */
+int hi_oracle_tune_configs(const int64_t dims[3], uint8_t* interp_out, uint8_t* order_out)
+{
+    int act[3], na = 0, inact[3], ni = 0, d, i, cnt = 0, sp;
+    int perms[6][3], np = 0;
+    for (d = 0; d < 3; d++) {
+        if (dims[d] > 1)
+            act[na++] = d;
+        else
+            inact[ni++] = d;
+    }
+    if (na == 0) {
+        perms[0][0] = 0;
+        perms[0][1] = 1;
+        perms[0][2] = 2;
+        np = 1;
+    } else if (na == 1) {
+        perms[0][0] = act[0];
+        np = 1;
+    } else if (na == 2) {
+        perms[0][0] = act[0];
+        perms[0][1] = act[1];
+        perms[1][0] = act[1];
+        perms[1][1] = act[0];
+        np = 2;
+    } else {
+        int a, b, c;
+        for (a = 0; a < 3; a++)
+            for (b = 0; b < 3; b++)
+                for (c = 0; c < 3; c++)
+                    if (a != b && b != c && a != c) {
+                        perms[np][0] = a;
+                        perms[np][1] = b;
+                        perms[np][2] = c;
+                        np++;
+                    }
+    }
+    for (sp = 0; sp < 2; sp++) {
+        for (i = 0; i < np; i++) {
+            int q;
+            interp_out[cnt] = (uint8_t)(sp == 0 ? ORC_CUBIC : ORC_LINEAR);
+            if (na == 0) {
+                for (q = 0; q < 3; q++) order_out[3 * cnt + q] = (uint8_t)perms[i][q];
+            } else {
+                for (q = 0; q < na; q++) order_out[3 * cnt + q] = (uint8_t)perms[i][q];
+                for (q = 0; q < ni; q++) order_out[3 * cnt + na + q] = (uint8_t)inact[q];
+            }
+            cnt++;
+        }
+    }
+    return cnt;
+}
+
+/* err[l * ncfg + c]: sum over the sampled blocks of |x - p| for the points
+ * of level l under configuration c, predictions from original values.
+ * The sampled blocks are every (nblocks / m)-th block, starting at block 0. */
+int hi_oracle_tune_errors(const int64_t dims[3], int A, const float* x, double* err, int* ncfg_out)
+{
+    geom G;
+    block B;
+    block_mem M;
+    action act;
+    uint8_t cinterp[12], corder[36];
+    uint8_t lvl_interp[ORC_MAX_LEVELS], lvl_order[3 * ORC_MAX_LEVELS];
+    int64_t m, stride, k, nblocks;
+    int ncfg, c, l, rc = geom_init(&G, dims, A);
+    if (rc) return rc;
+    nblocks = G.nb[0] * G.nb[1] * G.nb[2];
+    m = hi_oracle_tune_samples(dims, A);
+    stride = nblocks / m;
+    ncfg = hi_oracle_tune_configs(dims, cinterp, corder);
+    *ncfg_out = ncfg;
+    for (k = 0; k < G.L * ncfg; k++) err[k] = 0.0;
+    if (block_mem_alloc(&M, A)) {
+        block_mem_free(&M);
+        return ORC_ENOMEM;
+    }
+    block_attach(&B, &M);
+    for (k = 0; k < m; k++) {
+        int64_t t = k * stride;
+        int64_t t0 = t / (G.nb[1] * G.nb[2]);
+        int64_t t1 = (t / G.nb[2]) % G.nb[1];
+        int64_t t2 = t % G.nb[2];
+        for (l = G.L - 1; l >= 0; l--) {
+            for (c = 0; c < ncfg; c++) {
+                int ll, q;
+                /* levels above l are irrelevant: open-loop predictions read
+                 * originals; mark them known by running them with config c */
+                for (ll = 0; ll < G.L; ll++) {
+                    lvl_interp[ll] = cinterp[c];
+                    for (q = 0; q < 3; q++) lvl_order[3 * ll + q] = corder[3 * c + q];
+                }
+                block_init(&B, &G, t0, t1, t2);
+                block_seed(&B, x, NULL, MODE_TUNE);
+                memset(&act, 0, sizeof act);
+                act.mode = MODE_TUNE;
+                for (ll = G.L - 1; ll > l; ll--) {
+                    run_level(&B, ll, lvl_interp[ll], lvl_order + 3 * ll, &act);
+                    if (act.status) break;
+                }
+                if (act.status) {
+                    rc = act.status;
+                    goto done;
+                }
+                act.err = 0.0;
+                run_level(&B, l, cinterp[c], corder + 3 * c, &act);
+                if (act.status) {
+                    rc = act.status;
+                    goto done;
+                }
+                err[l * ncfg + c] += act.err;
+            }
+        }
+    }
+done:
+    block_mem_free(&M);
+    return rc;
+}
+
+/* Per level, the configuration with the smallest error; ties go to the
+ * first in enumeration order. */
+int hi_oracle_tune_select(const int64_t dims[3], int A, const double* err, uint8_t* interp, uint8_t* order)
+{
+    uint8_t cinterp[12], corder[36];
+    int ncfg = hi_oracle_tune_configs(dims, cinterp, corder);
+    int L = ilog2_exact(A), l, c, q;
+    if (L < 1) return ORC_EINVAL;
+    for (l = 0; l < L; l++) {
+        int best = 0;
+        for (c = 1; c < ncfg; c++)
+            if (err[l * ncfg + c] < err[l * ncfg + best]) best = c;
+        interp[l] = cinterp[best];
+        for (q = 0; q < 3; q++) order[3 * l + q] = corder[3 * best + q];
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Traversal trace: for every point, the level, the dimension and the       */
+/* stencil case of its prediction (-1 for anchors).  Shared face points     */
+/* must be traced identically by both blocks.                               */
+/* ------------------------------------------------------------------------ */
+int hi_oracle_trace(const int64_t dims[3], int A, const uint8_t* interp, const uint8_t* order, int8_t* lvl,
+                    int8_t* dir, int8_t* kase)
+{
+    geom G;
+    block B;
+    block_mem M;
+    action act;
+    int64_t t, nblocks, g;
+    float* zeros;
+    int rc = geom_init(&G, dims, A);
+    if (rc) return rc;
+    rc = check_levels(G.L, interp, order);
+    if (rc) return rc;
+    nblocks = G.nb[0] * G.nb[1] * G.nb[2];
+    zeros = (float*)calloc((size_t)G.N, sizeof(float));
+    if (!zeros || block_mem_alloc(&M, A)) {
+        free(zeros);
+        return ORC_ENOMEM;
+    }
+    for (g = 0; g < G.N; g++) {
+        lvl[g] = -1;
+        dir[g] = -1;
+        kase[g] = -1;
+    }
+    block_attach(&B, &M);
+    memset(&act, 0, sizeof act);
+    act.mode = MODE_TUNE;
+    act.t_lvl = lvl;
+    act.t_dir = dir;
+    act.t_case = kase;
+    for (t = 0; t < nblocks; t++) {
+        block_init(&B, &G, t / (G.nb[1] * G.nb[2]), (t / G.nb[2]) % G.nb[1], t % G.nb[2]);
+        block_seed(&B, zeros, NULL, MODE_TUNE);
+        rc = block_run(&B, interp, order, &act);
+        if (rc) break;
+    }
+    free(zeros);
+    block_mem_free(&M);
+    return rc;
+}
