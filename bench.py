@@ -1,0 +1,399 @@
+"""Benchmark: interpolation predict/quantize + reconstruct on GB300.
+
+One step = one compression (header set-up, value range, auto-tune on 0.2% of
+the blocks, fused predict-quantize with outlier compaction and code
+histogram) plus one decompression (outlier scatter, level-by-level
+reconstruction) of a 512^3 float32 log-normal Gaussian random field
+(P(k) ~ k^-3) at value-range-relative error bound 1e-3, anchor stride 16.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints ONE JSON line (rank 0).  ``value`` = input bytes (4 B per point, all
+ranks) per second of device time for compress + decompress; the per-stage
+CUDA-event times give the predict-quantize and reconstruct throughputs and
+the HBM roofline fraction of the dominant kernel.  ``--impl reference`` times
+the CPU oracle (the reference arm of this benchmark) on host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SHAPE = (512, 512, 512)
+EB = 1e-3
+A = 16
+SEED = 1
+WORKLOAD = "512^3 float32 log-normal GRF P(k)~k^-3 (seed 1), rel eb 1e-3, anchor stride 16, auto-tuned levels"
+METRIC = "compress / decompress input GB/s per GB300 at rel eb 1e-3 (% HBM peak), bit-exact"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index, period_ms=50):
+        self.index = index
+        self.period_ms = period_ms
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", str(self.period_ms)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.06)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+        return False
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [v.strip() for v in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return dict(sm_mhz=None, sm_max_mhz=mx, reasons=sorted(reasons), samples=0)
+        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=mx, reasons=sorted(reasons), samples=len(sm))
+
+
+def traffic_record(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    r = rec.get(kernel)
+    if not r:
+        return None
+    if r.get("source_sha") != kernel_source_sha():
+        return None
+    return r.get("bytes_per_launch")
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2507_11165_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+# ---------------------------------------------------------------------------
+# reference arm / CPU baseline: the oracle, as it stands, on host cores
+# ---------------------------------------------------------------------------
+def oracle_roundtrip(x):
+    import oracle
+    import numpy as np
+    cst = oracle.eps_constants(x, oracle.REL, EB)
+    err = oracle.tune_errors(x, A)
+    interp, order = oracle.tune_select(x.shape, A, err)
+    out = oracle.compress(x, A, interp, order, cst)
+    col = oracle.collect(x, out["codes"], A)
+    y = oracle.decompress(x.shape, A, interp, order, cst["ebx2_f"], out["codes"], out["anchors"], col["out_idx"],
+                          col["out_val"])
+    return out, y, (interp, order)
+
+
+def cpu_baseline(x, planes):
+    """Oracle compress + decompress of the first ``planes`` planes (bounded sample)."""
+    import numpy as np
+    sub = np.ascontiguousarray(x[:planes])
+    t0 = time.perf_counter()
+    out, y, cfg = oracle_roundtrip(sub)
+    dt = time.perf_counter() - t0
+    return dict(value=4.0 * sub.size / dt / 1e9, unit="GB/s", cores=1, kind="oracle",
+                sample="compress+decompress of planes [0,%d) of the workload field (%d x %d x %d), "
+                       "single-threaded C oracle" % (planes, planes, x.shape[1], x.shape[2]),
+                seconds=dt), out
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if ws > 1 and rank != 0:
+        return
+    from paper_2507_11165_gb300 import fields
+    import numpy as np
+    x = fields.lognormal_grf(SHAPE, seed=SEED)
+    planes = args.ref_planes
+    sub = np.ascontiguousarray(x[:planes])
+    for _ in range(args.warmup):
+        oracle_roundtrip(sub)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_roundtrip(sub)
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    v = 4.0 * sub.size / t / 1e9
+    line = dict(metric=METRIC, value=v, unit="GB/s", impl="reference", n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=t * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f32", data="synthetic",
+                config=dict(workload=WORKLOAD, sample="planes [0,%d) per step" % planes),
+                cpu_baseline=dict(value=v, unit="GB/s", cores=1, kind="oracle",
+                                  sample="compress+decompress of planes [0,%d) (%d x 512 x 512) per step, "
+                                         "single-threaded C oracle" % (planes, planes)),
+                e2e=dict(value=v, unit="GB/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2507_11165_gb300 import fields, hi
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    x_host = fields.lognormal_grf(SHAPE, seed=SEED)
+    N = x_host.size
+    x = torch.from_numpy(x_host).to(dev)
+    p = hi.make_params(SHAPE, EB, "rel", A, autotune=True)
+    b = hi.alloc(p, SHAPE, dev, hist=True, recon=False)
+    out = torch.empty(SHAPE, dtype=torch.float32, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def step():
+        hi.compress_into(x, b)
+        hi.decompress_into(b, out, status)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    h = hi.read_header(b.header)
+    assert h.status == 0 and int(status.item()) == 0, (h.status, int(status.item()))
+
+    # per-stage events on a bounded number of steps inside the timed region
+    n_ev = min(args.steps, 256)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(n_ev)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_start.record(stream)
+        for k in range(args.steps):
+            if k < n_ev:
+                hi.set_stage_events(ev[k])
+            elif k == n_ev:
+                hi.set_stage_events(None)
+            step()
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    hi.set_stage_events(None)
+    if ws > 1:
+        dist.barrier()
+    ms = t_start.elapsed_time(t_end) / args.steps
+    if ws > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    stage_names = ["setup", "range", "autotune", "predict_quantize", "scatter", "reconstruct"]
+    pairs = [(0, 1), (1, 2), (2, 3), (3, 4), (5, 6), (6, 7)]
+    st = {n: sum(e[a].elapsed_time(e[b_]) for e in ev) / n_ev for n, (a, b_) in zip(stage_names, pairs)}
+
+    # results of the last step: quality and size
+    h = hi.read_header(b.header)
+    assert h.status == 0 and int(status.item()) == 0
+    hist = b.hist.cpu().numpy().view(np.uint32)
+    est = hi.estimate_cr(hist, int(h.n_outliers), int(h.n_anchors), N)
+    err = (out - x).abs().max().item()
+    mse = float(((out.double() - x.double()) ** 2).mean().item())
+    vrange = float(h.vmax) - float(h.vmin)
+    psnr = 20 * math.log10(vrange) - 10 * math.log10(mse) if mse > 0 else float("inf")
+
+    bytes_in = 4.0 * N
+    n_out = int(h.n_outliers)
+    n_anc = int(h.n_anchors)
+    alg = {"predict_quantize": 4.0 * N + N + 4.0 * n_anc + 8.0 * n_out,
+           "reconstruct": N + 4.0 * n_anc + 4.0 * N}
+    peak, peak_kind = peaks()
+    dom = max(("predict_quantize", "reconstruct"), key=lambda k: st[k])
+    achieved = alg[dom] / (st[dom] * 1e-3) / 1e9
+    kname = {"predict_quantize": "k_compress", "reconstruct": "k_decompress"}[dom]
+    traffic = traffic_record(kname)
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(x_host).pin_memory()
+        codes_h = torch.empty(N, dtype=torch.uint8).pin_memory()
+        anch_h = torch.empty(b.anchors.numel(), dtype=torch.float32).pin_memory()
+        oidx_h = torch.empty(b.out_cap, dtype=torch.int32).pin_memory()
+        oval_h = torch.empty(b.out_cap, dtype=torch.float32).pin_memory()
+        hdr_h = torch.empty(hi.HEADER_BYTES, dtype=torch.uint8).pin_memory()
+        y_h = torch.empty(SHAPE, dtype=torch.float32).pin_memory()
+        xd = torch.empty_like(x)
+        b2 = hi.alloc(p, SHAPE, dev, hist=True, recon=False)
+        io = {"h2d": 0, "d2h": 0}
+
+        def e2e_step():
+            # host field -> device -> compressed record on the host -> device -> host field
+            xd.copy_(xh, non_blocking=True)
+            hi.compress_into(xd, b)
+            hdr = hi.read_header(b.header)  # the record's size is known only now
+            k = min(int(hdr.n_outliers), b.out_cap)
+            codes_h.copy_(b.codes, non_blocking=True)
+            anch_h.copy_(b.anchors, non_blocking=True)
+            hdr_h.copy_(b.header, non_blocking=True)
+            if k:
+                oidx_h[:k].copy_(b.out_idx[:k], non_blocking=True)
+                oval_h[:k].copy_(b.out_val[:k], non_blocking=True)
+            b2.codes.copy_(codes_h, non_blocking=True)
+            b2.anchors.copy_(anch_h, non_blocking=True)
+            b2.header.copy_(hdr_h, non_blocking=True)
+            if k:
+                b2.out_idx[:k].copy_(oidx_h[:k], non_blocking=True)
+                b2.out_val[:k].copy_(oval_h[:k], non_blocking=True)
+            hi.decompress_into(b2, out, status)
+            y_h.copy_(out, non_blocking=True)
+            return k
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        ke = max(3, min(args.steps, 20))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ks = []
+        for _ in range(ke):
+            ks.append(e2e_step())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1) / ke
+        kmean = sum(ks) / len(ks)
+        h2d = 4 * N + (N + 4 * b.anchors.numel() + hi.HEADER_BYTES + 8 * kmean)
+        d2h = (N + 4 * b.anchors.numel() + hi.HEADER_BYTES + 8 * kmean) + hi.HEADER_BYTES + 4 * N
+        assert torch.equal(y_h.to(dev), out)
+        if ws > 1:
+            tt = torch.tensor([ems], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ems = float(tt.item())
+        e2e = dict(value=ws * bytes_in / (ems * 1e-3) / 1e9, unit="GB/s", ms_per_step=ems,
+                   h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h))
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu, ref = cpu_baseline(x_host, args.cpu_planes)
+        if args.cpu_planes == SHAPE[0]:
+            # same field, same eb: the oracle's codes must equal this run's, bit for bit
+            cpu["codes_match_gpu"] = bool(np.array_equal(b.codes.cpu().numpy().reshape(SHAPE), ref["codes"]))
+
+    if rank == 0:
+        clocks = clk.summary()
+        line = dict(
+            metric=METRIC, value=ws * bytes_in / (ms * 1e-3) / 1e9, unit="GB/s", n_gpus=ws, steps=args.steps,
+            warmup=args.warmup, ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None,
+            dtype="f32", data="synthetic",
+            config=dict(workload=WORKLOAD, shape=list(SHAPE), eb_mode="rel", eb=EB, anchor_stride=A,
+                        l2="input 512 MiB and outputs exceed the 126 MB L2: no flush between steps",
+                        step="compress (setup, range, autotune, predict_quantize) + decompress (scatter, "
+                             "reconstruct)", parallelism="replicas" if ws > 1 else "single"),
+            compress_gbs=bytes_in / ((st["setup"] + st["range"] + st["autotune"] + st["predict_quantize"])
+                                     * 1e-3) / 1e9,
+            decompress_gbs=bytes_in / ((st["scatter"] + st["reconstruct"]) * 1e-3) / 1e9,
+            predict_quantize_gbs=bytes_in / (st["predict_quantize"] * 1e-3) / 1e9,
+            reconstruct_gbs=bytes_in / (st["reconstruct"] * 1e-3) / 1e9,
+            stage_ms=st,
+            roofline=dict(bound="hbm", kernel=kname, achieved=achieved, peak=peak, unit="GB/s",
+                          frac=achieved / peak, traffic=traffic, peak_kind=peak_kind,
+                          alg_bytes_per_launch=alg[dom],
+                          other={k: dict(achieved=alg[k] / (st[k] * 1e-3) / 1e9,
+                                         frac=alg[k] / (st[k] * 1e-3) / 1e9 / peak) for k in alg}),
+            quality=dict(max_abs_err=err, eps=h.eps, max_err_over_eps=err / h.eps, psnr_db=psnr,
+                         n_outliers=n_out, entropy_bits=est["entropy_bits"], cr_est=est["cr"],
+                         bit_rate=est["bit_rate"],
+                         levels=[(int(h.level[l].interp), list(h.level[l].order)) for l in range(h.n_levels)]),
+            e2e=e2e,
+            gpu_launches=7 * args.steps,
+            cpu_baseline=cpu,
+            clocks=clocks,
+        )
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-planes", type=int, default=512)
+    ap.add_argument("--ref-planes", type=int, default=64)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * hi.h -- C ABI of the GB300 interpolation predictor / error-bounded
+ * quantizer (the lossy decomposition stage of cuSZ-Hi, arXiv 2507.11165).
+ *
+ * Model of the data (Sec. 3.2, Sec. 5.1.1):
+ *   A float32 field x[n0][n1][n2] (row-major, n2 fastest; a 1D or 2D field
+ *   uses leading dims of 1; a dim of size 1 is inactive) is cut into blocks
+ *   of (A+1) points per active dim that share their faces.  Points whose
+ *   coordinates are all multiples of the anchor stride A form the anchor
+ *   grid and are stored verbatim.  Every other point is predicted level by
+ *   level (stride 2^l, l = log2(A)-1 .. 0) by 1D linear or cubic spline
+ *   interpolation along a per-level dimension sequence, from values that are
+ *   already reconstructed, and its prediction error is quantized linearly
+ *   into a one-byte code (Sec. 5.2.1): code = q + 128 with q in [-127,127];
+ *   code 0 marks an outlier, stored separately as (index, value).
+ *   Reconstruction repeats the traversal (Eq. 1: |x - x'| <= eps).
+ *
+ * Conventions:
+ *   - Every pointer named d_* is device memory owned by the caller; h_* is
+ *     host memory.  The library never allocates or frees memory.
+ *   - All work is enqueued on the given stream and is asynchronous; results
+ *     that are device-resident (the header, the outlier count, the status
+ *     word) are read after synchronising, e.g. with hi_header_read().
+ *   - Functions validate their host arguments synchronously and return
+ *     HI_EINVAL (nothing is enqueued) on a bad argument.  Conditions found
+ *     on the device (outlier capacity exceeded, a corrupt record, a bounded
+ *     wait that ran out) are recorded in the status word of the header
+ *     (first error wins) and never fault or hang the GPU.
+ *   - Re-entrant: independent calls on different streams may overlap as long
+ *     as they use distinct buffers and workspaces.
+ *   - Index type: outlier indices are uint32, so a field holds fewer than
+ *     2^32 points (HI_EINVAL otherwise).
+ */
+#ifndef HI_H
+#define HI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* cudaStream_t;
+
+#if defined(__GNUC__)
+#define HI_API __attribute__((visibility("default")))
+#else
+#define HI_API
+#endif
+
+typedef enum {
+    HI_OK = 0,
+    HI_EINVAL = 1,    /* bad argument (checked on the host, nothing enqueued)   */
+    HI_ENOMEM = 2,    /* workspace too small                                    */
+    HI_ECAPACITY = 3, /* more outliers than the caller's capacity (device)      */
+    HI_ECUDA = 4,     /* a CUDA launch or runtime call failed                   */
+    HI_ETIMEOUT = 5,  /* a bounded device-side wait ran out (device)            */
+    HI_ECORRUPT = 6   /* decompress input is inconsistent (device)              */
+} hi_status;
+
+enum { HI_EB_ABS = 0, HI_EB_REL = 1 };
+enum { HI_LINEAR = 0, HI_CUBIC = 1 };
+
+#define HI_MAX_LEVELS 8
+#define HI_MAGIC 0x48693235u /* "Hi25" */
+#define HI_VERSION 1u
+
+/* Interpolation configuration of one level (Sec. 5.1.2, Sec. 5.1.3):
+ * the spline and the sequence of dimensions of its 1D passes.  order[] is a
+ * permutation of {0,1,2}; passes along inactive dims are empty. */
+typedef struct {
+    uint8_t interp;   /* HI_LINEAR or HI_CUBIC */
+    uint8_t order[3]; /* dimension sequence, 0 = slowest */
+} hi_level;
+
+/* Compression parameters (host memory). */
+typedef struct {
+    uint64_t dims[3];       /* n0, n1, n2: slowest -> fastest, each >= 1          */
+    double eb;              /* error bound: absolute, or relative to max - min    */
+    uint32_t eb_mode;       /* HI_EB_ABS or HI_EB_REL (Sec. 6.1.4)                */
+    uint32_t anchor_stride; /* A: 2, 4, 8, 16 or 32 (Sec. 5.1.1 uses 16)          */
+    uint32_t autotune;      /* 1: choose level[] on the device (Sec. 5.1.3)       */
+    uint32_t reserved;      /* must be 0                                          */
+    hi_level level[HI_MAX_LEVELS]; /* level[l]: stride 2^l; used when !autotune  */
+} hi_params;
+
+/* Self-describing record of one compressed field (device memory, written by
+ * hi_compress, read by hi_decompress).  It fixes everything needed to
+ * reconstruct: geometry, the resolved per-level configuration and the
+ * float32 quantizer constants. */
+typedef struct {
+    uint32_t magic;         /* HI_MAGIC                                             */
+    uint32_t version;       /* HI_VERSION                                           */
+    uint64_t dims[3];
+    uint32_t anchor_stride;
+    uint32_t eb_mode;
+    double eb;              /* as requested                                         */
+    double eps;             /* resolved absolute bound: eb or eb * (vmax - vmin)    */
+    float eb_f;             /* largest float <= eps: |x - x'| < eb_f is enforced    */
+    float ebx2_f;           /* fl(2 eps): x' = p + q * ebx2_f                       */
+    float r_f;              /* fl(1 / (2 eps)): q = rint((x - p) * r_f)             */
+    float vmin, vmax;       /* range over finite values (REL mode; 0 otherwise)     */
+    uint32_t status;        /* hi_status of device-side conditions, 0 = OK          */
+    uint64_t n_outliers;    /* outliers found (may exceed out_cap)                  */
+    uint64_t out_cap;       /* capacity of the outlier arrays at compression        */
+    uint64_t n_anchors;
+    hi_level level[HI_MAX_LEVELS];
+    uint32_t n_levels;
+    uint32_t reserved[7];
+} hi_header;
+
+/* Sizes of a compression of p (host call, no GPU work).
+ *   n_points  = n0 n1 n2 = entries of the code array (uint8) and of a field;
+ *   n_anchors = prod_d ((n_d - 1) / A + 1) = entries of the anchor grid;
+ *   n_blocks  = prod over active dims of ceil((n_d - 1) / A);
+ *   ws_bytes  = device workspace hi_compress needs (range partials and the
+ *               auto-tuner's per-sample error sums).
+ * Any output pointer may be NULL. */
+HI_API hi_status hi_query(const hi_params* p, uint64_t* n_points, uint64_t* n_anchors, uint64_t* n_blocks,
+                   size_t* ws_bytes);
+
+/* Compress (Sec. 3.2, Sec. 5.1, Sec. 5.2.1).  Enqueues, in order: header
+ * set-up; for HI_EB_REL the value range of d_x and eps = eb * (max - min)
+ * (eps = eb if the range is 0); for autotune the per-level choice of spline
+ * and dimension sequence on 0.2% of the blocks; then the fused
+ * predict-quantize pass.
+ *   d_x        [n_points] float32 input, 4-byte aligned (16 for the fast path)
+ *   d_codes    [n_points] uint8 codes in the layout of d_x (anchors get 128)
+ *   d_anchors  [n_anchors] float32 anchor grid, row-major
+ *   d_out_idx, d_out_val [out_cap] outliers (linear index, value) in an
+ *              unspecified order; the count goes to d_header->n_outliers and
+ *              a count above out_cap sets HI_ECAPACITY (the codes stay valid;
+ *              call again with a larger capacity)
+ *   d_hist     [256] uint32 histogram of the codes of non-anchor points, or NULL
+ *   d_recon    [n_points] float32 reconstructed field x', or NULL
+ *   d_header   one hi_header
+ *   d_ws       workspace of at least hi_query's ws_bytes (8-byte aligned) */
+HI_API hi_status hi_compress(const hi_params* p, const float* d_x, uint8_t* d_codes, float* d_anchors,
+                      uint32_t* d_out_idx, float* d_out_val, uint64_t out_cap, uint32_t* d_hist,
+                      float* d_recon, hi_header* d_header, void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Decompress (Eq. 1; the same traversal as hi_compress): x' = p + (code -
+ * 128) * ebx2_f, or the stored outlier value for code 0.  p supplies the
+ * geometry for the launch (dims, anchor_stride) and must match d_header,
+ * which also supplies the per-level configuration and constants.
+ *   d_out_idx/d_out_val hold out_cap entries, of which
+ *   min(d_header->n_outliers, out_cap) are used; an index outside the field
+ *   or n_outliers > out_cap sets HI_ECORRUPT / HI_ECAPACITY in *d_status.
+ *   d_out      [n_points] float32 output
+ *   d_status   one uint32 (may be NULL): 0 on success, else a hi_status. */
+HI_API hi_status hi_decompress(const hi_params* p, const hi_header* d_header, const uint8_t* d_codes,
+                        const float* d_anchors, const uint32_t* d_out_idx, const float* d_out_val,
+                        uint64_t out_cap, float* d_out, uint32_t* d_status, cudaStream_t stream);
+
+/* Auto-tune only (Sec. 5.1.3): writes the chosen level[] and n_levels into
+ * d_header (other fields untouched).  Uniformly sampled blocks (every
+ * (n_blocks / m)-th, m = max(1, round(0.002 n_points / A^d))); per level and
+ * per candidate (cubic before linear, dimension sequences in lexicographic
+ * order) the sum of |x - p| with predictions from the original values; the
+ * smallest sum wins, ties to the first candidate.  Uses the same workspace
+ * as hi_compress. */
+HI_API hi_status hi_autotune(const hi_params* p, const float* d_x, hi_header* d_header, void* d_ws, size_t ws_bytes,
+                      cudaStream_t stream);
+
+/* Per-sample, per-level, per-candidate error sums of the last hi_autotune /
+ * hi_compress(autotune) call on this workspace, for inspection: copies
+ * m * L * ncfg doubles (sample-major, then level, then candidate) into
+ * h_err (synchronises the stream).  *m, *L, *ncfg may be NULL. */
+HI_API hi_status hi_autotune_errors(const hi_params* p, const void* d_ws, double* h_err, size_t h_err_len,
+                             uint32_t* m, uint32_t* L, uint32_t* ncfg, cudaStream_t stream);
+
+/* Measurement hook: record CUDA events between the stages of later
+ * hi_compress / hi_decompress calls made by the calling host thread.
+ * events[0..7] (cudaEvent_t handles created by the caller):
+ *   hi_compress:   0 before header set-up, 1 before the range pass, 2 before
+ *                  the auto-tuner, 3 before predict-quantize, 4 after it;
+ *   hi_decompress: 5 before the outlier scatter, 6 before reconstruction,
+ *                  7 after it.
+ * A stage that does not run still records its event.  n must be 8; pass
+ * events = NULL to switch recording off.  No GPU work of its own. */
+HI_API hi_status hi_set_stage_events(void* const* events, uint32_t n);
+
+/* Copy the device header to the host (synchronises the stream). */
+HI_API hi_status hi_header_read(const hi_header* d_header, hi_header* h_header, cudaStream_t stream);
+
+/* Short text for a status code. */
+HI_API const char* hi_status_str(int status);
+
+/* Library version (HI_VERSION). */
+HI_API uint32_t hi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HI_H */

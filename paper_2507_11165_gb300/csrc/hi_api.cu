@@ -1,0 +1,421 @@
+// hi_api.cu -- the C ABI (include/hi.h): argument validation, geometry,
+// workspace layout, TMA descriptors and the launch sequence of each call.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include <cudaTypedefs.h>
+
+#include "hi_device.cuh"
+#include "hi_internal.h"
+
+namespace hi {
+namespace {
+
+struct Geometry {
+    FieldGeo g;
+    int A, L;
+    uint64_t n_anchors;
+    int ndim_active;
+    int m, stride;  // auto-tune samples
+    TuneCands cands;
+};
+
+int ilog2_pow2(uint32_t A)
+{
+    if (A < 2 || A > 32 || (A & (A - 1))) return -1;
+    int l = 0;
+    while ((1u << l) < A) ++l;
+    return l;
+}
+
+// Candidates of one level (Sec. 5.1.3): cubic before linear; permutations of
+// the active dims in lexicographic order with inactive dims appended.
+TuneCands make_cands(const uint64_t dims[3])
+{
+    TuneCands tc{};
+    int act[3], na = 0, ina[3], ni = 0;
+    for (int d = 0; d < 3; ++d) (dims[d] > 1 ? act[na++] : ina[ni++]) = d;
+    int perms[6][3];
+    int np = 0;
+    if (na == 0) {
+        perms[0][0] = 0, perms[0][1] = 1, perms[0][2] = 2;
+        np = 1;
+    } else {
+        int idx[3] = {0, 1, 2};
+        // lexicographic permutations of idx[0..na)
+        do {
+            for (int k = 0; k < na; ++k) perms[np][k] = act[idx[k]];
+            for (int k = 0; k < ni; ++k) perms[np][na + k] = ina[k];
+            ++np;
+            // next permutation over the first na entries
+            int i = na - 2;
+            while (i >= 0 && idx[i] > idx[i + 1]) --i;
+            if (i < 0) break;
+            int j = na - 1;
+            while (idx[j] < idx[i]) --j;
+            int t = idx[i];
+            idx[i] = idx[j], idx[j] = t;
+            for (int a = i + 1, b = na - 1; a < b; ++a, --b) t = idx[a], idx[a] = idx[b], idx[b] = t;
+        } while (true);
+    }
+    tc.nperm = np;
+    tc.ncfg = 2 * np;
+    for (int sp = 0; sp < 2; ++sp)
+        for (int i = 0; i < np; ++i) {
+            const int c = sp * np + i;
+            tc.interp[c] = (uint8_t)(sp == 0 ? HI_CUBIC : HI_LINEAR);
+            for (int k = 0; k < 3; ++k) tc.order[c][k] = (uint8_t)perms[i][k];
+        }
+    return tc;
+}
+
+hi_status make_geometry(const hi_params* p, Geometry* G)
+{
+    if (!p || p->reserved != 0) return HI_EINVAL;
+    const int L = ilog2_pow2(p->anchor_stride);
+    if (L < 0) return HI_EINVAL;
+    if (!(p->eb > 0.0) || !std::isfinite(p->eb)) return HI_EINVAL;
+    if (p->eb_mode != HI_EB_ABS && p->eb_mode != HI_EB_REL) return HI_EINVAL;
+    if (p->autotune > 1) return HI_EINVAL;
+    const int A = (int)p->anchor_stride;
+    G->A = A;
+    G->L = L;
+    uint64_t N = 1, na_all = 1, nt = 1;
+    int nact = 0;
+    for (int d = 0; d < 3; ++d) {
+        const uint64_t n = p->dims[d];
+        if (n < 1 || n > 0x7fffffffull) return HI_EINVAL;
+        N *= n;
+        if (N >= (1ull << 32)) return HI_EINVAL;  // uint32 outlier indices
+        G->g.n[d] = (int64_t)n;
+        G->g.nb[d] = (n == 1) ? 1 : (int)((n - 1 + A - 1) / A);
+        G->g.na[d] = (int)((n - 1) / A + 1);
+        na_all *= (uint64_t)G->g.na[d];
+        nt *= (uint64_t)G->g.nb[d];
+        if (n > 1) ++nact;
+    }
+    if (nt > 0x7fffffffull) return HI_EINVAL;
+    if (!p->autotune) {
+        for (int l = 0; l < L; ++l) {
+            const hi_level& lv = p->level[l];
+            if (lv.interp != HI_LINEAR && lv.interp != HI_CUBIC) return HI_EINVAL;
+            int seen = 0;
+            for (int k = 0; k < 3; ++k) {
+                if (lv.order[k] > 2) return HI_EINVAL;
+                seen |= 1 << lv.order[k];
+            }
+            if (seen != 7) return HI_EINVAL;
+        }
+    }
+    G->g.N = (int64_t)N;
+    G->g.ntiles = (int)nt;
+    G->g.b0 = (p->dims[0] > 1) ? A + 1 : 1;
+    G->n_anchors = na_all;
+    G->ndim_active = nact;
+    // auto-tune sample: 0.2% of the points in whole blocks, every (nt/m)-th block
+    double vol = 1.0;
+    for (int k = 0; k < nact; ++k) vol *= A;
+    long long m = (long long)std::floor(0.002 * (double)N / vol + 0.5);
+    if (m < 1) m = 1;
+    if (m > (long long)nt) m = (long long)nt;
+    G->m = (int)m;
+    G->stride = (int)(nt / (uint64_t)m);
+    G->cands = make_cands(p->dims);
+    return HI_OK;
+}
+
+constexpr size_t kWsTicket = 0;
+constexpr size_t kWsPartials = 256;
+constexpr size_t kWsTune = kWsPartials + sizeof(float2) * kRangeBlocks;
+
+size_t workspace_bytes(const Geometry& G)
+{
+    return kWsTune + sizeof(double) * (size_t)G.m * G.L * 12;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    });
+    return fn;
+}
+
+// 3D box descriptor over a row-major [n0][n1][n2] array of elem-byte values;
+// box = (bx, P, b0) elements, zero fill outside the field.
+bool encode_box(CUtensorMap* map, const void* base, CUtensorMapDataType dt, int elem, const FieldGeo& g, int bx,
+                int P)
+{
+    auto enc = get_encode();
+    if (!enc) return false;
+    if ((reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
+    if (((uint64_t)g.n[2] * elem) % 16 != 0) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)g.n[2], (cuuint64_t)g.n[1], (cuuint64_t)g.n[0]};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.n[2] * elem, (cuuint64_t)g.n[1] * g.n[2] * elem};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)P, (cuuint32_t)g.b0};
+    const cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc(map, dt, 3, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int A>
+struct PX_of {
+    static constexpr int PX = TileGeom<A>::PX;
+    static constexpr int CX = TileGeom<A>::CX;
+};
+
+void pitches(int A, int* PX, int* CX)
+{
+    switch (A) {
+    case 2: *PX = PX_of<2>::PX, *CX = PX_of<2>::CX; break;
+    case 4: *PX = PX_of<4>::PX, *CX = PX_of<4>::CX; break;
+    case 8: *PX = PX_of<8>::PX, *CX = PX_of<8>::CX; break;
+    case 16: *PX = PX_of<16>::PX, *CX = PX_of<16>::CX; break;
+    default: *PX = PX_of<32>::PX, *CX = PX_of<32>::CX; break;
+    }
+}
+
+int num_sms()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
+int threads_for(const Geometry& G)
+{
+    // work per pass grows with the tile volume; small 1D/2D tiles use fewer threads
+    const long long vol = (long long)G.g.b0 * (G.A + 1) * ((G.g.n[1] > 1) ? (G.A + 1) : 1);
+    if (vol >= 2048) return 256;
+    if (vol >= 512) return 128;
+    return 64;
+}
+
+thread_local cudaEvent_t t_events[8];
+thread_local bool t_events_on = false;
+
+inline void stage_event(int k, cudaStream_t st)
+{
+    if (t_events_on) cudaEventRecord(t_events[k], st);
+}
+
+inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+hi_status cuda_status(cudaError_t e) { return e == cudaSuccess ? HI_OK : HI_ECUDA; }
+
+}  // namespace
+}  // namespace hi
+
+using namespace hi;
+
+extern "C" {
+
+uint32_t hi_version(void) { return HI_VERSION; }
+
+const char* hi_status_str(int s)
+{
+    switch (s) {
+    case HI_OK: return "ok";
+    case HI_EINVAL: return "invalid argument";
+    case HI_ENOMEM: return "workspace too small";
+    case HI_ECAPACITY: return "outlier capacity exceeded";
+    case HI_ECUDA: return "CUDA error";
+    case HI_ETIMEOUT: return "device wait timed out";
+    case HI_ECORRUPT: return "corrupt compressed record";
+    default: return "unknown status";
+    }
+}
+
+hi_status hi_query(const hi_params* p, uint64_t* n_points, uint64_t* n_anchors, uint64_t* n_blocks,
+                   size_t* ws_bytes)
+{
+    Geometry G;
+    const hi_status s = make_geometry(p, &G);
+    if (s != HI_OK) return s;
+    if (n_points) *n_points = (uint64_t)G.g.N;
+    if (n_anchors) *n_anchors = G.n_anchors;
+    if (n_blocks) *n_blocks = (uint64_t)G.g.ntiles;
+    if (ws_bytes) *ws_bytes = workspace_bytes(G);
+    return HI_OK;
+}
+
+static hi_status enqueue_tune(const Geometry& G, const float* d_x, hi_header* d_header, void* d_ws,
+                              cudaStream_t stream)
+{
+    double* err = reinterpret_cast<double*>(static_cast<char*>(d_ws) + kWsTune);
+    return cuda_status(launch_tune(G.A, G.g, d_x, G.cands, G.m, G.stride, err, d_header, stream));
+}
+
+hi_status hi_compress(const hi_params* p, const float* d_x, uint8_t* d_codes, float* d_anchors,
+                      uint32_t* d_out_idx, float* d_out_val, uint64_t out_cap, uint32_t* d_hist,
+                      float* d_recon, hi_header* d_header, void* d_ws, size_t ws_bytes, cudaStream_t stream)
+{
+    Geometry G;
+    hi_status s = make_geometry(p, &G);
+    if (s != HI_OK) return s;
+    if (!d_x || !d_codes || !d_anchors || !d_header || !d_ws) return HI_EINVAL;
+    if (out_cap > 0 && (!d_out_idx || !d_out_val)) return HI_EINVAL;
+    if (!aligned(d_x, 4) || !aligned(d_ws, 8) || !aligned(d_header, 8)) return HI_EINVAL;
+    if (ws_bytes < workspace_bytes(G)) return HI_ENOMEM;
+
+    char* ws = static_cast<char*>(d_ws);
+    uint32_t* ticket = reinterpret_cast<uint32_t*>(ws + kWsTicket);
+    stage_event(0, stream);
+    cudaError_t e = launch_prologue(d_header, *p, G.n_anchors, out_cap, (uint32_t)G.L, d_hist, ticket, stream);
+    if (e != cudaSuccess) return HI_ECUDA;
+    stage_event(1, stream);
+    if (p->eb_mode == HI_EB_REL) {
+        int nb = kRangeBlocks;
+        const int64_t need = (G.g.N + 4095) / 4096;
+        if (need < nb) nb = (int)(need > 0 ? need : 1);
+        e = launch_range(d_x, G.g.N, reinterpret_cast<float2*>(ws + kWsPartials), nb, ticket, d_header, stream);
+        if (e != cudaSuccess) return HI_ECUDA;
+    }
+    stage_event(2, stream);
+    if (p->autotune) {
+        s = enqueue_tune(G, d_x, d_header, d_ws, stream);
+        if (s != HI_OK) return s;
+    }
+    stage_event(3, stream);
+    CompressLaunch c{};
+    int PX, CX;
+    pitches(G.A, &PX, &CX);
+    // a TMA box must start at an x coordinate whose byte offset is a multiple
+    // of 16: tile origins are multiples of A, so floats need A >= 4
+    const bool tma = G.A >= 4 && encode_box(&c.tmap, d_x, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, G.g, PX, G.A + 1);
+    c.g = G.g;
+    c.x = d_x;
+    c.codes = d_codes;
+    c.anchors = d_anchors;
+    c.out_idx = d_out_idx;
+    c.out_val = d_out_val;
+    c.out_cap = out_cap;
+    c.hist = d_hist;
+    c.recon = d_recon;
+    c.hdr = d_header;
+    c.tma_bytes = (uint32_t)(PX * (G.A + 1) * G.g.b0 * 4);
+    const int ch = G.A >= 16 ? 16 : 8;
+    c.flags = (tma ? kFlagTma : 0) |
+              ((G.g.n[2] % ch == 0 && aligned(d_codes, 16)) ? kFlagVecCodes : 0);
+    c.threads = threads_for(G);
+    c.num_sms = num_sms();
+    c.max_ctas = 0;
+    s = cuda_status(launch_compress(G.A, c, stream));
+    stage_event(4, stream);
+    return s;
+}
+
+hi_status hi_decompress(const hi_params* p, const hi_header* d_header, const uint8_t* d_codes,
+                        const float* d_anchors, const uint32_t* d_out_idx, const float* d_out_val,
+                        uint64_t out_cap, float* d_out, uint32_t* d_status, cudaStream_t stream)
+{
+    Geometry G;
+    hi_params q = *p;
+    q.autotune = 1;  // the level configuration comes from the header
+    hi_status s = make_geometry(&q, &G);
+    if (s != HI_OK) return s;
+    if (!d_header || !d_codes || !d_anchors || !d_out) return HI_EINVAL;
+    if (out_cap > 0 && (!d_out_idx || !d_out_val)) return HI_EINVAL;
+    if (!aligned(d_out, 4)) return HI_EINVAL;
+    cudaError_t e;
+    stage_event(5, stream);
+    if (d_status) {
+        e = cudaMemsetAsync(d_status, 0, sizeof(uint32_t), stream);
+        if (e != cudaSuccess) return HI_ECUDA;
+    }
+    e = launch_scatter(d_out_idx, d_out_val, out_cap, d_header, G.g.N, d_out, d_status, stream);
+    if (e != cudaSuccess) return HI_ECUDA;
+    stage_event(6, stream);
+    DecompressLaunch c{};
+    int PX, CX;
+    pitches(G.A, &PX, &CX);
+    // byte-sized codes: the box origin x = t * A is 16-byte aligned only for A >= 16
+    const bool tma = G.A >= 16 && encode_box(&c.cmap, d_codes, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, G.g, CX, G.A + 1);
+    c.g = G.g;
+    c.codes = d_codes;
+    c.anchors = d_anchors;
+    c.out = d_out;
+    c.hdr = d_header;
+    c.status = d_status;
+    c.tma_bytes = (uint32_t)(CX * (G.A + 1) * G.g.b0);
+    c.flags = (tma ? kFlagTma : 0) | ((G.g.n[2] % 4 == 0 && aligned(d_out, 16)) ? kFlagVecOut : 0);
+    c.threads = threads_for(G);
+    c.num_sms = num_sms();
+    c.max_ctas = 0;
+    s = cuda_status(launch_decompress(G.A, c, stream));
+    stage_event(7, stream);
+    return s;
+}
+
+hi_status hi_autotune(const hi_params* p, const float* d_x, hi_header* d_header, void* d_ws, size_t ws_bytes,
+                      cudaStream_t stream)
+{
+    Geometry G;
+    hi_params q = *p;
+    q.autotune = 1;
+    hi_status s = make_geometry(&q, &G);
+    if (s != HI_OK) return s;
+    if (!d_x || !d_header || !d_ws || !aligned(d_ws, 8)) return HI_EINVAL;
+    if (ws_bytes < workspace_bytes(G)) return HI_ENOMEM;
+    return enqueue_tune(G, d_x, d_header, d_ws, stream);
+}
+
+hi_status hi_autotune_errors(const hi_params* p, const void* d_ws, double* h_err, size_t h_err_len, uint32_t* m,
+                             uint32_t* L, uint32_t* ncfg, cudaStream_t stream)
+{
+    Geometry G;
+    hi_params q = *p;
+    q.autotune = 1;
+    hi_status s = make_geometry(&q, &G);
+    if (s != HI_OK) return s;
+    if (m) *m = (uint32_t)G.m;
+    if (L) *L = (uint32_t)G.L;
+    if (ncfg) *ncfg = (uint32_t)G.cands.ncfg;
+    const size_t n = (size_t)G.m * G.L * G.cands.ncfg;
+    if (!h_err) return HI_OK;
+    if (h_err_len < n || !d_ws) return HI_EINVAL;
+    cudaError_t e = cudaMemcpyAsync(h_err, static_cast<const char*>(d_ws) + kWsTune, n * sizeof(double),
+                                    cudaMemcpyDeviceToHost, stream);
+    if (e != cudaSuccess) return HI_ECUDA;
+    return cuda_status(cudaStreamSynchronize(stream));
+}
+
+hi_status hi_set_stage_events(void* const* events, uint32_t n)
+{
+    if (!events) {
+        t_events_on = false;
+        return HI_OK;
+    }
+    if (n != 8) return HI_EINVAL;
+    for (int k = 0; k < 8; ++k) {
+        if (!events[k]) return HI_EINVAL;
+        t_events[k] = static_cast<cudaEvent_t>(events[k]);
+    }
+    t_events_on = true;
+    return HI_OK;
+}
+
+hi_status hi_header_read(const hi_header* d_header, hi_header* h_header, cudaStream_t stream)
+{
+    if (!d_header || !h_header) return HI_EINVAL;
+    cudaError_t e = cudaMemcpyAsync(h_header, d_header, sizeof(hi_header), cudaMemcpyDeviceToHost, stream);
+    if (e != cudaSuccess) return HI_ECUDA;
+    return cuda_status(cudaStreamSynchronize(stream));
+}
+
+}  // extern "C"
+
+static_assert(sizeof(hi_header) == 168, "hi_header layout");
+static_assert(sizeof(hi_params) == 80, "hi_params layout");

@@ -1,0 +1,315 @@
+// hi_aux.cu -- the smaller stages around the predict/quantize kernel:
+//   * header set-up (and the absolute error bound's constants),
+//   * the value range for the value-range-relative bound (Sec. 6.1.4) and the
+//     float32 quantizer constants derived from it (Eq. 1),
+//   * the outlier scatter that precedes reconstruction,
+//   * the auto-tuner (Sec. 5.1.3): per-level error of every spline and
+//     dimension sequence on uniformly sampled blocks, then the argmin.
+#include <cstdint>
+
+#include "hi_device.cuh"
+#include "hi_internal.h"
+
+namespace hi {
+
+// eps and the float32 constants the quantizer uses (device, IEEE double):
+//   eps = eb (absolute) or eb * (vmax - vmin) (relative; eb if the range is 0);
+//   eb_f = eps rounded toward zero (the largest float <= eps),
+//   ebx2_f = fl(2 eps), r_f = fl(1 / (2 eps)).
+__device__ void finalize_eps(hi_header* h, float vmin, float vmax)
+{
+    double eps;
+    if (h->eb_mode == HI_EB_ABS) {
+        eps = h->eb;
+    } else {
+        const double range = __dsub_rn((double)vmax, (double)vmin);
+        eps = (range > 0.0) ? __dmul_rn(h->eb, range) : h->eb;
+    }
+    const double two_eps = __dmul_rn(2.0, eps);
+    const float eb_f = __double2float_rz(eps);
+    const float ebx2_f = __double2float_rn(two_eps);
+    const float r_f = __double2float_rn(__ddiv_rn(1.0, two_eps));
+    h->eps = eps;
+    h->eb_f = eb_f;
+    h->ebx2_f = ebx2_f;
+    h->r_f = r_f;
+    h->vmin = vmin;
+    h->vmax = vmax;
+    const bool ok = (eps > 0.0) && (eps < INFINITY) && (eb_f > 0.0f) && (fabsf(ebx2_f) < INFINITY) &&
+                    (r_f > 0.0f) && (r_f < INFINITY);
+    if (!ok) set_status(&h->status, HI_EINVAL);
+}
+
+__global__ void k_prologue(hi_header* hdr, const hi_params p, uint64_t n_anchors, uint64_t out_cap,
+                           uint32_t n_levels, uint32_t* hist, uint32_t* ticket)
+{
+    const int tid = threadIdx.x;
+    if (hist)
+        for (int i = tid; i < 256; i += blockDim.x) hist[i] = 0;
+    if (tid == 0) {
+        hdr->magic = HI_MAGIC;
+        hdr->version = HI_VERSION;
+        for (int d = 0; d < 3; ++d) hdr->dims[d] = p.dims[d];
+        hdr->anchor_stride = p.anchor_stride;
+        hdr->eb_mode = p.eb_mode;
+        hdr->eb = p.eb;
+        hdr->status = 0;
+        hdr->n_outliers = 0;
+        hdr->out_cap = out_cap;
+        hdr->n_anchors = n_anchors;
+        hdr->n_levels = n_levels;
+        for (int l = 0; l < HI_MAX_LEVELS; ++l) hdr->level[l] = p.level[l];
+        for (int k = 0; k < 7; ++k) hdr->reserved[k] = 0;
+        if (ticket) *ticket = 0;
+        if (p.eb_mode == HI_EB_ABS) finalize_eps(hdr, 0.0f, 0.0f);
+    }
+}
+
+// Order-preserving integer keys of finite floats, so that min/max reduce with
+// integer atomics-free comparisons; -0 sorts below +0 (reported as +0).
+__device__ __forceinline__ bool finite_f(float v) { return fabsf(v) < INFINITY; }
+
+// Value range over the finite values: one grid-strided streaming read; the
+// last CTA to finish (ticket) folds the per-CTA partials and derives eps.
+__global__ void __launch_bounds__(512) k_range(const float* __restrict__ x, int64_t N, float2* partials,
+                                               uint32_t* ticket, hi_header* hdr)
+{
+    float mn = INFINITY, mx = -INFINITY;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool vec = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+    int64_t head = 0;
+    if (vec) {
+        const int64_t n4 = N / 4;
+        const float4* x4 = reinterpret_cast<const float4*>(x);
+        for (int64_t i = t0; i < n4; i += stride) {
+            const float4 f = __ldcs(x4 + i);
+            if (finite_f(f.x)) mn = fminf(mn, f.x), mx = fmaxf(mx, f.x);
+            if (finite_f(f.y)) mn = fminf(mn, f.y), mx = fmaxf(mx, f.y);
+            if (finite_f(f.z)) mn = fminf(mn, f.z), mx = fmaxf(mx, f.z);
+            if (finite_f(f.w)) mn = fminf(mn, f.w), mx = fmaxf(mx, f.w);
+        }
+        head = n4 * 4;
+    }
+    for (int64_t i = head + t0; i < N; i += stride) {
+        const float f = x[i];
+        if (finite_f(f)) mn = fminf(mn, f), mx = fmaxf(mx, f);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    __shared__ float s_mn[32], s_mx[32];
+    __shared__ bool s_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) s_mn[warp] = mn, s_mx[warp] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nw; ++w) mn = fminf(mn, s_mn[w]), mx = fmaxf(mx, s_mx[w]);
+        partials[blockIdx.x] = make_float2(mn, mx);
+        __threadfence();
+        const uint32_t t = atomicAdd(ticket, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x == 0) {
+        float a = INFINITY, b = -INFINITY;
+        for (unsigned k = 0; k < gridDim.x; ++k) {
+            const float2 pk = __ldcg(partials + k);
+            a = fminf(a, pk.x);
+            b = fmaxf(b, pk.y);
+        }
+        if (!(a <= b)) a = 0.0f, b = 0.0f;  // no finite value
+        a = __fadd_rn(a, 0.0f);              // a signed zero is reported as +0
+        b = __fadd_rn(b, 0.0f);
+        finalize_eps(hdr, a, b);
+        *ticket = 0;
+    }
+}
+
+// Outlier values go to their place in the output before reconstruction reads
+// them there (code 0 means "take the stored value").
+__global__ void k_scatter(const uint32_t* __restrict__ idx, const float* __restrict__ val, uint64_t cap,
+                          const hi_header* __restrict__ hdr, int64_t N, float* __restrict__ out,
+                          uint32_t* __restrict__ status)
+{
+    const uint64_t n_all = hdr->n_outliers;
+    const uint64_t n = n_all < cap ? n_all : cap;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (hdr->magic != HI_MAGIC) set_status(status, HI_ECORRUPT);
+        if (n_all > cap) set_status(status, HI_ECAPACITY);
+    }
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = idx[i];
+        if ((int64_t)k < N)
+            out[k] = val[i];
+        else
+            set_status(status, HI_ECORRUPT);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Auto-tune: CTA (sample, candidate) computes, for every level, the sum of
+// |x - p| over that level's points of its sampled block, with every
+// prediction taken from the original values (no quantization), in the
+// candidate's pass order.  Per-thread double partials, then a fixed-order
+// block reduction: the sums are deterministic run to run.
+// ---------------------------------------------------------------------------
+template <int A>
+__global__ void __launch_bounds__(256) k_tune(const FieldGeo g, const float* __restrict__ x, const TuneCands cands,
+                                              int stride, double* __restrict__ err)
+{
+    using TG = TileGeom<A>;
+    constexpr int L = TG::L;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float* v = reinterpret_cast<float*>(smem);
+    __shared__ double s_red[L][8];
+
+    const int sample = blockIdx.x, c = blockIdx.y;
+    const int tile = sample * stride;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int t[3], o[3], e[3];
+    tile_coords(g, tile, t);
+    for (int d = 0; d < 3; ++d) {
+        o[d] = t[d] * A;
+        const int rem = (int)(g.n[d] - 1 - o[d]);
+        e[d] = (g.n[d] == 1) ? 0 : (rem < A ? rem : A);
+    }
+    const int rows = (e[0] + 1) * (e[1] + 1);
+    for (int rr = warp; rr < rows; rr += (blockDim.x >> 5)) {
+        const int c0 = rr / (e[1] + 1), c1 = rr - c0 * (e[1] + 1);
+        const float* src = x + ((int64_t)(o[0] + c0) * g.n[1] + (o[1] + c1)) * g.n[2] + o[2];
+        for (int c2 = lane; c2 <= e[2]; c2 += 32) v[c0 * TG::PY + c1 * TG::PX + c2] = src[c2];
+    }
+    __syncthreads();
+
+    const bool cubic = cands.interp[c] == HI_CUBIC;
+    hi_level lv;
+    lv.interp = cands.interp[c];
+    lv.order[0] = cands.order[c][0];
+    lv.order[1] = cands.order[c][1];
+    lv.order[2] = cands.order[c][2];
+    const int vp[3] = {TG::PY, TG::PX, 1};
+    double acc[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) acc[l] = 0.0;
+
+#pragma unroll
+    for (int l = L - 1; l >= 0; --l) {
+        const int s = 1 << l;
+        for (int p = 0; p < 3; ++p) {
+            const int d = lv.order[p];
+            int st[3];
+            for (int k = 0; k < 3; ++k) st[lv.order[k]] = (k < p) ? s : 2 * s;
+            const int q = (d == 0) ? 1 : 0, r = (d == 2) ? 1 : 2;
+            const int ed = e[d];
+            const int nd = (ed >= s) ? ((ed - s) / (2 * s) + 1) : 0;
+            if (nd == 0) continue;
+            const int nq = e[q] / st[q] + 1, nr = e[r] / st[r] + 1;
+            const int vpd = vp[d] * s;
+            for (int line = tid; line < nq * nr; line += blockDim.x) {
+                const int jq = line / nr, jr = line - jq * nr;
+                const int vb = jq * st[q] * vp[q] + jr * st[r] * vp[r];
+                float fa = 0.0f, fb = v[vb];
+                float fu = (2 * s <= ed) ? v[vb + 2 * vpd] : 0.0f;
+                float fv = (4 * s <= ed) ? v[vb + 4 * vpd] : 0.0f;
+                for (int k = 0; k < nd; ++k) {
+                    const int cc = (2 * k + 1) * s;
+                    const float pr = predict(cubic, k >= 1, cc + s <= ed, cc + 3 * s <= ed, fa, fb, fu, fv);
+                    acc[l] += (double)fabsf(__fsub_rn(v[vb + (2 * k + 1) * vpd], pr));
+                    fa = fb;
+                    fb = fu;
+                    fu = fv;
+                    fv = ((2 * k + 6) * s <= ed) ? v[vb + (2 * k + 6) * vpd] : 0.0f;
+                }
+            }
+        }
+    }
+    // fixed-order reduction: warp butterfly, then warps in index order
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        double a = acc[l];
+        for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+        if (lane == 0) s_red[l][warp] = a;
+    }
+    __syncthreads();
+    if (tid < L) {
+        double a = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += s_red[tid][w];
+        err[((size_t)sample * L + tid) * cands.ncfg + c] = a;
+    }
+}
+
+// Sum the samples in index order and keep the first smallest candidate.
+__global__ void k_tune_select(const double* __restrict__ err, int m, int L, const TuneCands cands, hi_header* hdr)
+{
+    const int l = threadIdx.x;
+    if (l >= L) return;
+    int best = 0;
+    double best_e = 0.0;
+    for (int c = 0; c < cands.ncfg; ++c) {
+        double s = 0.0;
+        for (int k = 0; k < m; ++k) s += err[((size_t)k * L + l) * cands.ncfg + c];
+        if (c == 0 || s < best_e) best = c, best_e = s;
+    }
+    hi_level lv;
+    lv.interp = cands.interp[best];
+    lv.order[0] = cands.order[best][0];
+    lv.order[1] = cands.order[best][1];
+    lv.order[2] = cands.order[best][2];
+    hdr->level[l] = lv;
+}
+
+cudaError_t launch_prologue(hi_header* hdr, const hi_params& p, uint64_t n_anchors, uint64_t out_cap,
+                            uint32_t n_levels, uint32_t* hist, uint32_t* ticket, cudaStream_t st)
+{
+    k_prologue<<<1, 256, 0, st>>>(hdr, p, n_anchors, out_cap, n_levels, hist, ticket);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_range(const float* x, int64_t N, float2* partials, int nblocks, uint32_t* ticket,
+                         hi_header* hdr, cudaStream_t st)
+{
+    k_range<<<nblocks, 512, 0, st>>>(x, N, partials, ticket, hdr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const uint32_t* idx, const float* val, uint64_t cap, const hi_header* hdr, int64_t N,
+                           float* out, uint32_t* status, cudaStream_t st)
+{
+    k_scatter<<<256, 256, 0, st>>>(idx, val, cap, hdr, N, out, status);
+    return cudaGetLastError();
+}
+
+template <int A>
+static cudaError_t launch_tune_t(const FieldGeo& g, const float* x, const TuneCands& cands, int m, int stride,
+                                 double* err, hi_header* hdr, cudaStream_t st)
+{
+    using TG = TileGeom<A>;
+    const size_t smem = (size_t)g.b0 * TG::P * TG::PX * 4;
+    auto kern = k_tune<A>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<dim3(m, cands.ncfg), 256, smem, st>>>(g, x, cands, stride, err);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_tune_select<<<1, 32, 0, st>>>(err, m, TG::L, cands, hdr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tune(int A, const FieldGeo& g, const float* x, const TuneCands& cands, int m, int stride,
+                        double* err, hi_header* hdr, cudaStream_t st)
+{
+    switch (A) {
+    case 2: return launch_tune_t<2>(g, x, cands, m, stride, err, hdr, st);
+    case 4: return launch_tune_t<4>(g, x, cands, m, stride, err, hdr, st);
+    case 8: return launch_tune_t<8>(g, x, cands, m, stride, err, hdr, st);
+    case 16: return launch_tune_t<16>(g, x, cands, m, stride, err, hdr, st);
+    case 32: return launch_tune_t<32>(g, x, cands, m, stride, err, hdr, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace hi

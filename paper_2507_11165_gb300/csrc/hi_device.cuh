@@ -1,0 +1,159 @@
+// hi_device.cuh -- device-side building blocks shared by the kernels of the
+// interpolation predictor / quantizer (cuSZ-Hi, arXiv 2507.11165).
+//
+// Everything here is compiled with -fmad=false: every float operation is
+// rounded on its own, in the order written, so that the kernels reproduce the
+// fixed evaluation order the method's reconstruction depends on (Eq. 1: the
+// decompressor must rebuild exactly the values the compressor predicted from).
+#pragma once
+
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "../../include/hi.h"
+
+namespace hi {
+
+constexpr int kRadius = 128;      // code = q + 128, q in [-127, 127] (Sec. 5.2.1)
+constexpr float kQmax = 127.5f;   // |t| must stay below this for a valid code
+constexpr uint32_t kSpinLimit = 1u << 22;  // bound on every mbarrier wait
+
+// Block geometry for anchor stride A (Sec. 5.1.1): (A+1) points per active
+// dim.  Shared-memory tiles keep the field's row-major order with the fastest
+// dim padded so that every row starts on a 16-byte boundary (the unit a TMA
+// box row is written in).
+template <int A>
+struct TileGeom {
+    static constexpr int P = A + 1;
+    static constexpr int L = (A == 2) ? 1 : (A == 4) ? 2 : (A == 8) ? 3 : (A == 16) ? 4 : 5;
+    static constexpr int PX = (P + 3) / 4 * 4;     // float pitch of dim 2
+    static constexpr int PY = P * PX;              // float pitch of dim 0 (dim 1 pitch = PX)
+    static constexpr int CX = (P + 15) / 16 * 16;  // byte pitch of dim 2 for codes
+    static constexpr int CY = P * CX;              // byte pitch of dim 0 for codes
+};
+
+// Geometry of a field, passed by value to every kernel.
+struct FieldGeo {
+    int64_t n[3];   // dims, slowest -> fastest
+    int nb[3];      // blocks per dim
+    int na[3];      // anchors per dim
+    int64_t N;      // points
+    int ntiles;     // nb0 * nb1 * nb2
+    int b0;         // planes of a tile along dim 0 in shared memory: A+1, or 1 if n0 == 1
+};
+
+// ---------------------------------------------------------------------------
+// Stencils (Sec. 5.1.2) -- a = f(c-3s), b = f(c-s), u = f(c+s), v = f(c+3s).
+// Lagrange midpoint weights: linear (1,1)/2, cubic (-1,9,9,-1)/16, one-sided
+// quadratics (3,6,-1)/8 and (-1,6,3)/8; with no right neighbour (global
+// upper edge only) linear extrapolation (3b - a)/2, else a copy of b.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float predict(bool cubic, bool have_l3, bool have_r, bool have_r3, float a, float b,
+                                         float u, float v)
+{
+    if (!have_r) return have_l3 ? __fmul_rn(__fsub_rn(__fmul_rn(3.0f, b), a), 0.5f) : b;
+    if (!cubic) return __fmul_rn(__fadd_rn(b, u), 0.5f);
+    if (have_l3 && have_r3)
+        return __fmul_rn(__fsub_rn(__fmul_rn(9.0f, __fadd_rn(b, u)), __fadd_rn(a, v)), 0.0625f);
+    if (have_r3) return __fmul_rn(__fsub_rn(__fadd_rn(__fmul_rn(3.0f, b), __fmul_rn(6.0f, u)), v), 0.125f);
+    if (have_l3) return __fmul_rn(__fsub_rn(__fadd_rn(__fmul_rn(6.0f, b), __fmul_rn(3.0f, u)), a), 0.125f);
+    return __fmul_rn(__fadd_rn(b, u), 0.5f);
+}
+
+// Linear quantization (Sec. 5.2.1): returns the code (0 = outlier) and the
+// reconstructed value.  t = (x - p) * r; q = rint(t) (ties to even);
+// x' = p + q * 2eps; an outlier when !(|t| < 127.5) or !(|x - x'| < eb_f).
+__device__ __forceinline__ int quantize(float x, float p, float eb_f, float ebx2_f, float r_f, float& xr_out)
+{
+    const float t = __fmul_rn(__fsub_rn(x, p), r_f);
+    const int q = __float2int_rn(t);
+    const float xr = __fadd_rn(p, __fmul_rn((float)q, ebx2_f));
+    const bool ok = (fabsf(t) < kQmax) && (fabsf(__fsub_rn(x, xr)) < eb_f);
+    xr_out = ok ? xr : x;
+    return ok ? q + kRadius : 0;
+}
+
+__device__ __forceinline__ float dequantize(int code, float p, float ebx2_f)
+{
+    return __fadd_rn(p, __fmul_rn((float)(code - kRadius), ebx2_f));
+}
+
+// First error wins.
+__device__ __forceinline__ void set_status(uint32_t* status, uint32_t code)
+{
+    if (status) atomicCAS(status, 0u, code);
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier + TMA (inline PTX, sm_90+ forms that sm_103a keeps)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bounded wait on the given phase parity; false when the bound ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint32_t limit)
+{
+    const uint32_t a = smem_addr(mbar);
+    for (uint32_t it = 0; it < limit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// 3D tiled TMA load of one box into shared memory, completing on mbar.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(mbar))
+        : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map)
+{
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// Tile coordinates of a linear block id (row-major over the block grid).
+__device__ __forceinline__ void tile_coords(const FieldGeo& g, int tile, int t[3])
+{
+    t[2] = tile % g.nb[2];
+    const int r = tile / g.nb[2];
+    t[1] = r % g.nb[1];
+    t[0] = r / g.nb[1];
+}
+
+}  // namespace hi

@@ -1,0 +1,337 @@
+"""Thin ctypes binding of the C ABI in ``include/hi.h`` (``_build/libhi.so``).
+
+Argument marshalling only: every step of compression and decompression runs
+in the library's CUDA kernels; PyTorch provides device memory and streams.
+There is no fallback: without the built library every call raises.
+
+High-level use::
+
+    from paper_2507_11165_gb300 import hi
+    c = hi.compress(x, eb=1e-3, mode="rel", anchor_stride=16, autotune=True)
+    y = hi.decompress(c)            # |x - y| < eps everywhere (Eq. 1)
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+from dataclasses import dataclass, field
+from typing import Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhi.so")
+
+HI_OK, HI_EINVAL, HI_ENOMEM, HI_ECAPACITY, HI_ECUDA, HI_ETIMEOUT, HI_ECORRUPT = range(7)
+EB_ABS, EB_REL = 0, 1
+LINEAR, CUBIC = 0, 1
+MAX_LEVELS = 8
+MAGIC = 0x48693235
+RADIUS = 128
+
+
+class HiLevel(ctypes.Structure):
+    _fields_ = [("interp", ctypes.c_uint8), ("order", ctypes.c_uint8 * 3)]
+
+
+class HiParams(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_uint64 * 3), ("eb", ctypes.c_double), ("eb_mode", ctypes.c_uint32),
+                ("anchor_stride", ctypes.c_uint32), ("autotune", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("level", HiLevel * MAX_LEVELS)]
+
+
+class HiHeader(ctypes.Structure):
+    _fields_ = [("magic", ctypes.c_uint32), ("version", ctypes.c_uint32), ("dims", ctypes.c_uint64 * 3),
+                ("anchor_stride", ctypes.c_uint32), ("eb_mode", ctypes.c_uint32), ("eb", ctypes.c_double),
+                ("eps", ctypes.c_double), ("eb_f", ctypes.c_float), ("ebx2_f", ctypes.c_float),
+                ("r_f", ctypes.c_float), ("vmin", ctypes.c_float), ("vmax", ctypes.c_float),
+                ("status", ctypes.c_uint32), ("n_outliers", ctypes.c_uint64), ("out_cap", ctypes.c_uint64),
+                ("n_anchors", ctypes.c_uint64), ("level", HiLevel * MAX_LEVELS), ("n_levels", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 7)]
+
+
+HEADER_BYTES = ctypes.sizeof(HiHeader)
+SYMBOLS = ("hi_query", "hi_compress", "hi_decompress", "hi_autotune", "hi_autotune_errors", "hi_header_read",
+           "hi_status_str", "hi_version", "hi_set_stage_events")
+
+
+class HiError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = int(status)
+        super().__init__("%s: %s (%d)" % (what or "hi", status_str(status), self.status))
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """The loaded C library (ctypes), with argument types set."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libhi.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+            L = ctypes.CDLL(LIB_PATH)
+            P, u64, sz = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_size_t
+            L.hi_query.argtypes = [ctypes.POINTER(HiParams), ctypes.POINTER(u64), ctypes.POINTER(u64),
+                                   ctypes.POINTER(u64), ctypes.POINTER(sz)]
+            L.hi_compress.argtypes = [ctypes.POINTER(HiParams), P, P, P, P, P, u64, P, P, P, P, sz, P]
+            L.hi_decompress.argtypes = [ctypes.POINTER(HiParams), P, P, P, P, P, u64, P, P, P]
+            L.hi_autotune.argtypes = [ctypes.POINTER(HiParams), P, P, P, sz, P]
+            L.hi_autotune_errors.argtypes = [ctypes.POINTER(HiParams), P, P, sz, P, P, P, P]
+            L.hi_header_read.argtypes = [P, ctypes.POINTER(HiHeader), P]
+            L.hi_set_stage_events.argtypes = [P, ctypes.c_uint32]
+            L.hi_status_str.argtypes = [ctypes.c_int]
+            L.hi_status_str.restype = ctypes.c_char_p
+            L.hi_version.restype = ctypes.c_uint32
+            for f in ("hi_query", "hi_compress", "hi_decompress", "hi_autotune", "hi_autotune_errors",
+                      "hi_header_read", "hi_set_stage_events"):
+                getattr(L, f).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def status_str(s):
+    try:
+        return lib().hi_status_str(int(s)).decode()
+    except Exception:  # library missing: still describe the code
+        return {0: "ok", 1: "invalid argument", 2: "workspace too small", 3: "outlier capacity exceeded",
+                4: "CUDA error", 5: "device wait timed out", 6: "corrupt compressed record"}.get(int(s), "?")
+
+
+def _check(rc, what):
+    if rc != HI_OK:
+        raise HiError(rc, what)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def dims3(shape):
+    shape = tuple(int(s) for s in shape)
+    if not 1 <= len(shape) <= 3:
+        raise ValueError("fields are 1-3 dimensional")
+    return (1,) * (3 - len(shape)) + shape
+
+
+def make_params(shape, eb, mode="rel", anchor_stride=16, autotune=True, levels=None):
+    """HiParams for a field of ``shape``.  ``levels``: list of (interp, order) per
+    level (level l = stride 2^l), or one (interp, order) for every level."""
+    p = HiParams()
+    for d, n in enumerate(dims3(shape)):
+        p.dims[d] = n
+    p.eb = float(eb)
+    p.eb_mode = EB_REL if mode in ("rel", EB_REL) else EB_ABS
+    p.anchor_stride = int(anchor_stride)
+    p.autotune = 1 if autotune else 0
+    p.reserved = 0
+    L = max(1, int(anchor_stride).bit_length() - 1)
+    if levels is None:
+        levels = (CUBIC, (0, 1, 2))
+    if isinstance(levels, tuple) and len(levels) == 2 and isinstance(levels[0], int):
+        levels = [levels] * L
+    for l in range(MAX_LEVELS):
+        ip, od = levels[min(l, len(levels) - 1)]
+        p.level[l].interp = int(ip)
+        for k in range(3):
+            p.level[l].order[k] = int(od[k])
+    return p
+
+
+def query(p):
+    n, na, nb = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    ws = ctypes.c_size_t()
+    _check(lib().hi_query(ctypes.byref(p), ctypes.byref(n), ctypes.byref(na), ctypes.byref(nb), ctypes.byref(ws)),
+           "hi_query")
+    return dict(n_points=n.value, n_anchors=na.value, n_blocks=nb.value, ws_bytes=ws.value)
+
+
+def set_stage_events(events):
+    """Record ``events`` (8 torch.cuda.Event) between stages of later calls on this thread; None = off."""
+    if events is None:
+        _check(lib().hi_set_stage_events(None, 0), "hi_set_stage_events")
+        return
+    arr = (ctypes.c_void_p * 8)(*[ctypes.c_void_p(e.cuda_event) for e in events])
+    _check(lib().hi_set_stage_events(ctypes.cast(arr, ctypes.c_void_p), 8), "hi_set_stage_events")
+
+
+def read_header(d_header, stream=None):
+    h = HiHeader()
+    _check(lib().hi_header_read(_ptr(d_header), ctypes.byref(h), _stream(stream)), "hi_header_read")
+    return h
+
+
+def header_dict(h):
+    return dict(magic=h.magic, version=h.version, dims=tuple(h.dims), anchor_stride=h.anchor_stride,
+                eb_mode=h.eb_mode, eb=h.eb, eps=h.eps, eb_f=h.eb_f, ebx2_f=h.ebx2_f, r_f=h.r_f, vmin=h.vmin,
+                vmax=h.vmax, status=h.status, n_outliers=h.n_outliers, out_cap=h.out_cap, n_anchors=h.n_anchors,
+                n_levels=h.n_levels,
+                levels=[(h.level[l].interp, tuple(h.level[l].order)) for l in range(h.n_levels)])
+
+
+@dataclass
+class Buffers:
+    """Device buffers of one compression (all owned by PyTorch)."""
+    params: HiParams
+    shape: tuple
+    codes: torch.Tensor
+    anchors: torch.Tensor
+    out_idx: torch.Tensor
+    out_val: torch.Tensor
+    hist: Optional[torch.Tensor]
+    recon: Optional[torch.Tensor]
+    header: torch.Tensor
+    ws: torch.Tensor
+    out_cap: int
+    sizes: dict = field(default_factory=dict)
+
+
+def default_out_cap(n_points):
+    return max(4096, n_points // 16)
+
+
+def alloc(p, shape, device, out_cap=None, hist=True, recon=False):
+    """Allocate the device buffers of a compression of ``shape`` under ``p``."""
+    sz = query(p)
+    n = sz["n_points"]
+    cap = default_out_cap(n) if out_cap is None else int(out_cap)
+    dev = torch.device(device)
+    return Buffers(
+        params=p, shape=tuple(shape), sizes=sz, out_cap=cap,
+        codes=torch.empty(n, dtype=torch.uint8, device=dev),
+        anchors=torch.empty(max(1, sz["n_anchors"]), dtype=torch.float32, device=dev),
+        out_idx=torch.empty(max(1, cap), dtype=torch.int32, device=dev),
+        out_val=torch.empty(max(1, cap), dtype=torch.float32, device=dev),
+        hist=torch.empty(256, dtype=torch.int32, device=dev) if hist else None,
+        recon=torch.empty(n, dtype=torch.float32, device=dev) if recon else None,
+        header=torch.zeros(HEADER_BYTES, dtype=torch.uint8, device=dev),
+        ws=torch.empty(max(8, sz["ws_bytes"]), dtype=torch.uint8, device=dev))
+
+
+def compress_into(x, b: Buffers, stream=None):
+    """Enqueue hi_compress of device tensor ``x`` into preallocated buffers (no sync)."""
+    if not x.is_cuda or x.dtype != torch.float32 or not x.is_contiguous():
+        raise ValueError("x must be a contiguous float32 CUDA tensor")
+    rc = lib().hi_compress(ctypes.byref(b.params), _ptr(x), _ptr(b.codes), _ptr(b.anchors), _ptr(b.out_idx),
+                           _ptr(b.out_val), b.out_cap, _ptr(b.hist), _ptr(b.recon), _ptr(b.header), _ptr(b.ws),
+                           b.ws.numel(), _stream(stream))
+    _check(rc, "hi_compress")
+
+
+def decompress_into(b: Buffers, out, status=None, stream=None):
+    """Enqueue hi_decompress of the record in ``b`` into ``out`` (no sync)."""
+    rc = lib().hi_decompress(ctypes.byref(b.params), _ptr(b.header), _ptr(b.codes), _ptr(b.anchors),
+                             _ptr(b.out_idx), _ptr(b.out_val), b.out_cap, _ptr(out), _ptr(status),
+                             _stream(stream))
+    _check(rc, "hi_decompress")
+
+
+def autotune_errors(b: Buffers, stream=None):
+    """Per-(sample, level, candidate) auto-tune error sums left in the workspace."""
+    import numpy as np
+    m, L, nc = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    _check(lib().hi_autotune_errors(ctypes.byref(b.params), None, None, 0, ctypes.byref(m), ctypes.byref(L),
+                                    ctypes.byref(nc), _stream(stream)), "hi_autotune_errors")
+    out = np.zeros(m.value * L.value * nc.value, dtype=np.float64)
+    _check(lib().hi_autotune_errors(ctypes.byref(b.params), _ptr(b.ws), out.ctypes.data_as(ctypes.c_void_p),
+                                    out.size, None, None, None, _stream(stream)), "hi_autotune_errors")
+    return out.reshape(m.value, L.value, nc.value)
+
+
+class Compressed:
+    """A compressed field: device buffers plus the host copy of its header."""
+
+    def __init__(self, b: Buffers, header: HiHeader):
+        self.buffers = b
+        self.h = header
+        self.shape = b.shape
+
+    @property
+    def n_outliers(self):
+        return int(self.h.n_outliers)
+
+    @property
+    def codes(self):
+        return self.buffers.codes.view(self.shape)
+
+    @property
+    def anchors(self):
+        return self.buffers.anchors[: int(self.h.n_anchors)]
+
+    @property
+    def outliers(self):
+        k = min(self.n_outliers, self.buffers.out_cap)
+        return self.buffers.out_idx[:k], self.buffers.out_val[:k]
+
+    @property
+    def hist(self):
+        return self.buffers.hist
+
+    @property
+    def recon(self):
+        return None if self.buffers.recon is None else self.buffers.recon.view(self.shape)
+
+    def info(self):
+        return header_dict(self.h)
+
+    def estimate(self):
+        return estimate_cr(self.hist.cpu().numpy(), self.n_outliers, int(self.h.n_anchors),
+                           int(math.prod(self.shape)))
+
+
+def compress(x, eb, mode="rel", anchor_stride=16, autotune=True, levels=None, out_cap=None, hist=True,
+             recon=False, stream=None):
+    """Compress a float32 field (device tensor, or host tensor copied to the current device).
+
+    Synchronises once to read the header; if the outliers overflow the
+    capacity, compresses again with the exact capacity."""
+    if not x.is_cuda:
+        x = x.to("cuda", non_blocking=True)
+    x = x.contiguous()
+    p = make_params(x.shape, eb, mode, anchor_stride, autotune, levels)
+    b = alloc(p, x.shape, x.device, out_cap, hist, recon)
+    compress_into(x, b, stream)
+    h = read_header(b.header, stream)
+    if h.status == HI_ECAPACITY:
+        b = alloc(p, x.shape, x.device, int(h.n_outliers), hist, recon)
+        compress_into(x, b, stream)
+        h = read_header(b.header, stream)
+    if h.status != HI_OK:
+        raise HiError(h.status, "hi_compress (device)")
+    return Compressed(b, h)
+
+
+def decompress(c: Compressed, out=None, stream=None):
+    b = c.buffers
+    if out is None:
+        out = torch.empty(b.shape, dtype=torch.float32, device=b.codes.device)
+    status = torch.zeros(1, dtype=torch.int32, device=b.codes.device)
+    decompress_into(b, out, status, stream)
+    st = int(status.item())
+    if st != HI_OK:
+        raise HiError(st, "hi_decompress (device)")
+    return out
+
+
+def estimate_cr(hist, n_out, n_anchors, n_points, header_bytes=None):
+    """Entropy-estimated size: ceil(N_pred H / 8) + 8 n_out + 4 n_anchors + header.
+
+    H = order-0 entropy of the code histogram in bits (what an ideal entropy
+    coder such as the Huffman stage of Sec. 5.2.2 approaches)."""
+    import numpy as np
+    hb = HEADER_BYTES if header_bytes is None else header_bytes
+    h = np.asarray(hist, dtype=np.float64)
+    tot = float(h.sum())
+    nz = h[h > 0] / tot if tot > 0 else np.zeros(0)
+    H = float(-(nz * np.log2(nz)).sum()) if nz.size else 0.0
+    nbytes = math.ceil(tot * H / 8.0) + 8 * n_out + 4 * n_anchors + hb
+    return dict(entropy_bits=H, est_bytes=int(nbytes), cr=4.0 * n_points / nbytes, bit_rate=32.0 * nbytes / (4.0 * n_points))

@@ -1,0 +1,65 @@
+"""The C-ABI library builds, loads and exports every entry point include/*.h
+declares; host-only calls (sizes, validation, status text) work without a GPU."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2507_11165_gb300 import build as hb
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    hb.build()
+    from paper_2507_11165_gb300 import hi
+    return hi
+
+
+def declared_symbols():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        names += re.findall(r"HI_API\s+[\w\s\*]+?\b(hi_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert len(names) >= 8
+    L = ctypes.CDLL(lib.LIB_PATH)
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(lib.SYMBOLS) <= set(names)
+
+
+def test_struct_layouts(lib):
+    assert ctypes.sizeof(lib.HiHeader) == 168
+    assert ctypes.sizeof(lib.HiParams) == 80
+
+
+def test_host_calls_without_gpu(lib):
+    assert lib.lib().hi_version() == 1
+    assert lib.status_str(lib.HI_ECAPACITY) == "outlier capacity exceeded"
+    q = lib.query(lib.make_params((512, 512, 512), 1e-3, "rel", 16))
+    assert q["n_points"] == 512 ** 3 and q["n_anchors"] == 32 ** 3 and q["n_blocks"] == 32 ** 3
+    q = lib.query(lib.make_params((1800, 3600), 1e-3, "rel", 16))
+    assert q["n_anchors"] == 113 * 225 and q["n_blocks"] == 113 * 225
+    q = lib.query(lib.make_params((100, 500, 500), 1e-3, "rel", 16))
+    assert q["n_blocks"] == 7 * 32 * 32 and q["n_anchors"] == 7 * 32 * 32
+    for bad in [dict(anchor_stride=12), dict(anchor_stride=64), dict(eb=-1.0), dict(eb=float("inf"))]:
+        p = lib.make_params((9, 9, 9), 1e-3, "rel", 8)
+        for k, v in bad.items():
+            setattr(p, k, v)
+        with pytest.raises(lib.HiError):
+            lib.query(p)
+    p = lib.make_params((70000, 70000), 1e-3, "rel", 16)  # 4.9e9 points: beyond uint32 indices
+    with pytest.raises(lib.HiError):
+        lib.query(p)
+    p = lib.make_params((9, 9, 9), 1e-3, "rel", 8, autotune=False)
+    p.level[0].interp = 7
+    with pytest.raises(lib.HiError):
+        lib.query(p)
