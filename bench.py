@@ -230,6 +230,10 @@ def run_gpu(args):
     # per-stage events on a bounded number of steps inside the timed region
     n_ev = min(args.steps, 256)
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(n_ev)]
+    for row in ev:  # torch creates the CUDA event on its first record
+        for e in row:
+            e.record(stream)
+    torch.cuda.synchronize()
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if ws > 1:
         dist.barrier()
@@ -388,7 +392,14 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-planes", type=int, default=512)
     ap.add_argument("--ref-planes", type=int, default=64)
+    ap.add_argument("--shape", type=int, default=None,
+                    help="cube side of a smaller field of the same recipe (profiling captures)")
     args = ap.parse_args()
+    if args.shape:
+        global SHAPE, WORKLOAD
+        SHAPE = (args.shape,) * 3
+        WORKLOAD = WORKLOAD.replace("512^3", "%d^3" % args.shape)
+        args.cpu_planes = min(args.cpu_planes, args.shape)
     if args.impl == "reference":
         run_reference(args)
     else:

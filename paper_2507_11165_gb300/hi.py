@@ -160,6 +160,8 @@ def set_stage_events(events):
     if events is None:
         _check(lib().hi_set_stage_events(None, 0), "hi_set_stage_events")
         return
+    if any(e.cuda_event == 0 for e in events):
+        raise ValueError("record each event once before handing it over (torch creates events lazily)")
     arr = (ctypes.c_void_p * 8)(*[ctypes.c_void_p(e.cuda_event) for e in events])
     _check(lib().hi_set_stage_events(ctypes.cast(arr, ctypes.c_void_p), 8), "hi_set_stage_events")
 

@@ -34,7 +34,8 @@ def run_gpu(hi, x, A, eb, mode, interp=None, order=None, autotune=False, out_cap
     levels = None if interp is None else _levels_from(interp, order)
     p = hi.make_params(x.shape, eb, mode, A, autotune, levels)
     xd = torch.from_numpy(np.ascontiguousarray(x)).cuda() if x_dev is None else x_dev
-    b = hi.alloc(p, x.shape, "cuda", out_cap=out_cap, hist=True, recon=recon)
+    cap = x.size if out_cap is None else out_cap
+    b = hi.alloc(p, x.shape, "cuda", out_cap=cap, hist=True, recon=recon)
     hi.compress_into(xd, b)
     h = hi.read_header(b.header)
     return p, b, h
