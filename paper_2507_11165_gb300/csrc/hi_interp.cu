@@ -2,16 +2,25 @@
 // inverse, the level-by-level reconstruction (cuSZ-Hi, arXiv 2507.11165,
 // Sec. 3.2, Sec. 5.1.1-5.1.2, Sec. 5.2.1).
 //
-// One CTA works through blocks ("tiles") of (A+1)^d points in a grid-strided
-// loop.  A tile is staged in shared memory by one 3D TMA box load (or by
-// plain loads when the field's strides do not meet the TMA rules), then every
-// level (stride s = A/2 .. 1) runs its three 1D passes in the configured
-// dimension sequence.  Within a pass each thread owns one whole line along
-// the pass dimension: the line's already-known nodes (even multiples of s)
-// slide through four registers, so every predicted point costs one new node
-// load, one load of its own value and one store.  Predictions read values
-// already reconstructed in shared memory (closed loop), so the decompressor
-// repeats exactly the same arithmetic.
+// Persistent CTAs walk the blocks ("tiles") of (A+1)^d points in a
+// grid-strided loop.  Each tile is staged in shared memory by one 3D TMA box
+// load, double buffered: the next tile's load is in flight while the current
+// one is processed (plain loads when the field's strides do not meet the TMA
+// rules).  Every level (stride s = A/2 .. 1) runs its three 1D passes in the
+// configured dimension sequence; predictions read values already
+// reconstructed in shared memory (closed loop), so the decompressor repeats
+// exactly the same arithmetic.
+//
+// Two code paths share that structure:
+//   * full 3D tiles (extent A in every dim) at A = 8 or 16 -- the bulk of any
+//     large field -- run passes whose geometry is fixed at compile time for
+//     each (level, dimension sequence, spline): stencil cases, line counts and
+//     shared-memory offsets are constants.  Passes along the contiguous dim
+//     move whole rows with 16-byte shared-memory accesses (conflict-free at the
+//     20-float row pitch); passes along the other dims give each thread one
+//     line, lanes adjacent along the contiguous dim.
+//   * every other tile (ragged field edges, 1D/2D fields, other A) runs the
+//     same passes with the geometry held in registers.
 //
 // Shared faces between tiles are computed by both tiles with identical
 // results; only the owning tile (the one with the lower block index, or the
@@ -25,69 +34,32 @@
 namespace hi {
 
 constexpr int kOutCap = 1024;  // staged outliers per tile before the direct path
+constexpr int kBlock = 256;    // threads per CTA of the 3D paths
 
-struct PassGeom {
-    int d, q, r;      // pass dim and the two others
-    int stq, str;     // strides of the other two dims (s or 2s)
-    int nd;           // predicted points per line
-    int nq, nr;       // lines along q and r
+// Shared-memory layouts of one tile (3D, planes b0 = A+1).
+template <int A>
+struct Lay {
+    using TG = TileGeom<A>;
+    static constexpr int P = A + 1;
+    static constexpr int PX = TG::PX;          // floats per row (16-byte multiple)
+    static constexpr int PY = P * PX;          // floats per plane
+    static constexpr int CXC = PX;             // compress code staging: bytes per row (odd multiple of 4 words)
+    static constexpr int CYC = P * CXC;
+    static constexpr int CXD = TG::CX;         // decompress codes (TMA box rows, 16-byte multiple)
+    static constexpr int CYD = P * CXD;
 };
 
-// a[i] for a runtime i in {0,1,2}, without indexing (keeps a[] in registers)
-__device__ __forceinline__ int pick3(const int a[3], int i) { return i == 0 ? a[0] : (i == 1 ? a[1] : a[2]); }
-
-__device__ __forceinline__ PassGeom pass_geom(const hi_level& lv, int p, int s, const int e[3])
-{
-    PassGeom pg;
-    pg.d = lv.order[p];
-    pg.q = (pg.d == 0) ? 1 : 0;
-    pg.r = (pg.d == 2) ? 1 : 2;
-    // dims refined earlier in this level step by s; later ones by 2s
-    const int posq = (lv.order[0] == pg.q) ? 0 : ((lv.order[1] == pg.q) ? 1 : 2);
-    const int posr = (lv.order[0] == pg.r) ? 0 : ((lv.order[1] == pg.r) ? 1 : 2);
-    pg.stq = (posq < p) ? s : 2 * s;
-    pg.str = (posr < p) ? s : 2 * s;
-    const int ed = pick3(e, pg.d);
-    pg.nd = (ed >= s) ? ((ed - s) / (2 * s) + 1) : 0;
-    pg.nq = pick3(e, pg.q) / pg.stq + 1;
-    pg.nr = pick3(e, pg.r) / pg.str + 1;
-    return pg;
-}
+__host__ __device__ constexpr int round128(int b) { return (b + 127) / 128 * 128; }
 
 template <int A>
-__device__ __forceinline__ int vpitch(int d)
+__host__ __device__ constexpr int vbuf_bytes(int b0)
 {
-    using TG = TileGeom<A>;
-    return d == 0 ? TG::PY : (d == 1 ? TG::PX : 1);
+    return round128(b0 * Lay<A>::P * Lay<A>::PX * 4);
 }
 
-template <int A>
-__device__ __forceinline__ int cpitch(int d)
-{
-    using TG = TileGeom<A>;
-    return d == 0 ? TG::CY : (d == 1 ? TG::CX : 1);
-}
-
-// Warp-aggregated histogram update: lanes with equal codes add once.
-__device__ __forceinline__ void hist_add(uint32_t* s_hist, int code, bool valid, int lane)
-{
-    const int key = valid ? code : 256;
-    const unsigned m = __match_any_sync(0xffffffffu, key);
-    if (valid && lane == __ffs(m) - 1) atomicAdd(&s_hist[code], (uint32_t)__popc(m));
-}
-
-// Global linear index of a local shared-memory float offset.
-template <int A>
-__device__ __forceinline__ int64_t global_index(const FieldGeo& g, const int o[3], int vi)
-{
-    using TG = TileGeom<A>;
-    const int c0 = vi / TG::PY;
-    const int rem = vi - c0 * TG::PY;
-    const int c1 = rem / TG::PX;
-    const int c2 = rem - c1 * TG::PX;
-    return ((int64_t)(o[0] + c0) * g.n[1] + (o[1] + c1)) * g.n[2] + (o[2] + c2);
-}
-
+// ---------------------------------------------------------------------------
+// per-CTA context
+// ---------------------------------------------------------------------------
 struct TileInfo {
     int o[3];    // origin (global coords)
     int e[3];    // extent: last local coordinate per dim (0 for inactive dims)
@@ -100,6 +72,7 @@ __device__ __forceinline__ TileInfo tile_info(const FieldGeo& g, int tile)
     TileInfo ti;
     int t[3];
     tile_coords(g, tile, t);
+#pragma unroll
     for (int d = 0; d < 3; ++d) {
         ti.o[d] = t[d] * A;
         const int rem = (int)(g.n[d] - 1 - ti.o[d]);
@@ -109,18 +82,309 @@ __device__ __forceinline__ TileInfo tile_info(const FieldGeo& g, int tile)
     return ti;
 }
 
-// Plain (non-TMA) staging of a float tile into the padded layout.
+// Global linear index of a float offset in the tile buffer.
+template <int A>
+__device__ __forceinline__ int64_t global_index(const FieldGeo& g, const int o[3], int vi)
+{
+    constexpr int PY = Lay<A>::PY, PX = Lay<A>::PX;
+    const int c0 = vi / PY;
+    const int rem = vi - c0 * PY;
+    const int c1 = rem / PX;
+    const int c2 = rem - c1 * PX;
+    return ((int64_t)(o[0] + c0) * g.n[1] + (o[1] + c1)) * g.n[2] + (o[2] + c2);
+}
+
+// What one point of a pass needs, compress or decompress.  The hot values are
+// passed by value; the rarely used ones (outlier spill, decompress outlier
+// reads) live in shared memory so that no pass keeps them in registers.
+struct Hot {
+    float eb_f, ebx2_f, r_f;
+    int own0, own1, own2;  // last owned local coordinate per dim
+};
+
+struct Rare {
+    hi_header* hdr;
+    uint32_t* out_idx;
+    float* out_val;
+    uint64_t out_cap;
+    const float* out;  // decompress: outlier values were scattered here beforehand
+    FieldGeo g;
+    int o[3];
+};
+
+__shared__ Rare s_rare;
+__shared__ uint16_t s_out[kOutCap];  // compress: staged outliers (float offsets in the tile)
+__shared__ int s_nout;
+
+template <int A>
+__device__ __noinline__ void outlier_overflow(int vi, float xv)
+{
+    const unsigned long long pos =
+        atomicAdd(reinterpret_cast<unsigned long long*>(&s_rare.hdr->n_outliers), 1ull);
+    if (pos < s_rare.out_cap) {
+        s_rare.out_idx[pos] = (uint32_t)global_index<A>(s_rare.g, s_rare.o, vi);
+        s_rare.out_val[pos] = xv;
+    } else {
+        set_status(&s_rare.hdr->status, HI_ECAPACITY);
+    }
+}
+
+template <int A>
+__device__ __noinline__ float outlier_value(int vi)
+{
+    return s_rare.out[global_index<A>(s_rare.g, s_rare.o, vi)];
+}
+
+// compress: quantize x against p, stage the code, return the reconstruction
+template <int A>
+__device__ __forceinline__ float point_compress(const Hot& h, float xv, float pr, int vi, uint8_t* code_slot,
+                                                bool owned)
+{
+    float xr;
+    const int code = quantize(xv, pr, h.eb_f, h.ebx2_f, h.r_f, xr);
+    *code_slot = (uint8_t)code;
+    if (code == 0 && owned) {
+        const int slot = atomicAdd(&s_nout, 1);
+        if (slot < kOutCap)
+            s_out[slot] = (uint16_t)vi;
+        else
+            outlier_overflow<A>(vi, xv);
+    }
+    return xr;
+}
+
+// decompress: the reconstruction from the staged code
+template <int A>
+__device__ __forceinline__ float point_decompress(const Hot& h, int code, float pr, int vi)
+{
+    float xr = dequantize(code, pr, h.ebx2_f);
+    if (code == 0) xr = outlier_value<A>(vi);
+    return xr;
+}
+
+// ---------------------------------------------------------------------------
+// Full-tile passes with compile-time geometry (A = 8, 16)
+// ---------------------------------------------------------------------------
+// Step of dim `dim` in pass p of a level with sequence (D0, D1, D2): dims
+// refined earlier in this level step by S, later ones by 2S.
+template <int D0, int D1, int D2, int DIM, int PASS, int S>
+__host__ __device__ constexpr int step_of()
+{
+    return ((DIM == D0 ? 0 : (DIM == D1 ? 1 : 2)) < PASS) ? S : 2 * S;
+}
+
+// Pass along D in {0,1}: one line per thread, lanes adjacent along dim 2.
+template <int A, int S, int D, int STQ, int STR, bool CUBIC, bool COMP>
+__device__ __forceinline__ void pass_cols(float* __restrict__ v, uint8_t* __restrict__ cs, const Hot h)
+{
+    using Lw = Lay<A>;
+    constexpr int Q = (D == 0) ? 1 : 0;  // the other two dims: Q and 2
+    constexpr int NQ = A / STQ + 1, NR = A / STR + 1, NL = NQ * NR, ND = A / (2 * S);
+    constexpr int VPD = (D == 0 ? Lw::PY : Lw::PX) * S, VPQ = (Q == 0 ? Lw::PY : Lw::PX);
+    constexpr int CX = COMP ? Lw::CXC : Lw::CXD, CY = COMP ? Lw::CYC : Lw::CYD;
+    constexpr int CPD = (D == 0 ? CY : CX) * S, CPQ = (Q == 0 ? CY : CX);
+    for (int line = threadIdx.x; line < NL; line += blockDim.x) {
+        const int jq = line / NR, jr = line - jq * NR;
+        const int cq = jq * STQ, cr = jr * STR;
+        const int vb = cq * VPQ + cr, cb = cq * CPQ + cr;
+        const bool lown = (cq <= (Q == 0 ? h.own0 : h.own1)) && (cr <= h.own2);
+        float f[ND + 1];  // known nodes at even multiples of S along D
+#pragma unroll
+        for (int m = 0; m <= ND; ++m) f[m] = v[vb + 2 * m * VPD];
+#pragma unroll
+        for (int k = 0; k < ND; ++k) {
+            const float pr = predict(CUBIC, k >= 1, true, k + 2 <= ND, k >= 1 ? f[k - 1] : 0.0f, f[k], f[k + 1],
+                                     k + 2 <= ND ? f[k + 2] : 0.0f);
+            const int vi = vb + (2 * k + 1) * VPD;
+            if constexpr (COMP) {
+                v[vi] = point_compress<A>(h, v[vi], pr, vi, cs + cb + (2 * k + 1) * CPD, lown);
+            } else {
+                v[vi] = point_decompress<A>(h, cs[cb + (2 * k + 1) * CPD], pr, vi);
+            }
+        }
+    }
+}
+
+// Pass along dim 2: one row per thread, moved with 16-byte accesses.
+template <int A, int S, int STQ, int STR, bool CUBIC, bool COMP>
+__device__ __forceinline__ void pass_rows(float* __restrict__ v, uint8_t* __restrict__ cs, const Hot h)
+{
+    using Lw = Lay<A>;
+    constexpr int NQ = A / STQ + 1, NR = A / STR + 1, NL = NQ * NR, ND = A / (2 * S);
+    constexpr int CX = COMP ? Lw::CXC : Lw::CXD, CY = COMP ? Lw::CYC : Lw::CYD;
+    constexpr int NCW = (A + 4) / 4;  // code words covering positions 0..A
+    for (int line = threadIdx.x; line < NL; line += blockDim.x) {
+        const int jq = line / NR, jr = line - jq * NR;
+        const int c0 = jq * STQ, c1 = jr * STR;
+        float* row = v + c0 * Lw::PY + c1 * Lw::PX;
+        const int cb = c0 * CY + c1 * CX;
+        const bool lown = (c0 <= h.own0) && (c1 <= h.own1);
+        float r[A + 1];
+#pragma unroll
+        for (int j = 0; j < A / 4; ++j) {
+            const float4 q = reinterpret_cast<const float4*>(row)[j];
+            r[4 * j] = q.x, r[4 * j + 1] = q.y, r[4 * j + 2] = q.z, r[4 * j + 3] = q.w;
+        }
+        r[A] = row[A];
+        uint32_t cw[NCW];  // decompress: the row's codes, 4 per word
+        if constexpr (!COMP) {
+            const uint32_t* cwp = reinterpret_cast<const uint32_t*>(cs + cb);
+#pragma unroll
+            for (int j = 0; j < NCW; ++j) cw[j] = cwp[j];
+        }
+#pragma unroll
+        for (int k = 0; k < ND; ++k) {
+            const int c = (2 * k + 1) * S;
+            const float pr = predict(CUBIC, k >= 1, true, k + 2 <= ND, k >= 1 ? r[c - 3 * S] : 0.0f, r[c - S],
+                                     r[c + S], k + 2 <= ND ? r[c + 3 * S] : 0.0f);
+            const int vi = c0 * Lw::PY + c1 * Lw::PX + c;
+            if constexpr (COMP) {
+                r[c] = point_compress<A>(h, r[c], pr, vi, cs + cb + c, lown);
+            } else {
+                r[c] = point_decompress<A>(h, (cw[c >> 2] >> (8 * (c & 3))) & 0xff, pr, vi);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < A / 4; ++j)
+            reinterpret_cast<float4*>(row)[j] = make_float4(r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
+    }
+}
+
+template <int A, int S, int D, int PASS, int D0, int D1, int D2, bool CUBIC, bool COMP>
+__device__ __forceinline__ void pass_full(float* v, uint8_t* cs, const Hot h)
+{
+    if constexpr (D == 2) {
+        pass_rows<A, S, step_of<D0, D1, D2, 0, PASS, S>(), step_of<D0, D1, D2, 1, PASS, S>(), CUBIC, COMP>(v, cs, h);
+    } else {
+        constexpr int Q = (D == 0) ? 1 : 0;
+        pass_cols<A, S, D, step_of<D0, D1, D2, Q, PASS, S>(), step_of<D0, D1, D2, 2, PASS, S>(), CUBIC, COMP>(v, cs, h);
+    }
+}
+
+template <int A, int S, int D0, int D1, int D2, bool CUBIC, bool COMP>
+__device__ __noinline__ void level_full(float* v, uint8_t* cs, const Hot h)
+{
+    pass_full<A, S, D0, 0, D0, D1, D2, CUBIC, COMP>(v, cs, h);
+    __syncthreads();
+    pass_full<A, S, D1, 1, D0, D1, D2, CUBIC, COMP>(v, cs, h);
+    __syncthreads();
+    pass_full<A, S, D2, 2, D0, D1, D2, CUBIC, COMP>(v, cs, h);
+    __syncthreads();
+}
+
+// sel = 2 * perm + cubic; perm: 0 (0,1,2) 1 (0,2,1) 2 (1,0,2) 3 (1,2,0) 4 (2,0,1) 5 (2,1,0)
+template <int A, int S, bool COMP>
+__device__ __forceinline__ void level_dispatch(int sel, float* v, uint8_t* cs, const Hot h)
+{
+    switch (sel) {
+    case 0: level_full<A, S, 0, 1, 2, false, COMP>(v, cs, h); break;
+    case 1: level_full<A, S, 0, 1, 2, true, COMP>(v, cs, h); break;
+    case 2: level_full<A, S, 0, 2, 1, false, COMP>(v, cs, h); break;
+    case 3: level_full<A, S, 0, 2, 1, true, COMP>(v, cs, h); break;
+    case 4: level_full<A, S, 1, 0, 2, false, COMP>(v, cs, h); break;
+    case 5: level_full<A, S, 1, 0, 2, true, COMP>(v, cs, h); break;
+    case 6: level_full<A, S, 1, 2, 0, false, COMP>(v, cs, h); break;
+    case 7: level_full<A, S, 1, 2, 0, true, COMP>(v, cs, h); break;
+    case 8: level_full<A, S, 2, 0, 1, false, COMP>(v, cs, h); break;
+    case 9: level_full<A, S, 2, 0, 1, true, COMP>(v, cs, h); break;
+    case 10: level_full<A, S, 2, 1, 0, false, COMP>(v, cs, h); break;
+    default: level_full<A, S, 2, 1, 0, true, COMP>(v, cs, h); break;
+    }
+}
+
+template <int A, int LV, bool COMP>
+__device__ __forceinline__ void levels_full(const int* s_sel, float* v, uint8_t* cs, const Hot h)
+{
+    level_dispatch<A, (1 << LV), COMP>(s_sel[LV], v, cs, h);
+    if constexpr (LV > 0) levels_full<A, LV - 1, COMP>(s_sel, v, cs, h);
+}
+
+__device__ __forceinline__ int perm_sel(const hi_level& lv)
+{
+    const int a = lv.order[0], b = lv.order[1];
+    const int p = (a == 0) ? (b == 1 ? 0 : 1) : (a == 1) ? (b == 0 ? 2 : 3) : (b == 0 ? 4 : 5);
+    return 2 * p + (lv.interp == HI_CUBIC ? 1 : 0);
+}
+
+template <int A>
+struct HasFull {
+    static constexpr bool value = (A == 8 || A == 16);
+};
+
+// ---------------------------------------------------------------------------
+// Generic passes (geometry in registers): ragged tiles, 1D/2D, any A
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int pick3(const int a[3], int i) { return i == 0 ? a[0] : (i == 1 ? a[1] : a[2]); }
+
+template <int A, bool COMP>
+__device__ __noinline__ void levels_generic(const hi_level* s_lv, float* v, uint8_t* cs, const Hot h,
+                                            const TileInfo ti)
+{
+    using Lw = Lay<A>;
+    constexpr int L = TileGeom<A>::L;
+    const int vp[3] = {Lw::PY, Lw::PX, 1};
+    const int cp[3] = {COMP ? Lw::CYC : Lw::CYD, COMP ? Lw::CXC : Lw::CXD, 1};
+    for (int l = L - 1; l >= 0; --l) {
+        const hi_level lv = s_lv[l];
+        const bool cubic = lv.interp == HI_CUBIC;
+        const int s = 1 << l;
+        for (int p = 0; p < 3; ++p) {
+            const int d = lv.order[p];
+            const int q = (d == 0) ? 1 : 0, r = (d == 2) ? 1 : 2;
+            const int posq = (lv.order[0] == q) ? 0 : ((lv.order[1] == q) ? 1 : 2);
+            const int posr = (lv.order[0] == r) ? 0 : ((lv.order[1] == r) ? 1 : 2);
+            const int stq = (posq < p) ? s : 2 * s, str = (posr < p) ? s : 2 * s;
+            const int ed = pick3(ti.e, d);
+            const int nd = (ed >= s) ? ((ed - s) / (2 * s) + 1) : 0;
+            if (nd == 0) continue;  // CTA-uniform
+            const int nq = pick3(ti.e, q) / stq + 1, nr = pick3(ti.e, r) / str + 1;
+            const int vpd = pick3(vp, d) * s, cpd = pick3(cp, d) * s;
+            const int vpq = pick3(vp, q), vpr = pick3(vp, r), cpq = pick3(cp, q), cpr = pick3(cp, r);
+            const int ownq = pick3(ti.own, q), ownr = pick3(ti.own, r), ownd = pick3(ti.own, d);
+            (void)h.own0;
+            const int nlines = nq * nr;
+            for (int line = threadIdx.x; line < nlines; line += blockDim.x) {
+                const int jq = line / nr, jr = line - jq * nr;
+                const int cq = jq * stq, cr = jr * str;
+                const int vb = cq * vpq + cr * vpr, cb = cq * cpq + cr * cpr;
+                const bool lown = cq <= ownq && cr <= ownr;
+                float fa = 0.0f, fb = v[vb];
+                float fu = (2 * s <= ed) ? v[vb + 2 * vpd] : 0.0f;
+                float fv = (4 * s <= ed) ? v[vb + 4 * vpd] : 0.0f;
+                for (int k = 0; k < nd; ++k) {
+                    const int c = (2 * k + 1) * s;
+                    const float pr = predict(cubic, k >= 1, c + s <= ed, c + 3 * s <= ed, fa, fb, fu, fv);
+                    const int vi = vb + (2 * k + 1) * vpd;
+                    if constexpr (COMP) {
+                        v[vi] = point_compress<A>(h, v[vi], pr, vi, cs + cb + (2 * k + 1) * cpd, lown && c <= ownd);
+                    } else {
+                        v[vi] = point_decompress<A>(h, cs[cb + (2 * k + 1) * cpd], pr, vi);
+                    }
+                    fa = fb;
+                    fb = fu;
+                    fu = fv;
+                    fv = ((2 * k + 6) * s <= ed) ? v[vb + (2 * k + 6) * vpd] : 0.0f;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Staging
+// ---------------------------------------------------------------------------
 template <int A>
 __device__ void load_tile_plain(float* v, const float* __restrict__ x, const FieldGeo& g, const TileInfo& ti)
 {
-    using TG = TileGeom<A>;
+    using Lw = Lay<A>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int rows = (ti.e[0] + 1) * (ti.e[1] + 1);
     for (int rr = warp; rr < rows; rr += nw) {
         const int c0 = rr / (ti.e[1] + 1);
         const int c1 = rr - c0 * (ti.e[1] + 1);
         const float* src = x + ((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2];
-        for (int c2 = lane; c2 <= ti.e[2]; c2 += 32) v[c0 * TG::PY + c1 * TG::PX + c2] = src[c2];
+        for (int c2 = lane; c2 <= ti.e[2]; c2 += 32) v[c0 * Lw::PY + c1 * Lw::PX + c2] = src[c2];
     }
 }
 
@@ -128,79 +392,108 @@ template <int A>
 __device__ void load_codes_plain(uint8_t* cs, const uint8_t* __restrict__ codes, const FieldGeo& g,
                                  const TileInfo& ti)
 {
-    using TG = TileGeom<A>;
+    using Lw = Lay<A>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int rows = (ti.e[0] + 1) * (ti.e[1] + 1);
     for (int rr = warp; rr < rows; rr += nw) {
         const int c0 = rr / (ti.e[1] + 1);
         const int c1 = rr - c0 * (ti.e[1] + 1);
         const uint8_t* src = codes + ((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2];
-        for (int c2 = lane; c2 <= ti.e[2]; c2 += 32) cs[c0 * TG::CY + c1 * TG::CX + c2] = src[c2];
+        for (int c2 = lane; c2 <= ti.e[2]; c2 += 32) cs[c0 * Lw::CYD + c1 * Lw::CXD + c2] = src[c2];
     }
 }
 
-// Stage one tile with TMA (one elected thread issues, everybody waits on the
-// mbarrier phase).  Returns false, CTA-uniformly, if the bounded wait ran out.
-__device__ __forceinline__ bool tma_stage(void* dst, const CUtensorMap* map, const int o[3], uint64_t* mbar,
-                                          uint32_t bytes, uint32_t& phase)
+__device__ __forceinline__ void tma_issue(void* dst, const CUtensorMap* map, const FieldGeo& g, int tile, int A,
+                                          uint64_t* mbar, uint32_t bytes)
 {
-    if (threadIdx.x == 0) {
-        mbar_arrive_expect_tx(mbar, bytes);
-        tma_load_3d(dst, map, o[2], o[1], o[0], mbar);
-    }
-    const bool ok = mbar_wait(mbar, phase, kSpinLimit);
-    phase ^= 1u;
-    return __syncthreads_and(ok) != 0;
+    int t[3];
+    tile_coords(g, tile, t);
+    mbar_arrive_expect_tx(mbar, bytes);
+    tma_load_3d(dst, map, t[2] * A, t[1] * A, t[0] * A, mbar);
+}
+
+// Warp-aggregated histogram update: lanes with equal codes add once.
+__device__ __forceinline__ void hist_add(uint32_t* s_hist, int code, bool valid, int lane)
+{
+    const int key = valid ? code : 256;
+    const unsigned m = __match_any_sync(0xffffffffu, key);
+    if (valid && lane == __ffs(m) - 1) atomicAdd(&s_hist[code], (uint32_t)__popc(m));
 }
 
 // ---------------------------------------------------------------------------
 // Predict + quantize
 // ---------------------------------------------------------------------------
 template <int A>
-__global__ void __launch_bounds__(256) k_compress(const __grid_constant__ CUtensorMap tmap, const FieldGeo g,
-                                                  const float* __restrict__ x, uint8_t* __restrict__ codes,
-                                                  float* __restrict__ anchors, uint32_t* __restrict__ out_idx,
-                                                  float* __restrict__ out_val, const uint64_t out_cap,
-                                                  uint32_t* __restrict__ hist_g, float* __restrict__ recon_g,
-                                                  hi_header* __restrict__ hdr, const uint32_t tma_bytes,
-                                                  const int flags)
+__global__ void __launch_bounds__(kBlock, 4) k_compress(const __grid_constant__ CUtensorMap tmap, const FieldGeo g,
+                                                     const float* __restrict__ x, uint8_t* __restrict__ codes,
+                                                     float* __restrict__ anchors, uint32_t* __restrict__ out_idx,
+                                                     float* __restrict__ out_val, const uint64_t out_cap,
+                                                     uint32_t* __restrict__ hist_g, float* __restrict__ recon_g,
+                                                     hi_header* __restrict__ hdr, const uint32_t tma_bytes,
+                                                     const int flags)
 {
-    using TG = TileGeom<A>;
+    using Lw = Lay<A>;
     extern __shared__ __align__(128) unsigned char smem[];
-    float* v = reinterpret_cast<float*>(smem);
-    uint8_t* cs = smem + ((g.b0 * TG::P * TG::PX * 4 + 127) / 128) * 128;
+    const int vb_bytes = vbuf_bytes<A>(g.b0);
+    float* vbuf[2] = {reinterpret_cast<float*>(smem), reinterpret_cast<float*>(smem + vb_bytes)};
+    uint8_t* cs = smem + 2 * vb_bytes;
     __shared__ uint32_t s_hist[256];
-    __shared__ uint16_t s_out[kOutCap];
-    __shared__ int s_nout;
     __shared__ unsigned long long s_obase;
-    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ __align__(8) uint64_t s_mbar[2];
     __shared__ hi_level s_lv[HI_MAX_LEVELS];
+    __shared__ int s_sel[HI_MAX_LEVELS];
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     const bool use_tma = flags & kFlagTma;
     {   // an earlier stage failed (bad range, device-side EINVAL): leave outputs untouched
         const uint32_t st = hdr->status;
         if (__syncthreads_or(st != 0 && st != HI_ECAPACITY)) return;
     }
-    const float eb_f = hdr->eb_f, ebx2_f = hdr->ebx2_f, r_f = hdr->r_f;
+    Hot h;
+    h.eb_f = hdr->eb_f;
+    h.ebx2_f = hdr->ebx2_f;
+    h.r_f = hdr->r_f;
+    if (tid == 0) {
+        s_rare.hdr = hdr;
+        s_rare.out_idx = out_idx;
+        s_rare.out_val = out_val;
+        s_rare.out_cap = out_cap;
+        s_rare.out = nullptr;
+        s_rare.g = g;
+    }
 
     for (int i = tid; i < 256; i += blockDim.x) s_hist[i] = 0;
-    if (tid < HI_MAX_LEVELS) s_lv[tid] = hdr->level[tid];
+    if (tid < HI_MAX_LEVELS) {
+        s_lv[tid] = hdr->level[tid];
+        s_sel[tid] = perm_sel(s_lv[tid]);
+    }
     if (tid == 0) {
-        mbar_init(&s_mbar, 1);
+        mbar_init(&s_mbar[0], 1);
+        mbar_init(&s_mbar[1], 1);
         fence_mbar_init();
-        if (use_tma) prefetch_tmap(&tmap);
+        if (use_tma) {
+            prefetch_tmap(&tmap);
+            if ((int)blockIdx.x < g.ntiles) tma_issue(vbuf[0], &tmap, g, blockIdx.x, A, &s_mbar[0], tma_bytes);
+        }
     }
     __syncthreads();
+    const bool full_ok = HasFull<A>::value && g.n[0] > 1 && g.n[1] > 1 && g.n[2] > 1;
 
-    uint32_t phase = 0;
-    for (int tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
+    int it = 0;
+    for (int tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x, ++it) {
+        const int buf = it & 1;
+        float* v = vbuf[buf];
         const TileInfo ti = tile_info<A>(g, tile);
-        if (tid == 0) s_nout = 0;
+        const int next = tile + gridDim.x;
+        if (tid == 0) {
+            s_nout = 0;
+            if (use_tma && next < g.ntiles) tma_issue(vbuf[buf ^ 1], &tmap, g, next, A, &s_mbar[buf ^ 1], tma_bytes);
+        }
         if (use_tma) {
-            if (!tma_stage(v, &tmap, ti.o, &s_mbar, tma_bytes, phase)) {
+            const bool ok = mbar_wait(&s_mbar[buf], (it >> 1) & 1, kSpinLimit);
+            if (!__syncthreads_and(ok)) {
                 if (tid == 0) set_status(&hdr->status, HI_ETIMEOUT);
-                mbar_wait(&s_mbar, phase ^ 1u, kSpinLimit);
+                if (next < g.ntiles) mbar_wait(&s_mbar[buf ^ 1], ((it + 1) >> 1) & 1, kSpinLimit);
                 return;
             }
         } else {
@@ -211,111 +504,60 @@ __global__ void __launch_bounds__(256) k_compress(const __grid_constant__ CUtens
         if (tid < 8) {
             const int a0 = (tid >> 2) & 1, a1 = (tid >> 1) & 1, a2 = tid & 1;
             if (a0 * A <= ti.e[0] && a1 * A <= ti.e[1] && a2 * A <= ti.e[2])
-                cs[a0 * A * TG::CY + a1 * A * TG::CX + a2 * A] = (uint8_t)kRadius;
+                cs[a0 * A * Lw::CYC + a1 * A * Lw::CXC + a2 * A] = (uint8_t)kRadius;
         }
-
-        for (int l = TG::L - 1; l >= 0; --l) {
-            const hi_level lv = s_lv[l];
-            const bool cubic = lv.interp == HI_CUBIC;
-            const int s = 1 << l;
-            for (int p = 0; p < 3; ++p) {
-                const PassGeom pg = pass_geom(lv, p, s, ti.e);
-                if (pg.nd == 0) continue;  // CTA-uniform
-                const int ed = pick3(ti.e, pg.d);
-                const int vpd = vpitch<A>(pg.d) * s, cpd = cpitch<A>(pg.d) * s;
-                const int nlines = pg.nq * pg.nr;
-                for (int l0 = warp * 32; l0 < nlines; l0 += blockDim.x) {
-                    const int line = l0 + lane;
-                    const bool act = line < nlines;
-                    const int jq = act ? line / pg.nr : 0;
-                    const int jr = act ? line - jq * pg.nr : 0;
-                    const int cq = jq * pg.stq, cr = jr * pg.str;
-                    const int vb = cq * vpitch<A>(pg.q) + cr * vpitch<A>(pg.r);
-                    const int cb = cq * cpitch<A>(pg.q) + cr * cpitch<A>(pg.r);
-                    const bool lown = act && cq <= pick3(ti.own, pg.q) && cr <= pick3(ti.own, pg.r);
-                    const int ownd = pick3(ti.own, pg.d);
-                    float fa = 0.0f, fb = v[vb];
-                    float fu = (2 * s <= ed) ? v[vb + 2 * vpd] : 0.0f;
-                    float fv = (4 * s <= ed) ? v[vb + 4 * vpd] : 0.0f;
-                    for (int k = 0; k < pg.nd; ++k) {
-                        const int c = (2 * k + 1) * s;
-                        const bool have_r = c + s <= ed, have_l3 = k >= 1, have_r3 = c + 3 * s <= ed;
-                        const float pr = predict(cubic, have_l3, have_r, have_r3, fa, fb, fu, fv);
-                        const int vi = vb + (2 * k + 1) * vpd;
-                        const float xv = v[vi];
-                        float xr;
-                        const int code = quantize(xv, pr, eb_f, ebx2_f, r_f, xr);
-                        if (act) {
-                            v[vi] = xr;
-                            cs[cb + (2 * k + 1) * cpd] = (uint8_t)code;
-                        }
-                        if (code == 0 && lown && c <= ownd) {
-                            const int slot = atomicAdd(&s_nout, 1);
-                            if (slot < kOutCap) {
-                                s_out[slot] = (uint16_t)vi;
-                            } else {  // overflow: write through directly
-                                const unsigned long long pos = atomicAdd(
-                                    reinterpret_cast<unsigned long long*>(&hdr->n_outliers), 1ull);
-                                if (pos < out_cap) {
-                                    out_idx[pos] = (uint32_t)global_index<A>(g, ti.o, vi);
-                                    out_val[pos] = xv;
-                                } else {
-                                    set_status(&hdr->status, HI_ECAPACITY);
-                                }
-                            }
-                        }
-                        fa = fb;
-                        fb = fu;
-                        fu = fv;
-                        fv = ((2 * k + 6) * s <= ed) ? v[vb + (2 * k + 6) * vpd] : 0.0f;
-                    }
-                }
-                __syncthreads();
-            }
+        if (tid == 0) s_rare.o[0] = ti.o[0], s_rare.o[1] = ti.o[1], s_rare.o[2] = ti.o[2];
+        __syncthreads();
+        h.own0 = ti.own[0], h.own1 = ti.own[1], h.own2 = ti.own[2];
+        const bool full = full_ok && ti.e[0] == A && ti.e[1] == A && ti.e[2] == A;
+        if constexpr (HasFull<A>::value) {
+            if (full)
+                levels_full<A, TileGeom<A>::L - 1, true>(s_sel, v, cs, h);
+            else
+                levels_generic<A, true>(s_lv, v, cs, h, ti);
+        } else {
+            levels_generic<A, true>(s_lv, v, cs, h, ti);
         }
 
         // ---- epilogue: owned codes (+ histogram), recon, anchors, outliers
         const int own0 = ti.own[0] + 1, own1 = ti.own[1] + 1, own2 = ti.own[2] + 1;
         const int rows = own0 * own1;
         const bool vec_codes = (flags & kFlagVecCodes) && own2 == A && A >= 8;
-        if constexpr (A < 8) {
-            (void)vec_codes;
-        } else if (vec_codes) {
-            constexpr int CH = (A >= 16) ? 16 : 8;  // bytes per chunk
-            constexpr int NCH = A / CH;
+        if (vec_codes) {
+            constexpr int NW = (A >= 8) ? A / 4 : 1;  // 32-bit words per owned row
+            constexpr int CH = (A >= 16) ? 4 : 2;     // words per global vector store
+            constexpr int NCH = NW / CH > 0 ? NW / CH : 1;
             const int items = rows * NCH;
             for (int i0 = 0; i0 < items; i0 += blockDim.x) {
                 const int i = i0 + tid;
                 const bool act = i < items;
                 const int row = act ? i / NCH : 0, ch = act ? i - row * NCH : 0;
                 const int c0 = row / own1, c1 = row - c0 * own1;
-                const uint8_t* src = cs + c0 * TG::CY + c1 * TG::CX + ch * CH;
+                const uint32_t* src = reinterpret_cast<const uint32_t*>(cs + c0 * Lw::CYC + c1 * Lw::CXC) + ch * CH;
                 uint8_t* dst = codes + ((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2] +
-                               ch * CH;
+                               ch * CH * 4;
                 uint32_t w[4];
-                if (CH == 16) {
-                    const uint4 q4 = *reinterpret_cast<const uint4*>(src);
-                    w[0] = q4.x, w[1] = q4.y, w[2] = q4.z, w[3] = q4.w;
-                    if (act) *reinterpret_cast<uint4*>(dst) = q4;
-                } else {
-                    const uint2 q2 = *reinterpret_cast<const uint2*>(src);
-                    w[0] = q2.x, w[1] = q2.y, w[2] = 0, w[3] = 0;
-                    if (act) *reinterpret_cast<uint2*>(dst) = q2;
+#pragma unroll
+                for (int j = 0; j < CH; ++j) w[j] = src[j];
+                if (act) {
+                    if constexpr (CH == 4)
+                        *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+                    else
+                        *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
                 }
                 if (hist_g) {
 #pragma unroll
-                    for (int b = 0; b < CH; ++b) hist_add(s_hist, (w[b >> 2] >> (8 * (b & 3))) & 0xff, act, lane);
+                    for (int b = 0; b < 4 * CH; ++b) hist_add(s_hist, (w[b >> 2] >> (8 * (b & 3))) & 0xff, act, lane);
                 }
             }
-        }
-        if (!(A >= 8 && vec_codes)) {
+        } else {
             const int items = rows * own2;
             for (int i0 = 0; i0 < items; i0 += blockDim.x) {
                 const int i = i0 + tid;
                 const bool act = i < items;
                 const int row = act ? i / own2 : 0, c2 = act ? i - row * own2 : 0;
                 const int c0 = row / own1, c1 = row - c0 * own1;
-                const int code = cs[c0 * TG::CY + c1 * TG::CX + c2];
+                const int code = cs[c0 * Lw::CYC + c1 * Lw::CXC + c2];
                 if (act)
                     codes[((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2] + c2] =
                         (uint8_t)code;
@@ -328,7 +570,7 @@ __global__ void __launch_bounds__(256) k_compress(const __grid_constant__ CUtens
                 const int row = i / own2, c2 = i - row * own2;
                 const int c0 = row / own1, c1 = row - c0 * own1;
                 recon_g[((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2] + c2] =
-                    v[c0 * TG::PY + c1 * TG::PX + c2];
+                    v[c0 * Lw::PY + c1 * Lw::PX + c2];
             }
         }
         if (tid < 8) {  // owned anchors, verbatim (Sec. 3.2)
@@ -337,7 +579,7 @@ __global__ void __launch_bounds__(256) k_compress(const __grid_constant__ CUtens
             if (l0 <= ti.own[0] && l1 <= ti.own[1] && l2 <= ti.own[2]) {
                 const int64_t ai = ((int64_t)(ti.o[0] / A + a0) * g.na[1] + (ti.o[1] / A + a1)) * g.na[2] +
                                    (ti.o[2] / A + a2);
-                anchors[ai] = v[l0 * TG::PY + l1 * TG::PX + l2];
+                anchors[ai] = v[l0 * Lw::PY + l1 * Lw::PX + l2];
                 if (hist_g) atomicSub(&s_hist[kRadius], 1u);  // anchors are not predicted
             }
         }
@@ -360,7 +602,7 @@ __global__ void __launch_bounds__(256) k_compress(const __grid_constant__ CUtens
             }
         }
         // keep the buffers until every thread is done; order the generic-proxy
-        // writes above before the next TMA overwrite
+        // writes above before the TMA overwrite two tiles later
         fence_proxy_async_smem();
         __syncthreads();
     }
@@ -374,119 +616,116 @@ __global__ void __launch_bounds__(256) k_compress(const __grid_constant__ CUtens
 // Reconstruct
 // ---------------------------------------------------------------------------
 template <int A>
-__global__ void __launch_bounds__(256) k_decompress(const __grid_constant__ CUtensorMap cmap, const FieldGeo g,
-                                                    const uint8_t* __restrict__ codes,
-                                                    const float* __restrict__ anchors, float* out,
-                                                    const hi_header* __restrict__ hdr,
-                                                    uint32_t* __restrict__ status, const uint32_t tma_bytes,
-                                                    const int flags)
+__global__ void __launch_bounds__(kBlock, 4) k_decompress(const __grid_constant__ CUtensorMap cmap, const FieldGeo g,
+                                                       const uint8_t* __restrict__ codes,
+                                                       const float* __restrict__ anchors, float* out,
+                                                       const hi_header* __restrict__ hdr,
+                                                       uint32_t* __restrict__ status, const uint32_t tma_bytes,
+                                                       const int flags)
 {
-    using TG = TileGeom<A>;
+    using Lw = Lay<A>;
     extern __shared__ __align__(128) unsigned char smem[];
+    const int vb_bytes = vbuf_bytes<A>(g.b0);
+    const int cb_bytes = round128(g.b0 * Lw::P * Lw::CXD);
     float* v = reinterpret_cast<float*>(smem);
-    uint8_t* cs = smem + ((g.b0 * TG::P * TG::PX * 4 + 127) / 128) * 128;
-    __shared__ __align__(8) uint64_t s_mbar;
+    uint8_t* cbuf[2] = {smem + vb_bytes, smem + vb_bytes + cb_bytes};
+    __shared__ __align__(8) uint64_t s_mbar[2];
     __shared__ hi_level s_lv[HI_MAX_LEVELS];
+    __shared__ int s_sel[HI_MAX_LEVELS];
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const bool use_tma = flags & kFlagTma;
     if (__syncthreads_or(status != nullptr && *status != 0)) return;
-    const float ebx2_f = hdr->ebx2_f;
-    if (tid < HI_MAX_LEVELS) s_lv[tid] = hdr->level[tid];
+    Hot h;
+    h.eb_f = 0.0f;
+    h.ebx2_f = hdr->ebx2_f;
+    h.r_f = 0.0f;
     if (tid == 0) {
-        mbar_init(&s_mbar, 1);
+        s_rare.hdr = nullptr;
+        s_rare.out_idx = nullptr;
+        s_rare.out_val = nullptr;
+        s_rare.out_cap = 0;
+        s_rare.out = out;
+        s_rare.g = g;
+    }
+    if (tid < HI_MAX_LEVELS) {
+        s_lv[tid] = hdr->level[tid];
+        s_sel[tid] = perm_sel(s_lv[tid]);
+    }
+    if (tid == 0) {
+        mbar_init(&s_mbar[0], 1);
+        mbar_init(&s_mbar[1], 1);
         fence_mbar_init();
-        if (use_tma) prefetch_tmap(&cmap);
+        if (use_tma) {
+            prefetch_tmap(&cmap);
+            if ((int)blockIdx.x < g.ntiles) tma_issue(cbuf[0], &cmap, g, blockIdx.x, A, &s_mbar[0], tma_bytes);
+        }
     }
     __syncthreads();
+    const bool full_ok = HasFull<A>::value && g.n[0] > 1 && g.n[1] > 1 && g.n[2] > 1;
 
-    uint32_t phase = 0;
-    for (int tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
+    int it = 0;
+    for (int tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x, ++it) {
+        const int buf = it & 1;
+        uint8_t* cs = cbuf[buf];
         const TileInfo ti = tile_info<A>(g, tile);
+        const int next = tile + gridDim.x;
+        if (tid == 0 && use_tma && next < g.ntiles)
+            tma_issue(cbuf[buf ^ 1], &cmap, g, next, A, &s_mbar[buf ^ 1], tma_bytes);
         if (tid < 8) {  // seed the anchors
             const int a0 = (tid >> 2) & 1, a1 = (tid >> 1) & 1, a2 = tid & 1;
             const int l0 = a0 * A, l1 = a1 * A, l2 = a2 * A;
             if (l0 <= ti.e[0] && l1 <= ti.e[1] && l2 <= ti.e[2]) {
                 const int64_t ai = ((int64_t)(ti.o[0] / A + a0) * g.na[1] + (ti.o[1] / A + a1)) * g.na[2] +
                                    (ti.o[2] / A + a2);
-                v[l0 * TG::PY + l1 * TG::PX + l2] = anchors[ai];
+                v[l0 * Lw::PY + l1 * Lw::PX + l2] = anchors[ai];
             }
         }
         if (use_tma) {
-            if (!tma_stage(cs, &cmap, ti.o, &s_mbar, tma_bytes, phase)) {
+            const bool ok = mbar_wait(&s_mbar[buf], (it >> 1) & 1, kSpinLimit);
+            if (!__syncthreads_and(ok)) {
                 if (tid == 0) set_status(status, HI_ETIMEOUT);
-                mbar_wait(&s_mbar, phase ^ 1u, kSpinLimit);
+                if (next < g.ntiles) mbar_wait(&s_mbar[buf ^ 1], ((it + 1) >> 1) & 1, kSpinLimit);
                 return;
             }
         } else {
             load_codes_plain<A>(cs, codes, g, ti);
             __syncthreads();
         }
-
-        for (int l = TG::L - 1; l >= 0; --l) {
-            const hi_level lv = s_lv[l];
-            const bool cubic = lv.interp == HI_CUBIC;
-            const int s = 1 << l;
-            for (int p = 0; p < 3; ++p) {
-                const PassGeom pg = pass_geom(lv, p, s, ti.e);
-                if (pg.nd == 0) continue;
-                const int ed = pick3(ti.e, pg.d);
-                const int vpd = vpitch<A>(pg.d) * s, cpd = cpitch<A>(pg.d) * s;
-                const int nlines = pg.nq * pg.nr;
-                for (int l0 = warp * 32; l0 < nlines; l0 += blockDim.x) {
-                    const int line = l0 + lane;
-                    const bool act = line < nlines;
-                    const int jq = act ? line / pg.nr : 0;
-                    const int jr = act ? line - jq * pg.nr : 0;
-                    const int cq = jq * pg.stq, cr = jr * pg.str;
-                    const int vb = cq * vpitch<A>(pg.q) + cr * vpitch<A>(pg.r);
-                    const int cb = cq * cpitch<A>(pg.q) + cr * cpitch<A>(pg.r);
-                    float fa = 0.0f, fb = v[vb];
-                    float fu = (2 * s <= ed) ? v[vb + 2 * vpd] : 0.0f;
-                    float fv = (4 * s <= ed) ? v[vb + 4 * vpd] : 0.0f;
-                    for (int k = 0; k < pg.nd; ++k) {
-                        const int c = (2 * k + 1) * s;
-                        const bool have_r = c + s <= ed, have_l3 = k >= 1, have_r3 = c + 3 * s <= ed;
-                        const float pr = predict(cubic, have_l3, have_r, have_r3, fa, fb, fu, fv);
-                        const int vi = vb + (2 * k + 1) * vpd;
-                        const int code = cs[cb + (2 * k + 1) * cpd];
-                        float xr = dequantize(code, pr, ebx2_f);
-                        if (code == 0 && act) xr = out[global_index<A>(g, ti.o, vi)];
-                        if (act) v[vi] = xr;
-                        fa = fb;
-                        fb = fu;
-                        fu = fv;
-                        fv = ((2 * k + 6) * s <= ed) ? v[vb + (2 * k + 6) * vpd] : 0.0f;
-                    }
-                }
-                __syncthreads();
-            }
+        if (tid == 0) s_rare.o[0] = ti.o[0], s_rare.o[1] = ti.o[1], s_rare.o[2] = ti.o[2];
+        __syncthreads();
+        h.own0 = ti.own[0], h.own1 = ti.own[1], h.own2 = ti.own[2];
+        const bool full = full_ok && ti.e[0] == A && ti.e[1] == A && ti.e[2] == A;
+        if constexpr (HasFull<A>::value) {
+            if (full)
+                levels_full<A, TileGeom<A>::L - 1, false>(s_sel, v, cs, h);
+            else
+                levels_generic<A, false>(s_lv, v, cs, h, ti);
+        } else {
+            levels_generic<A, false>(s_lv, v, cs, h, ti);
         }
 
         // ---- epilogue: owned reconstructed values
         const int own0 = ti.own[0] + 1, own1 = ti.own[1] + 1, own2 = ti.own[2] + 1;
         const int rows = own0 * own1;
         const bool vec_out = (flags & kFlagVecOut) && own2 == A && A >= 4;
-        if constexpr (A < 4) {
-            (void)vec_out;
-        } else if (vec_out) {
-            constexpr int NCH = A / 4;
+        if (vec_out) {
+            constexpr int NCH = (A >= 4) ? A / 4 : 1;
             const int items = rows * NCH;
             for (int i = tid; i < items; i += blockDim.x) {
                 const int row = i / NCH, ch = i - row * NCH;
                 const int c0 = row / own1, c1 = row - c0 * own1;
-                const float4 f4 = *reinterpret_cast<const float4*>(v + c0 * TG::PY + c1 * TG::PX + ch * 4);
+                const float4 f4 = *reinterpret_cast<const float4*>(v + c0 * Lw::PY + c1 * Lw::PX + ch * 4);
                 *reinterpret_cast<float4*>(out + ((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] +
                                            ti.o[2] + ch * 4) = f4;
             }
-        }
-        if (!(A >= 4 && vec_out)) {
+        } else {
             const int items = rows * own2;
             for (int i = tid; i < items; i += blockDim.x) {
                 const int row = i / own2, c2 = i - row * own2;
                 const int c0 = row / own1, c1 = row - c0 * own1;
                 out[((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2] + c2] =
-                    v[c0 * TG::PY + c1 * TG::PX + c2];
+                    v[c0 * Lw::PY + c1 * Lw::PX + c2];
             }
         }
         fence_proxy_async_smem();
@@ -498,27 +737,41 @@ __global__ void __launch_bounds__(256) k_decompress(const __grid_constant__ CUte
 // Launchers
 // ---------------------------------------------------------------------------
 template <int A>
-size_t tile_smem_bytes(int b0)
+size_t compress_smem_t(int b0)
 {
-    using TG = TileGeom<A>;
-    const size_t vb = ((size_t)b0 * TG::P * TG::PX * 4 + 127) / 128 * 128;
-    return vb + (size_t)b0 * TG::P * TG::CX;
+    return 2 * (size_t)vbuf_bytes<A>(b0) + (size_t)round128(b0 * Lay<A>::P * Lay<A>::CXC);
+}
+
+template <int A>
+size_t decompress_smem_t(int b0)
+{
+    return (size_t)vbuf_bytes<A>(b0) + 2 * (size_t)round128(b0 * Lay<A>::P * Lay<A>::CXD);
+}
+
+template <typename K>
+static cudaError_t persistent_grid(K kern, int threads, size_t smem, int num_sms, int ntiles, int max_ctas, int* grid)
+{
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) per_sm = 1;
+    int g = per_sm * num_sms;
+    if (g > ntiles) g = ntiles;
+    if (max_ctas > 0 && g > max_ctas) g = max_ctas;
+    *grid = g > 0 ? g : 1;
+    return cudaSuccess;
 }
 
 template <int A>
 static cudaError_t launch_compress_t(const CompressLaunch& c, cudaStream_t st)
 {
-    const size_t smem = tile_smem_bytes<A>(c.g.b0);
+    const size_t smem = compress_smem_t<A>(c.g.b0);
     auto kern = k_compress<A>;
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int grid = 0;
+    cudaError_t err = persistent_grid(kern, c.threads, smem, c.num_sms, c.g.ntiles, c.max_ctas, &grid);
     if (err != cudaSuccess) return err;
-    int per_sm = 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, c.threads, smem);
-    if (err != cudaSuccess) return err;
-    if (per_sm < 1) per_sm = 1;
-    int grid = per_sm * c.num_sms;
-    if (grid > c.g.ntiles) grid = c.g.ntiles;
-    if (c.max_ctas > 0 && grid > c.max_ctas) grid = c.max_ctas;
     kern<<<grid, c.threads, smem, st>>>(c.tmap, c.g, c.x, c.codes, c.anchors, c.out_idx, c.out_val, c.out_cap,
                                         c.hist, c.recon, c.hdr, c.tma_bytes, c.flags);
     return cudaGetLastError();
@@ -527,17 +780,11 @@ static cudaError_t launch_compress_t(const CompressLaunch& c, cudaStream_t st)
 template <int A>
 static cudaError_t launch_decompress_t(const DecompressLaunch& c, cudaStream_t st)
 {
-    const size_t smem = tile_smem_bytes<A>(c.g.b0);
+    const size_t smem = decompress_smem_t<A>(c.g.b0);
     auto kern = k_decompress<A>;
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int grid = 0;
+    cudaError_t err = persistent_grid(kern, c.threads, smem, c.num_sms, c.g.ntiles, c.max_ctas, &grid);
     if (err != cudaSuccess) return err;
-    int per_sm = 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, c.threads, smem);
-    if (err != cudaSuccess) return err;
-    if (per_sm < 1) per_sm = 1;
-    int grid = per_sm * c.num_sms;
-    if (grid > c.g.ntiles) grid = c.g.ntiles;
-    if (c.max_ctas > 0 && grid > c.max_ctas) grid = c.max_ctas;
     kern<<<grid, c.threads, smem, st>>>(c.cmap, c.g, c.codes, c.anchors, c.out, c.hdr, c.status, c.tma_bytes,
                                         c.flags);
     return cudaGetLastError();
@@ -570,11 +817,11 @@ cudaError_t launch_decompress(int A, const DecompressLaunch& c, cudaStream_t st)
 size_t compress_smem_bytes(int A, int b0)
 {
     switch (A) {
-    case 2: return tile_smem_bytes<2>(b0);
-    case 4: return tile_smem_bytes<4>(b0);
-    case 8: return tile_smem_bytes<8>(b0);
-    case 16: return tile_smem_bytes<16>(b0);
-    case 32: return tile_smem_bytes<32>(b0);
+    case 2: return compress_smem_t<2>(b0);
+    case 4: return compress_smem_t<4>(b0);
+    case 8: return compress_smem_t<8>(b0);
+    case 16: return compress_smem_t<16>(b0);
+    case 32: return compress_smem_t<32>(b0);
     default: return 0;
     }
 }
