@@ -16,6 +16,7 @@ enum : int {
     kFlagTma = 1,       // stage tiles with TMA (strides meet the 16-byte rules)
     kFlagVecCodes = 2,  // code rows may be stored as 8/16-byte vectors
     kFlagVecOut = 4,    // float rows may be stored as 16-byte vectors
+    kFlagDoubleBuf = 8, // two tile buffers fit in shared memory: prefetch the next tile
 };
 
 struct CompressLaunch {

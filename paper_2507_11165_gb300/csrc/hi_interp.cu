@@ -434,9 +434,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_compress(const __grid_constant__ 
 {
     using Lw = Lay<A>;
     extern __shared__ __align__(128) unsigned char smem[];
+    const bool dbuf = flags & kFlagDoubleBuf;
     const int vb_bytes = vbuf_bytes<A>(g.b0);
-    float* vbuf[2] = {reinterpret_cast<float*>(smem), reinterpret_cast<float*>(smem + vb_bytes)};
-    uint8_t* cs = smem + 2 * vb_bytes;
+    float* vbuf[2] = {reinterpret_cast<float*>(smem), reinterpret_cast<float*>(smem + (dbuf ? vb_bytes : 0))};
+    uint8_t* cs = smem + (dbuf ? 2 : 1) * vb_bytes;
     __shared__ uint32_t s_hist[256];
     __shared__ unsigned long long s_obase;
     __shared__ __align__(8) uint64_t s_mbar[2];
@@ -481,19 +482,21 @@ __global__ void __launch_bounds__(kBlock, 4) k_compress(const __grid_constant__ 
 
     int it = 0;
     for (int tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x, ++it) {
-        const int buf = it & 1;
+        const int buf = dbuf ? (it & 1) : 0;
         float* v = vbuf[buf];
         const TileInfo ti = tile_info<A>(g, tile);
         const int next = tile + gridDim.x;
         if (tid == 0) {
             s_nout = 0;
-            if (use_tma && next < g.ntiles) tma_issue(vbuf[buf ^ 1], &tmap, g, next, A, &s_mbar[buf ^ 1], tma_bytes);
+            if (use_tma && dbuf && next < g.ntiles)
+                tma_issue(vbuf[buf ^ 1], &tmap, g, next, A, &s_mbar[buf ^ 1], tma_bytes);
+            if (use_tma && !dbuf && it > 0) tma_issue(v, &tmap, g, tile, A, &s_mbar[0], tma_bytes);
         }
         if (use_tma) {
-            const bool ok = mbar_wait(&s_mbar[buf], (it >> 1) & 1, kSpinLimit);
+            const bool ok = mbar_wait(&s_mbar[buf], dbuf ? ((it >> 1) & 1) : (it & 1), kSpinLimit);
             if (!__syncthreads_and(ok)) {
                 if (tid == 0) set_status(&hdr->status, HI_ETIMEOUT);
-                if (next < g.ntiles) mbar_wait(&s_mbar[buf ^ 1], ((it + 1) >> 1) & 1, kSpinLimit);
+                if (dbuf && next < g.ntiles) mbar_wait(&s_mbar[buf ^ 1], ((it + 1) >> 1) & 1, kSpinLimit);
                 return;
             }
         } else {
@@ -627,8 +630,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_decompress(const __grid_constant_
     extern __shared__ __align__(128) unsigned char smem[];
     const int vb_bytes = vbuf_bytes<A>(g.b0);
     const int cb_bytes = round128(g.b0 * Lw::P * Lw::CXD);
+    const bool dbuf = flags & kFlagDoubleBuf;
     float* v = reinterpret_cast<float*>(smem);
-    uint8_t* cbuf[2] = {smem + vb_bytes, smem + vb_bytes + cb_bytes};
+    uint8_t* cbuf[2] = {smem + vb_bytes, smem + vb_bytes + (dbuf ? cb_bytes : 0)};
     __shared__ __align__(8) uint64_t s_mbar[2];
     __shared__ hi_level s_lv[HI_MAX_LEVELS];
     __shared__ int s_sel[HI_MAX_LEVELS];
@@ -666,12 +670,14 @@ __global__ void __launch_bounds__(kBlock, 4) k_decompress(const __grid_constant_
 
     int it = 0;
     for (int tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x, ++it) {
-        const int buf = it & 1;
+        const int buf = dbuf ? (it & 1) : 0;
         uint8_t* cs = cbuf[buf];
         const TileInfo ti = tile_info<A>(g, tile);
         const int next = tile + gridDim.x;
-        if (tid == 0 && use_tma && next < g.ntiles)
-            tma_issue(cbuf[buf ^ 1], &cmap, g, next, A, &s_mbar[buf ^ 1], tma_bytes);
+        if (tid == 0 && use_tma) {
+            if (dbuf && next < g.ntiles) tma_issue(cbuf[buf ^ 1], &cmap, g, next, A, &s_mbar[buf ^ 1], tma_bytes);
+            if (!dbuf && it > 0) tma_issue(cs, &cmap, g, tile, A, &s_mbar[0], tma_bytes);
+        }
         if (tid < 8) {  // seed the anchors
             const int a0 = (tid >> 2) & 1, a1 = (tid >> 1) & 1, a2 = tid & 1;
             const int l0 = a0 * A, l1 = a1 * A, l2 = a2 * A;
@@ -682,10 +688,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_decompress(const __grid_constant_
             }
         }
         if (use_tma) {
-            const bool ok = mbar_wait(&s_mbar[buf], (it >> 1) & 1, kSpinLimit);
+            const bool ok = mbar_wait(&s_mbar[buf], dbuf ? ((it >> 1) & 1) : (it & 1), kSpinLimit);
             if (!__syncthreads_and(ok)) {
                 if (tid == 0) set_status(status, HI_ETIMEOUT);
-                if (next < g.ntiles) mbar_wait(&s_mbar[buf ^ 1], ((it + 1) >> 1) & 1, kSpinLimit);
+                if (dbuf && next < g.ntiles) mbar_wait(&s_mbar[buf ^ 1], ((it + 1) >> 1) & 1, kSpinLimit);
                 return;
             }
         } else {
@@ -737,15 +743,27 @@ __global__ void __launch_bounds__(kBlock, 4) k_decompress(const __grid_constant_
 // Launchers
 // ---------------------------------------------------------------------------
 template <int A>
-size_t compress_smem_t(int b0)
+size_t compress_smem_t(int b0, bool dbuf)
 {
-    return 2 * (size_t)vbuf_bytes<A>(b0) + (size_t)round128(b0 * Lay<A>::P * Lay<A>::CXC);
+    return (dbuf ? 2 : 1) * (size_t)vbuf_bytes<A>(b0) + (size_t)round128(b0 * Lay<A>::P * Lay<A>::CXC);
 }
 
 template <int A>
-size_t decompress_smem_t(int b0)
+size_t decompress_smem_t(int b0, bool dbuf)
 {
-    return (size_t)vbuf_bytes<A>(b0) + 2 * (size_t)round128(b0 * Lay<A>::P * Lay<A>::CXD);
+    return (size_t)vbuf_bytes<A>(b0) + (dbuf ? 2 : 1) * (size_t)round128(b0 * Lay<A>::P * Lay<A>::CXD);
+}
+
+// Double buffering when both buffers and the kernel's static shared memory fit.
+template <typename K>
+static bool fits_double(K kern, size_t dyn_double)
+{
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
+    if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return false;
+    return dyn_double + fa.sharedSizeBytes <= (size_t)optin;
 }
 
 template <typename K>
@@ -767,26 +785,29 @@ static cudaError_t persistent_grid(K kern, int threads, size_t smem, int num_sms
 template <int A>
 static cudaError_t launch_compress_t(const CompressLaunch& c, cudaStream_t st)
 {
-    const size_t smem = compress_smem_t<A>(c.g.b0);
     auto kern = k_compress<A>;
+    const bool dbuf = fits_double(kern, compress_smem_t<A>(c.g.b0, true));
+    const size_t smem = compress_smem_t<A>(c.g.b0, dbuf);
     int grid = 0;
     cudaError_t err = persistent_grid(kern, c.threads, smem, c.num_sms, c.g.ntiles, c.max_ctas, &grid);
     if (err != cudaSuccess) return err;
     kern<<<grid, c.threads, smem, st>>>(c.tmap, c.g, c.x, c.codes, c.anchors, c.out_idx, c.out_val, c.out_cap,
-                                        c.hist, c.recon, c.hdr, c.tma_bytes, c.flags);
+                                        c.hist, c.recon, c.hdr, c.tma_bytes,
+                                        c.flags | (dbuf ? kFlagDoubleBuf : 0));
     return cudaGetLastError();
 }
 
 template <int A>
 static cudaError_t launch_decompress_t(const DecompressLaunch& c, cudaStream_t st)
 {
-    const size_t smem = decompress_smem_t<A>(c.g.b0);
     auto kern = k_decompress<A>;
+    const bool dbuf = fits_double(kern, decompress_smem_t<A>(c.g.b0, true));
+    const size_t smem = decompress_smem_t<A>(c.g.b0, dbuf);
     int grid = 0;
     cudaError_t err = persistent_grid(kern, c.threads, smem, c.num_sms, c.g.ntiles, c.max_ctas, &grid);
     if (err != cudaSuccess) return err;
     kern<<<grid, c.threads, smem, st>>>(c.cmap, c.g, c.codes, c.anchors, c.out, c.hdr, c.status, c.tma_bytes,
-                                        c.flags);
+                                        c.flags | (dbuf ? kFlagDoubleBuf : 0));
     return cudaGetLastError();
 }
 
@@ -817,11 +838,11 @@ cudaError_t launch_decompress(int A, const DecompressLaunch& c, cudaStream_t st)
 size_t compress_smem_bytes(int A, int b0)
 {
     switch (A) {
-    case 2: return compress_smem_t<2>(b0);
-    case 4: return compress_smem_t<4>(b0);
-    case 8: return compress_smem_t<8>(b0);
-    case 16: return compress_smem_t<16>(b0);
-    case 32: return compress_smem_t<32>(b0);
+    case 2: return compress_smem_t<2>(b0, false);
+    case 4: return compress_smem_t<4>(b0, false);
+    case 8: return compress_smem_t<8>(b0, false);
+    case 16: return compress_smem_t<16>(b0, false);
+    case 32: return compress_smem_t<32>(b0, false);
     default: return 0;
     }
 }
