@@ -148,10 +148,14 @@ HI_API hi_status hi_compress(const hi_params* p, const float* d_x, uint8_t* d_co
  *   min(d_header->n_outliers, out_cap) are used; an index outside the field
  *   or n_outliers > out_cap sets HI_ECORRUPT / HI_ECAPACITY in *d_status.
  *   d_out      [n_points] float32 output
- *   d_status   one uint32 (may be NULL): 0 on success, else a hi_status. */
+ *   d_status   one uint32 (may be NULL): 0 on success, else a hi_status.
+ *   d_ws       at least HI_DECOMPRESS_WS_BYTES of device workspace (8-byte
+ *              aligned; hi_query's ws_bytes always suffices). */
+#define HI_DECOMPRESS_WS_BYTES 256
 HI_API hi_status hi_decompress(const hi_params* p, const hi_header* d_header, const uint8_t* d_codes,
                         const float* d_anchors, const uint32_t* d_out_idx, const float* d_out_val,
-                        uint64_t out_cap, float* d_out, uint32_t* d_status, cudaStream_t stream);
+                        uint64_t out_cap, float* d_out, uint32_t* d_status, void* d_ws, size_t ws_bytes,
+                        cudaStream_t stream);
 
 /* Auto-tune only (Sec. 5.1.3): writes the chosen level[] and n_levels into
  * d_header (other fields untouched).  Uniformly sampled blocks (every

@@ -126,12 +126,14 @@ hi_status make_geometry(const hi_params* p, Geometry* G)
     return HI_OK;
 }
 
-constexpr size_t kWsTicket = 0;
+constexpr size_t kWsTicket = 0;  // uint32: last-CTA ticket of the range pass
+constexpr size_t kWsQueue = 4;   // uint32: tile queue of the predict / reconstruct kernels
 constexpr size_t kWsPartials = 256;
 constexpr size_t kWsTune = kWsPartials + sizeof(float2) * kRangeBlocks;
 
 size_t workspace_bytes(const Geometry& G)
 {
+    static_assert(kWsTune >= HI_DECOMPRESS_WS_BYTES, "workspace layout");
     return kWsTune + sizeof(double) * (size_t)G.m * G.L * 12;
 }
 
@@ -272,8 +274,10 @@ hi_status hi_compress(const hi_params* p, const float* d_x, uint8_t* d_codes, fl
 
     char* ws = static_cast<char*>(d_ws);
     uint32_t* ticket = reinterpret_cast<uint32_t*>(ws + kWsTicket);
+    uint32_t* queue = reinterpret_cast<uint32_t*>(ws + kWsQueue);
     stage_event(0, stream);
-    cudaError_t e = launch_prologue(d_header, *p, G.n_anchors, out_cap, (uint32_t)G.L, d_hist, ticket, stream);
+    cudaError_t e =
+        launch_prologue(d_header, *p, G.n_anchors, out_cap, (uint32_t)G.L, d_hist, ticket, queue, stream);
     if (e != cudaSuccess) return HI_ECUDA;
     stage_event(1, stream);
     if (p->eb_mode == HI_EB_REL) {
@@ -305,6 +309,7 @@ hi_status hi_compress(const hi_params* p, const float* d_x, uint8_t* d_codes, fl
     c.hist = d_hist;
     c.recon = d_recon;
     c.hdr = d_header;
+    c.queue = queue;
     c.tma_bytes = (uint32_t)(PX * (G.A + 1) * G.g.b0 * 4);
     const int ch = G.A >= 16 ? 16 : 8;
     c.flags = (tma ? kFlagTma : 0) |
@@ -319,7 +324,8 @@ hi_status hi_compress(const hi_params* p, const float* d_x, uint8_t* d_codes, fl
 
 hi_status hi_decompress(const hi_params* p, const hi_header* d_header, const uint8_t* d_codes,
                         const float* d_anchors, const uint32_t* d_out_idx, const float* d_out_val,
-                        uint64_t out_cap, float* d_out, uint32_t* d_status, cudaStream_t stream)
+                        uint64_t out_cap, float* d_out, uint32_t* d_status, void* d_ws, size_t ws_bytes,
+                        cudaStream_t stream)
 {
     Geometry G;
     hi_params q = *p;
@@ -328,14 +334,16 @@ hi_status hi_decompress(const hi_params* p, const hi_header* d_header, const uin
     if (s != HI_OK) return s;
     if (!d_header || !d_codes || !d_anchors || !d_out) return HI_EINVAL;
     if (out_cap > 0 && (!d_out_idx || !d_out_val)) return HI_EINVAL;
-    if (!aligned(d_out, 4)) return HI_EINVAL;
+    if (!aligned(d_out, 4) || !d_ws || !aligned(d_ws, 8)) return HI_EINVAL;
+    if (ws_bytes < HI_DECOMPRESS_WS_BYTES) return HI_ENOMEM;
+    uint32_t* queue = reinterpret_cast<uint32_t*>(static_cast<char*>(d_ws) + kWsQueue);
     cudaError_t e;
     stage_event(5, stream);
     if (d_status) {
         e = cudaMemsetAsync(d_status, 0, sizeof(uint32_t), stream);
         if (e != cudaSuccess) return HI_ECUDA;
     }
-    e = launch_scatter(d_out_idx, d_out_val, out_cap, d_header, G.g.N, d_out, d_status, stream);
+    e = launch_scatter(d_out_idx, d_out_val, out_cap, d_header, G.g.N, d_out, d_status, queue, stream);
     if (e != cudaSuccess) return HI_ECUDA;
     stage_event(6, stream);
     DecompressLaunch c{};
@@ -349,6 +357,7 @@ hi_status hi_decompress(const hi_params* p, const hi_header* d_header, const uin
     c.out = d_out;
     c.hdr = d_header;
     c.status = d_status;
+    c.queue = queue;
     c.tma_bytes = (uint32_t)(CX * (G.A + 1) * G.g.b0);
     c.flags = (tma ? kFlagTma : 0) | ((G.g.n[2] % 4 == 0 && aligned(d_out, 16)) ? kFlagVecOut : 0);
     c.threads = threads_for(G);

@@ -41,7 +41,7 @@ __device__ void finalize_eps(hi_header* h, float vmin, float vmax)
 }
 
 __global__ void k_prologue(hi_header* hdr, const hi_params p, uint64_t n_anchors, uint64_t out_cap,
-                           uint32_t n_levels, uint32_t* hist, uint32_t* ticket)
+                           uint32_t n_levels, uint32_t* hist, uint32_t* ticket, uint32_t* queue)
 {
     const int tid = threadIdx.x;
     if (hist)
@@ -61,12 +61,12 @@ __global__ void k_prologue(hi_header* hdr, const hi_params p, uint64_t n_anchors
         for (int l = 0; l < HI_MAX_LEVELS; ++l) hdr->level[l] = p.level[l];
         for (int k = 0; k < 7; ++k) hdr->reserved[k] = 0;
         if (ticket) *ticket = 0;
+        if (queue) *queue = 0;
         if (p.eb_mode == HI_EB_ABS) finalize_eps(hdr, 0.0f, 0.0f);
     }
 }
 
-// Order-preserving integer keys of finite floats, so that min/max reduce with
-// integer atomics-free comparisons; -0 sorts below +0 (reported as +0).
+// A finite value (NaN and +-Inf are left out of the range).
 __device__ __forceinline__ bool finite_f(float v) { return fabsf(v) < INFINITY; }
 
 // Value range over the finite values: one grid-strided streaming read; the
@@ -133,11 +133,12 @@ __global__ void __launch_bounds__(512) k_range(const float* __restrict__ x, int6
 // them there (code 0 means "take the stored value").
 __global__ void k_scatter(const uint32_t* __restrict__ idx, const float* __restrict__ val, uint64_t cap,
                           const hi_header* __restrict__ hdr, int64_t N, float* __restrict__ out,
-                          uint32_t* __restrict__ status)
+                          uint32_t* __restrict__ status, uint32_t* __restrict__ queue)
 {
     const uint64_t n_all = hdr->n_outliers;
     const uint64_t n = n_all < cap ? n_all : cap;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *queue = 0;  // the reconstruction kernel's tile queue
         if (hdr->magic != HI_MAGIC) set_status(status, HI_ECORRUPT);
         if (n_all > cap) set_status(status, HI_ECAPACITY);
     }
@@ -263,9 +264,9 @@ __global__ void k_tune_select(const double* __restrict__ err, int m, int L, cons
 }
 
 cudaError_t launch_prologue(hi_header* hdr, const hi_params& p, uint64_t n_anchors, uint64_t out_cap,
-                            uint32_t n_levels, uint32_t* hist, uint32_t* ticket, cudaStream_t st)
+                            uint32_t n_levels, uint32_t* hist, uint32_t* ticket, uint32_t* queue, cudaStream_t st)
 {
-    k_prologue<<<1, 256, 0, st>>>(hdr, p, n_anchors, out_cap, n_levels, hist, ticket);
+    k_prologue<<<1, 256, 0, st>>>(hdr, p, n_anchors, out_cap, n_levels, hist, ticket, queue);
     return cudaGetLastError();
 }
 
@@ -277,9 +278,9 @@ cudaError_t launch_range(const float* x, int64_t N, float2* partials, int nblock
 }
 
 cudaError_t launch_scatter(const uint32_t* idx, const float* val, uint64_t cap, const hi_header* hdr, int64_t N,
-                           float* out, uint32_t* status, cudaStream_t st)
+                           float* out, uint32_t* status, uint32_t* queue, cudaStream_t st)
 {
-    k_scatter<<<256, 256, 0, st>>>(idx, val, cap, hdr, N, out, status);
+    k_scatter<<<256, 256, 0, st>>>(idx, val, cap, hdr, N, out, status, queue);
     return cudaGetLastError();
 }
 

@@ -31,6 +31,7 @@ struct CompressLaunch {
     uint32_t* hist;
     float* recon;
     hi_header* hdr;
+    uint32_t* queue;  // tile queue counter, zero at launch
     uint32_t tma_bytes;
     int flags;
     int threads;
@@ -46,6 +47,7 @@ struct DecompressLaunch {
     float* out;
     const hi_header* hdr;
     uint32_t* status;
+    uint32_t* queue;  // tile queue counter, zero at launch
     uint32_t tma_bytes;
     int flags;
     int threads;
@@ -67,11 +69,11 @@ size_t compress_smem_bytes(int A, int b0);
 
 // hi_aux.cu
 cudaError_t launch_prologue(hi_header* hdr, const hi_params& p, uint64_t n_anchors, uint64_t out_cap,
-                            uint32_t n_levels, uint32_t* hist, uint32_t* ticket, cudaStream_t st);
+                            uint32_t n_levels, uint32_t* hist, uint32_t* ticket, uint32_t* queue, cudaStream_t st);
 cudaError_t launch_range(const float* x, int64_t N, float2* partials, int nblocks, uint32_t* ticket,
                          hi_header* hdr, cudaStream_t st);
 cudaError_t launch_scatter(const uint32_t* idx, const float* val, uint64_t cap, const hi_header* hdr, int64_t N,
-                           float* out, uint32_t* status, cudaStream_t st);
+                           float* out, uint32_t* status, uint32_t* queue, cudaStream_t st);
 cudaError_t launch_tune(int A, const FieldGeo& g, const float* x, const TuneCands& cands, int m, int stride,
                         double* err, hi_header* hdr, cudaStream_t st);
 

@@ -429,8 +429,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_compress(const __grid_constant__ 
                                                      float* __restrict__ anchors, uint32_t* __restrict__ out_idx,
                                                      float* __restrict__ out_val, const uint64_t out_cap,
                                                      uint32_t* __restrict__ hist_g, float* __restrict__ recon_g,
-                                                     hi_header* __restrict__ hdr, const uint32_t tma_bytes,
-                                                     const int flags)
+                                                     hi_header* __restrict__ hdr, uint32_t* __restrict__ queue,
+                                                     const uint32_t tma_bytes, const int flags)
 {
     using Lw = Lay<A>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -443,6 +443,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_compress(const __grid_constant__ 
     __shared__ __align__(8) uint64_t s_mbar[2];
     __shared__ hi_level s_lv[HI_MAX_LEVELS];
     __shared__ int s_sel[HI_MAX_LEVELS];
+    __shared__ int s_next;
 
     const int tid = threadIdx.x, lane = tid & 31;
     const bool use_tma = flags & kFlagTma;
@@ -480,29 +481,34 @@ __global__ void __launch_bounds__(kBlock, 4) k_compress(const __grid_constant__ 
     __syncthreads();
     const bool full_ok = HasFull<A>::value && g.n[0] > 1 && g.n[1] > 1 && g.n[2] > 1;
 
+    // tiles after each CTA's first come from a queue in ascending order: the
+    // load stays balanced (edge tiles cost more) and neighbouring tiles, which
+    // share faces, are in flight together
     int it = 0;
-    for (int tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x, ++it) {
+    for (int tile = blockIdx.x; tile < g.ntiles; ++it) {
         const int buf = dbuf ? (it & 1) : 0;
         float* v = vbuf[buf];
         const TileInfo ti = tile_info<A>(g, tile);
-        const int next = tile + gridDim.x;
         if (tid == 0) {
             s_nout = 0;
-            if (use_tma && dbuf && next < g.ntiles)
-                tma_issue(vbuf[buf ^ 1], &tmap, g, next, A, &s_mbar[buf ^ 1], tma_bytes);
+            const int nx = (int)gridDim.x + (int)atomicAdd(queue, 1u);
+            s_next = nx;
+            if (use_tma && dbuf && nx < g.ntiles)
+                tma_issue(vbuf[buf ^ 1], &tmap, g, nx, A, &s_mbar[buf ^ 1], tma_bytes);
             if (use_tma && !dbuf && it > 0) tma_issue(v, &tmap, g, tile, A, &s_mbar[0], tma_bytes);
         }
         if (use_tma) {
             const bool ok = mbar_wait(&s_mbar[buf], dbuf ? ((it >> 1) & 1) : (it & 1), kSpinLimit);
             if (!__syncthreads_and(ok)) {
                 if (tid == 0) set_status(&hdr->status, HI_ETIMEOUT);
-                if (dbuf && next < g.ntiles) mbar_wait(&s_mbar[buf ^ 1], ((it + 1) >> 1) & 1, kSpinLimit);
+                if (dbuf && s_next < g.ntiles) mbar_wait(&s_mbar[buf ^ 1], ((it + 1) >> 1) & 1, kSpinLimit);
                 return;
             }
         } else {
             load_tile_plain<A>(v, x, g, ti);
             __syncthreads();
         }
+        const int next = s_next;
         // anchors keep the zero-error code
         if (tid < 8) {
             const int a0 = (tid >> 2) & 1, a1 = (tid >> 1) & 1, a2 = tid & 1;
@@ -608,6 +614,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_compress(const __grid_constant__ 
         // writes above before the TMA overwrite two tiles later
         fence_proxy_async_smem();
         __syncthreads();
+        tile = next;
     }
     if (hist_g) {
         for (int i = tid; i < 256; i += blockDim.x)
@@ -623,8 +630,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_decompress(const __grid_constant_
                                                        const uint8_t* __restrict__ codes,
                                                        const float* __restrict__ anchors, float* out,
                                                        const hi_header* __restrict__ hdr,
-                                                       uint32_t* __restrict__ status, const uint32_t tma_bytes,
-                                                       const int flags)
+                                                       uint32_t* __restrict__ status, uint32_t* __restrict__ queue,
+                                                       const uint32_t tma_bytes, const int flags)
 {
     using Lw = Lay<A>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -636,6 +643,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_decompress(const __grid_constant_
     __shared__ __align__(8) uint64_t s_mbar[2];
     __shared__ hi_level s_lv[HI_MAX_LEVELS];
     __shared__ int s_sel[HI_MAX_LEVELS];
+    __shared__ int s_next;
 
     const int tid = threadIdx.x;
     const bool use_tma = flags & kFlagTma;
@@ -669,14 +677,16 @@ __global__ void __launch_bounds__(kBlock, 4) k_decompress(const __grid_constant_
     const bool full_ok = HasFull<A>::value && g.n[0] > 1 && g.n[1] > 1 && g.n[2] > 1;
 
     int it = 0;
-    for (int tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x, ++it) {
+    for (int tile = blockIdx.x; tile < g.ntiles; ++it) {
         const int buf = dbuf ? (it & 1) : 0;
         uint8_t* cs = cbuf[buf];
         const TileInfo ti = tile_info<A>(g, tile);
-        const int next = tile + gridDim.x;
-        if (tid == 0 && use_tma) {
-            if (dbuf && next < g.ntiles) tma_issue(cbuf[buf ^ 1], &cmap, g, next, A, &s_mbar[buf ^ 1], tma_bytes);
-            if (!dbuf && it > 0) tma_issue(cs, &cmap, g, tile, A, &s_mbar[0], tma_bytes);
+        if (tid == 0) {
+            const int nx = (int)gridDim.x + (int)atomicAdd(queue, 1u);
+            s_next = nx;
+            if (use_tma && dbuf && nx < g.ntiles)
+                tma_issue(cbuf[buf ^ 1], &cmap, g, nx, A, &s_mbar[buf ^ 1], tma_bytes);
+            if (use_tma && !dbuf && it > 0) tma_issue(cs, &cmap, g, tile, A, &s_mbar[0], tma_bytes);
         }
         if (tid < 8) {  // seed the anchors
             const int a0 = (tid >> 2) & 1, a1 = (tid >> 1) & 1, a2 = tid & 1;
@@ -691,13 +701,14 @@ __global__ void __launch_bounds__(kBlock, 4) k_decompress(const __grid_constant_
             const bool ok = mbar_wait(&s_mbar[buf], dbuf ? ((it >> 1) & 1) : (it & 1), kSpinLimit);
             if (!__syncthreads_and(ok)) {
                 if (tid == 0) set_status(status, HI_ETIMEOUT);
-                if (dbuf && next < g.ntiles) mbar_wait(&s_mbar[buf ^ 1], ((it + 1) >> 1) & 1, kSpinLimit);
+                if (dbuf && s_next < g.ntiles) mbar_wait(&s_mbar[buf ^ 1], ((it + 1) >> 1) & 1, kSpinLimit);
                 return;
             }
         } else {
             load_codes_plain<A>(cs, codes, g, ti);
             __syncthreads();
         }
+        const int next = s_next;
         if (tid == 0) s_rare.o[0] = ti.o[0], s_rare.o[1] = ti.o[1], s_rare.o[2] = ti.o[2];
         __syncthreads();
         h.own0 = ti.own[0], h.own1 = ti.own[1], h.own2 = ti.own[2];
@@ -736,6 +747,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_decompress(const __grid_constant_
         }
         fence_proxy_async_smem();
         __syncthreads();
+        tile = next;
     }
 }
 
@@ -792,7 +804,7 @@ static cudaError_t launch_compress_t(const CompressLaunch& c, cudaStream_t st)
     cudaError_t err = persistent_grid(kern, c.threads, smem, c.num_sms, c.g.ntiles, c.max_ctas, &grid);
     if (err != cudaSuccess) return err;
     kern<<<grid, c.threads, smem, st>>>(c.tmap, c.g, c.x, c.codes, c.anchors, c.out_idx, c.out_val, c.out_cap,
-                                        c.hist, c.recon, c.hdr, c.tma_bytes,
+                                        c.hist, c.recon, c.hdr, c.queue, c.tma_bytes,
                                         c.flags | (dbuf ? kFlagDoubleBuf : 0));
     return cudaGetLastError();
 }
@@ -806,8 +818,8 @@ static cudaError_t launch_decompress_t(const DecompressLaunch& c, cudaStream_t s
     int grid = 0;
     cudaError_t err = persistent_grid(kern, c.threads, smem, c.num_sms, c.g.ntiles, c.max_ctas, &grid);
     if (err != cudaSuccess) return err;
-    kern<<<grid, c.threads, smem, st>>>(c.cmap, c.g, c.codes, c.anchors, c.out, c.hdr, c.status, c.tma_bytes,
-                                        c.flags | (dbuf ? kFlagDoubleBuf : 0));
+    kern<<<grid, c.threads, smem, st>>>(c.cmap, c.g, c.codes, c.anchors, c.out, c.hdr, c.status, c.queue,
+                                        c.tma_bytes, c.flags | (dbuf ? kFlagDoubleBuf : 0));
     return cudaGetLastError();
 }
 

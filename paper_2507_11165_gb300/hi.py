@@ -79,7 +79,7 @@ def lib():
             L.hi_query.argtypes = [ctypes.POINTER(HiParams), ctypes.POINTER(u64), ctypes.POINTER(u64),
                                    ctypes.POINTER(u64), ctypes.POINTER(sz)]
             L.hi_compress.argtypes = [ctypes.POINTER(HiParams), P, P, P, P, P, u64, P, P, P, P, sz, P]
-            L.hi_decompress.argtypes = [ctypes.POINTER(HiParams), P, P, P, P, P, u64, P, P, P]
+            L.hi_decompress.argtypes = [ctypes.POINTER(HiParams), P, P, P, P, P, u64, P, P, P, sz, P]
             L.hi_autotune.argtypes = [ctypes.POINTER(HiParams), P, P, P, sz, P]
             L.hi_autotune_errors.argtypes = [ctypes.POINTER(HiParams), P, P, sz, P, P, P, P]
             L.hi_header_read.argtypes = [P, ctypes.POINTER(HiHeader), P]
@@ -229,11 +229,14 @@ def compress_into(x, b: Buffers, stream=None):
     _check(rc, "hi_compress")
 
 
-def decompress_into(b: Buffers, out, status=None, stream=None):
-    """Enqueue hi_decompress of the record in ``b`` into ``out`` (no sync)."""
+def decompress_into(b: Buffers, out, status=None, stream=None, ws=None):
+    """Enqueue hi_decompress of the record in ``b`` into ``out`` (no sync).
+
+    Uses ``b.ws`` as workspace unless ``ws`` (a uint8 device tensor) is given."""
+    w = b.ws if ws is None else ws
     rc = lib().hi_decompress(ctypes.byref(b.params), _ptr(b.header), _ptr(b.codes), _ptr(b.anchors),
-                             _ptr(b.out_idx), _ptr(b.out_val), b.out_cap, _ptr(out), _ptr(status),
-                             _stream(stream))
+                             _ptr(b.out_idx), _ptr(b.out_val), b.out_cap, _ptr(out), _ptr(status), _ptr(w),
+                             w.numel(), _stream(stream))
     _check(rc, "hi_decompress")
 
 
