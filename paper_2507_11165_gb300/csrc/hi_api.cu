@@ -73,7 +73,7 @@ TuneCands make_cands(const uint64_t dims[3])
 
 hi_status make_geometry(const hi_params* p, Geometry* G)
 {
-    if (!p || p->reserved != 0) return HI_EINVAL;
+    if (!p || (p->tuning & ~0xFu) != 0 || ((p->tuning >> 2) & 3u) == 3u) return HI_EINVAL;
     const int L = ilog2_pow2(p->anchor_stride);
     if (L < 0) return HI_EINVAL;
     if (!(p->eb > 0.0) || !std::isfinite(p->eb)) return HI_EINVAL;
@@ -196,11 +196,13 @@ int num_sms()
     return n > 0 ? n : 1;
 }
 
-int threads_for(const Geometry& G)
+int threads_for(const Geometry& G, uint32_t tuning)
 {
-    // work per pass grows with the tile volume; small 1D/2D tiles use fewer threads
+    static const int kThreads[4] = {0, 64, 128, 256};
+    if (tuning & 3u) return kThreads[tuning & 3u];
+    // one tile per CTA: 128 threads keep the passes busy and let several tiles
+    // share an SM (measured on GB300 for 17^3 tiles); small 1D/2D tiles use 64
     const long long vol = (long long)G.g.b0 * (G.A + 1) * ((G.g.n[1] > 1) ? (G.A + 1) : 1);
-    if (vol >= 2048) return 256;
     if (vol >= 512) return 128;
     return 64;
 }
@@ -314,7 +316,8 @@ hi_status hi_compress(const hi_params* p, const float* d_x, uint8_t* d_codes, fl
     const int ch = G.A >= 16 ? 16 : 8;
     c.flags = (tma ? kFlagTma : 0) |
               ((G.g.n[2] % ch == 0 && aligned(d_codes, 16)) ? kFlagVecCodes : 0);
-    c.threads = threads_for(G);
+    c.threads = threads_for(G, p->tuning);
+    c.buffers = (int)((p->tuning >> 2) & 3u);
     c.num_sms = num_sms();
     c.max_ctas = 0;
     s = cuda_status(launch_compress(G.A, c, stream));
@@ -360,7 +363,8 @@ hi_status hi_decompress(const hi_params* p, const hi_header* d_header, const uin
     c.queue = queue;
     c.tma_bytes = (uint32_t)(CX * (G.A + 1) * G.g.b0);
     c.flags = (tma ? kFlagTma : 0) | ((G.g.n[2] % 4 == 0 && aligned(d_out, 16)) ? kFlagVecOut : 0);
-    c.threads = threads_for(G);
+    c.threads = threads_for(G, p->tuning);
+    c.buffers = (int)((p->tuning >> 2) & 3u);
     c.num_sms = num_sms();
     c.max_ctas = 0;
     s = cuda_status(launch_decompress(G.A, c, stream));

@@ -35,6 +35,7 @@ struct CompressLaunch {
     uint32_t tma_bytes;
     int flags;
     int threads;
+    int buffers;   // 0 = two when they fit, 1 = one, 2 = two
     int num_sms;
     int max_ctas;  // 0 = occupancy-limited persistent grid
 };
@@ -51,6 +52,7 @@ struct DecompressLaunch {
     uint32_t tma_bytes;
     int flags;
     int threads;
+    int buffers;
     int num_sms;
     int max_ctas;
 };

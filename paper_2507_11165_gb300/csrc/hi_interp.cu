@@ -2,30 +2,33 @@
 // inverse, the level-by-level reconstruction (cuSZ-Hi, arXiv 2507.11165,
 // Sec. 3.2, Sec. 5.1.1-5.1.2, Sec. 5.2.1).
 //
-// Persistent CTAs walk the blocks ("tiles") of (A+1)^d points in a
-// grid-strided loop.  Each tile is staged in shared memory by one 3D TMA box
-// load, double buffered: the next tile's load is in flight while the current
-// one is processed (plain loads when the field's strides do not meet the TMA
-// rules).  Every level (stride s = A/2 .. 1) runs its three 1D passes in the
-// configured dimension sequence; predictions read values already
+// Persistent CTAs take blocks ("tiles") of (A+1)^d points from a queue in
+// ascending order.  A tile is staged in shared memory by one 3D TMA box load
+// (plain loads when the field's strides do not meet the TMA rules); with two
+// tile buffers the next tile's load is in flight while the current one is
+// processed.  Every level (stride S = A/2 .. 1) runs its three 1D passes in
+// the configured dimension sequence; predictions read values already
 // reconstructed in shared memory (closed loop), so the decompressor repeats
 // exactly the same arithmetic.
 //
-// Two code paths share that structure:
-//   * full 3D tiles (extent A in every dim) at A = 8 or 16 -- the bulk of any
-//     large field -- run passes whose geometry is fixed at compile time for
-//     each (level, dimension sequence, spline): stencil cases, line counts and
-//     shared-memory offsets are constants.  Passes along the contiguous dim
-//     move whole rows with 16-byte shared-memory accesses (conflict-free at the
-//     20-float row pitch); passes along the other dims give each thread one
-//     line, lanes adjacent along the contiguous dim.
-//   * every other tile (ragged field edges, 1D/2D fields, other A) runs the
-//     same passes with the geometry held in registers.
+// Pass geometry is compile-time wherever possible: every (level, spline,
+// pass dimension) is its own instantiation.
+//   * full 3D tiles (extent A in every dim, A = 8 or 16) -- the bulk of any
+//     large field -- also fix the dimension sequence at compile time, so line
+//     counts, stencil cases and shared-memory offsets are constants;
+//   * all other tiles (ragged field edges, 1D/2D fields, other A) take the
+//     extents at run time.
+// Passes along the contiguous dim move whole rows with 16-byte shared-memory
+// accesses (conflict-free at the 16-byte-multiple, odd-word row pitch);
+// passes along the other dims give each thread one line, lanes adjacent along
+// the contiguous dim.
 //
 // Shared faces between tiles are computed by both tiles with identical
 // results; only the owning tile (the one with the lower block index, or the
 // last block for the field's upper face) writes codes, histogram counts,
-// outliers and reconstructed values.
+// outliers and reconstructed values.  Codes are staged in shared memory and
+// leave the tile in its epilogue, which also finds the outliers (code 0) and
+// counts the histogram.
 #include <cstdint>
 
 #include "hi_device.cuh"
@@ -34,18 +37,19 @@
 namespace hi {
 
 constexpr int kOutCap = 1024;  // staged outliers per tile before the direct path
-constexpr int kBlock = 256;    // threads per CTA of the 3D paths
+constexpr int kMaxThreads = 256;
+constexpr int kHistBase = 112;  // codes kHistBase .. kHistBase+31 are counted by warp ballots
 
-// Shared-memory layouts of one tile (3D, planes b0 = A+1).
+// Shared-memory layouts of one tile (planes b0 = A+1, or 1 for 1D/2D fields).
 template <int A>
 struct Lay {
     using TG = TileGeom<A>;
     static constexpr int P = A + 1;
-    static constexpr int PX = TG::PX;          // floats per row (16-byte multiple)
-    static constexpr int PY = P * PX;          // floats per plane
-    static constexpr int CXC = PX;             // compress code staging: bytes per row (odd multiple of 4 words)
+    static constexpr int PX = TG::PX;   // floats per row (16-byte multiple)
+    static constexpr int PY = P * PX;   // floats per plane
+    static constexpr int CXC = PX;      // compress code staging: bytes per row
     static constexpr int CYC = P * CXC;
-    static constexpr int CXD = TG::CX;         // decompress codes (TMA box rows, 16-byte multiple)
+    static constexpr int CXD = TG::CX;  // decompress codes (TMA box rows, 16-byte multiple)
     static constexpr int CYD = P * CXD;
 };
 
@@ -57,9 +61,6 @@ __host__ __device__ constexpr int vbuf_bytes(int b0)
     return round128(b0 * Lay<A>::P * Lay<A>::PX * 4);
 }
 
-// ---------------------------------------------------------------------------
-// per-CTA context
-// ---------------------------------------------------------------------------
 struct TileInfo {
     int o[3];    // origin (global coords)
     int e[3];    // extent: last local coordinate per dim (0 for inactive dims)
@@ -94,40 +95,19 @@ __device__ __forceinline__ int64_t global_index(const FieldGeo& g, const int o[3
     return ((int64_t)(o[0] + c0) * g.n[1] + (o[1] + c1)) * g.n[2] + (o[2] + c2);
 }
 
-// What one point of a pass needs, compress or decompress.  The hot values are
-// passed by value; the rarely used ones (outlier spill, decompress outlier
-// reads) live in shared memory so that no pass keeps them in registers.
+// Values every point needs, passed by value; the decompressor's rare outlier
+// read goes through shared memory so that no pass keeps it in registers.
 struct Hot {
     float eb_f, ebx2_f, r_f;
-    int own0, own1, own2;  // last owned local coordinate per dim
 };
 
 struct Rare {
-    hi_header* hdr;
-    uint32_t* out_idx;
-    float* out_val;
-    uint64_t out_cap;
     const float* out;  // decompress: outlier values were scattered here beforehand
     FieldGeo g;
     int o[3];
 };
 
 __shared__ Rare s_rare;
-__shared__ uint16_t s_out[kOutCap];  // compress: staged outliers (float offsets in the tile)
-__shared__ int s_nout;
-
-template <int A>
-__device__ __noinline__ void outlier_overflow(int vi, float xv)
-{
-    const unsigned long long pos =
-        atomicAdd(reinterpret_cast<unsigned long long*>(&s_rare.hdr->n_outliers), 1ull);
-    if (pos < s_rare.out_cap) {
-        s_rare.out_idx[pos] = (uint32_t)global_index<A>(s_rare.g, s_rare.o, vi);
-        s_rare.out_val[pos] = xv;
-    } else {
-        set_status(&s_rare.hdr->status, HI_ECAPACITY);
-    }
-}
 
 template <int A>
 __device__ __noinline__ float outlier_value(int vi)
@@ -136,20 +116,10 @@ __device__ __noinline__ float outlier_value(int vi)
 }
 
 // compress: quantize x against p, stage the code, return the reconstruction
-template <int A>
-__device__ __forceinline__ float point_compress(const Hot& h, float xv, float pr, int vi, uint8_t* code_slot,
-                                                bool owned)
+__device__ __forceinline__ float point_compress(const Hot& h, float xv, float pr, uint8_t* code_slot)
 {
     float xr;
-    const int code = quantize(xv, pr, h.eb_f, h.ebx2_f, h.r_f, xr);
-    *code_slot = (uint8_t)code;
-    if (code == 0 && owned) {
-        const int slot = atomicAdd(&s_nout, 1);
-        if (slot < kOutCap)
-            s_out[slot] = (uint16_t)vi;
-        else
-            outlier_overflow<A>(vi, xv);
-    }
+    *code_slot = (uint8_t)quantize(xv, pr, h.eb_f, h.ebx2_f, h.r_f, xr);
     return xr;
 }
 
@@ -163,41 +133,42 @@ __device__ __forceinline__ float point_decompress(const Hot& h, int code, float 
 }
 
 // ---------------------------------------------------------------------------
-// Full-tile passes with compile-time geometry (A = 8, 16)
+// Passes.  A pass along D predicts, on every line parallel to D, the points
+// at odd multiples of S from the nodes at even multiples (stencil cases from
+// the extent ED of the line).  Lines are indexed by the two other dims,
+// stepping by STQ / STR.
 // ---------------------------------------------------------------------------
-// Step of dim `dim` in pass p of a level with sequence (D0, D1, D2): dims
-// refined earlier in this level step by S, later ones by 2S.
-template <int D0, int D1, int D2, int DIM, int PASS, int S>
-__host__ __device__ constexpr int step_of()
+template <int A, int S, int D, bool CUBIC, bool COMP, bool FULL>
+__device__ __forceinline__ void pass_cols(float* __restrict__ v, uint8_t* __restrict__ cs, const Hot h, int stq,
+                                          int str, int nq, int nr, int ed)
 {
-    return ((DIM == D0 ? 0 : (DIM == D1 ? 1 : 2)) < PASS) ? S : 2 * S;
-}
-
-// Pass along D in {0,1}: one line per thread, lanes adjacent along dim 2.
-template <int A, int S, int D, int STQ, int STR, bool CUBIC, bool COMP>
-__device__ __forceinline__ void pass_cols(float* __restrict__ v, uint8_t* __restrict__ cs, const Hot h)
-{
+    static_assert(D == 0 || D == 1, "columns");
     using Lw = Lay<A>;
     constexpr int Q = (D == 0) ? 1 : 0;  // the other two dims: Q and 2
-    constexpr int NQ = A / STQ + 1, NR = A / STR + 1, NL = NQ * NR, ND = A / (2 * S);
+    constexpr int NDM = A / (2 * S);
     constexpr int VPD = (D == 0 ? Lw::PY : Lw::PX) * S, VPQ = (Q == 0 ? Lw::PY : Lw::PX);
     constexpr int CX = COMP ? Lw::CXC : Lw::CXD, CY = COMP ? Lw::CYC : Lw::CYD;
     constexpr int CPD = (D == 0 ? CY : CX) * S, CPQ = (Q == 0 ? CY : CX);
-    for (int line = threadIdx.x; line < NL; line += blockDim.x) {
-        const int jq = line / NR, jr = line - jq * NR;
-        const int cq = jq * STQ, cr = jr * STR;
+    const int nd = FULL ? NDM : ((ed >= S) ? ((ed - S) / (2 * S) + 1) : 0);
+    const int nl = nq * nr;
+    for (int line = threadIdx.x; line < nl; line += blockDim.x) {
+        const int jq = line / nr, jr = line - jq * nr;
+        const int cq = jq * stq, cr = jr * str;
         const int vb = cq * VPQ + cr, cb = cq * CPQ + cr;
-        const bool lown = (cq <= (Q == 0 ? h.own0 : h.own1)) && (cr <= h.own2);
-        float f[ND + 1];  // known nodes at even multiples of S along D
+        float f[NDM + 1];  // known nodes at even multiples of S along D
 #pragma unroll
-        for (int m = 0; m <= ND; ++m) f[m] = v[vb + 2 * m * VPD];
+        for (int m = 0; m <= NDM; ++m) f[m] = (FULL || 2 * m * S <= ed) ? v[vb + 2 * m * VPD] : 0.0f;
 #pragma unroll
-        for (int k = 0; k < ND; ++k) {
-            const float pr = predict(CUBIC, k >= 1, true, k + 2 <= ND, k >= 1 ? f[k - 1] : 0.0f, f[k], f[k + 1],
-                                     k + 2 <= ND ? f[k + 2] : 0.0f);
+        for (int k = 0; k < NDM; ++k) {
+            if (!FULL && k >= nd) break;
+            const int c = (2 * k + 1) * S;
+            const bool have_r = FULL ? true : (c + S <= ed);
+            const bool have_r3 = FULL ? (k + 2 <= NDM) : (c + 3 * S <= ed);
+            const float pr = predict(CUBIC, k >= 1, have_r, have_r3, k >= 1 ? f[k - 1] : 0.0f, f[k],
+                                     have_r ? f[k + 1] : 0.0f, (k + 2 <= NDM && have_r3) ? f[k + 2] : 0.0f);
             const int vi = vb + (2 * k + 1) * VPD;
             if constexpr (COMP) {
-                v[vi] = point_compress<A>(h, v[vi], pr, vi, cs + cb + (2 * k + 1) * CPD, lown);
+                v[vi] = point_compress(h, v[vi], pr, cs + cb + (2 * k + 1) * CPD);
             } else {
                 v[vi] = point_decompress<A>(h, cs[cb + (2 * k + 1) * CPD], pr, vi);
             }
@@ -206,26 +177,30 @@ __device__ __forceinline__ void pass_cols(float* __restrict__ v, uint8_t* __rest
 }
 
 // Pass along dim 2: one row per thread, moved with 16-byte accesses.
-template <int A, int S, int STQ, int STR, bool CUBIC, bool COMP>
-__device__ __forceinline__ void pass_rows(float* __restrict__ v, uint8_t* __restrict__ cs, const Hot h)
+template <int A, int S, bool CUBIC, bool COMP, bool FULL>
+__device__ __forceinline__ void pass_rows(float* __restrict__ v, uint8_t* __restrict__ cs, const Hot h, int stq,
+                                          int str, int nq, int nr, int ed)
 {
     using Lw = Lay<A>;
-    constexpr int NQ = A / STQ + 1, NR = A / STR + 1, NL = NQ * NR, ND = A / (2 * S);
+    constexpr int NDM = A / (2 * S);
+    constexpr int NV = A / 4;  // float4 chunks of a row; elements 4*NV .. A one by one
     constexpr int CX = COMP ? Lw::CXC : Lw::CXD, CY = COMP ? Lw::CYC : Lw::CYD;
     constexpr int NCW = (A + 4) / 4;  // code words covering positions 0..A
-    for (int line = threadIdx.x; line < NL; line += blockDim.x) {
-        const int jq = line / NR, jr = line - jq * NR;
-        const int c0 = jq * STQ, c1 = jr * STR;
+    const int nd = FULL ? NDM : ((ed >= S) ? ((ed - S) / (2 * S) + 1) : 0);
+    const int nl = nq * nr;
+    for (int line = threadIdx.x; line < nl; line += blockDim.x) {
+        const int jq = line / nr, jr = line - jq * nr;
+        const int c0 = jq * stq, c1 = jr * str;
         float* row = v + c0 * Lw::PY + c1 * Lw::PX;
         const int cb = c0 * CY + c1 * CX;
-        const bool lown = (c0 <= h.own0) && (c1 <= h.own1);
         float r[A + 1];
 #pragma unroll
-        for (int j = 0; j < A / 4; ++j) {
+        for (int j = 0; j < NV; ++j) {
             const float4 q = reinterpret_cast<const float4*>(row)[j];
             r[4 * j] = q.x, r[4 * j + 1] = q.y, r[4 * j + 2] = q.z, r[4 * j + 3] = q.w;
         }
-        r[A] = row[A];
+#pragma unroll
+        for (int j = 4 * NV; j <= A; ++j) r[j] = row[j];
         uint32_t cw[NCW];  // decompress: the row's codes, 4 per word
         if constexpr (!COMP) {
             const uint32_t* cwp = reinterpret_cast<const uint32_t*>(cs + cb);
@@ -233,32 +208,55 @@ __device__ __forceinline__ void pass_rows(float* __restrict__ v, uint8_t* __rest
             for (int j = 0; j < NCW; ++j) cw[j] = cwp[j];
         }
 #pragma unroll
-        for (int k = 0; k < ND; ++k) {
+        for (int k = 0; k < NDM; ++k) {
+            if (!FULL && k >= nd) break;
             const int c = (2 * k + 1) * S;
-            const float pr = predict(CUBIC, k >= 1, true, k + 2 <= ND, k >= 1 ? r[c - 3 * S] : 0.0f, r[c - S],
-                                     r[c + S], k + 2 <= ND ? r[c + 3 * S] : 0.0f);
-            const int vi = c0 * Lw::PY + c1 * Lw::PX + c;
+            const bool have_r = FULL ? true : (c + S <= ed);
+            const bool have_r3 = FULL ? (k + 2 <= NDM) : (c + 3 * S <= ed);
+            const float pr = predict(CUBIC, k >= 1, have_r, have_r3, k >= 1 ? r[c - 3 * S] : 0.0f, r[c - S],
+                                     have_r ? r[c + S] : 0.0f, (c + 3 * S <= A && have_r3) ? r[c + 3 * S] : 0.0f);
             if constexpr (COMP) {
-                r[c] = point_compress<A>(h, r[c], pr, vi, cs + cb + c, lown);
+                r[c] = point_compress(h, r[c], pr, cs + cb + c);
             } else {
-                r[c] = point_decompress<A>(h, (cw[c >> 2] >> (8 * (c & 3))) & 0xff, pr, vi);
+                r[c] = point_decompress<A>(h, (cw[c >> 2] >> (8 * (c & 3))) & 0xff, pr,
+                                           c0 * Lw::PY + c1 * Lw::PX + c);
             }
         }
 #pragma unroll
-        for (int j = 0; j < A / 4; ++j)
+        for (int j = 0; j < NV; ++j)
             reinterpret_cast<float4*>(row)[j] = make_float4(r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
+#pragma unroll
+        for (int j = 4 * NV; j < A; ++j) row[j] = r[j];
     }
+}
+
+template <int A, int S, int D, bool CUBIC, bool COMP, bool FULL>
+__device__ __forceinline__ void pass_any(float* v, uint8_t* cs, const Hot h, int stq, int str, int nq, int nr,
+                                         int ed)
+{
+    if constexpr (D == 2)
+        pass_rows<A, S, CUBIC, COMP, FULL>(v, cs, h, stq, str, nq, nr, ed);
+    else
+        pass_cols<A, S, D, CUBIC, COMP, FULL>(v, cs, h, stq, str, nq, nr, ed);
+}
+
+// ---------------------------------------------------------------------------
+// Full 3D tiles: the whole level at compile time
+// ---------------------------------------------------------------------------
+// Step of dim DIM in pass PASS of a level with sequence (D0, D1, D2): dims
+// refined earlier in this level step by S, later ones by 2S.
+template <int D0, int D1, int D2, int DIM, int PASS, int S>
+__host__ __device__ constexpr int step_of()
+{
+    return ((DIM == D0 ? 0 : (DIM == D1 ? 1 : 2)) < PASS) ? S : 2 * S;
 }
 
 template <int A, int S, int D, int PASS, int D0, int D1, int D2, bool CUBIC, bool COMP>
 __device__ __forceinline__ void pass_full(float* v, uint8_t* cs, const Hot h)
 {
-    if constexpr (D == 2) {
-        pass_rows<A, S, step_of<D0, D1, D2, 0, PASS, S>(), step_of<D0, D1, D2, 1, PASS, S>(), CUBIC, COMP>(v, cs, h);
-    } else {
-        constexpr int Q = (D == 0) ? 1 : 0;
-        pass_cols<A, S, D, step_of<D0, D1, D2, Q, PASS, S>(), step_of<D0, D1, D2, 2, PASS, S>(), CUBIC, COMP>(v, cs, h);
-    }
+    constexpr int Q = (D == 0) ? 1 : 0, R = (D == 2) ? 1 : 2;
+    constexpr int STQ = step_of<D0, D1, D2, Q, PASS, S>(), STR = step_of<D0, D1, D2, R, PASS, S>();
+    pass_any<A, S, D, CUBIC, COMP, true>(v, cs, h, STQ, STR, A / STQ + 1, A / STR + 1, A);
 }
 
 template <int A, int S, int D0, int D1, int D2, bool CUBIC, bool COMP>
@@ -312,63 +310,42 @@ struct HasFull {
 };
 
 // ---------------------------------------------------------------------------
-// Generic passes (geometry in registers): ragged tiles, 1D/2D, any A
+// Other tiles: extents at run time, one instantiation per (level, dim, spline)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int pick3(const int a[3], int i) { return i == 0 ? a[0] : (i == 1 ? a[1] : a[2]); }
 
-template <int A, bool COMP>
-__device__ __noinline__ void levels_generic(const hi_level* s_lv, float* v, uint8_t* cs, const Hot h,
-                                            const TileInfo ti)
+template <int A, int LV, bool COMP>
+__device__ __noinline__ void level_ragged(const hi_level lv, float* v, uint8_t* cs, const Hot h, const TileInfo ti)
 {
-    using Lw = Lay<A>;
-    constexpr int L = TileGeom<A>::L;
-    const int vp[3] = {Lw::PY, Lw::PX, 1};
-    const int cp[3] = {COMP ? Lw::CYC : Lw::CYD, COMP ? Lw::CXC : Lw::CXD, 1};
-    for (int l = L - 1; l >= 0; --l) {
-        const hi_level lv = s_lv[l];
-        const bool cubic = lv.interp == HI_CUBIC;
-        const int s = 1 << l;
-        for (int p = 0; p < 3; ++p) {
-            const int d = lv.order[p];
-            const int q = (d == 0) ? 1 : 0, r = (d == 2) ? 1 : 2;
-            const int posq = (lv.order[0] == q) ? 0 : ((lv.order[1] == q) ? 1 : 2);
-            const int posr = (lv.order[0] == r) ? 0 : ((lv.order[1] == r) ? 1 : 2);
-            const int stq = (posq < p) ? s : 2 * s, str = (posr < p) ? s : 2 * s;
-            const int ed = pick3(ti.e, d);
-            const int nd = (ed >= s) ? ((ed - s) / (2 * s) + 1) : 0;
-            if (nd == 0) continue;  // CTA-uniform
-            const int nq = pick3(ti.e, q) / stq + 1, nr = pick3(ti.e, r) / str + 1;
-            const int vpd = pick3(vp, d) * s, cpd = pick3(cp, d) * s;
-            const int vpq = pick3(vp, q), vpr = pick3(vp, r), cpq = pick3(cp, q), cpr = pick3(cp, r);
-            const int ownq = pick3(ti.own, q), ownr = pick3(ti.own, r), ownd = pick3(ti.own, d);
-            (void)h.own0;
-            const int nlines = nq * nr;
-            for (int line = threadIdx.x; line < nlines; line += blockDim.x) {
-                const int jq = line / nr, jr = line - jq * nr;
-                const int cq = jq * stq, cr = jr * str;
-                const int vb = cq * vpq + cr * vpr, cb = cq * cpq + cr * cpr;
-                const bool lown = cq <= ownq && cr <= ownr;
-                float fa = 0.0f, fb = v[vb];
-                float fu = (2 * s <= ed) ? v[vb + 2 * vpd] : 0.0f;
-                float fv = (4 * s <= ed) ? v[vb + 4 * vpd] : 0.0f;
-                for (int k = 0; k < nd; ++k) {
-                    const int c = (2 * k + 1) * s;
-                    const float pr = predict(cubic, k >= 1, c + s <= ed, c + 3 * s <= ed, fa, fb, fu, fv);
-                    const int vi = vb + (2 * k + 1) * vpd;
-                    if constexpr (COMP) {
-                        v[vi] = point_compress<A>(h, v[vi], pr, vi, cs + cb + (2 * k + 1) * cpd, lown && c <= ownd);
-                    } else {
-                        v[vi] = point_decompress<A>(h, cs[cb + (2 * k + 1) * cpd], pr, vi);
-                    }
-                    fa = fb;
-                    fb = fu;
-                    fu = fv;
-                    fv = ((2 * k + 6) * s <= ed) ? v[vb + (2 * k + 6) * vpd] : 0.0f;
-                }
-            }
-            __syncthreads();
+    constexpr int S = 1 << LV;
+    const bool cubic = lv.interp == HI_CUBIC;
+    for (int p = 0; p < 3; ++p) {
+        const int d = lv.order[p];
+        const int q = (d == 0) ? 1 : 0, r = (d == 2) ? 1 : 2;
+        const int posq = (lv.order[0] == q) ? 0 : ((lv.order[1] == q) ? 1 : 2);
+        const int posr = (lv.order[0] == r) ? 0 : ((lv.order[1] == r) ? 1 : 2);
+        const int stq = (posq < p) ? S : 2 * S, str = (posr < p) ? S : 2 * S;
+        const int ed = pick3(ti.e, d);
+        if (ed < S) continue;  // no point on this pass (CTA-uniform)
+        const int nq = pick3(ti.e, q) / stq + 1, nr = pick3(ti.e, r) / str + 1;
+        switch (2 * d + (cubic ? 1 : 0)) {
+        case 0: pass_any<A, S, 0, false, COMP, false>(v, cs, h, stq, str, nq, nr, ed); break;
+        case 1: pass_any<A, S, 0, true, COMP, false>(v, cs, h, stq, str, nq, nr, ed); break;
+        case 2: pass_any<A, S, 1, false, COMP, false>(v, cs, h, stq, str, nq, nr, ed); break;
+        case 3: pass_any<A, S, 1, true, COMP, false>(v, cs, h, stq, str, nq, nr, ed); break;
+        case 4: pass_any<A, S, 2, false, COMP, false>(v, cs, h, stq, str, nq, nr, ed); break;
+        default: pass_any<A, S, 2, true, COMP, false>(v, cs, h, stq, str, nq, nr, ed); break;
         }
+        __syncthreads();
     }
+}
+
+template <int A, int LV, bool COMP>
+__device__ __forceinline__ void levels_ragged(const hi_level* s_lv, float* v, uint8_t* cs, const Hot h,
+                                              const TileInfo& ti)
+{
+    level_ragged<A, LV, COMP>(s_lv[LV], v, cs, h, ti);
+    if constexpr (LV > 0) levels_ragged<A, LV - 1, COMP>(s_lv, v, cs, h, ti);
 }
 
 // ---------------------------------------------------------------------------
@@ -412,25 +389,70 @@ __device__ __forceinline__ void tma_issue(void* dst, const CUtensorMap* map, con
     tma_load_3d(dst, map, t[2] * A, t[1] * A, t[0] * A, mbar);
 }
 
-// Warp-aggregated histogram update: lanes with equal codes add once.
-__device__ __forceinline__ void hist_add(uint32_t* s_hist, int code, bool valid, int lane)
+// ---------------------------------------------------------------------------
+// Epilogue helpers (all lanes of the warp call them)
+// ---------------------------------------------------------------------------
+// Histogram of one code per lane: codes in [kHistBase, kHistBase+32) are
+// counted by bit-plane ballots -- lane j ends up with the number of lanes
+// holding code kHistBase+j and keeps it in its own counter -- the rest go to
+// shared-memory atomics.  Returns true for a valid code outside that window.
+__device__ __forceinline__ bool hist_ballot(int code, bool valid, uint32_t& cnt, uint32_t* s_hist, bool on)
 {
-    const int key = valid ? code : 256;
-    const unsigned m = __match_any_sync(0xffffffffu, key);
-    if (valid && lane == __ffs(m) - 1) atomicAdd(&s_hist[code], (uint32_t)__popc(m));
+    const int key = code - kHistBase;
+    const bool inw = valid && (unsigned)key < 32u;
+    if (on) {
+        unsigned m = __ballot_sync(0xffffffffu, inw);
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const unsigned bk = __ballot_sync(0xffffffffu, (key >> k) & 1);
+            m &= ((lane >> k) & 1) ? bk : ~bk;
+        }
+        cnt += __popc(m);
+        if (valid && !inw) atomicAdd(&s_hist[code], 1u);
+    }
+    return valid && !inw;
+}
+
+// Outliers (code 0) of the tile, one candidate per lane, appended in warp
+// batches to the tile's staging list, or straight to the output past it.
+template <int A>
+__device__ __forceinline__ void outlier_append(bool is_out, int vi, const float* v, int* s_nout, uint16_t* s_out,
+                                               hi_header* hdr, uint32_t* out_idx, float* out_val, uint64_t out_cap,
+                                               const FieldGeo& g, const int o[3])
+{
+    const unsigned m = __ballot_sync(0xffffffffu, is_out);
+    if (m == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(s_nout, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (!is_out) return;
+    const int slot = base + __popc(m & ((1u << lane) - 1u));
+    if (slot < kOutCap) {
+        s_out[slot] = (uint16_t)vi;
+    } else {
+        const unsigned long long pos = atomicAdd(reinterpret_cast<unsigned long long*>(&hdr->n_outliers), 1ull);
+        if (pos < out_cap) {
+            out_idx[pos] = (uint32_t)global_index<A>(g, o, vi);
+            out_val[pos] = v[vi];
+        } else {
+            set_status(&hdr->status, HI_ECAPACITY);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
 // Predict + quantize
 // ---------------------------------------------------------------------------
 template <int A>
-__global__ void __launch_bounds__(kBlock, 4) k_compress(const __grid_constant__ CUtensorMap tmap, const FieldGeo g,
-                                                     const float* __restrict__ x, uint8_t* __restrict__ codes,
-                                                     float* __restrict__ anchors, uint32_t* __restrict__ out_idx,
-                                                     float* __restrict__ out_val, const uint64_t out_cap,
-                                                     uint32_t* __restrict__ hist_g, float* __restrict__ recon_g,
-                                                     hi_header* __restrict__ hdr, uint32_t* __restrict__ queue,
-                                                     const uint32_t tma_bytes, const int flags)
+__global__ void __launch_bounds__(kMaxThreads, 4)
+    k_compress(const __grid_constant__ CUtensorMap tmap, const FieldGeo g, const float* __restrict__ x,
+               uint8_t* __restrict__ codes, float* __restrict__ anchors, uint32_t* __restrict__ out_idx,
+               float* __restrict__ out_val, const uint64_t out_cap, uint32_t* __restrict__ hist_g,
+               float* __restrict__ recon_g, hi_header* __restrict__ hdr, uint32_t* __restrict__ queue,
+               const uint32_t tma_bytes, const int flags)
 {
     using Lw = Lay<A>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -439,6 +461,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_compress(const __grid_constant__ 
     float* vbuf[2] = {reinterpret_cast<float*>(smem), reinterpret_cast<float*>(smem + (dbuf ? vb_bytes : 0))};
     uint8_t* cs = smem + (dbuf ? 2 : 1) * vb_bytes;
     __shared__ uint32_t s_hist[256];
+    __shared__ uint16_t s_out[kOutCap];
+    __shared__ int s_nout;
     __shared__ unsigned long long s_obase;
     __shared__ __align__(8) uint64_t s_mbar[2];
     __shared__ hi_level s_lv[HI_MAX_LEVELS];
@@ -455,14 +479,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_compress(const __grid_constant__ 
     h.eb_f = hdr->eb_f;
     h.ebx2_f = hdr->ebx2_f;
     h.r_f = hdr->r_f;
-    if (tid == 0) {
-        s_rare.hdr = hdr;
-        s_rare.out_idx = out_idx;
-        s_rare.out_val = out_val;
-        s_rare.out_cap = out_cap;
-        s_rare.out = nullptr;
-        s_rare.g = g;
-    }
+    const bool hist_on = hist_g != nullptr;
+    uint32_t hcnt = 0;  // this lane's count of code kHistBase + lane
 
     for (int i = tid; i < 256; i += blockDim.x) s_hist[i] = 0;
     if (tid < HI_MAX_LEVELS) {
@@ -497,6 +515,11 @@ __global__ void __launch_bounds__(kBlock, 4) k_compress(const __grid_constant__ 
                 tma_issue(vbuf[buf ^ 1], &tmap, g, nx, A, &s_mbar[buf ^ 1], tma_bytes);
             if (use_tma && !dbuf && it > 0) tma_issue(v, &tmap, g, tile, A, &s_mbar[0], tma_bytes);
         }
+        if (tid < 8) {  // anchors keep the zero-error code
+            const int a0 = (tid >> 2) & 1, a1 = (tid >> 1) & 1, a2 = tid & 1;
+            if (a0 * A <= ti.e[0] && a1 * A <= ti.e[1] && a2 * A <= ti.e[2])
+                cs[a0 * A * Lw::CYC + a1 * A * Lw::CXC + a2 * A] = (uint8_t)kRadius;
+        }
         if (use_tma) {
             const bool ok = mbar_wait(&s_mbar[buf], dbuf ? ((it >> 1) & 1) : (it & 1), kSpinLimit);
             if (!__syncthreads_and(ok)) {
@@ -509,33 +532,23 @@ __global__ void __launch_bounds__(kBlock, 4) k_compress(const __grid_constant__ 
             __syncthreads();
         }
         const int next = s_next;
-        // anchors keep the zero-error code
-        if (tid < 8) {
-            const int a0 = (tid >> 2) & 1, a1 = (tid >> 1) & 1, a2 = tid & 1;
-            if (a0 * A <= ti.e[0] && a1 * A <= ti.e[1] && a2 * A <= ti.e[2])
-                cs[a0 * A * Lw::CYC + a1 * A * Lw::CXC + a2 * A] = (uint8_t)kRadius;
-        }
-        if (tid == 0) s_rare.o[0] = ti.o[0], s_rare.o[1] = ti.o[1], s_rare.o[2] = ti.o[2];
-        __syncthreads();
-        h.own0 = ti.own[0], h.own1 = ti.own[1], h.own2 = ti.own[2];
         const bool full = full_ok && ti.e[0] == A && ti.e[1] == A && ti.e[2] == A;
         if constexpr (HasFull<A>::value) {
             if (full)
                 levels_full<A, TileGeom<A>::L - 1, true>(s_sel, v, cs, h);
             else
-                levels_generic<A, true>(s_lv, v, cs, h, ti);
+                levels_ragged<A, TileGeom<A>::L - 1, true>(s_lv, v, cs, h, ti);
         } else {
-            levels_generic<A, true>(s_lv, v, cs, h, ti);
+            levels_ragged<A, TileGeom<A>::L - 1, true>(s_lv, v, cs, h, ti);
         }
 
-        // ---- epilogue: owned codes (+ histogram), recon, anchors, outliers
+        // ---- epilogue: owned codes, histogram and outliers; recon; anchors
         const int own0 = ti.own[0] + 1, own1 = ti.own[1] + 1, own2 = ti.own[2] + 1;
         const int rows = own0 * own1;
         const bool vec_codes = (flags & kFlagVecCodes) && own2 == A && A >= 8;
         if (vec_codes) {
-            constexpr int NW = (A >= 8) ? A / 4 : 1;  // 32-bit words per owned row
-            constexpr int CH = (A >= 16) ? 4 : 2;     // words per global vector store
-            constexpr int NCH = NW / CH > 0 ? NW / CH : 1;
+            constexpr int CH = (A >= 16) ? 4 : 2;  // words per global vector store
+            constexpr int NCH = (A >= 8) ? A / (4 * CH) : 1;
             const int items = rows * NCH;
             for (int i0 = 0; i0 < items; i0 += blockDim.x) {
                 const int i = i0 + tid;
@@ -554,9 +567,13 @@ __global__ void __launch_bounds__(kBlock, 4) k_compress(const __grid_constant__ 
                     else
                         *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
                 }
-                if (hist_g) {
 #pragma unroll
-                    for (int b = 0; b < 4 * CH; ++b) hist_add(s_hist, (w[b >> 2] >> (8 * (b & 3))) & 0xff, act, lane);
+                for (int b = 0; b < 4 * CH; ++b) {
+                    const int code = (w[b >> 2] >> (8 * (b & 3))) & 0xff;
+                    const bool rare = hist_ballot(code, act, hcnt, s_hist, hist_on);
+                    if (__any_sync(0xffffffffu, rare || (act && code == 0)))
+                        outlier_append<A>(act && code == 0, c0 * Lw::PY + c1 * Lw::PX + ch * CH * 4 + b, v, &s_nout,
+                                          s_out, hdr, out_idx, out_val, out_cap, g, ti.o);
                 }
             }
         } else {
@@ -570,7 +587,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_compress(const __grid_constant__ 
                 if (act)
                     codes[((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2] + c2] =
                         (uint8_t)code;
-                if (hist_g) hist_add(s_hist, code, act, lane);
+                hist_ballot(code, act, hcnt, s_hist, hist_on);
+                outlier_append<A>(act && code == 0, c0 * Lw::PY + c1 * Lw::PX + c2, v, &s_nout, s_out, hdr, out_idx,
+                                  out_val, out_cap, g, ti.o);
             }
         }
         if (recon_g) {
@@ -589,7 +608,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_compress(const __grid_constant__ 
                 const int64_t ai = ((int64_t)(ti.o[0] / A + a0) * g.na[1] + (ti.o[1] / A + a1)) * g.na[2] +
                                    (ti.o[2] / A + a2);
                 anchors[ai] = v[l0 * Lw::PY + l1 * Lw::PX + l2];
-                if (hist_g) atomicSub(&s_hist[kRadius], 1u);  // anchors are not predicted
+                if (hist_on) atomicSub(&s_hist[kRadius], 1u);  // anchors are not predicted
             }
         }
         __syncthreads();
@@ -611,12 +630,14 @@ __global__ void __launch_bounds__(kBlock, 4) k_compress(const __grid_constant__ 
             }
         }
         // keep the buffers until every thread is done; order the generic-proxy
-        // writes above before the TMA overwrite two tiles later
+        // writes above before the TMA overwrite of this buffer
         fence_proxy_async_smem();
         __syncthreads();
         tile = next;
     }
-    if (hist_g) {
+    if (hist_on) {
+        atomicAdd(&s_hist[kHistBase + lane], hcnt);
+        __syncthreads();
         for (int i = tid; i < 256; i += blockDim.x)
             if (s_hist[i]) atomicAdd(&hist_g[i], s_hist[i]);
     }
@@ -626,12 +647,11 @@ __global__ void __launch_bounds__(kBlock, 4) k_compress(const __grid_constant__ 
 // Reconstruct
 // ---------------------------------------------------------------------------
 template <int A>
-__global__ void __launch_bounds__(kBlock, 4) k_decompress(const __grid_constant__ CUtensorMap cmap, const FieldGeo g,
-                                                       const uint8_t* __restrict__ codes,
-                                                       const float* __restrict__ anchors, float* out,
-                                                       const hi_header* __restrict__ hdr,
-                                                       uint32_t* __restrict__ status, uint32_t* __restrict__ queue,
-                                                       const uint32_t tma_bytes, const int flags)
+__global__ void __launch_bounds__(kMaxThreads, 4)
+    k_decompress(const __grid_constant__ CUtensorMap cmap, const FieldGeo g, const uint8_t* __restrict__ codes,
+                 const float* __restrict__ anchors, float* out, const hi_header* __restrict__ hdr,
+                 uint32_t* __restrict__ status, uint32_t* __restrict__ queue, const uint32_t tma_bytes,
+                 const int flags)
 {
     using Lw = Lay<A>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -653,10 +673,6 @@ __global__ void __launch_bounds__(kBlock, 4) k_decompress(const __grid_constant_
     h.ebx2_f = hdr->ebx2_f;
     h.r_f = 0.0f;
     if (tid == 0) {
-        s_rare.hdr = nullptr;
-        s_rare.out_idx = nullptr;
-        s_rare.out_val = nullptr;
-        s_rare.out_cap = 0;
         s_rare.out = out;
         s_rare.g = g;
     }
@@ -684,6 +700,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_decompress(const __grid_constant_
         if (tid == 0) {
             const int nx = (int)gridDim.x + (int)atomicAdd(queue, 1u);
             s_next = nx;
+            s_rare.o[0] = ti.o[0], s_rare.o[1] = ti.o[1], s_rare.o[2] = ti.o[2];
             if (use_tma && dbuf && nx < g.ntiles)
                 tma_issue(cbuf[buf ^ 1], &cmap, g, nx, A, &s_mbar[buf ^ 1], tma_bytes);
             if (use_tma && !dbuf && it > 0) tma_issue(cs, &cmap, g, tile, A, &s_mbar[0], tma_bytes);
@@ -709,17 +726,14 @@ __global__ void __launch_bounds__(kBlock, 4) k_decompress(const __grid_constant_
             __syncthreads();
         }
         const int next = s_next;
-        if (tid == 0) s_rare.o[0] = ti.o[0], s_rare.o[1] = ti.o[1], s_rare.o[2] = ti.o[2];
-        __syncthreads();
-        h.own0 = ti.own[0], h.own1 = ti.own[1], h.own2 = ti.own[2];
         const bool full = full_ok && ti.e[0] == A && ti.e[1] == A && ti.e[2] == A;
         if constexpr (HasFull<A>::value) {
             if (full)
                 levels_full<A, TileGeom<A>::L - 1, false>(s_sel, v, cs, h);
             else
-                levels_generic<A, false>(s_lv, v, cs, h, ti);
+                levels_ragged<A, TileGeom<A>::L - 1, false>(s_lv, v, cs, h, ti);
         } else {
-            levels_generic<A, false>(s_lv, v, cs, h, ti);
+            levels_ragged<A, TileGeom<A>::L - 1, false>(s_lv, v, cs, h, ti);
         }
 
         // ---- epilogue: owned reconstructed values
@@ -798,7 +812,7 @@ template <int A>
 static cudaError_t launch_compress_t(const CompressLaunch& c, cudaStream_t st)
 {
     auto kern = k_compress<A>;
-    const bool dbuf = fits_double(kern, compress_smem_t<A>(c.g.b0, true));
+    const bool dbuf = c.buffers == 2 && fits_double(kern, compress_smem_t<A>(c.g.b0, true));
     const size_t smem = compress_smem_t<A>(c.g.b0, dbuf);
     int grid = 0;
     cudaError_t err = persistent_grid(kern, c.threads, smem, c.num_sms, c.g.ntiles, c.max_ctas, &grid);
@@ -813,7 +827,7 @@ template <int A>
 static cudaError_t launch_decompress_t(const DecompressLaunch& c, cudaStream_t st)
 {
     auto kern = k_decompress<A>;
-    const bool dbuf = fits_double(kern, decompress_smem_t<A>(c.g.b0, true));
+    const bool dbuf = c.buffers == 2 && fits_double(kern, decompress_smem_t<A>(c.g.b0, true));
     const size_t smem = decompress_smem_t<A>(c.g.b0, dbuf);
     int grid = 0;
     cudaError_t err = persistent_grid(kern, c.threads, smem, c.num_sms, c.g.ntiles, c.max_ctas, &grid);
