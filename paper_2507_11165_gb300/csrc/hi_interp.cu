@@ -38,7 +38,6 @@ namespace hi {
 
 constexpr int kOutCap = 1024;  // staged outliers per tile before the direct path
 constexpr int kMaxThreads = 256;
-constexpr int kHistBase = 112;  // codes kHistBase .. kHistBase+31 are counted by warp ballots
 
 // Shared-memory layouts of one tile (planes b0 = A+1, or 1 for 1D/2D fields).
 template <int A>
@@ -314,28 +313,45 @@ struct HasFull {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int pick3(const int a[3], int i) { return i == 0 ? a[0] : (i == 1 ? a[1] : a[2]); }
 
+template <int A, int S, int D, bool COMP>
+__device__ __forceinline__ void pass_dispatch(bool cubic, float* v, uint8_t* cs, const Hot h, int stq, int str,
+                                              int nq, int nr, int ed)
+{
+    if (ed == A) {  // the pass dim is whole: only the line counts are shorter
+        if (cubic)
+            pass_any<A, S, D, true, COMP, true>(v, cs, h, stq, str, nq, nr, ed);
+        else
+            pass_any<A, S, D, false, COMP, true>(v, cs, h, stq, str, nq, nr, ed);
+    } else {
+        if (cubic)
+            pass_any<A, S, D, true, COMP, false>(v, cs, h, stq, str, nq, nr, ed);
+        else
+            pass_any<A, S, D, false, COMP, false>(v, cs, h, stq, str, nq, nr, ed);
+    }
+}
+
 template <int A, int LV, bool COMP>
-__device__ __noinline__ void level_ragged(const hi_level lv, float* v, uint8_t* cs, const Hot h, const TileInfo ti)
+__device__ __noinline__ void level_ragged(const hi_level lv, float* v, uint8_t* cs, const Hot h, int e0, int e1,
+                                          int e2)
 {
     constexpr int S = 1 << LV;
     const bool cubic = lv.interp == HI_CUBIC;
+    const int e[3] = {e0, e1, e2};
     for (int p = 0; p < 3; ++p) {
         const int d = lv.order[p];
         const int q = (d == 0) ? 1 : 0, r = (d == 2) ? 1 : 2;
         const int posq = (lv.order[0] == q) ? 0 : ((lv.order[1] == q) ? 1 : 2);
         const int posr = (lv.order[0] == r) ? 0 : ((lv.order[1] == r) ? 1 : 2);
         const int stq = (posq < p) ? S : 2 * S, str = (posr < p) ? S : 2 * S;
-        const int ed = pick3(ti.e, d);
+        const int ed = pick3(e, d);
         if (ed < S) continue;  // no point on this pass (CTA-uniform)
-        const int nq = pick3(ti.e, q) / stq + 1, nr = pick3(ti.e, r) / str + 1;
-        switch (2 * d + (cubic ? 1 : 0)) {
-        case 0: pass_any<A, S, 0, false, COMP, false>(v, cs, h, stq, str, nq, nr, ed); break;
-        case 1: pass_any<A, S, 0, true, COMP, false>(v, cs, h, stq, str, nq, nr, ed); break;
-        case 2: pass_any<A, S, 1, false, COMP, false>(v, cs, h, stq, str, nq, nr, ed); break;
-        case 3: pass_any<A, S, 1, true, COMP, false>(v, cs, h, stq, str, nq, nr, ed); break;
-        case 4: pass_any<A, S, 2, false, COMP, false>(v, cs, h, stq, str, nq, nr, ed); break;
-        default: pass_any<A, S, 2, true, COMP, false>(v, cs, h, stq, str, nq, nr, ed); break;
-        }
+        const int nq = pick3(e, q) / stq + 1, nr = pick3(e, r) / str + 1;
+        if (d == 0)
+            pass_dispatch<A, S, 0, COMP>(cubic, v, cs, h, stq, str, nq, nr, ed);
+        else if (d == 1)
+            pass_dispatch<A, S, 1, COMP>(cubic, v, cs, h, stq, str, nq, nr, ed);
+        else
+            pass_dispatch<A, S, 2, COMP>(cubic, v, cs, h, stq, str, nq, nr, ed);
         __syncthreads();
     }
 }
@@ -344,7 +360,7 @@ template <int A, int LV, bool COMP>
 __device__ __forceinline__ void levels_ragged(const hi_level* s_lv, float* v, uint8_t* cs, const Hot h,
                                               const TileInfo& ti)
 {
-    level_ragged<A, LV, COMP>(s_lv[LV], v, cs, h, ti);
+    level_ragged<A, LV, COMP>(s_lv[LV], v, cs, h, ti.e[0], ti.e[1], ti.e[2]);
     if constexpr (LV > 0) levels_ragged<A, LV - 1, COMP>(s_lv, v, cs, h, ti);
 }
 
@@ -392,26 +408,13 @@ __device__ __forceinline__ void tma_issue(void* dst, const CUtensorMap* map, con
 // ---------------------------------------------------------------------------
 // Epilogue helpers (all lanes of the warp call them)
 // ---------------------------------------------------------------------------
-// Histogram of one code per lane: codes in [kHistBase, kHistBase+32) are
-// counted by bit-plane ballots -- lane j ends up with the number of lanes
-// holding code kHistBase+j and keeps it in its own counter -- the rest go to
-// shared-memory atomics.  Returns true for a valid code outside that window.
-__device__ __forceinline__ bool hist_ballot(int code, bool valid, uint32_t& cnt, uint32_t* s_hist, bool on)
+// Histogram of one code per lane, warp-aggregated: lanes holding equal codes
+// are matched and their leader adds the count with one shared-memory atomic.
+__device__ __forceinline__ void hist_add(uint32_t* s_hist, int code, bool valid)
 {
-    const int key = code - kHistBase;
-    const bool inw = valid && (unsigned)key < 32u;
-    if (on) {
-        unsigned m = __ballot_sync(0xffffffffu, inw);
-        const int lane = threadIdx.x & 31;
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            const unsigned bk = __ballot_sync(0xffffffffu, (key >> k) & 1);
-            m &= ((lane >> k) & 1) ? bk : ~bk;
-        }
-        cnt += __popc(m);
-        if (valid && !inw) atomicAdd(&s_hist[code], 1u);
-    }
-    return valid && !inw;
+    const int key = valid ? code : 256;
+    const unsigned m = __match_any_sync(0xffffffffu, key);
+    if (valid && (threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(&s_hist[code], (uint32_t)__popc(m));
 }
 
 // Outliers (code 0) of the tile, one candidate per lane, appended in warp
@@ -480,7 +483,6 @@ __global__ void __launch_bounds__(kMaxThreads, 4)
     h.ebx2_f = hdr->ebx2_f;
     h.r_f = hdr->r_f;
     const bool hist_on = hist_g != nullptr;
-    uint32_t hcnt = 0;  // this lane's count of code kHistBase + lane
 
     for (int i = tid; i < 256; i += blockDim.x) s_hist[i] = 0;
     if (tid < HI_MAX_LEVELS) {
@@ -570,8 +572,8 @@ __global__ void __launch_bounds__(kMaxThreads, 4)
 #pragma unroll
                 for (int b = 0; b < 4 * CH; ++b) {
                     const int code = (w[b >> 2] >> (8 * (b & 3))) & 0xff;
-                    const bool rare = hist_ballot(code, act, hcnt, s_hist, hist_on);
-                    if (__any_sync(0xffffffffu, rare || (act && code == 0)))
+                    if (hist_on) hist_add(s_hist, code, act);
+                    if (__any_sync(0xffffffffu, act && code == 0))
                         outlier_append<A>(act && code == 0, c0 * Lw::PY + c1 * Lw::PX + ch * CH * 4 + b, v, &s_nout,
                                           s_out, hdr, out_idx, out_val, out_cap, g, ti.o);
                 }
@@ -587,7 +589,7 @@ __global__ void __launch_bounds__(kMaxThreads, 4)
                 if (act)
                     codes[((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2] + c2] =
                         (uint8_t)code;
-                hist_ballot(code, act, hcnt, s_hist, hist_on);
+                if (hist_on) hist_add(s_hist, code, act);
                 outlier_append<A>(act && code == 0, c0 * Lw::PY + c1 * Lw::PX + c2, v, &s_nout, s_out, hdr, out_idx,
                                   out_val, out_cap, g, ti.o);
             }
@@ -636,7 +638,6 @@ __global__ void __launch_bounds__(kMaxThreads, 4)
         tile = next;
     }
     if (hist_on) {
-        atomicAdd(&s_hist[kHistBase + lane], hcnt);
         __syncthreads();
         for (int i = tid; i < 256; i += blockDim.x)
             if (s_hist[i]) atomicAdd(&hist_g[i], s_hist[i]);
