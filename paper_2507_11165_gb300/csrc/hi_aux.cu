@@ -155,9 +155,68 @@ __global__ void k_scatter(const uint32_t* __restrict__ idx, const float* __restr
 // Auto-tune: CTA (sample, candidate) computes, for every level, the sum of
 // |x - p| over that level's points of its sampled block, with every
 // prediction taken from the original values (no quantization), in the
-// candidate's pass order.  Per-thread double partials, then a fixed-order
-// block reduction: the sums are deterministic run to run.
+// candidate's pass order.  Each term is a float, summed in double: per line
+// into independent per-point accumulators (no long FP64 dependency chain),
+// then over the block in a fixed order, so the sums are deterministic run to
+// run.
 // ---------------------------------------------------------------------------
+template <int A, int S>
+__device__ __forceinline__ double tune_pass(const float* __restrict__ v, bool cubic, int d, int stq, int str,
+                                            const int e[3])
+{
+    using TG = TileGeom<A>;
+    constexpr int NDM = A / (2 * S);
+    const int q = (d == 0) ? 1 : 0, r = (d == 2) ? 1 : 2;
+    const int ed = d == 0 ? e[0] : (d == 1 ? e[1] : e[2]);
+    const int eq = q == 0 ? e[0] : e[1], er = r == 1 ? e[1] : e[2];
+    if (ed < S) return 0.0;
+    const int nd = (ed - S) / (2 * S) + 1;
+    const int nq = eq / stq + 1, nr = er / str + 1;
+    const int vpd = (d == 0 ? TG::PY : (d == 1 ? TG::PX : 1)) * S;
+    const int vpq = q == 0 ? TG::PY : TG::PX, vpr = r == 1 ? TG::PX : 1;
+    double acc = 0.0;
+    for (int line = threadIdx.x; line < nq * nr; line += blockDim.x) {
+        const int jq = line / nr, jr = line - jq * nr;
+        const int vb = jq * stq * vpq + jr * str * vpr;
+        float f[NDM + 1];
+#pragma unroll
+        for (int m = 0; m <= NDM; ++m) f[m] = (2 * m * S <= ed) ? v[vb + 2 * m * vpd] : 0.0f;
+        double part[NDM];
+#pragma unroll
+        for (int k = 0; k < NDM; ++k) {
+            part[k] = 0.0;
+            if (k < nd) {
+                const int c = (2 * k + 1) * S;
+                const bool have_r = c + S <= ed, have_r3 = c + 3 * S <= ed;
+                const float pr = predict(cubic, k >= 1, have_r, have_r3, k >= 1 ? f[k - 1] : 0.0f, f[k],
+                                         have_r ? f[k + 1] : 0.0f, (k + 2 <= NDM && have_r3) ? f[k + 2] : 0.0f);
+                part[k] = (double)fabsf(__fsub_rn(v[vb + (2 * k + 1) * vpd], pr));
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NDM; ++k) acc += part[k];
+    }
+    return acc;
+}
+
+template <int A, int LV>
+__device__ __forceinline__ void tune_levels(const float* v, const hi_level& lv, const int e[3], double* acc)
+{
+    constexpr int S = 1 << LV;
+    const bool cubic = lv.interp == HI_CUBIC;
+    double a = 0.0;
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        const int d = lv.order[p];
+        const int q = (d == 0) ? 1 : 0, r = (d == 2) ? 1 : 2;
+        const int posq = (lv.order[0] == q) ? 0 : ((lv.order[1] == q) ? 1 : 2);
+        const int posr = (lv.order[0] == r) ? 0 : ((lv.order[1] == r) ? 1 : 2);
+        a += tune_pass<A, S>(v, cubic, d, (posq < p) ? S : 2 * S, (posr < p) ? S : 2 * S, e);
+    }
+    acc[LV] = a;
+    if constexpr (LV > 0) tune_levels<A, LV - 1>(v, lv, e, acc);
+}
+
 template <int A>
 __global__ void __launch_bounds__(256) k_tune(const FieldGeo g, const float* __restrict__ x, const TuneCands cands,
                                               int stride, double* __restrict__ err)
@@ -186,48 +245,13 @@ __global__ void __launch_bounds__(256) k_tune(const FieldGeo g, const float* __r
     }
     __syncthreads();
 
-    const bool cubic = cands.interp[c] == HI_CUBIC;
     hi_level lv;
     lv.interp = cands.interp[c];
     lv.order[0] = cands.order[c][0];
     lv.order[1] = cands.order[c][1];
     lv.order[2] = cands.order[c][2];
-    const int vp[3] = {TG::PY, TG::PX, 1};
     double acc[L];
-#pragma unroll
-    for (int l = 0; l < L; ++l) acc[l] = 0.0;
-
-#pragma unroll
-    for (int l = L - 1; l >= 0; --l) {
-        const int s = 1 << l;
-        for (int p = 0; p < 3; ++p) {
-            const int d = lv.order[p];
-            int st[3];
-            for (int k = 0; k < 3; ++k) st[lv.order[k]] = (k < p) ? s : 2 * s;
-            const int q = (d == 0) ? 1 : 0, r = (d == 2) ? 1 : 2;
-            const int ed = e[d];
-            const int nd = (ed >= s) ? ((ed - s) / (2 * s) + 1) : 0;
-            if (nd == 0) continue;
-            const int nq = e[q] / st[q] + 1, nr = e[r] / st[r] + 1;
-            const int vpd = vp[d] * s;
-            for (int line = tid; line < nq * nr; line += blockDim.x) {
-                const int jq = line / nr, jr = line - jq * nr;
-                const int vb = jq * st[q] * vp[q] + jr * st[r] * vp[r];
-                float fa = 0.0f, fb = v[vb];
-                float fu = (2 * s <= ed) ? v[vb + 2 * vpd] : 0.0f;
-                float fv = (4 * s <= ed) ? v[vb + 4 * vpd] : 0.0f;
-                for (int k = 0; k < nd; ++k) {
-                    const int cc = (2 * k + 1) * s;
-                    const float pr = predict(cubic, k >= 1, cc + s <= ed, cc + 3 * s <= ed, fa, fb, fu, fv);
-                    acc[l] += (double)fabsf(__fsub_rn(v[vb + (2 * k + 1) * vpd], pr));
-                    fa = fb;
-                    fb = fu;
-                    fu = fv;
-                    fv = ((2 * k + 6) * s <= ed) ? v[vb + (2 * k + 6) * vpd] : 0.0f;
-                }
-            }
-        }
-    }
+    tune_levels<A, L - 1>(v, lv, e, acc);
     // fixed-order reduction: warp butterfly, then warps in index order
 #pragma unroll
     for (int l = 0; l < L; ++l) {
