@@ -111,6 +111,11 @@ hi_status make_geometry(const hi_params* p, Geometry* G)
     }
     G->g.N = (int64_t)N;
     G->g.ntiles = (int)nt;
+    // whole 3D tiles first in the queue when the field's far faces are ragged
+    for (int d = 0; d < 3; ++d) {
+        const bool ragged = p->dims[d] > 1 && (p->dims[d] - 1) % (uint64_t)A != 0;
+        G->g.ni[d] = G->g.nb[d] - ((nact == 3 && ragged) ? 1 : 0);
+    }
     G->g.b0 = (p->dims[0] > 1) ? A + 1 : 1;
     G->n_anchors = na_all;
     G->ndim_active = nact;
@@ -128,6 +133,7 @@ hi_status make_geometry(const hi_params* p, Geometry* G)
 
 constexpr size_t kWsTicket = 0;  // uint32: last-CTA ticket of the range pass
 constexpr size_t kWsQueue = 4;   // uint32: tile queue of the predict / reconstruct kernels
+constexpr size_t kWsTuneTicket = 8;  // uint32: last-CTA ticket of the auto-tuner (left at 0)
 constexpr size_t kWsPartials = 256;
 constexpr size_t kWsTune = kWsPartials + sizeof(float2) * kRangeBlocks;
 
@@ -259,7 +265,8 @@ static hi_status enqueue_tune(const Geometry& G, const float* d_x, hi_header* d_
                               cudaStream_t stream)
 {
     double* err = reinterpret_cast<double*>(static_cast<char*>(d_ws) + kWsTune);
-    return cuda_status(launch_tune(G.A, G.g, d_x, G.cands, G.m, G.stride, err, d_header, stream));
+    uint32_t* ticket = reinterpret_cast<uint32_t*>(static_cast<char*>(d_ws) + kWsTuneTicket);
+    return cuda_status(launch_tune(G.A, G.g, d_x, G.cands, G.m, G.stride, err, ticket, d_header, stream));
 }
 
 hi_status hi_compress(const hi_params* p, const float* d_x, uint8_t* d_codes, float* d_anchors,
@@ -382,6 +389,8 @@ hi_status hi_autotune(const hi_params* p, const float* d_x, hi_header* d_header,
     if (s != HI_OK) return s;
     if (!d_x || !d_header || !d_ws || !aligned(d_ws, 8)) return HI_EINVAL;
     if (ws_bytes < workspace_bytes(G)) return HI_ENOMEM;
+    if (cudaMemsetAsync(static_cast<char*>(d_ws) + kWsTuneTicket, 0, sizeof(uint32_t), stream) != cudaSuccess)
+        return HI_ECUDA;
     return enqueue_tune(G, d_x, d_header, d_ws, stream);
 }
 

@@ -60,7 +60,7 @@ __global__ void k_prologue(hi_header* hdr, const hi_params p, uint64_t n_anchors
         hdr->n_levels = n_levels;
         for (int l = 0; l < HI_MAX_LEVELS; ++l) hdr->level[l] = p.level[l];
         for (int k = 0; k < 7; ++k) hdr->reserved[k] = 0;
-        if (ticket) *ticket = 0;
+        if (ticket) ticket[0] = 0, ticket[2] = 0;  // range ticket, auto-tune ticket
         if (queue) *queue = 0;
         if (p.eb_mode == HI_EB_ABS) finalize_eps(hdr, 0.0f, 0.0f);
     }
@@ -219,7 +219,8 @@ __device__ __forceinline__ void tune_levels(const float* v, const hi_level& lv, 
 
 template <int A>
 __global__ void __launch_bounds__(256) k_tune(const FieldGeo g, const float* __restrict__ x, const TuneCands cands,
-                                              int stride, double* __restrict__ err)
+                                              int stride, double* __restrict__ err, uint32_t* ticket,
+                                              hi_header* __restrict__ hdr)
 {
     using TG = TileGeom<A>;
     constexpr int L = TG::L;
@@ -231,7 +232,7 @@ __global__ void __launch_bounds__(256) k_tune(const FieldGeo g, const float* __r
     const int tile = sample * stride;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     int t[3], o[3], e[3];
-    tile_coords(g, tile, t);
+    tile_coords_rm(g, tile, t);
     for (int d = 0; d < 3; ++d) {
         o[d] = t[d] * A;
         const int rem = (int)(g.n[d] - 1 - o[d]);
@@ -265,26 +266,37 @@ __global__ void __launch_bounds__(256) k_tune(const FieldGeo g, const float* __r
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += s_red[tid][w];
         err[((size_t)sample * L + tid) * cands.ncfg + c] = a;
     }
-}
 
-// Sum the samples in index order and keep the first smallest candidate.
-__global__ void k_tune_select(const double* __restrict__ err, int m, int L, const TuneCands cands, hi_header* hdr)
-{
-    const int l = threadIdx.x;
-    if (l >= L) return;
-    int best = 0;
-    double best_e = 0.0;
-    for (int c = 0; c < cands.ncfg; ++c) {
-        double s = 0.0;
-        for (int k = 0; k < m; ++k) s += err[((size_t)k * L + l) * cands.ncfg + c];
-        if (c == 0 || s < best_e) best = c, best_e = s;
+    // the last CTA to finish sums the samples and picks each level's candidate
+    __shared__ bool s_last;
+    __shared__ double s_tot[L * 12];
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int m = gridDim.x, ncfg = cands.ncfg;
+    for (int pr = warp; pr < L * ncfg; pr += (blockDim.x >> 5)) {  // one warp per (level, candidate)
+        const int l = pr / ncfg, cc = pr - l * ncfg;
+        double a = 0.0;
+        for (int k = lane; k < m; k += 32) a += __ldcg(err + ((size_t)k * L + l) * ncfg + cc);
+        for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+        if (lane == 0) s_tot[pr] = a;
     }
-    hi_level lv;
-    lv.interp = cands.interp[best];
-    lv.order[0] = cands.order[best][0];
-    lv.order[1] = cands.order[best][1];
-    lv.order[2] = cands.order[best][2];
-    hdr->level[l] = lv;
+    __syncthreads();
+    if (tid < L) {  // smallest sum, ties to the first candidate
+        int best = 0;
+        for (int cc = 1; cc < ncfg; ++cc)
+            if (s_tot[tid * ncfg + cc] < s_tot[tid * ncfg + best]) best = cc;
+        hi_level lv;
+        lv.interp = cands.interp[best];
+        lv.order[0] = cands.order[best][0];
+        lv.order[1] = cands.order[best][1];
+        lv.order[2] = cands.order[best][2];
+        hdr->level[tid] = lv;
+    }
+    if (tid == 0) *ticket = 0;
 }
 
 cudaError_t launch_prologue(hi_header* hdr, const hi_params& p, uint64_t n_anchors, uint64_t out_cap,
@@ -310,29 +322,26 @@ cudaError_t launch_scatter(const uint32_t* idx, const float* val, uint64_t cap, 
 
 template <int A>
 static cudaError_t launch_tune_t(const FieldGeo& g, const float* x, const TuneCands& cands, int m, int stride,
-                                 double* err, hi_header* hdr, cudaStream_t st)
+                                 double* err, uint32_t* ticket, hi_header* hdr, cudaStream_t st)
 {
     using TG = TileGeom<A>;
     const size_t smem = (size_t)g.b0 * TG::P * TG::PX * 4;
     auto kern = k_tune<A>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<dim3(m, cands.ncfg), 256, smem, st>>>(g, x, cands, stride, err);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_tune_select<<<1, 32, 0, st>>>(err, m, TG::L, cands, hdr);
+    kern<<<dim3(m, cands.ncfg), 256, smem, st>>>(g, x, cands, stride, err, ticket, hdr);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tune(int A, const FieldGeo& g, const float* x, const TuneCands& cands, int m, int stride,
-                        double* err, hi_header* hdr, cudaStream_t st)
+                        double* err, uint32_t* ticket, hi_header* hdr, cudaStream_t st)
 {
     switch (A) {
-    case 2: return launch_tune_t<2>(g, x, cands, m, stride, err, hdr, st);
-    case 4: return launch_tune_t<4>(g, x, cands, m, stride, err, hdr, st);
-    case 8: return launch_tune_t<8>(g, x, cands, m, stride, err, hdr, st);
-    case 16: return launch_tune_t<16>(g, x, cands, m, stride, err, hdr, st);
-    case 32: return launch_tune_t<32>(g, x, cands, m, stride, err, hdr, st);
+    case 2: return launch_tune_t<2>(g, x, cands, m, stride, err, ticket, hdr, st);
+    case 4: return launch_tune_t<4>(g, x, cands, m, stride, err, ticket, hdr, st);
+    case 8: return launch_tune_t<8>(g, x, cands, m, stride, err, ticket, hdr, st);
+    case 16: return launch_tune_t<16>(g, x, cands, m, stride, err, ticket, hdr, st);
+    case 32: return launch_tune_t<32>(g, x, cands, m, stride, err, ticket, hdr, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -29,7 +29,9 @@ struct TileGeom {
     static constexpr int L = (A == 2) ? 1 : (A == 4) ? 2 : (A == 8) ? 3 : (A == 16) ? 4 : 5;
     static constexpr int PX = (P + 3) / 4 * 4;     // float pitch of dim 2
     static constexpr int PY = P * PX;              // float pitch of dim 0 (dim 1 pitch = PX)
-    static constexpr int CX = (P + 15) / 16 * 16;  // byte pitch of dim 2 for codes
+    // byte pitch of dim 2 for codes: an odd number of 16-byte chunks, so that
+    // 16-byte accesses to consecutive rows hit distinct banks
+    static constexpr int CX = ((P + 15) / 16 % 2 == 1) ? (P + 15) / 16 * 16 : (P + 15) / 16 * 16 + 16;
     static constexpr int CY = P * CX;              // byte pitch of dim 0 for codes
 };
 
@@ -41,6 +43,7 @@ struct FieldGeo {
     int64_t N;      // points
     int ntiles;     // nb0 * nb1 * nb2
     int b0;         // planes of a tile along dim 0 in shared memory: A+1, or 1 if n0 == 1
+    int ni[3];      // queue order: tiles with t_d < ni_d for all d (whole tiles) come first
 };
 
 // ---------------------------------------------------------------------------
@@ -147,13 +150,48 @@ __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map)
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
-// Tile coordinates of a linear block id (row-major over the block grid).
-__device__ __forceinline__ void tile_coords(const FieldGeo& g, int tile, int t[3])
+// Tile coordinates of a row-major block id.
+__device__ __forceinline__ void tile_coords_rm(const FieldGeo& g, int tile, int t[3])
 {
     t[2] = tile % g.nb[2];
     const int r = tile / g.nb[2];
     t[1] = r % g.nb[1];
     t[0] = r / g.nb[1];
+}
+
+// Tile coordinates of queue position `pos`: the ni0 x ni1 x ni2 interior
+// tiles in row-major order first, then the tiles of the upper faces (the
+// field's edge tiles when its extent is not a multiple of A), face by face.
+// With ni = nb this is plain row-major order over the block grid.
+__device__ __forceinline__ void tile_coords(const FieldGeo& g, int pos, int t[3])
+{
+    const int n_int = g.ni[0] * g.ni[1] * g.ni[2];
+    if (pos < n_int) {
+        t[2] = pos % g.ni[2];
+        const int r = pos / g.ni[2];
+        t[1] = r % g.ni[1];
+        t[0] = r / g.ni[1];
+        return;
+    }
+    int q = pos - n_int;
+    if (g.ni[0] < g.nb[0]) {  // face t0 = nb0 - 1: nb1 x nb2 tiles
+        const int n = g.nb[1] * g.nb[2];
+        if (q < n) {
+            t[0] = g.nb[0] - 1, t[1] = q / g.nb[2], t[2] = q % g.nb[2];
+            return;
+        }
+        q -= n;
+    }
+    if (g.ni[1] < g.nb[1]) {  // face t1 = nb1 - 1, t0 < ni0: ni0 x nb2 tiles
+        const int n = g.ni[0] * g.nb[2];
+        if (q < n) {
+            t[1] = g.nb[1] - 1, t[0] = q / g.nb[2], t[2] = q % g.nb[2];
+            return;
+        }
+        q -= n;
+    }
+    // face t2 = nb2 - 1, t0 < ni0, t1 < ni1
+    t[2] = g.nb[2] - 1, t[0] = q / g.ni[1], t[1] = q % g.ni[1];
 }
 
 }  // namespace hi

@@ -77,7 +77,7 @@ cudaError_t launch_range(const float* x, int64_t N, float2* partials, int nblock
 cudaError_t launch_scatter(const uint32_t* idx, const float* val, uint64_t cap, const hi_header* hdr, int64_t N,
                            float* out, uint32_t* status, uint32_t* queue, cudaStream_t st);
 cudaError_t launch_tune(int A, const FieldGeo& g, const float* x, const TuneCands& cands, int m, int stride,
-                        double* err, hi_header* hdr, cudaStream_t st);
+                        double* err, uint32_t* ticket, hi_header* hdr, cudaStream_t st);
 
 constexpr int kRangeBlocks = 1024;
 

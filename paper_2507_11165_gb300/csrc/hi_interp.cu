@@ -200,11 +200,14 @@ __device__ __forceinline__ void pass_rows(float* __restrict__ v, uint8_t* __rest
         }
 #pragma unroll
         for (int j = 4 * NV; j <= A; ++j) r[j] = row[j];
-        uint32_t cw[NCW];  // decompress: the row's codes, 4 per word
+        uint32_t cw[(NCW + 3) / 4 * 4];  // decompress: the row's codes, 4 per word
         if constexpr (!COMP) {
-            const uint32_t* cwp = reinterpret_cast<const uint32_t*>(cs + cb);
+            const uint4* cwp = reinterpret_cast<const uint4*>(cs + cb);
 #pragma unroll
-            for (int j = 0; j < NCW; ++j) cw[j] = cwp[j];
+            for (int j = 0; j < (NCW + 3) / 4; ++j) {
+                const uint4 q = cwp[j];
+                cw[4 * j] = q.x, cw[4 * j + 1] = q.y, cw[4 * j + 2] = q.z, cw[4 * j + 3] = q.w;
+            }
         }
 #pragma unroll
         for (int k = 0; k < NDM; ++k) {
