@@ -373,7 +373,7 @@ def run_gpu(args):
                          bit_rate=est["bit_rate"],
                          levels=[(int(h.level[l].interp), list(h.level[l].order)) for l in range(h.n_levels)]),
             e2e=e2e,
-            gpu_launches=7 * args.steps,
+            gpu_launches=6 * args.steps,  # setup, range, autotune, predict-quantize, scatter, reconstruct
             cpu_baseline=cpu,
             clocks=clocks,
         )

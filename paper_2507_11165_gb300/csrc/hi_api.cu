@@ -264,9 +264,20 @@ hi_status hi_query(const hi_params* p, uint64_t* n_points, uint64_t* n_anchors, 
 static hi_status enqueue_tune(const Geometry& G, const float* d_x, hi_header* d_header, void* d_ws,
                               cudaStream_t stream)
 {
-    double* err = reinterpret_cast<double*>(static_cast<char*>(d_ws) + kWsTune);
-    uint32_t* ticket = reinterpret_cast<uint32_t*>(static_cast<char*>(d_ws) + kWsTuneTicket);
-    return cuda_status(launch_tune(G.A, G.g, d_x, G.cands, G.m, G.stride, err, ticket, d_header, stream));
+    TuneLaunch t{};
+    int PX, CX;
+    pitches(G.A, &PX, &CX);
+    t.use_tma = G.A >= 4 && encode_box(&t.tmap, d_x, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, G.g, PX, G.A + 1);
+    t.tma_bytes = (uint32_t)(PX * (G.A + 1) * G.g.b0 * 4);
+    t.g = G.g;
+    t.x = d_x;
+    t.cands = G.cands;
+    t.m = G.m;
+    t.stride = G.stride;
+    t.err = reinterpret_cast<double*>(static_cast<char*>(d_ws) + kWsTune);
+    t.ticket = reinterpret_cast<uint32_t*>(static_cast<char*>(d_ws) + kWsTuneTicket);
+    t.hdr = d_header;
+    return cuda_status(launch_tune(G.A, t, stream));
 }
 
 hi_status hi_compress(const hi_params* p, const float* d_x, uint8_t* d_codes, float* d_anchors,

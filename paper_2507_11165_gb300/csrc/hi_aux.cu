@@ -82,7 +82,20 @@ __global__ void __launch_bounds__(512) k_range(const float* __restrict__ x, int6
     if (vec) {
         const int64_t n4 = N / 4;
         const float4* x4 = reinterpret_cast<const float4*>(x);
-        for (int64_t i = t0; i < n4; i += stride) {
+        int64_t i = t0;
+        for (; i + 3 * stride < n4; i += 4 * stride) {  // four 16-byte loads in flight per thread
+            float4 f[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) f[u] = __ldcs(x4 + i + u * stride);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (finite_f(f[u].x)) mn = fminf(mn, f[u].x), mx = fmaxf(mx, f[u].x);
+                if (finite_f(f[u].y)) mn = fminf(mn, f[u].y), mx = fmaxf(mx, f[u].y);
+                if (finite_f(f[u].z)) mn = fminf(mn, f[u].z), mx = fmaxf(mx, f[u].z);
+                if (finite_f(f[u].w)) mn = fminf(mn, f[u].w), mx = fmaxf(mx, f[u].w);
+            }
+        }
+        for (; i < n4; i += stride) {
             const float4 f = __ldcs(x4 + i);
             if (finite_f(f.x)) mn = fminf(mn, f.x), mx = fmaxf(mx, f.x);
             if (finite_f(f.y)) mn = fminf(mn, f.y), mx = fmaxf(mx, f.y);
@@ -114,13 +127,23 @@ __global__ void __launch_bounds__(512) k_range(const float* __restrict__ x, int6
     __syncthreads();
     if (!s_last) return;
     __threadfence();
+    // the last CTA folds the partials (min / max are exact in any order)
+    mn = INFINITY, mx = -INFINITY;
+    for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x) {
+        const float2 pk = __ldcg(partials + k);
+        mn = fminf(mn, pk.x);
+        mx = fmaxf(mx, pk.y);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    __syncthreads();
+    if (lane == 0) s_mn[warp] = mn, s_mx[warp] = mx;
+    __syncthreads();
     if (threadIdx.x == 0) {
         float a = INFINITY, b = -INFINITY;
-        for (unsigned k = 0; k < gridDim.x; ++k) {
-            const float2 pk = __ldcg(partials + k);
-            a = fminf(a, pk.x);
-            b = fmaxf(b, pk.y);
-        }
+        for (int w = 0; w < nw; ++w) a = fminf(a, s_mn[w]), b = fmaxf(b, s_mx[w]);
         if (!(a <= b)) a = 0.0f, b = 0.0f;  // no finite value
         a = __fadd_rn(a, 0.0f);              // a signed zero is reported as +0
         b = __fadd_rn(b, 0.0f);
@@ -218,15 +241,17 @@ __device__ __forceinline__ void tune_levels(const float* v, const hi_level& lv, 
 }
 
 template <int A>
-__global__ void __launch_bounds__(256) k_tune(const FieldGeo g, const float* __restrict__ x, const TuneCands cands,
-                                              int stride, double* __restrict__ err, uint32_t* ticket,
-                                              hi_header* __restrict__ hdr)
+__global__ void __launch_bounds__(256) k_tune(const __grid_constant__ CUtensorMap tmap, const FieldGeo g,
+                                              const float* __restrict__ x, const TuneCands cands, int stride,
+                                              double* __restrict__ err, uint32_t* ticket,
+                                              hi_header* __restrict__ hdr, const uint32_t tma_bytes, const int use_tma)
 {
     using TG = TileGeom<A>;
     constexpr int L = TG::L;
     extern __shared__ __align__(128) unsigned char smem[];
     float* v = reinterpret_cast<float*>(smem);
     __shared__ double s_red[L][8];
+    __shared__ __align__(8) uint64_t s_mbar;
 
     const int sample = blockIdx.x, c = blockIdx.y;
     const int tile = sample * stride;
@@ -238,13 +263,28 @@ __global__ void __launch_bounds__(256) k_tune(const FieldGeo g, const float* __r
         const int rem = (int)(g.n[d] - 1 - o[d]);
         e[d] = (g.n[d] == 1) ? 0 : (rem < A ? rem : A);
     }
-    const int rows = (e[0] + 1) * (e[1] + 1);
-    for (int rr = warp; rr < rows; rr += (blockDim.x >> 5)) {
-        const int c0 = rr / (e[1] + 1), c1 = rr - c0 * (e[1] + 1);
-        const float* src = x + ((int64_t)(o[0] + c0) * g.n[1] + (o[1] + c1)) * g.n[2] + o[2];
-        for (int c2 = lane; c2 <= e[2]; c2 += 32) v[c0 * TG::PY + c1 * TG::PX + c2] = src[c2];
+    if (use_tma) {  // one TMA box for the sampled tile
+        if (tid == 0) {
+            mbar_init(&s_mbar, 1);
+            fence_mbar_init();
+            mbar_arrive_expect_tx(&s_mbar, tma_bytes);
+            tma_load_3d(v, &tmap, o[2], o[1], o[0], &s_mbar);
+        }
+        __syncthreads();
+        const bool ok = mbar_wait(&s_mbar, 0, kSpinLimit);
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) set_status(&hdr->status, HI_ETIMEOUT);
+            return;
+        }
+    } else {
+        const int rows = (e[0] + 1) * (e[1] + 1);
+        for (int rr = warp; rr < rows; rr += (blockDim.x >> 5)) {
+            const int c0 = rr / (e[1] + 1), c1 = rr - c0 * (e[1] + 1);
+            const float* src = x + ((int64_t)(o[0] + c0) * g.n[1] + (o[1] + c1)) * g.n[2] + o[2];
+            for (int c2 = lane; c2 <= e[2]; c2 += 32) v[c0 * TG::PY + c1 * TG::PX + c2] = src[c2];
+        }
+        __syncthreads();
     }
-    __syncthreads();
 
     hi_level lv;
     lv.interp = cands.interp[c];
@@ -321,27 +361,26 @@ cudaError_t launch_scatter(const uint32_t* idx, const float* val, uint64_t cap, 
 }
 
 template <int A>
-static cudaError_t launch_tune_t(const FieldGeo& g, const float* x, const TuneCands& cands, int m, int stride,
-                                 double* err, uint32_t* ticket, hi_header* hdr, cudaStream_t st)
+static cudaError_t launch_tune_t(const TuneLaunch& t, cudaStream_t st)
 {
     using TG = TileGeom<A>;
-    const size_t smem = (size_t)g.b0 * TG::P * TG::PX * 4;
+    const size_t smem = (size_t)t.g.b0 * TG::P * TG::PX * 4;
     auto kern = k_tune<A>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<dim3(m, cands.ncfg), 256, smem, st>>>(g, x, cands, stride, err, ticket, hdr);
+    kern<<<dim3(t.m, t.cands.ncfg), 256, smem, st>>>(t.tmap, t.g, t.x, t.cands, t.stride, t.err, t.ticket, t.hdr,
+                                                     t.tma_bytes, t.use_tma ? 1 : 0);
     return cudaGetLastError();
 }
 
-cudaError_t launch_tune(int A, const FieldGeo& g, const float* x, const TuneCands& cands, int m, int stride,
-                        double* err, uint32_t* ticket, hi_header* hdr, cudaStream_t st)
+cudaError_t launch_tune(int A, const TuneLaunch& t, cudaStream_t st)
 {
     switch (A) {
-    case 2: return launch_tune_t<2>(g, x, cands, m, stride, err, ticket, hdr, st);
-    case 4: return launch_tune_t<4>(g, x, cands, m, stride, err, ticket, hdr, st);
-    case 8: return launch_tune_t<8>(g, x, cands, m, stride, err, ticket, hdr, st);
-    case 16: return launch_tune_t<16>(g, x, cands, m, stride, err, ticket, hdr, st);
-    case 32: return launch_tune_t<32>(g, x, cands, m, stride, err, ticket, hdr, st);
+    case 2: return launch_tune_t<2>(t, st);
+    case 4: return launch_tune_t<4>(t, st);
+    case 8: return launch_tune_t<8>(t, st);
+    case 16: return launch_tune_t<16>(t, st);
+    case 32: return launch_tune_t<32>(t, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -76,8 +76,19 @@ cudaError_t launch_range(const float* x, int64_t N, float2* partials, int nblock
                          hi_header* hdr, cudaStream_t st);
 cudaError_t launch_scatter(const uint32_t* idx, const float* val, uint64_t cap, const hi_header* hdr, int64_t N,
                            float* out, uint32_t* status, uint32_t* queue, cudaStream_t st);
-cudaError_t launch_tune(int A, const FieldGeo& g, const float* x, const TuneCands& cands, int m, int stride,
-                        double* err, uint32_t* ticket, hi_header* hdr, cudaStream_t st);
+struct TuneLaunch {
+    CUtensorMap tmap;
+    FieldGeo g;
+    const float* x;
+    TuneCands cands;
+    int m, stride;
+    double* err;
+    uint32_t* ticket;
+    hi_header* hdr;
+    uint32_t tma_bytes;
+    bool use_tma;
+};
+cudaError_t launch_tune(int A, const TuneLaunch& t, cudaStream_t st);
 
 constexpr int kRangeBlocks = 1024;
 

@@ -150,6 +150,32 @@ __device__ __forceinline__ void pass_cols(float* __restrict__ v, uint8_t* __rest
     constexpr int CPD = (D == 0 ? CY : CX) * S, CPQ = (Q == 0 ? CY : CX);
     const int nd = FULL ? NDM : ((ed >= S) ? ((ed - S) / (2 * S) + 1) : 0);
     const int nl = nq * nr;
+    if constexpr (FULL && NDM >= 4) {
+        // whole line: first and last points peeled, the interior loops over
+        // the cubic (or linear) midpoint with the nodes sliding through registers
+        for (int line = threadIdx.x; line < nl; line += blockDim.x) {
+            const int jq = line / nr, jr = line - jq * nr;
+            const int cq = jq * stq, cr = jr * str;
+            const int vb = cq * VPQ + cr, cb = cq * CPQ + cr;
+            float fa = 0.0f, fb = v[vb], fu = v[vb + 2 * VPD], fv = v[vb + 4 * VPD];
+            auto point = [&](int k, float pr) {
+                const int vi = vb + (2 * k + 1) * VPD;
+                if constexpr (COMP)
+                    v[vi] = point_compress(h, v[vi], pr, cs + cb + (2 * k + 1) * CPD);
+                else
+                    v[vi] = point_decompress<A>(h, cs[cb + (2 * k + 1) * CPD], pr, vi);
+            };
+            point(0, predict(CUBIC, false, true, true, 0.0f, fb, fu, fv));
+#pragma unroll 2
+            for (int k = 1; k <= NDM - 2; ++k) {
+                fa = fb, fb = fu, fu = fv;
+                fv = v[vb + (2 * k + 4) * VPD];
+                point(k, predict(CUBIC, true, true, true, fa, fb, fu, fv));
+            }
+            point(NDM - 1, predict(CUBIC, true, true, false, fb, fu, fv, 0.0f));
+        }
+        return;
+    }
     for (int line = threadIdx.x; line < nl; line += blockDim.x) {
         const int jq = line / nr, jr = line - jq * nr;
         const int cq = jq * stq, cr = jr * str;
