@@ -36,7 +36,7 @@
 
 namespace hi {
 
-constexpr int kOutCap = 1024;  // staged outliers per tile before the direct path
+constexpr int kOutCap = 512;  // staged outliers per tile before the direct path
 constexpr int kMaxThreads = 256;
 
 // Shared-memory layouts of one tile (planes b0 = A+1, or 1 for 1D/2D fields).
@@ -500,8 +500,9 @@ __global__ void __launch_bounds__(kMaxThreads, 4)
     __shared__ hi_level s_lv[HI_MAX_LEVELS];
     __shared__ int s_sel[HI_MAX_LEVELS];
     __shared__ int s_next;
+    __shared__ TileInfo s_ti[2];  // this tile's geometry and the next one's (thread 0 decodes)
 
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x;
     const bool use_tma = flags & kFlagTma;
     {   // an earlier stage failed (bad range, device-side EINVAL): leave outputs untouched
         const uint32_t st = hdr->status;
@@ -522,6 +523,7 @@ __global__ void __launch_bounds__(kMaxThreads, 4)
         mbar_init(&s_mbar[0], 1);
         mbar_init(&s_mbar[1], 1);
         fence_mbar_init();
+        if ((int)blockIdx.x < g.ntiles) s_ti[0] = tile_info<A>(g, blockIdx.x);
         if (use_tma) {
             prefetch_tmap(&tmap);
             if ((int)blockIdx.x < g.ntiles) tma_issue(vbuf[0], &tmap, g, blockIdx.x, A, &s_mbar[0], tma_bytes);
@@ -537,11 +539,12 @@ __global__ void __launch_bounds__(kMaxThreads, 4)
     for (int tile = blockIdx.x; tile < g.ntiles; ++it) {
         const int buf = dbuf ? (it & 1) : 0;
         float* v = vbuf[buf];
-        const TileInfo ti = tile_info<A>(g, tile);
+        const TileInfo ti = s_ti[it & 1];
         if (tid == 0) {
             s_nout = 0;
             const int nx = (int)gridDim.x + (int)atomicAdd(queue, 1u);
             s_next = nx;
+            if (nx < g.ntiles) s_ti[(it + 1) & 1] = tile_info<A>(g, nx);
             if (use_tma && dbuf && nx < g.ntiles)
                 tma_issue(vbuf[buf ^ 1], &tmap, g, nx, A, &s_mbar[buf ^ 1], tma_bytes);
             if (use_tma && !dbuf && it > 0) tma_issue(v, &tmap, g, tile, A, &s_mbar[0], tma_bytes);
@@ -580,31 +583,41 @@ __global__ void __launch_bounds__(kMaxThreads, 4)
         if (vec_codes) {
             constexpr int CH = (A >= 16) ? 4 : 2;  // words per global vector store
             constexpr int NCH = (A >= 8) ? A / (4 * CH) : 1;
+            const bool square = own0 == A && own1 == A;  // rows decompose with shifts
             const int items = rows * NCH;
             for (int i0 = 0; i0 < items; i0 += blockDim.x) {
                 const int i = i0 + tid;
                 const bool act = i < items;
                 const int row = act ? i / NCH : 0, ch = act ? i - row * NCH : 0;
-                const int c0 = row / own1, c1 = row - c0 * own1;
+                const int c0 = square ? row / A : row / own1;
+                const int c1 = row - c0 * (square ? A : own1);
                 const uint32_t* src = reinterpret_cast<const uint32_t*>(cs + c0 * Lw::CYC + c1 * Lw::CXC) + ch * CH;
                 uint8_t* dst = codes + ((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2] +
                                ch * CH * 4;
                 uint32_t w[4];
+                uint32_t z = 0;  // nonzero iff some code of the chunk is 0 (an outlier)
 #pragma unroll
-                for (int j = 0; j < CH; ++j) w[j] = src[j];
+                for (int j = 0; j < CH; ++j) {
+                    w[j] = src[j];
+                    z |= (w[j] - 0x01010101u) & ~w[j] & 0x80808080u;
+                }
                 if (act) {
                     if constexpr (CH == 4)
                         *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
                     else
                         *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
                 }
+                if (__any_sync(0xffffffffu, act && z != 0)) {
 #pragma unroll
-                for (int b = 0; b < 4 * CH; ++b) {
-                    const int code = (w[b >> 2] >> (8 * (b & 3))) & 0xff;
-                    if (hist_on) hist_add(s_hist, code, act);
-                    if (__any_sync(0xffffffffu, act && code == 0))
-                        outlier_append<A>(act && code == 0, c0 * Lw::PY + c1 * Lw::PX + ch * CH * 4 + b, v, &s_nout,
-                                          s_out, hdr, out_idx, out_val, out_cap, g, ti.o);
+                    for (int b = 0; b < 4 * CH; ++b) {
+                        const int code = (w[b >> 2] >> (8 * (b & 3))) & 0xff;
+                        outlier_append<A>(act && code == 0, c0 * Lw::PY + c1 * Lw::PX + ch * CH * 4 + b, v,
+                                          &s_nout, s_out, hdr, out_idx, out_val, out_cap, g, ti.o);
+                    }
+                }
+                if (hist_on) {
+#pragma unroll
+                    for (int b = 0; b < 4 * CH; ++b) hist_add(s_hist, (w[b >> 2] >> (8 * (b & 3))) & 0xff, act);
                 }
             }
         } else {
@@ -694,6 +707,7 @@ __global__ void __launch_bounds__(kMaxThreads, 4)
     __shared__ hi_level s_lv[HI_MAX_LEVELS];
     __shared__ int s_sel[HI_MAX_LEVELS];
     __shared__ int s_next;
+    __shared__ TileInfo s_ti[2];
 
     const int tid = threadIdx.x;
     const bool use_tma = flags & kFlagTma;
@@ -714,6 +728,7 @@ __global__ void __launch_bounds__(kMaxThreads, 4)
         mbar_init(&s_mbar[0], 1);
         mbar_init(&s_mbar[1], 1);
         fence_mbar_init();
+        if ((int)blockIdx.x < g.ntiles) s_ti[0] = tile_info<A>(g, blockIdx.x);
         if (use_tma) {
             prefetch_tmap(&cmap);
             if ((int)blockIdx.x < g.ntiles) tma_issue(cbuf[0], &cmap, g, blockIdx.x, A, &s_mbar[0], tma_bytes);
@@ -722,14 +737,24 @@ __global__ void __launch_bounds__(kMaxThreads, 4)
     __syncthreads();
     const bool full_ok = HasFull<A>::value && g.n[0] > 1 && g.n[1] > 1 && g.n[2] > 1;
 
+    // the 8 corner anchors of a tile, loaded one tile ahead by threads 0..7
+    auto anchor_of = [&](int pos, const TileInfo& tn) -> float {
+        if (tid >= 8 || pos >= g.ntiles) return 0.0f;
+        const int a0 = (tid >> 2) & 1, a1 = (tid >> 1) & 1, a2 = tid & 1;
+        if (a0 * A > tn.e[0] || a1 * A > tn.e[1] || a2 * A > tn.e[2]) return 0.0f;
+        return anchors[((int64_t)(tn.o[0] / A + a0) * g.na[1] + (tn.o[1] / A + a1)) * g.na[2] + (tn.o[2] / A + a2)];
+    };
+    float a_cur = anchor_of(blockIdx.x, s_ti[0]);
+
     int it = 0;
     for (int tile = blockIdx.x; tile < g.ntiles; ++it) {
         const int buf = dbuf ? (it & 1) : 0;
         uint8_t* cs = cbuf[buf];
-        const TileInfo ti = tile_info<A>(g, tile);
+        const TileInfo ti = s_ti[it & 1];
         if (tid == 0) {
             const int nx = (int)gridDim.x + (int)atomicAdd(queue, 1u);
             s_next = nx;
+            if (nx < g.ntiles) s_ti[(it + 1) & 1] = tile_info<A>(g, nx);
             s_rare.o[0] = ti.o[0], s_rare.o[1] = ti.o[1], s_rare.o[2] = ti.o[2];
             if (use_tma && dbuf && nx < g.ntiles)
                 tma_issue(cbuf[buf ^ 1], &cmap, g, nx, A, &s_mbar[buf ^ 1], tma_bytes);
@@ -738,11 +763,7 @@ __global__ void __launch_bounds__(kMaxThreads, 4)
         if (tid < 8) {  // seed the anchors
             const int a0 = (tid >> 2) & 1, a1 = (tid >> 1) & 1, a2 = tid & 1;
             const int l0 = a0 * A, l1 = a1 * A, l2 = a2 * A;
-            if (l0 <= ti.e[0] && l1 <= ti.e[1] && l2 <= ti.e[2]) {
-                const int64_t ai = ((int64_t)(ti.o[0] / A + a0) * g.na[1] + (ti.o[1] / A + a1)) * g.na[2] +
-                                   (ti.o[2] / A + a2);
-                v[l0 * Lw::PY + l1 * Lw::PX + l2] = anchors[ai];
-            }
+            if (l0 <= ti.e[0] && l1 <= ti.e[1] && l2 <= ti.e[2]) v[l0 * Lw::PY + l1 * Lw::PX + l2] = a_cur;
         }
         if (use_tma) {
             const bool ok = mbar_wait(&s_mbar[buf], dbuf ? ((it >> 1) & 1) : (it & 1), kSpinLimit);
@@ -756,6 +777,7 @@ __global__ void __launch_bounds__(kMaxThreads, 4)
             __syncthreads();
         }
         const int next = s_next;
+        const float a_nxt = anchor_of(next, s_ti[(it + 1) & 1]);  // in flight while this tile is reconstructed
         const bool full = full_ok && ti.e[0] == A && ti.e[1] == A && ti.e[2] == A;
         if constexpr (HasFull<A>::value) {
             if (full)
@@ -792,6 +814,7 @@ __global__ void __launch_bounds__(kMaxThreads, 4)
         fence_proxy_async_smem();
         __syncthreads();
         tile = next;
+        a_cur = a_nxt;
     }
 }
 
