@@ -794,10 +794,12 @@ __global__ void __launch_bounds__(kMaxThreads, 4)
         const bool vec_out = (flags & kFlagVecOut) && own2 == A && A >= 4;
         if (vec_out) {
             constexpr int NCH = (A >= 4) ? A / 4 : 1;
+            const bool square = own0 == A && own1 == A;  // rows decompose with shifts
             const int items = rows * NCH;
             for (int i = tid; i < items; i += blockDim.x) {
                 const int row = i / NCH, ch = i - row * NCH;
-                const int c0 = row / own1, c1 = row - c0 * own1;
+                const int c0 = square ? row / A : row / own1;
+                const int c1 = row - c0 * (square ? A : own1);
                 const float4 f4 = *reinterpret_cast<const float4*>(v + c0 * Lw::PY + c1 * Lw::PX + ch * 4);
                 *reinterpret_cast<float4*>(out + ((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] +
                                            ti.o[2] + ch * 4) = f4;
