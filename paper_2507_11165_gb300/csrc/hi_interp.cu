@@ -36,7 +36,6 @@
 
 namespace hi {
 
-constexpr int kOutCap = 512;  // staged outliers per tile before the direct path
 constexpr int kMaxThreads = 256;
 
 // Shared-memory layouts of one tile (planes b0 = A+1, or 1 for 1D/2D fields).
@@ -437,41 +436,45 @@ __device__ __forceinline__ void tma_issue(void* dst, const CUtensorMap* map, con
 // ---------------------------------------------------------------------------
 // Epilogue helpers (all lanes of the warp call them)
 // ---------------------------------------------------------------------------
-// Histogram of one code per lane, warp-aggregated: lanes holding equal codes
-// are matched and their leader adds the count with one shared-memory atomic.
-__device__ __forceinline__ void hist_add(uint32_t* s_hist, int code, bool valid)
-{
-    const int key = valid ? code : 256;
-    const unsigned m = __match_any_sync(0xffffffffu, key);
-    if (valid && (threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(&s_hist[code], (uint32_t)__popc(m));
-}
-
-// Outliers (code 0) of the tile, one candidate per lane, appended in warp
-// batches to the tile's staging list, or straight to the output past it.
+// Outliers (code 0) of the tile, one candidate per lane: the warp reserves
+// its slots in the output list with one atomic and writes them.
 template <int A>
-__device__ __forceinline__ void outlier_append(bool is_out, int vi, const float* v, int* s_nout, uint16_t* s_out,
-                                               hi_header* hdr, uint32_t* out_idx, float* out_val, uint64_t out_cap,
+__device__ __forceinline__ void outlier_append(bool is_out, int vi, const float* v, hi_header* hdr,
+                                               uint32_t* out_idx, float* out_val, uint64_t out_cap,
                                                const FieldGeo& g, const int o[3])
 {
     const unsigned m = __ballot_sync(0xffffffffu, is_out);
     if (m == 0) return;
     const int lane = threadIdx.x & 31;
     const int leader = __ffs(m) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(s_nout, __popc(m));
+    unsigned long long base = 0;
+    if (lane == leader)
+        base = atomicAdd(reinterpret_cast<unsigned long long*>(&hdr->n_outliers), (unsigned long long)__popc(m));
     base = __shfl_sync(0xffffffffu, base, leader);
     if (!is_out) return;
-    const int slot = base + __popc(m & ((1u << lane) - 1u));
-    if (slot < kOutCap) {
-        s_out[slot] = (uint16_t)vi;
+    const unsigned long long pos = base + __popc(m & ((1u << lane) - 1u));
+    if (pos < out_cap) {
+        out_idx[pos] = (uint32_t)global_index<A>(g, o, vi);
+        out_val[pos] = v[vi];
     } else {
-        const unsigned long long pos = atomicAdd(reinterpret_cast<unsigned long long*>(&hdr->n_outliers), 1ull);
-        if (pos < out_cap) {
-            out_idx[pos] = (uint32_t)global_index<A>(g, o, vi);
-            out_val[pos] = v[vi];
-        } else {
-            set_status(&hdr->status, HI_ECAPACITY);
-        }
+        set_status(&hdr->status, HI_ECAPACITY);
+    }
+}
+
+// Histogram: codes 120..135 (the bulk at any practical error bound) go to
+// per-thread 16-bit counters laid out bin-major, so that a warp's updates hit
+// 32 consecutive half-words (no bank conflict, no atomics); other codes go
+// to shared-memory atomics.  Folded into the CTA histogram at kernel end.
+constexpr int kHistLo = 120, kHistBins = 16;
+
+__device__ __forceinline__ void hist_count(uint16_t* hc, uint32_t* s_hist, int code, bool valid)
+{
+    const unsigned k = (unsigned)(code - kHistLo);
+    if (valid) {
+        if (k < (unsigned)kHistBins)
+            hc[k * blockDim.x + threadIdx.x] += 1;
+        else
+            atomicAdd(&s_hist[code], 1u);
     }
 }
 
@@ -492,10 +495,8 @@ __global__ void __launch_bounds__(kMaxThreads, 4)
     const int vb_bytes = vbuf_bytes<A>(g.b0);
     float* vbuf[2] = {reinterpret_cast<float*>(smem), reinterpret_cast<float*>(smem + (dbuf ? vb_bytes : 0))};
     uint8_t* cs = smem + (dbuf ? 2 : 1) * vb_bytes;
+    uint16_t* hc = reinterpret_cast<uint16_t*>(cs + round128(g.b0 * Lw::P * Lw::CXC));  // [kHistBins][threads]
     __shared__ uint32_t s_hist[256];
-    __shared__ uint16_t s_out[kOutCap];
-    __shared__ int s_nout;
-    __shared__ unsigned long long s_obase;
     __shared__ __align__(8) uint64_t s_mbar[2];
     __shared__ hi_level s_lv[HI_MAX_LEVELS];
     __shared__ int s_sel[HI_MAX_LEVELS];
@@ -515,6 +516,8 @@ __global__ void __launch_bounds__(kMaxThreads, 4)
     const bool hist_on = hist_g != nullptr;
 
     for (int i = tid; i < 256; i += blockDim.x) s_hist[i] = 0;
+    if (hist_on)
+        for (int k = 0; k < kHistBins; ++k) hc[k * blockDim.x + tid] = 0;
     if (tid < HI_MAX_LEVELS) {
         s_lv[tid] = hdr->level[tid];
         s_sel[tid] = perm_sel(s_lv[tid]);
@@ -541,7 +544,6 @@ __global__ void __launch_bounds__(kMaxThreads, 4)
         float* v = vbuf[buf];
         const TileInfo ti = s_ti[it & 1];
         if (tid == 0) {
-            s_nout = 0;
             const int nx = (int)gridDim.x + (int)atomicAdd(queue, 1u);
             s_next = nx;
             if (nx < g.ntiles) s_ti[(it + 1) & 1] = tile_info<A>(g, nx);
@@ -611,13 +613,13 @@ __global__ void __launch_bounds__(kMaxThreads, 4)
 #pragma unroll
                     for (int b = 0; b < 4 * CH; ++b) {
                         const int code = (w[b >> 2] >> (8 * (b & 3))) & 0xff;
-                        outlier_append<A>(act && code == 0, c0 * Lw::PY + c1 * Lw::PX + ch * CH * 4 + b, v,
-                                          &s_nout, s_out, hdr, out_idx, out_val, out_cap, g, ti.o);
+                        outlier_append<A>(act && code == 0, c0 * Lw::PY + c1 * Lw::PX + ch * CH * 4 + b, v, hdr,
+                                          out_idx, out_val, out_cap, g, ti.o);
                     }
                 }
                 if (hist_on) {
 #pragma unroll
-                    for (int b = 0; b < 4 * CH; ++b) hist_add(s_hist, (w[b >> 2] >> (8 * (b & 3))) & 0xff, act);
+                    for (int b = 0; b < 4 * CH; ++b) hist_count(hc, s_hist, (w[b >> 2] >> (8 * (b & 3))) & 0xff, act);
                 }
             }
         } else {
@@ -631,9 +633,9 @@ __global__ void __launch_bounds__(kMaxThreads, 4)
                 if (act)
                     codes[((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2] + c2] =
                         (uint8_t)code;
-                if (hist_on) hist_add(s_hist, code, act);
-                outlier_append<A>(act && code == 0, c0 * Lw::PY + c1 * Lw::PX + c2, v, &s_nout, s_out, hdr, out_idx,
-                                  out_val, out_cap, g, ti.o);
+                if (hist_on) hist_count(hc, s_hist, code, act);
+                outlier_append<A>(act && code == 0, c0 * Lw::PY + c1 * Lw::PX + c2, v, hdr, out_idx, out_val, out_cap,
+                                  g, ti.o);
             }
         }
         if (recon_g) {
@@ -655,24 +657,6 @@ __global__ void __launch_bounds__(kMaxThreads, 4)
                 if (hist_on) atomicSub(&s_hist[kRadius], 1u);  // anchors are not predicted
             }
         }
-        __syncthreads();
-        const int nout = s_nout < kOutCap ? s_nout : kOutCap;
-        if (nout > 0) {  // CTA-uniform
-            if (tid == 0)
-                s_obase = atomicAdd(reinterpret_cast<unsigned long long*>(&hdr->n_outliers),
-                                    (unsigned long long)nout);
-            __syncthreads();
-            for (int i = tid; i < nout; i += blockDim.x) {
-                const unsigned long long pos = s_obase + i;
-                const int vi = s_out[i];
-                if (pos < out_cap) {
-                    out_idx[pos] = (uint32_t)global_index<A>(g, ti.o, vi);
-                    out_val[pos] = v[vi];
-                } else if (i == 0 || pos == out_cap) {
-                    set_status(&hdr->status, HI_ECAPACITY);
-                }
-            }
-        }
         // keep the buffers until every thread is done; order the generic-proxy
         // writes above before the TMA overwrite of this buffer
         fence_proxy_async_smem();
@@ -680,6 +664,11 @@ __global__ void __launch_bounds__(kMaxThreads, 4)
         tile = next;
     }
     if (hist_on) {
+        for (int k = 0; k < kHistBins; ++k) {  // fold this thread's counters, a warp at a time
+            uint32_t c = hc[k * blockDim.x + tid];
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+            if ((tid & 31) == 0) atomicAdd(&s_hist[kHistLo + k], c);
+        }
         __syncthreads();
         for (int i = tid; i < 256; i += blockDim.x)
             if (s_hist[i]) atomicAdd(&hist_g[i], s_hist[i]);
@@ -824,9 +813,10 @@ __global__ void __launch_bounds__(kMaxThreads, 4)
 // Launchers
 // ---------------------------------------------------------------------------
 template <int A>
-size_t compress_smem_t(int b0, bool dbuf)
+size_t compress_smem_t(int b0, bool dbuf, int threads)
 {
-    return (dbuf ? 2 : 1) * (size_t)vbuf_bytes<A>(b0) + (size_t)round128(b0 * Lay<A>::P * Lay<A>::CXC);
+    return (dbuf ? 2 : 1) * (size_t)vbuf_bytes<A>(b0) + (size_t)round128(b0 * Lay<A>::P * Lay<A>::CXC) +
+           (size_t)kHistBins * threads * sizeof(uint16_t);
 }
 
 template <int A>
@@ -867,8 +857,8 @@ template <int A>
 static cudaError_t launch_compress_t(const CompressLaunch& c, cudaStream_t st)
 {
     auto kern = k_compress<A>;
-    const bool dbuf = c.buffers == 2 && fits_double(kern, compress_smem_t<A>(c.g.b0, true));
-    const size_t smem = compress_smem_t<A>(c.g.b0, dbuf);
+    const bool dbuf = c.buffers == 2 && fits_double(kern, compress_smem_t<A>(c.g.b0, true, c.threads));
+    const size_t smem = compress_smem_t<A>(c.g.b0, dbuf, c.threads);
     int grid = 0;
     cudaError_t err = persistent_grid(kern, c.threads, smem, c.num_sms, c.g.ntiles, c.max_ctas, &grid);
     if (err != cudaSuccess) return err;
@@ -919,11 +909,11 @@ cudaError_t launch_decompress(int A, const DecompressLaunch& c, cudaStream_t st)
 size_t compress_smem_bytes(int A, int b0)
 {
     switch (A) {
-    case 2: return compress_smem_t<2>(b0, false);
-    case 4: return compress_smem_t<4>(b0, false);
-    case 8: return compress_smem_t<8>(b0, false);
-    case 16: return compress_smem_t<16>(b0, false);
-    case 32: return compress_smem_t<32>(b0, false);
+    case 2: return compress_smem_t<2>(b0, false, 256);
+    case 4: return compress_smem_t<4>(b0, false, 256);
+    case 8: return compress_smem_t<8>(b0, false, 256);
+    case 16: return compress_smem_t<16>(b0, false, 256);
+    case 32: return compress_smem_t<32>(b0, false, 256);
     default: return 0;
     }
 }
