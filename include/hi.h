@@ -82,8 +82,8 @@ typedef struct {
     uint32_t anchor_stride; /* A: 2, 4, 8, 16 or 32 (Sec. 5.1.1 uses 16)          */
     uint32_t autotune;      /* 1: choose level[] on the device (Sec. 5.1.3)       */
     uint32_t tuning;        /* launch shape, 0 = library default; else bits 0-1:  */
-                            /* threads per CTA (1: 64, 2: 128, 3: 256), bits 2-3: */
-                            /* tile buffers (1: one, 2: two, prefetching)         */
+                            /* threads per CTA (1: 64, 2: 128), bits 2-3: tile    */
+                            /* buffers (1: one, 2: two, prefetching)              */
     hi_level level[HI_MAX_LEVELS]; /* level[l]: stride 2^l; used when !autotune  */
 } hi_params;
 

@@ -73,7 +73,7 @@ TuneCands make_cands(const uint64_t dims[3])
 
 hi_status make_geometry(const hi_params* p, Geometry* G)
 {
-    if (!p || (p->tuning & ~0xFu) != 0 || ((p->tuning >> 2) & 3u) == 3u) return HI_EINVAL;
+    if (!p || (p->tuning & ~0xFu) != 0 || ((p->tuning >> 2) & 3u) == 3u || (p->tuning & 3u) == 3u) return HI_EINVAL;
     const int L = ilog2_pow2(p->anchor_stride);
     if (L < 0) return HI_EINVAL;
     if (!(p->eb > 0.0) || !std::isfinite(p->eb)) return HI_EINVAL;
@@ -204,7 +204,7 @@ int num_sms()
 
 int threads_for(const Geometry& G, uint32_t tuning)
 {
-    static const int kThreads[4] = {0, 64, 128, 256};
+    static const int kThreads[4] = {0, 64, 128, 128};
     if (tuning & 3u) return kThreads[tuning & 3u];
     // one tile per CTA: 128 threads keep the passes busy and let several tiles
     // share an SM (measured on GB300 for 17^3 tiles); small 1D/2D tiles use 64

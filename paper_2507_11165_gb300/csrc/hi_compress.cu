@@ -1,0 +1,245 @@
+// hi_compress.cu -- the fused interpolation-predict + quantize kernel
+// (cuSZ-Hi, arXiv 2507.11165, Sec. 3.2, Sec. 5.1.1-5.1.2, Sec. 5.2.1): tile
+// staging, the level passes (hi_passes.cuh), and the epilogue that stores the
+// owned codes and anchors, appends the outliers and counts the histogram.
+#include "hi_passes.cuh"
+
+namespace hi {
+
+// ---------------------------------------------------------------------------
+// Predict + quantize
+// ---------------------------------------------------------------------------
+template <int A>
+__global__ void __launch_bounds__(kMaxThreads, 6)
+    k_compress(const __grid_constant__ CUtensorMap tmap, const FieldGeo g, const float* __restrict__ x,
+               uint8_t* __restrict__ codes, float* __restrict__ anchors, uint32_t* __restrict__ out_idx,
+               float* __restrict__ out_val, const uint64_t out_cap, uint32_t* __restrict__ hist_g,
+               float* __restrict__ recon_g, hi_header* __restrict__ hdr, uint32_t* __restrict__ queue,
+               const uint32_t tma_bytes, const int flags)
+{
+    using Lw = Lay<A>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const bool dbuf = flags & kFlagDoubleBuf;
+    const int vb_bytes = vbuf_bytes<A>(g.b0);
+    float* vbuf[2] = {reinterpret_cast<float*>(smem), reinterpret_cast<float*>(smem + (dbuf ? vb_bytes : 0))};
+    uint8_t* cs = smem + (dbuf ? 2 : 1) * vb_bytes;
+    uint16_t* hc = reinterpret_cast<uint16_t*>(cs + round128(g.b0 * Lw::P * Lw::CXC));  // [kHistBins][threads]
+    __shared__ uint32_t s_hist[256];
+    __shared__ __align__(8) uint64_t s_mbar[2];
+    __shared__ hi_level s_lv[HI_MAX_LEVELS];
+    __shared__ int s_sel[HI_MAX_LEVELS];
+    __shared__ int s_next;
+    __shared__ TileInfo s_ti[2];  // this tile's geometry and the next one's (thread 0 decodes)
+
+    const int tid = threadIdx.x;
+    const bool use_tma = flags & kFlagTma;
+    {   // an earlier stage failed (bad range, device-side EINVAL): leave outputs untouched
+        const uint32_t st = hdr->status;
+        if (__syncthreads_or(st != 0 && st != HI_ECAPACITY)) return;
+    }
+    Hot h;
+    h.eb_f = hdr->eb_f;
+    h.ebx2_f = hdr->ebx2_f;
+    h.r_f = hdr->r_f;
+    const bool hist_on = hist_g != nullptr;
+
+    for (int i = tid; i < 256; i += blockDim.x) s_hist[i] = 0;
+    if (hist_on)
+        for (int k = 0; k < kHistBins; ++k) hc[k * blockDim.x + tid] = 0;
+    if (tid < HI_MAX_LEVELS) {
+        s_lv[tid] = hdr->level[tid];
+        s_sel[tid] = perm_sel(s_lv[tid]);
+    }
+    if (tid == 0) {
+        mbar_init(&s_mbar[0], 1);
+        mbar_init(&s_mbar[1], 1);
+        fence_mbar_init();
+        if ((int)blockIdx.x < g.ntiles) s_ti[0] = tile_info<A>(g, blockIdx.x);
+        if (use_tma) {
+            prefetch_tmap(&tmap);
+            if ((int)blockIdx.x < g.ntiles) tma_issue(vbuf[0], &tmap, g, blockIdx.x, A, &s_mbar[0], tma_bytes);
+        }
+    }
+    __syncthreads();
+    const bool full_ok = HasFull<A>::value && g.n[0] > 1 && g.n[1] > 1 && g.n[2] > 1;
+
+    // tiles after each CTA's first come from a queue in ascending order: the
+    // load stays balanced (edge tiles cost more) and neighbouring tiles, which
+    // share faces, are in flight together
+    int it = 0;
+    for (int tile = blockIdx.x; tile < g.ntiles; ++it) {
+        const int buf = dbuf ? (it & 1) : 0;
+        float* v = vbuf[buf];
+        const TileInfo ti = s_ti[it & 1];
+        if (tid == 0) {
+            const int nx = (int)gridDim.x + (int)atomicAdd(queue, 1u);
+            s_next = nx;
+            if (nx < g.ntiles) s_ti[(it + 1) & 1] = tile_info<A>(g, nx);
+            if (use_tma && dbuf && nx < g.ntiles)
+                tma_issue(vbuf[buf ^ 1], &tmap, g, nx, A, &s_mbar[buf ^ 1], tma_bytes);
+            if (use_tma && !dbuf && it > 0) tma_issue(v, &tmap, g, tile, A, &s_mbar[0], tma_bytes);
+        }
+        if (tid < 8) {  // anchors keep the zero-error code
+            const int a0 = (tid >> 2) & 1, a1 = (tid >> 1) & 1, a2 = tid & 1;
+            if (a0 * A <= ti.e[0] && a1 * A <= ti.e[1] && a2 * A <= ti.e[2])
+                cs[a0 * A * Lw::CYC + a1 * A * Lw::CXC + a2 * A] = (uint8_t)kRadius;
+        }
+        if (use_tma) {
+            const bool ok = mbar_wait(&s_mbar[buf], dbuf ? ((it >> 1) & 1) : (it & 1), kSpinLimit);
+            if (!__syncthreads_and(ok)) {
+                if (tid == 0) set_status(&hdr->status, HI_ETIMEOUT);
+                if (dbuf && s_next < g.ntiles) mbar_wait(&s_mbar[buf ^ 1], ((it + 1) >> 1) & 1, kSpinLimit);
+                return;
+            }
+        } else {
+            load_tile_plain<A>(v, x, g, ti);
+            __syncthreads();
+        }
+        const int next = s_next;
+        const bool full = full_ok && ti.e[0] == A && ti.e[1] == A && ti.e[2] == A;
+        if constexpr (HasFull<A>::value) {
+            if (full)
+                levels_full<A, TileGeom<A>::L - 1, true>(s_sel, v, cs, h);
+            else
+                levels_ragged<A, TileGeom<A>::L - 1, true>(s_lv, v, cs, h, ti);
+        } else {
+            levels_ragged<A, TileGeom<A>::L - 1, true>(s_lv, v, cs, h, ti);
+        }
+
+        // ---- epilogue: owned codes, histogram and outliers; recon; anchors
+        const int own0 = ti.own[0] + 1, own1 = ti.own[1] + 1, own2 = ti.own[2] + 1;
+        const int rows = own0 * own1;
+        const bool vec_codes = (flags & kFlagVecCodes) && own2 == A && A >= 8;
+        if (vec_codes) {
+            constexpr int CH = (A >= 16) ? 4 : 2;  // words per global vector store
+            constexpr int NCH = (A >= 8) ? A / (4 * CH) : 1;
+            const bool square = own0 == A && own1 == A;  // rows decompose with shifts
+            const int items = rows * NCH;
+            for (int i0 = 0; i0 < items; i0 += blockDim.x) {
+                const int i = i0 + tid;
+                const bool act = i < items;
+                const int row = act ? i / NCH : 0, ch = act ? i - row * NCH : 0;
+                const int c0 = square ? row / A : row / own1;
+                const int c1 = row - c0 * (square ? A : own1);
+                const uint32_t* src = reinterpret_cast<const uint32_t*>(cs + c0 * Lw::CYC + c1 * Lw::CXC) + ch * CH;
+                uint8_t* dst = codes + ((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2] +
+                               ch * CH * 4;
+                uint32_t w[4];
+                uint32_t z = 0;  // nonzero iff some code of the chunk is 0 (an outlier)
+#pragma unroll
+                for (int j = 0; j < CH; ++j) {
+                    w[j] = src[j];
+                    z |= (w[j] - 0x01010101u) & ~w[j] & 0x80808080u;
+                }
+                if (act) {
+                    if constexpr (CH == 4)
+                        *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+                    else
+                        *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
+                }
+                if (__any_sync(0xffffffffu, act && z != 0)) {
+#pragma unroll
+                    for (int b = 0; b < 4 * CH; ++b) {
+                        const int code = (w[b >> 2] >> (8 * (b & 3))) & 0xff;
+                        outlier_append<A>(act && code == 0, c0 * Lw::PY + c1 * Lw::PX + ch * CH * 4 + b, v, hdr,
+                                          out_idx, out_val, out_cap, g, ti.o);
+                    }
+                }
+                if (hist_on) {
+#pragma unroll
+                    for (int b = 0; b < 4 * CH; ++b) hist_count(hc, s_hist, (w[b >> 2] >> (8 * (b & 3))) & 0xff, act);
+                }
+            }
+        } else {
+            const int items = rows * own2;
+            for (int i0 = 0; i0 < items; i0 += blockDim.x) {
+                const int i = i0 + tid;
+                const bool act = i < items;
+                const int row = act ? i / own2 : 0, c2 = act ? i - row * own2 : 0;
+                const int c0 = row / own1, c1 = row - c0 * own1;
+                const int code = cs[c0 * Lw::CYC + c1 * Lw::CXC + c2];
+                if (act)
+                    codes[((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2] + c2] =
+                        (uint8_t)code;
+                if (hist_on) hist_count(hc, s_hist, code, act);
+                outlier_append<A>(act && code == 0, c0 * Lw::PY + c1 * Lw::PX + c2, v, hdr, out_idx, out_val, out_cap,
+                                  g, ti.o);
+            }
+        }
+        if (recon_g) {
+            const int items = rows * own2;
+            for (int i = tid; i < items; i += blockDim.x) {
+                const int row = i / own2, c2 = i - row * own2;
+                const int c0 = row / own1, c1 = row - c0 * own1;
+                recon_g[((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2] + c2] =
+                    v[c0 * Lw::PY + c1 * Lw::PX + c2];
+            }
+        }
+        if (tid < 8) {  // owned anchors, verbatim (Sec. 3.2)
+            const int a0 = (tid >> 2) & 1, a1 = (tid >> 1) & 1, a2 = tid & 1;
+            const int l0 = a0 * A, l1 = a1 * A, l2 = a2 * A;
+            if (l0 <= ti.own[0] && l1 <= ti.own[1] && l2 <= ti.own[2]) {
+                const int64_t ai = ((int64_t)(ti.o[0] / A + a0) * g.na[1] + (ti.o[1] / A + a1)) * g.na[2] +
+                                   (ti.o[2] / A + a2);
+                anchors[ai] = v[l0 * Lw::PY + l1 * Lw::PX + l2];
+                if (hist_on) atomicSub(&s_hist[kRadius], 1u);  // anchors are not predicted
+            }
+        }
+        // keep the buffers until every thread is done; order the generic-proxy
+        // writes above before the TMA overwrite of this buffer
+        fence_proxy_async_smem();
+        __syncthreads();
+        tile = next;
+    }
+    if (hist_on) {
+        for (int k = 0; k < kHistBins; ++k) {  // fold this thread's counters, a warp at a time
+            uint32_t c = hc[k * blockDim.x + tid];
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+            if ((tid & 31) == 0) atomicAdd(&s_hist[kHistLo + k], c);
+        }
+        __syncthreads();
+        for (int i = tid; i < 256; i += blockDim.x)
+            if (s_hist[i]) atomicAdd(&hist_g[i], s_hist[i]);
+    }
+}
+
+template <int A>
+static cudaError_t launch_compress_t(const CompressLaunch& c, cudaStream_t st)
+{
+    auto kern = k_compress<A>;
+    const bool dbuf = c.buffers == 2 && fits_double(kern, compress_smem_t<A>(c.g.b0, true, c.threads));
+    const size_t smem = compress_smem_t<A>(c.g.b0, dbuf, c.threads);
+    int grid = 0;
+    cudaError_t err = persistent_grid(kern, c.threads, smem, c.num_sms, c.g.ntiles, c.max_ctas, &grid);
+    if (err != cudaSuccess) return err;
+    kern<<<grid, c.threads, smem, st>>>(c.tmap, c.g, c.x, c.codes, c.anchors, c.out_idx, c.out_val, c.out_cap,
+                                        c.hist, c.recon, c.hdr, c.queue, c.tma_bytes,
+                                        c.flags | (dbuf ? kFlagDoubleBuf : 0));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compress(int A, const CompressLaunch& c, cudaStream_t st)
+{
+    switch (A) {
+    case 2: return launch_compress_t<2>(c, st);
+    case 4: return launch_compress_t<4>(c, st);
+    case 8: return launch_compress_t<8>(c, st);
+    case 16: return launch_compress_t<16>(c, st);
+    case 32: return launch_compress_t<32>(c, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+size_t compress_smem_bytes(int A, int b0)
+{
+    switch (A) {
+    case 2: return compress_smem_t<2>(b0, false, 256);
+    case 4: return compress_smem_t<4>(b0, false, 256);
+    case 8: return compress_smem_t<8>(b0, false, 256);
+    case 16: return compress_smem_t<16>(b0, false, 256);
+    case 32: return compress_smem_t<32>(b0, false, 256);
+    default: return 0;
+    }
+}
+
+}  // namespace hi

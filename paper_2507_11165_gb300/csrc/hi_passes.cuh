@@ -1,0 +1,549 @@
+// hi_passes.cuh -- the tile machinery shared by the fused interpolation-predict
+// + quantize kernel and its inverse, the level-by-level reconstruction (cuSZ-Hi, arXiv 2507.11165,
+// Sec. 3.2, Sec. 5.1.1-5.1.2, Sec. 5.2.1).
+//
+// Persistent CTAs take blocks ("tiles") of (A+1)^d points from a queue in
+// ascending order.  A tile is staged in shared memory by one 3D TMA box load
+// (plain loads when the field's strides do not meet the TMA rules); with two
+// tile buffers the next tile's load is in flight while the current one is
+// processed.  Every level (stride S = A/2 .. 1) runs its three 1D passes in
+// the configured dimension sequence; predictions read values already
+// reconstructed in shared memory (closed loop), so the decompressor repeats
+// exactly the same arithmetic.
+//
+// Pass geometry is compile-time wherever possible: every (level, spline,
+// pass dimension) is its own instantiation.
+//   * full 3D tiles (extent A in every dim, A = 8 or 16) -- the bulk of any
+//     large field -- also fix the dimension sequence at compile time, so line
+//     counts, stencil cases and shared-memory offsets are constants;
+//   * all other tiles (ragged field edges, 1D/2D fields, other A) take the
+//     extents at run time.
+// Passes along the contiguous dim move whole rows with 16-byte shared-memory
+// accesses (conflict-free at the 16-byte-multiple, odd-word row pitch);
+// passes along the other dims give each thread one line, lanes adjacent along
+// the contiguous dim.
+//
+// Shared faces between tiles are computed by both tiles with identical
+// results; only the owning tile (the one with the lower block index, or the
+// last block for the field's upper face) writes codes, histogram counts,
+// outliers and reconstructed values.  Codes are staged in shared memory and
+// leave the tile in its epilogue, which also finds the outliers (code 0) and
+// counts the histogram.
+#pragma once
+#include <cstdint>
+
+#include "hi_device.cuh"
+#include "hi_internal.h"
+
+namespace hi {
+
+constexpr int kMaxThreads = 128;  // CTA size cap: one 17^3 tile per CTA keeps 128 threads busy
+
+// Shared-memory layouts of one tile (planes b0 = A+1, or 1 for 1D/2D fields).
+template <int A>
+struct Lay {
+    using TG = TileGeom<A>;
+    static constexpr int P = A + 1;
+    static constexpr int PX = TG::PX;   // floats per row (16-byte multiple)
+    static constexpr int PY = P * PX;   // floats per plane
+    static constexpr int CXC = PX;      // compress code staging: bytes per row
+    static constexpr int CYC = P * CXC;
+    static constexpr int CXD = TG::CX;  // decompress codes (TMA box rows, 16-byte multiple)
+    static constexpr int CYD = P * CXD;
+};
+
+__host__ __device__ constexpr int round128(int b) { return (b + 127) / 128 * 128; }
+
+template <int A>
+__host__ __device__ constexpr int vbuf_bytes(int b0)
+{
+    return round128(b0 * Lay<A>::P * Lay<A>::PX * 4);
+}
+
+struct TileInfo {
+    int o[3];    // origin (global coords)
+    int e[3];    // extent: last local coordinate per dim (0 for inactive dims)
+    int own[3];  // last owned local coordinate per dim
+};
+
+template <int A>
+__device__ __forceinline__ TileInfo tile_info(const FieldGeo& g, int tile)
+{
+    TileInfo ti;
+    int t[3];
+    tile_coords(g, tile, t);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        ti.o[d] = t[d] * A;
+        const int rem = (int)(g.n[d] - 1 - ti.o[d]);
+        ti.e[d] = (g.n[d] == 1) ? 0 : (rem < A ? rem : A);
+        ti.own[d] = (t[d] == g.nb[d] - 1) ? ti.e[d] : A - 1;
+    }
+    return ti;
+}
+
+// Global linear index of a float offset in the tile buffer.
+template <int A>
+__device__ __forceinline__ int64_t global_index(const FieldGeo& g, const int o[3], int vi)
+{
+    constexpr int PY = Lay<A>::PY, PX = Lay<A>::PX;
+    const int c0 = vi / PY;
+    const int rem = vi - c0 * PY;
+    const int c1 = rem / PX;
+    const int c2 = rem - c1 * PX;
+    return ((int64_t)(o[0] + c0) * g.n[1] + (o[1] + c1)) * g.n[2] + (o[2] + c2);
+}
+
+// Values every point needs, passed by value; the decompressor's rare outlier
+// read goes through shared memory so that no pass keeps it in registers.
+struct Hot {
+    float eb_f, ebx2_f, r_f;
+};
+
+struct Rare {
+    const float* out;  // decompress: outlier values were scattered here beforehand
+    FieldGeo g;
+    int o[3];
+};
+
+__shared__ Rare s_rare;
+
+template <int A>
+__device__ __noinline__ float outlier_value(int vi)
+{
+    return s_rare.out[global_index<A>(s_rare.g, s_rare.o, vi)];
+}
+
+// compress: quantize x against p, stage the code, return the reconstruction
+__device__ __forceinline__ float point_compress(const Hot& h, float xv, float pr, uint8_t* code_slot)
+{
+    float xr;
+    *code_slot = (uint8_t)quantize(xv, pr, h.eb_f, h.ebx2_f, h.r_f, xr);
+    return xr;
+}
+
+// decompress: the reconstruction from the staged code
+template <int A>
+__device__ __forceinline__ float point_decompress(const Hot& h, int code, float pr, int vi)
+{
+    float xr = dequantize(code, pr, h.ebx2_f);
+    if (code == 0) xr = outlier_value<A>(vi);
+    return xr;
+}
+
+// ---------------------------------------------------------------------------
+// Passes.  A pass along D predicts, on every line parallel to D, the points
+// at odd multiples of S from the nodes at even multiples (stencil cases from
+// the extent ED of the line).  Lines are indexed by the two other dims,
+// stepping by STQ / STR.
+// ---------------------------------------------------------------------------
+// Line index -> (jq, jr) for nr lines along R.  With run-time line counts the
+// quotient comes from a float reciprocal: for line < 2^16 and nr <= 64 the
+// product is within 1e-3 of the exact quotient, whose fractional part stays
+// at least 1/(2 nr) away from an integer, so the truncation is exact.
+template <bool RT>
+__device__ __forceinline__ int line_q(int line, int nr, float inv_nr)
+{
+    if constexpr (RT)
+        return (int)__fmul_rn(__fadd_rn((float)line, 0.5f), inv_nr);
+    else
+        return line / nr;
+}
+
+// ED: the pass dim's extent when known at compile time (A for a whole tile,
+// A-1 for the usual ragged edge), 0 when it is only known at run time.
+template <int A, int S, int D, bool CUBIC, bool COMP, int ED, bool RT>
+__device__ __forceinline__ void pass_cols(float* __restrict__ v, uint8_t* __restrict__ cs, const Hot h, int stq,
+                                          int str, int nq, int nr, int ed_rt)
+{
+    static_assert(D == 0 || D == 1, "columns");
+    using Lw = Lay<A>;
+    constexpr int Q = (D == 0) ? 1 : 0;  // the other two dims: Q and 2
+    constexpr int NDM = A / (2 * S);
+    constexpr int VPD = (D == 0 ? Lw::PY : Lw::PX) * S, VPQ = (Q == 0 ? Lw::PY : Lw::PX);
+    constexpr int CX = COMP ? Lw::CXC : Lw::CXD, CY = COMP ? Lw::CYC : Lw::CYD;
+    constexpr int CPD = (D == 0 ? CY : CX) * S, CPQ = (Q == 0 ? CY : CX);
+    const int ed = ED ? ED : ed_rt;
+    const int nd = (ed >= S) ? ((ed - S) / (2 * S) + 1) : 0;
+    const int nl = nq * nr;
+    const float inv_nr = RT ? __frcp_rn((float)nr) : 0.0f;
+    if constexpr (ED == A && NDM >= 4) {
+        // whole line: first and last points peeled, the interior loops over
+        // the cubic (or linear) midpoint with the nodes sliding through registers
+        for (int line = threadIdx.x; line < nl; line += blockDim.x) {
+            const int jq = line_q<RT>(line, nr, inv_nr), jr = line - jq * nr;
+            const int cq = jq * stq, cr = jr * str;
+            const int vb = cq * VPQ + cr, cb = cq * CPQ + cr;
+            float fa = 0.0f, fb = v[vb], fu = v[vb + 2 * VPD], fv = v[vb + 4 * VPD];
+            auto point = [&](int k, float pr) {
+                const int vi = vb + (2 * k + 1) * VPD;
+                if constexpr (COMP)
+                    v[vi] = point_compress(h, v[vi], pr, cs + cb + (2 * k + 1) * CPD);
+                else
+                    v[vi] = point_decompress<A>(h, cs[cb + (2 * k + 1) * CPD], pr, vi);
+            };
+            point(0, predict(CUBIC, false, true, true, 0.0f, fb, fu, fv));
+#pragma unroll 2
+            for (int k = 1; k <= NDM - 2; ++k) {
+                fa = fb, fb = fu, fu = fv;
+                fv = v[vb + (2 * k + 4) * VPD];
+                point(k, predict(CUBIC, true, true, true, fa, fb, fu, fv));
+            }
+            point(NDM - 1, predict(CUBIC, true, true, false, fb, fu, fv, 0.0f));
+        }
+        return;
+    }
+    for (int line = threadIdx.x; line < nl; line += blockDim.x) {
+        const int jq = line_q<RT>(line, nr, inv_nr), jr = line - jq * nr;
+        const int cq = jq * stq, cr = jr * str;
+        const int vb = cq * VPQ + cr, cb = cq * CPQ + cr;
+        float f[NDM + 1];  // known nodes at even multiples of S along D
+#pragma unroll
+        for (int m = 0; m <= NDM; ++m) f[m] = (2 * m * S <= ed) ? v[vb + 2 * m * VPD] : 0.0f;
+#pragma unroll
+        for (int k = 0; k < NDM; ++k) {
+            if (k >= nd) break;
+            const int c = (2 * k + 1) * S;
+            const bool have_r = c + S <= ed;
+            const bool have_r3 = c + 3 * S <= ed;
+            const float pr = predict(CUBIC, k >= 1, have_r, have_r3, k >= 1 ? f[k - 1] : 0.0f, f[k],
+                                     have_r ? f[k + 1] : 0.0f, (k + 2 <= NDM && have_r3) ? f[k + 2] : 0.0f);
+            const int vi = vb + (2 * k + 1) * VPD;
+            if constexpr (COMP) {
+                v[vi] = point_compress(h, v[vi], pr, cs + cb + (2 * k + 1) * CPD);
+            } else {
+                v[vi] = point_decompress<A>(h, cs[cb + (2 * k + 1) * CPD], pr, vi);
+            }
+        }
+    }
+}
+
+// Pass along dim 2: one row per thread, moved with 16-byte accesses.
+template <int A, int S, bool CUBIC, bool COMP, int ED, bool RT>
+__device__ __forceinline__ void pass_rows(float* __restrict__ v, uint8_t* __restrict__ cs, const Hot h, int stq,
+                                          int str, int nq, int nr, int ed_rt)
+{
+    using Lw = Lay<A>;
+    constexpr int NDM = A / (2 * S);
+    constexpr int NV = A / 4;  // float4 chunks of a row; elements 4*NV .. A one by one
+    constexpr int CX = COMP ? Lw::CXC : Lw::CXD, CY = COMP ? Lw::CYC : Lw::CYD;
+    constexpr int NCW = (A + 4) / 4;  // code words covering positions 0..A
+    const int ed = ED ? ED : ed_rt;
+    const int nd = (ed >= S) ? ((ed - S) / (2 * S) + 1) : 0;
+    const int nl = nq * nr;
+    const float inv_nr = RT ? __frcp_rn((float)nr) : 0.0f;
+    for (int line = threadIdx.x; line < nl; line += blockDim.x) {
+        const int jq = line_q<RT>(line, nr, inv_nr), jr = line - jq * nr;
+        const int c0 = jq * stq, c1 = jr * str;
+        float* row = v + c0 * Lw::PY + c1 * Lw::PX;
+        const int cb = c0 * CY + c1 * CX;
+        float r[A + 1];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            const float4 q = reinterpret_cast<const float4*>(row)[j];
+            r[4 * j] = q.x, r[4 * j + 1] = q.y, r[4 * j + 2] = q.z, r[4 * j + 3] = q.w;
+        }
+#pragma unroll
+        for (int j = 4 * NV; j <= A; ++j) r[j] = row[j];
+        uint32_t cw[(NCW + 3) / 4 * 4];  // decompress: the row's codes, 4 per word
+        if constexpr (!COMP) {
+            const uint4* cwp = reinterpret_cast<const uint4*>(cs + cb);
+#pragma unroll
+            for (int j = 0; j < (NCW + 3) / 4; ++j) {
+                const uint4 q = cwp[j];
+                cw[4 * j] = q.x, cw[4 * j + 1] = q.y, cw[4 * j + 2] = q.z, cw[4 * j + 3] = q.w;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NDM; ++k) {
+            if (k >= nd) break;
+            const int c = (2 * k + 1) * S;
+            const bool have_r = c + S <= ed;
+            const bool have_r3 = c + 3 * S <= ed;
+            const float pr = predict(CUBIC, k >= 1, have_r, have_r3, k >= 1 ? r[c - 3 * S] : 0.0f, r[c - S],
+                                     have_r ? r[c + S] : 0.0f, (c + 3 * S <= A && have_r3) ? r[c + 3 * S] : 0.0f);
+            if constexpr (COMP) {
+                r[c] = point_compress(h, r[c], pr, cs + cb + c);
+            } else {
+                r[c] = point_decompress<A>(h, (cw[c >> 2] >> (8 * (c & 3))) & 0xff, pr,
+                                           c0 * Lw::PY + c1 * Lw::PX + c);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < NV; ++j)
+            reinterpret_cast<float4*>(row)[j] = make_float4(r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
+#pragma unroll
+        for (int j = 4 * NV; j < A; ++j) row[j] = r[j];
+    }
+}
+
+template <int A, int S, int D, bool CUBIC, bool COMP, int ED, bool RT>
+__device__ __forceinline__ void pass_any(float* v, uint8_t* cs, const Hot h, int stq, int str, int nq, int nr,
+                                         int ed)
+{
+    if constexpr (D == 2)
+        pass_rows<A, S, CUBIC, COMP, ED, RT>(v, cs, h, stq, str, nq, nr, ed);
+    else
+        pass_cols<A, S, D, CUBIC, COMP, ED, RT>(v, cs, h, stq, str, nq, nr, ed);
+}
+
+// ---------------------------------------------------------------------------
+// Full 3D tiles: the whole level at compile time
+// ---------------------------------------------------------------------------
+// Step of dim DIM in pass PASS of a level with sequence (D0, D1, D2): dims
+// refined earlier in this level step by S, later ones by 2S.
+template <int D0, int D1, int D2, int DIM, int PASS, int S>
+__host__ __device__ constexpr int step_of()
+{
+    return ((DIM == D0 ? 0 : (DIM == D1 ? 1 : 2)) < PASS) ? S : 2 * S;
+}
+
+template <int A, int S, int D, int PASS, int D0, int D1, int D2, bool CUBIC, bool COMP>
+__device__ __forceinline__ void pass_full(float* v, uint8_t* cs, const Hot h)
+{
+    constexpr int Q = (D == 0) ? 1 : 0, R = (D == 2) ? 1 : 2;
+    constexpr int STQ = step_of<D0, D1, D2, Q, PASS, S>(), STR = step_of<D0, D1, D2, R, PASS, S>();
+    pass_any<A, S, D, CUBIC, COMP, A, false>(v, cs, h, STQ, STR, A / STQ + 1, A / STR + 1, A);
+}
+
+template <int A, int S, int D0, int D1, int D2, bool CUBIC, bool COMP>
+__device__ __forceinline__ void level_full(float* v, uint8_t* cs, const Hot h)
+{
+    pass_full<A, S, D0, 0, D0, D1, D2, CUBIC, COMP>(v, cs, h);
+    __syncthreads();
+    pass_full<A, S, D1, 1, D0, D1, D2, CUBIC, COMP>(v, cs, h);
+    __syncthreads();
+    pass_full<A, S, D2, 2, D0, D1, D2, CUBIC, COMP>(v, cs, h);
+    __syncthreads();
+}
+
+// sel = 2 * perm + cubic; perm: 0 (0,1,2) 1 (0,2,1) 2 (1,0,2) 3 (1,2,0) 4 (2,0,1) 5 (2,1,0)
+template <int A, int S, bool COMP>
+__device__ __forceinline__ void level_dispatch(int sel, float* v, uint8_t* cs, const Hot h)
+{
+    switch (sel) {
+    case 0: level_full<A, S, 0, 1, 2, false, COMP>(v, cs, h); break;
+    case 1: level_full<A, S, 0, 1, 2, true, COMP>(v, cs, h); break;
+    case 2: level_full<A, S, 0, 2, 1, false, COMP>(v, cs, h); break;
+    case 3: level_full<A, S, 0, 2, 1, true, COMP>(v, cs, h); break;
+    case 4: level_full<A, S, 1, 0, 2, false, COMP>(v, cs, h); break;
+    case 5: level_full<A, S, 1, 0, 2, true, COMP>(v, cs, h); break;
+    case 6: level_full<A, S, 1, 2, 0, false, COMP>(v, cs, h); break;
+    case 7: level_full<A, S, 1, 2, 0, true, COMP>(v, cs, h); break;
+    case 8: level_full<A, S, 2, 0, 1, false, COMP>(v, cs, h); break;
+    case 9: level_full<A, S, 2, 0, 1, true, COMP>(v, cs, h); break;
+    case 10: level_full<A, S, 2, 1, 0, false, COMP>(v, cs, h); break;
+    default: level_full<A, S, 2, 1, 0, true, COMP>(v, cs, h); break;
+    }
+}
+
+template <int A, int LV, bool COMP>
+__device__ __forceinline__ void levels_full(const int* s_sel, float* v, uint8_t* cs, const Hot h)
+{
+    level_dispatch<A, (1 << LV), COMP>(s_sel[LV], v, cs, h);
+    if constexpr (LV > 0) levels_full<A, LV - 1, COMP>(s_sel, v, cs, h);
+}
+
+__device__ __forceinline__ int perm_sel(const hi_level& lv)
+{
+    const int a = lv.order[0], b = lv.order[1];
+    const int p = (a == 0) ? (b == 1 ? 0 : 1) : (a == 1) ? (b == 0 ? 2 : 3) : (b == 0 ? 4 : 5);
+    return 2 * p + (lv.interp == HI_CUBIC ? 1 : 0);
+}
+
+template <int A>
+struct HasFull {
+    static constexpr bool value = (A == 8 || A == 16);
+};
+
+// ---------------------------------------------------------------------------
+// Other tiles: extents at run time, one instantiation per (level, dim, spline)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int pick3(const int a[3], int i) { return i == 0 ? a[0] : (i == 1 ? a[1] : a[2]); }
+
+template <int A, int S, int D, bool COMP, int ED>
+__device__ __forceinline__ void pass_spline(bool cubic, float* v, uint8_t* cs, const Hot h, int stq, int str, int nq,
+                                            int nr, int ed)
+{
+    if (cubic)
+        pass_any<A, S, D, true, COMP, ED, true>(v, cs, h, stq, str, nq, nr, ed);
+    else
+        pass_any<A, S, D, false, COMP, ED, true>(v, cs, h, stq, str, nq, nr, ed);
+}
+
+template <int A, int S, int D, bool COMP>
+__device__ __forceinline__ void pass_dispatch(bool cubic, float* v, uint8_t* cs, const Hot h, int stq, int str,
+                                              int nq, int nr, int ed)
+{
+    if (ed == A)  // the pass dim is whole: only the line counts are shorter
+        pass_spline<A, S, D, COMP, A>(cubic, v, cs, h, stq, str, nq, nr, ed);
+    else if (ed == A - 1)  // the usual ragged edge (n - 1 = -1 mod A), stencil cases fixed too
+        pass_spline<A, S, D, COMP, A - 1>(cubic, v, cs, h, stq, str, nq, nr, ed);
+    else
+        pass_spline<A, S, D, COMP, 0>(cubic, v, cs, h, stq, str, nq, nr, ed);
+}
+
+template <int A, int LV, bool COMP>
+__device__ __forceinline__ void level_ragged(const hi_level lv, float* v, uint8_t* cs, const Hot h, int e0, int e1,
+                                          int e2)
+{
+    constexpr int S = 1 << LV;
+    const bool cubic = lv.interp == HI_CUBIC;
+    const int e[3] = {e0, e1, e2};
+    for (int p = 0; p < 3; ++p) {
+        const int d = lv.order[p];
+        const int q = (d == 0) ? 1 : 0, r = (d == 2) ? 1 : 2;
+        const int posq = (lv.order[0] == q) ? 0 : ((lv.order[1] == q) ? 1 : 2);
+        const int posr = (lv.order[0] == r) ? 0 : ((lv.order[1] == r) ? 1 : 2);
+        const int stq = (posq < p) ? S : 2 * S, str = (posr < p) ? S : 2 * S;
+        const int ed = pick3(e, d);
+        if (ed < S) continue;  // no point on this pass (CTA-uniform)
+        const int nq = pick3(e, q) / stq + 1, nr = pick3(e, r) / str + 1;
+        if (d == 0)
+            pass_dispatch<A, S, 0, COMP>(cubic, v, cs, h, stq, str, nq, nr, ed);
+        else if (d == 1)
+            pass_dispatch<A, S, 1, COMP>(cubic, v, cs, h, stq, str, nq, nr, ed);
+        else
+            pass_dispatch<A, S, 2, COMP>(cubic, v, cs, h, stq, str, nq, nr, ed);
+        __syncthreads();
+    }
+}
+
+template <int A, int LV, bool COMP>
+__device__ __forceinline__ void levels_ragged(const hi_level* s_lv, float* v, uint8_t* cs, const Hot h,
+                                              const TileInfo& ti)
+{
+    level_ragged<A, LV, COMP>(s_lv[LV], v, cs, h, ti.e[0], ti.e[1], ti.e[2]);
+    if constexpr (LV > 0) levels_ragged<A, LV - 1, COMP>(s_lv, v, cs, h, ti);
+}
+
+// ---------------------------------------------------------------------------
+// Staging
+// ---------------------------------------------------------------------------
+template <int A>
+__device__ void load_tile_plain(float* v, const float* __restrict__ x, const FieldGeo& g, const TileInfo& ti)
+{
+    using Lw = Lay<A>;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int rows = (ti.e[0] + 1) * (ti.e[1] + 1);
+    for (int rr = warp; rr < rows; rr += nw) {
+        const int c0 = rr / (ti.e[1] + 1);
+        const int c1 = rr - c0 * (ti.e[1] + 1);
+        const float* src = x + ((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2];
+        for (int c2 = lane; c2 <= ti.e[2]; c2 += 32) v[c0 * Lw::PY + c1 * Lw::PX + c2] = src[c2];
+    }
+}
+
+template <int A>
+__device__ void load_codes_plain(uint8_t* cs, const uint8_t* __restrict__ codes, const FieldGeo& g,
+                                 const TileInfo& ti)
+{
+    using Lw = Lay<A>;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int rows = (ti.e[0] + 1) * (ti.e[1] + 1);
+    for (int rr = warp; rr < rows; rr += nw) {
+        const int c0 = rr / (ti.e[1] + 1);
+        const int c1 = rr - c0 * (ti.e[1] + 1);
+        const uint8_t* src = codes + ((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2];
+        for (int c2 = lane; c2 <= ti.e[2]; c2 += 32) cs[c0 * Lw::CYD + c1 * Lw::CXD + c2] = src[c2];
+    }
+}
+
+__device__ __forceinline__ void tma_issue(void* dst, const CUtensorMap* map, const FieldGeo& g, int tile, int A,
+                                          uint64_t* mbar, uint32_t bytes)
+{
+    int t[3];
+    tile_coords(g, tile, t);
+    mbar_arrive_expect_tx(mbar, bytes);
+    tma_load_3d(dst, map, t[2] * A, t[1] * A, t[0] * A, mbar);
+}
+
+// ---------------------------------------------------------------------------
+// Epilogue helpers (all lanes of the warp call them)
+// ---------------------------------------------------------------------------
+// Outliers (code 0) of the tile, one candidate per lane: the warp reserves
+// its slots in the output list with one atomic and writes them.
+template <int A>
+__device__ __forceinline__ void outlier_append(bool is_out, int vi, const float* v, hi_header* hdr,
+                                               uint32_t* out_idx, float* out_val, uint64_t out_cap,
+                                               const FieldGeo& g, const int o[3])
+{
+    const unsigned m = __ballot_sync(0xffffffffu, is_out);
+    if (m == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader)
+        base = atomicAdd(reinterpret_cast<unsigned long long*>(&hdr->n_outliers), (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (!is_out) return;
+    const unsigned long long pos = base + __popc(m & ((1u << lane) - 1u));
+    if (pos < out_cap) {
+        out_idx[pos] = (uint32_t)global_index<A>(g, o, vi);
+        out_val[pos] = v[vi];
+    } else {
+        set_status(&hdr->status, HI_ECAPACITY);
+    }
+}
+
+// Histogram: codes 120..135 (the bulk at any practical error bound) go to
+// per-thread 16-bit counters laid out bin-major, so that a warp's updates hit
+// 32 consecutive half-words (no bank conflict, no atomics); other codes go
+// to shared-memory atomics.  Folded into the CTA histogram at kernel end.
+constexpr int kHistLo = 120, kHistBins = 16;
+
+__device__ __forceinline__ void hist_count(uint16_t* hc, uint32_t* s_hist, int code, bool valid)
+{
+    const unsigned k = (unsigned)(code - kHistLo);
+    if (valid) {
+        if (k < (unsigned)kHistBins)
+            hc[k * blockDim.x + threadIdx.x] += 1;
+        else
+            atomicAdd(&s_hist[code], 1u);
+    }
+}
+
+
+// Shared-memory footprint of the two kernels and the persistent launch.
+template <int A>
+size_t compress_smem_t(int b0, bool dbuf, int threads)
+{
+    return (dbuf ? 2 : 1) * (size_t)vbuf_bytes<A>(b0) + (size_t)round128(b0 * Lay<A>::P * Lay<A>::CXC) +
+           (size_t)kHistBins * threads * sizeof(uint16_t);
+}
+
+template <int A>
+size_t decompress_smem_t(int b0, bool dbuf)
+{
+    return (size_t)vbuf_bytes<A>(b0) + (dbuf ? 2 : 1) * (size_t)round128(b0 * Lay<A>::P * Lay<A>::CXD);
+}
+
+// Double buffering when both buffers and the kernel's static shared memory fit.
+template <typename K>
+static bool fits_double(K kern, size_t dyn_double)
+{
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
+    if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return false;
+    return dyn_double + fa.sharedSizeBytes <= (size_t)optin;
+}
+
+template <typename K>
+static cudaError_t persistent_grid(K kern, int threads, size_t smem, int num_sms, int ntiles, int max_ctas, int* grid)
+{
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) per_sm = 1;
+    int g = per_sm * num_sms;
+    if (g > ntiles) g = ntiles;
+    if (max_ctas > 0 && g > max_ctas) g = max_ctas;
+    *grid = g > 0 ? g : 1;
+    return cudaSuccess;
+}
+
+}  // namespace hi

@@ -126,7 +126,7 @@ def dims3(shape):
 def make_params(shape, eb, mode="rel", anchor_stride=16, autotune=True, levels=None, threads=0, buffers=0):
     """HiParams for a field of ``shape``.  ``levels``: list of (interp, order) per
     level (level l = stride 2^l), or one (interp, order) for every level.
-    ``threads`` (64/128/256) and ``buffers`` (1/2) pick the launch shape; 0 =
+    ``threads`` (64/128) and ``buffers`` (1/2) pick the launch shape; 0 =
     library default."""
     p = HiParams()
     for d, n in enumerate(dims3(shape)):
@@ -135,7 +135,7 @@ def make_params(shape, eb, mode="rel", anchor_stride=16, autotune=True, levels=N
     p.eb_mode = EB_REL if mode in ("rel", EB_REL) else EB_ABS
     p.anchor_stride = int(anchor_stride)
     p.autotune = 1 if autotune else 0
-    p.tuning = {0: 0, 64: 1, 128: 2, 256: 3}[int(threads)] | ({0: 0, 1: 1, 2: 2}[int(buffers)] << 2)
+    p.tuning = {0: 0, 64: 1, 128: 2}[int(threads)] | ({0: 0, 1: 1, 2: 2}[int(buffers)] << 2)
     L = max(1, int(anchor_stride).bit_length() - 1)
     if levels is None:
         levels = (CUBIC, (0, 1, 2))
