@@ -1,6 +1,7 @@
 // hi_decompress.cu -- the level-by-level reconstruction (cuSZ-Hi, arXiv
 // 2507.11165, Eq. 1, Sec. 3.2): staged code tiles, the level passes
 // (hi_passes.cuh) and the epilogue that stores the owned values.
+#define HI_LEVEL_FN __noinline__
 #include "hi_passes.cuh"
 
 namespace hi {

@@ -35,6 +35,12 @@
 #include "hi_device.cuh"
 #include "hi_internal.h"
 
+// Level functions are inlined into the compress kernel; the reconstruct
+// kernel keeps them as calls, which leaves it more registers per pass.
+#ifndef HI_LEVEL_FN
+#define HI_LEVEL_FN __forceinline__
+#endif
+
 namespace hi {
 
 constexpr int kMaxThreads = 128;  // CTA size cap: one 17^3 tile per CTA keeps 128 threads busy
@@ -307,7 +313,7 @@ __device__ __forceinline__ void pass_full(float* v, uint8_t* cs, const Hot h)
 }
 
 template <int A, int S, int D0, int D1, int D2, bool CUBIC, bool COMP>
-__device__ __forceinline__ void level_full(float* v, uint8_t* cs, const Hot h)
+__device__ HI_LEVEL_FN void level_full(float* v, uint8_t* cs, const Hot h)
 {
     pass_full<A, S, D0, 0, D0, D1, D2, CUBIC, COMP>(v, cs, h);
     __syncthreads();
@@ -384,7 +390,7 @@ __device__ __forceinline__ void pass_dispatch(bool cubic, float* v, uint8_t* cs,
 }
 
 template <int A, int LV, bool COMP>
-__device__ __forceinline__ void level_ragged(const hi_level lv, float* v, uint8_t* cs, const Hot h, int e0, int e1,
+__device__ HI_LEVEL_FN void level_ragged(const hi_level lv, float* v, uint8_t* cs, const Hot h, int e0, int e1,
                                           int e2)
 {
     constexpr int S = 1 << LV;
