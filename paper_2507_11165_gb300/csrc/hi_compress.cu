@@ -21,7 +21,8 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
     extern __shared__ __align__(128) unsigned char smem[];
     const bool dbuf = flags & kFlagDoubleBuf;
     const int vb_bytes = vbuf_bytes<A>(g.b0);
-    float* vbuf[2] = {reinterpret_cast<float*>(smem), reinterpret_cast<float*>(smem + (dbuf ? vb_bytes : 0))};
+    float* const vbuf0 = reinterpret_cast<float*>(smem);
+    float* const vbuf1 = reinterpret_cast<float*>(smem + (dbuf ? vb_bytes : 0));
     uint8_t* cs = smem + (dbuf ? 2 : 1) * vb_bytes;
     uint16_t* hc = reinterpret_cast<uint16_t*>(cs + round128(g.b0 * Lw::P * Lw::CXC));  // [kHistBins][threads]
     __shared__ uint32_t s_hist[256];
@@ -57,7 +58,7 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
         if ((int)blockIdx.x < g.ntiles) s_ti[0] = tile_info<A>(g, blockIdx.x);
         if (use_tma) {
             prefetch_tmap(&tmap);
-            if ((int)blockIdx.x < g.ntiles) tma_issue(vbuf[0], &tmap, g, blockIdx.x, A, &s_mbar[0], tma_bytes);
+            if ((int)blockIdx.x < g.ntiles) tma_issue(vbuf0, &tmap, g, blockIdx.x, A, &s_mbar[0], tma_bytes);
         }
     }
     __syncthreads();
@@ -69,14 +70,14 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
     int it = 0;
     for (int tile = blockIdx.x; tile < g.ntiles; ++it) {
         const int buf = dbuf ? (it & 1) : 0;
-        float* v = vbuf[buf];
+        float* v = buf ? vbuf1 : vbuf0;
         const TileInfo ti = s_ti[it & 1];
         if (tid == 0) {
             const int nx = (int)gridDim.x + (int)atomicAdd(queue, 1u);
             s_next = nx;
             if (nx < g.ntiles) s_ti[(it + 1) & 1] = tile_info<A>(g, nx);
             if (use_tma && dbuf && nx < g.ntiles)
-                tma_issue(vbuf[buf ^ 1], &tmap, g, nx, A, &s_mbar[buf ^ 1], tma_bytes);
+                tma_issue(buf ? vbuf0 : vbuf1, &tmap, g, nx, A, &s_mbar[buf ^ 1], tma_bytes);
             if (use_tma && !dbuf && it > 0) tma_issue(v, &tmap, g, tile, A, &s_mbar[0], tma_bytes);
         }
         if (tid < 8) {  // anchors keep the zero-error code

@@ -9,6 +9,18 @@ namespace hi {
 // ---------------------------------------------------------------------------
 // Reconstruct
 // ---------------------------------------------------------------------------
+// Corner anchor tid (0..7) of the tile at queue position pos, or 0.
+template <int A>
+__device__ __forceinline__ float anchor_of(const FieldGeo& g, const float* __restrict__ anchors, int pos,
+                                           const TileInfo& tn)
+{
+    const int tid = threadIdx.x;
+    if (tid >= 8 || pos >= g.ntiles) return 0.0f;
+    const int a0 = (tid >> 2) & 1, a1 = (tid >> 1) & 1, a2 = tid & 1;
+    if (a0 * A > tn.e[0] || a1 * A > tn.e[1] || a2 * A > tn.e[2]) return 0.0f;
+    return anchors[((int64_t)(tn.o[0] / A + a0) * g.na[1] + (tn.o[1] / A + a1)) * g.na[2] + (tn.o[2] / A + a2)];
+}
+
 template <int A>
 __global__ void __launch_bounds__(kMaxThreads, 6)
     k_decompress(const __grid_constant__ CUtensorMap cmap, const FieldGeo g, const uint8_t* __restrict__ codes,
@@ -22,7 +34,8 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
     const int cb_bytes = round128(g.b0 * Lw::P * Lw::CXD);
     const bool dbuf = flags & kFlagDoubleBuf;
     float* v = reinterpret_cast<float*>(smem);
-    uint8_t* cbuf[2] = {smem + vb_bytes, smem + vb_bytes + (dbuf ? cb_bytes : 0)};
+    uint8_t* const cbuf0 = smem + vb_bytes;
+    uint8_t* const cbuf1 = smem + vb_bytes + (dbuf ? cb_bytes : 0);
     __shared__ __align__(8) uint64_t s_mbar[2];
     __shared__ hi_level s_lv[HI_MAX_LEVELS];
     __shared__ int s_sel[HI_MAX_LEVELS];
@@ -51,25 +64,19 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
         if ((int)blockIdx.x < g.ntiles) s_ti[0] = tile_info<A>(g, blockIdx.x);
         if (use_tma) {
             prefetch_tmap(&cmap);
-            if ((int)blockIdx.x < g.ntiles) tma_issue(cbuf[0], &cmap, g, blockIdx.x, A, &s_mbar[0], tma_bytes);
+            if ((int)blockIdx.x < g.ntiles) tma_issue(cbuf0, &cmap, g, blockIdx.x, A, &s_mbar[0], tma_bytes);
         }
     }
     __syncthreads();
     const bool full_ok = HasFull<A>::value && g.n[0] > 1 && g.n[1] > 1 && g.n[2] > 1;
 
     // the 8 corner anchors of a tile, loaded one tile ahead by threads 0..7
-    auto anchor_of = [&](int pos, const TileInfo& tn) -> float {
-        if (tid >= 8 || pos >= g.ntiles) return 0.0f;
-        const int a0 = (tid >> 2) & 1, a1 = (tid >> 1) & 1, a2 = tid & 1;
-        if (a0 * A > tn.e[0] || a1 * A > tn.e[1] || a2 * A > tn.e[2]) return 0.0f;
-        return anchors[((int64_t)(tn.o[0] / A + a0) * g.na[1] + (tn.o[1] / A + a1)) * g.na[2] + (tn.o[2] / A + a2)];
-    };
-    float a_cur = anchor_of(blockIdx.x, s_ti[0]);
+    float a_cur = anchor_of<A>(g, anchors, blockIdx.x, s_ti[0]);
 
     int it = 0;
     for (int tile = blockIdx.x; tile < g.ntiles; ++it) {
         const int buf = dbuf ? (it & 1) : 0;
-        uint8_t* cs = cbuf[buf];
+        uint8_t* cs = buf ? cbuf1 : cbuf0;
         const TileInfo ti = s_ti[it & 1];
         if (tid == 0) {
             const int nx = (int)gridDim.x + (int)atomicAdd(queue, 1u);
@@ -77,7 +84,7 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
             if (nx < g.ntiles) s_ti[(it + 1) & 1] = tile_info<A>(g, nx);
             s_rare.o[0] = ti.o[0], s_rare.o[1] = ti.o[1], s_rare.o[2] = ti.o[2];
             if (use_tma && dbuf && nx < g.ntiles)
-                tma_issue(cbuf[buf ^ 1], &cmap, g, nx, A, &s_mbar[buf ^ 1], tma_bytes);
+                tma_issue(buf ? cbuf0 : cbuf1, &cmap, g, nx, A, &s_mbar[buf ^ 1], tma_bytes);
             if (use_tma && !dbuf && it > 0) tma_issue(cs, &cmap, g, tile, A, &s_mbar[0], tma_bytes);
         }
         if (tid < 8) {  // seed the anchors
@@ -97,7 +104,7 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
             __syncthreads();
         }
         const int next = s_next;
-        const float a_nxt = anchor_of(next, s_ti[(it + 1) & 1]);  // in flight while this tile is reconstructed
+        const float a_nxt = anchor_of<A>(g, anchors, next, s_ti[(it + 1) & 1]);  // in flight while this tile is reconstructed
         const bool full = full_ok && ti.e[0] == A && ti.e[1] == A && ti.e[2] == A;
         if constexpr (HasFull<A>::value) {
             if (full)

@@ -143,6 +143,17 @@ __device__ __forceinline__ float point_decompress(const Hot& h, int code, float 
 // the extent ED of the line).  Lines are indexed by the two other dims,
 // stepping by STQ / STR.
 // ---------------------------------------------------------------------------
+// One point of a column pass: float offset vi, code offset ci, prediction pr.
+template <int A, bool COMP>
+__device__ __forceinline__ void line_point(float* __restrict__ v, uint8_t* __restrict__ cs, const Hot& h, int vi,
+                                           int ci, float pr)
+{
+    if constexpr (COMP)
+        v[vi] = point_compress(h, v[vi], pr, cs + ci);
+    else
+        v[vi] = point_decompress<A>(h, cs[ci], pr, vi);
+}
+
 // Line index -> (jq, jr) for nr lines along R.  With run-time line counts the
 // quotient comes from a float reciprocal: for line < 2^16 and nr <= 64 the
 // product is within 1e-3 of the exact quotient, whose fractional part stays
@@ -181,21 +192,16 @@ __device__ __forceinline__ void pass_cols(float* __restrict__ v, uint8_t* __rest
             const int cq = jq * stq, cr = jr * str;
             const int vb = cq * VPQ + cr, cb = cq * CPQ + cr;
             float fa = 0.0f, fb = v[vb], fu = v[vb + 2 * VPD], fv = v[vb + 4 * VPD];
-            auto point = [&](int k, float pr) {
-                const int vi = vb + (2 * k + 1) * VPD;
-                if constexpr (COMP)
-                    v[vi] = point_compress(h, v[vi], pr, cs + cb + (2 * k + 1) * CPD);
-                else
-                    v[vi] = point_decompress<A>(h, cs[cb + (2 * k + 1) * CPD], pr, vi);
-            };
-            point(0, predict(CUBIC, false, true, true, 0.0f, fb, fu, fv));
+            line_point<A, COMP>(v, cs, h, vb + VPD, cb + CPD, predict(CUBIC, false, true, true, 0.0f, fb, fu, fv));
 #pragma unroll 2
             for (int k = 1; k <= NDM - 2; ++k) {
                 fa = fb, fb = fu, fu = fv;
                 fv = v[vb + (2 * k + 4) * VPD];
-                point(k, predict(CUBIC, true, true, true, fa, fb, fu, fv));
+                line_point<A, COMP>(v, cs, h, vb + (2 * k + 1) * VPD, cb + (2 * k + 1) * CPD,
+                                    predict(CUBIC, true, true, true, fa, fb, fu, fv));
             }
-            point(NDM - 1, predict(CUBIC, true, true, false, fb, fu, fv, 0.0f));
+            line_point<A, COMP>(v, cs, h, vb + (2 * NDM - 1) * VPD, cb + (2 * NDM - 1) * CPD,
+                                predict(CUBIC, true, true, false, fb, fu, fv, 0.0f));
         }
         return;
     }
