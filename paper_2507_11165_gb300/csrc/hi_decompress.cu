@@ -86,6 +86,8 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
             if (use_tma && dbuf && nx < g.ntiles)
                 tma_issue(buf ? cbuf0 : cbuf1, &cmap, g, nx, A, &s_mbar[buf ^ 1], tma_bytes);
             if (use_tma && !dbuf && it > 0) tma_issue(cs, &cmap, g, tile, A, &s_mbar[0], tma_bytes);
+            // one buffer: the next tile waits in L2 until this one is done
+            if (use_tma && !dbuf && nx < g.ntiles) tma_l2_prefetch(&cmap, g, nx, A);
         }
         if (tid < 8) {  // seed the anchors
             const int a0 = (tid >> 2) & 1, a1 = (tid >> 1) & 1, a2 = tid & 1;

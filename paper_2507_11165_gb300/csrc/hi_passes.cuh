@@ -461,6 +461,14 @@ __device__ void load_codes_plain(uint8_t* cs, const uint8_t* __restrict__ codes,
     }
 }
 
+// L2 prefetch of the box of the tile at queue position `tile`.
+__device__ __forceinline__ void tma_l2_prefetch(const CUtensorMap* map, const FieldGeo& g, int tile, int A)
+{
+    int t[3];
+    tile_coords(g, tile, t);
+    tma_prefetch_3d(map, t[2] * A, t[1] * A, t[0] * A);
+}
+
 __device__ __forceinline__ void tma_issue(void* dst, const CUtensorMap* map, const FieldGeo& g, int tile, int A,
                                           uint64_t* mbar, uint32_t bytes)
 {
