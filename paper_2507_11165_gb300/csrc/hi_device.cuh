@@ -17,7 +17,20 @@ namespace hi {
 
 constexpr int kRadius = 128;      // code = q + 128, q in [-127, 127] (Sec. 5.2.1)
 constexpr float kQmax = 127.5f;   // |t| must stay below this for a valid code
-constexpr uint32_t kSpinLimit = 1u << 22;  // bound on every mbarrier wait
+// Every mbarrier wait is bounded by wall-clock time: it gives up after
+// kWaitLimitNs of the global nanosecond timer.  Each try_wait may suspend the
+// thread for up to kSuspendNs instead of spinning.  kSpinLimit is a second,
+// iteration-count bound, kept far above what a healthy wait needs.
+constexpr uint32_t kSpinLimit = 1u << 30;
+constexpr uint32_t kSuspendNs = 100000;
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // Block geometry for anchor stride A (Sec. 5.1.1): (A+1) points per active
 // dim.  Shared-memory tiles keep the field's row-major order with the fastest
@@ -121,16 +134,22 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t b
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint32_t limit)
 {
     const uint32_t a = smem_addr(mbar);
+    uint64_t t0 = 0;
     for (uint32_t it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(done)
-            : "r"(a), "r"(parity)
+            : "r"(a), "r"(parity), "r"(kSuspendNs)
             : "memory");
         if (done) return true;
+        if (it == 0) {
+            t0 = global_ns();
+        } else if ((it & 15) == 0 && global_ns() - t0 > kWaitLimitNs) {
+            return false;
+        }
     }
     return false;
 }
