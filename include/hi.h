@@ -142,6 +142,36 @@ HI_API hi_status hi_compress(const hi_params* p, const float* d_x, uint8_t* d_co
                       uint32_t* d_out_idx, float* d_out_val, uint64_t out_cap, uint32_t* d_hist,
                       float* d_recon, hi_header* d_header, void* d_ws, size_t ws_bytes, cudaStream_t stream);
 
+/* hi_compress with no caller workspace and no allocation.  The paper has no
+ * counterpart; this is a convenience of this library.
+ *
+ * For callers that cannot hand the library a workspace buffer: code that
+ * must not call cudaMalloc (it synchronises the device and can fail under a
+ * fixed memory budget), or that runs inside a host which owns all device
+ * memory and offers no allocator.  The arguments and results are those of
+ * hi_compress without d_ws / ws_bytes; the workspace is instead a fixed
+ * scratch array of HI_STATIC_WS_BYTES inside the library's own device image,
+ * one per GPU.  Nothing is allocated or freed, by this call or on its behalf.
+ *
+ *   - Size limit: when hi_query's ws_bytes for p exceeds HI_STATIC_WS_BYTES
+ *     the call returns HI_ENOMEM and enqueues nothing; use hi_compress with
+ *     a workspace of your own then.  1 MiB holds every field of at most
+ *     10^7 points at any A, and every 3D field at A = 16.
+ *   - Set-up: the first call on each device (the device current at the
+ *     call) looks up the scratch array's device address, which may load the
+ *     library's device code; make that first call before any stream capture
+ *     begins.  A failed look-up returns HI_ECUDA.
+ *   - Zero state: nothing in the scratch has to start at zero; the call's
+ *     first kernel resets the counters it uses.
+ *   - Races: every call on a device shares that device's one scratch array.
+ *     Two calls that may run at the same time (different streams, or
+ *     different host threads without ordering) corrupt each other; order
+ *     them on one stream or synchronise between them. */
+#define HI_STATIC_WS_BYTES (1u << 20)
+HI_API hi_status hi_compress_static_ws(const hi_params* p, const float* d_x, uint8_t* d_codes, float* d_anchors,
+                                uint32_t* d_out_idx, float* d_out_val, uint64_t out_cap, uint32_t* d_hist,
+                                float* d_recon, hi_header* d_header, cudaStream_t stream);
+
 /* Decompress (Eq. 1; the same traversal as hi_compress): x' = p + (code -
  * 128) * ebx2_f, or the stored outlier value for code 0.  p supplies the
  * geometry for the launch (dims, anchor_stride) and must match d_header,

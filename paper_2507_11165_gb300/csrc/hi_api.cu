@@ -213,6 +213,29 @@ int threads_for(const Geometry& G, uint32_t tuning)
     return 64;
 }
 
+// Workspace of hi_compress_static_ws: one fixed array per device, part of
+// this library's device image, so that the call allocates nothing.
+static __device__ __align__(256) unsigned char g_static_ws[HI_STATIC_WS_BYTES];
+
+constexpr int kMaxDevices = 64;
+
+// Device address of g_static_ws on the current device, looked up once per
+// device; nullptr if the look-up fails.
+void* static_ws_address()
+{
+    static std::mutex mu;
+    static void* addr[kMaxDevices] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* a = nullptr;
+        if (cudaGetSymbolAddress(&a, g_static_ws) != cudaSuccess) return nullptr;
+        addr[dev] = a;
+    }
+    return addr[dev];
+}
+
 thread_local cudaEvent_t t_events[8];
 thread_local bool t_events_on = false;
 
@@ -341,6 +364,20 @@ hi_status hi_compress(const hi_params* p, const float* d_x, uint8_t* d_codes, fl
     s = cuda_status(launch_compress(G.A, c, stream));
     stage_event(4, stream);
     return s;
+}
+
+hi_status hi_compress_static_ws(const hi_params* p, const float* d_x, uint8_t* d_codes, float* d_anchors,
+                                uint32_t* d_out_idx, float* d_out_val, uint64_t out_cap, uint32_t* d_hist,
+                                float* d_recon, hi_header* d_header, cudaStream_t stream)
+{
+    Geometry G;
+    const hi_status s = make_geometry(p, &G);
+    if (s != HI_OK) return s;
+    if (workspace_bytes(G) > HI_STATIC_WS_BYTES) return HI_ENOMEM;
+    void* ws = static_ws_address();
+    if (!ws) return HI_ECUDA;
+    return hi_compress(p, d_x, d_codes, d_anchors, d_out_idx, d_out_val, out_cap, d_hist, d_recon, d_header, ws,
+                       HI_STATIC_WS_BYTES, stream);
 }
 
 hi_status hi_decompress(const hi_params* p, const hi_header* d_header, const uint8_t* d_codes,

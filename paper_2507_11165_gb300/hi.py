@@ -54,7 +54,8 @@ class HiHeader(ctypes.Structure):
 
 HEADER_BYTES = ctypes.sizeof(HiHeader)
 SYMBOLS = ("hi_query", "hi_compress", "hi_decompress", "hi_autotune", "hi_autotune_errors", "hi_header_read",
-           "hi_status_str", "hi_version", "hi_set_stage_events")
+           "hi_status_str", "hi_version", "hi_set_stage_events", "hi_compress_static_ws")
+STATIC_WS_BYTES = 1 << 20  # HI_STATIC_WS_BYTES
 
 
 class HiError(RuntimeError):
@@ -79,6 +80,7 @@ def lib():
             L.hi_query.argtypes = [ctypes.POINTER(HiParams), ctypes.POINTER(u64), ctypes.POINTER(u64),
                                    ctypes.POINTER(u64), ctypes.POINTER(sz)]
             L.hi_compress.argtypes = [ctypes.POINTER(HiParams), P, P, P, P, P, u64, P, P, P, P, sz, P]
+            L.hi_compress_static_ws.argtypes = [ctypes.POINTER(HiParams), P, P, P, P, P, u64, P, P, P, P]
             L.hi_decompress.argtypes = [ctypes.POINTER(HiParams), P, P, P, P, P, u64, P, P, P, sz, P]
             L.hi_autotune.argtypes = [ctypes.POINTER(HiParams), P, P, P, sz, P]
             L.hi_autotune_errors.argtypes = [ctypes.POINTER(HiParams), P, P, sz, P, P, P, P]
@@ -88,7 +90,7 @@ def lib():
             L.hi_status_str.restype = ctypes.c_char_p
             L.hi_version.restype = ctypes.c_uint32
             for f in ("hi_query", "hi_compress", "hi_decompress", "hi_autotune", "hi_autotune_errors",
-                      "hi_header_read", "hi_set_stage_events"):
+                      "hi_header_read", "hi_set_stage_events", "hi_compress_static_ws"):
                 getattr(L, f).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -229,6 +231,22 @@ def compress_into(x, b: Buffers, stream=None):
                            _ptr(b.out_val), b.out_cap, _ptr(b.hist), _ptr(b.recon), _ptr(b.header), _ptr(b.ws),
                            b.ws.numel(), _stream(stream))
     _check(rc, "hi_compress")
+
+
+def compress_static_ws_into(x, b: Buffers, stream=None):
+    """Enqueue hi_compress_static_ws of ``x`` into ``b`` (no sync).
+
+    The library's fixed per-device scratch serves as workspace, ``b.ws`` is
+    not touched; calls that may overlap on one device race on that scratch."""
+    if not x.is_cuda or x.dtype != torch.float32 or not x.is_contiguous():
+        raise ValueError("x must be a contiguous float32 CUDA tensor")
+    rc = lib().hi_compress_static_ws(ctypes.byref(b.params), _ptr(x), _ptr(b.codes), _ptr(b.anchors),
+                                     _ptr(b.out_idx), _ptr(b.out_val), b.out_cap, _ptr(b.hist), _ptr(b.recon),
+                                     _ptr(b.header), _stream(stream))
+    if rc == HI_ENOMEM:
+        raise HiError(rc, "hi_compress_static_ws: the field needs %d bytes of workspace, the fixed scratch "
+                          "holds %d" % (query(b.params)["ws_bytes"], STATIC_WS_BYTES))
+    _check(rc, "hi_compress_static_ws")
 
 
 def decompress_into(b: Buffers, out, status=None, stream=None, ws=None):
