@@ -206,6 +206,79 @@ HI_API hi_status hi_autotune(const hi_params* p, const float* d_x, hi_header* d_
 HI_API hi_status hi_autotune_errors(const hi_params* p, const void* d_ws, double* h_err, size_t h_err_len,
                              uint32_t* m, uint32_t* L, uint32_t* ncfg, cudaStream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many independent fields of uneven shapes compressed together,
+ * one launch per stage for the whole batch.  Each field's codes, anchors,
+ * outliers (as a set), histogram, reconstruction and header are those
+ * hi_compress gives for it alone.  The predict-quantize launch is
+ * persistent: its CTAs take (field, tile) work items from one queue over the
+ * concatenated tile lists, so small fields do not leave the GPU idle.
+ * Not in the paper, which compresses one field per call.
+ * ------------------------------------------------------------------------ */
+
+/* One field of a batch: its parameters and buffers, as for hi_compress.
+ * Every field of a batch has the same anchor_stride, 8 or 16. */
+typedef struct {
+    hi_params p;
+    const float* d_x;
+    uint8_t* d_codes;
+    float* d_anchors;
+    uint32_t* d_out_idx;
+    float* d_out_val;
+    uint64_t out_cap;
+    uint32_t* d_hist;   /* or NULL */
+    float* d_recon;     /* or NULL */
+    hi_header* d_header;
+} hi_batch_field;
+
+/* A prepared batch (host memory, written by hi_batch_prepare).  The
+ * offsets describe the library's layout of the workspace; callers read
+ * tuning and the totals and leave the rest alone. */
+typedef struct {
+    uint32_t n_fields;
+    uint32_t anchor_stride;
+    uint32_t tuning;        /* launch shape of predict-quantize (hi_params.tuning encoding) */
+    uint32_t all_tma;       /* every field is staged by TMA (two buffers possible)           */
+    uint64_t total_tiles;   /* work items of predict-quantize                                */
+    uint64_t total_chunks;  /* work items of the value range (relative-bound fields)        */
+    uint64_t total_samples; /* auto-tune samples over all auto-tuned fields                 */
+    uint64_t ws_bytes;      /* workspace the batch uses                                      */
+    uint64_t off_table, off_prefix, off_tickets, off_partials, off_err;
+    uint64_t reserved[4];
+} hi_batch_plan;
+
+/* Workspace bytes a batch of n fields needs (host call, no GPU work);
+ * HI_EINVAL for a field hi_compress would refuse, mixed or unsupported
+ * anchor strides, or n == 0. */
+HI_API hi_status hi_batch_query(uint32_t n, const hi_batch_field* h_fields, size_t* ws_bytes);
+
+/* Validate the batch, write its field table into d_ws (at least
+ * hi_batch_query's bytes, 256-byte aligned) and fill *h_plan.  The copy is
+ * synchronous: the call returns when the table is on the device.  tuning:
+ * the launch shape (hi_params.tuning encoding, 0 = 128 threads, one
+ * buffer).  The buffers of every field must stay valid while the plan is
+ * used; d_ws belongs to the plan until the caller is done with it. */
+HI_API hi_status hi_batch_prepare(uint32_t n, const hi_batch_field* h_fields, uint32_t tuning, void* d_ws,
+                                  size_t ws_bytes, hi_batch_plan* h_plan, cudaStream_t stream);
+
+/* Compress every field of a prepared batch.  Enqueues four launches on
+ * stream (header set-up; value range of every relative-bound field;
+ * auto-tune of every auto-tuned field; predict-quantize of all tiles) and
+ * nothing else: no host synchronisation, no memory copy.  The stage events
+ * of hi_set_stage_events (0..4) are recorded as for hi_compress.  Calls that
+ * share d_ws must not overlap. */
+HI_API hi_status hi_compress_batch(const hi_batch_plan* h_plan, void* d_ws, cudaStream_t stream);
+
+/* Launch-shape tuner of a prepared batch: times hi_compress_batch under
+ * each candidate shape (128 then 64 threads per CTA, each with one buffer,
+ * then two where every field is staged by TMA), reps timed runs each after
+ * one warm-up, and stores the fastest in h_plan->tuning.  h_ms (may be
+ * NULL) receives the mean ms per run of the four candidates in that order
+ * (0 for one not tried).  Synchronises the stream; the outputs of the
+ * fields are overwritten with the same values by every run. */
+HI_API hi_status hi_batch_tune_launch(hi_batch_plan* h_plan, void* d_ws, uint32_t reps, float* h_ms,
+                                      cudaStream_t stream);
+
 /* Measurement hook: record CUDA events between the stages of later
  * hi_compress / hi_decompress calls made by the calling host thread.
  * events[0..7] (cudaEvent_t handles created by the caller):

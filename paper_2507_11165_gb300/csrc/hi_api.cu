@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <new>
+#include <vector>
 
 #include <cudaTypedefs.h>
 
@@ -462,6 +464,210 @@ hi_status hi_autotune_errors(const hi_params* p, const void* d_ws, double* h_err
     return cuda_status(cudaStreamSynchronize(stream));
 }
 
+// ---------------------------------------------------------------------------
+// Batches
+// ---------------------------------------------------------------------------
+static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+// Geometry of every field and the workspace layout of the batch.
+static hi_status batch_layout(uint32_t n, const hi_batch_field* f, std::vector<Geometry>* geo, hi_batch_plan* plan)
+{
+    if (n == 0 || !f || !plan) return HI_EINVAL;
+    geo->resize(n);
+    std::memset(plan, 0, sizeof(*plan));
+    uint64_t tiles = 0, chunks = 0, samples = 0, err = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        Geometry& G = (*geo)[i];
+        const hi_status s = make_geometry(&f[i].p, &G);
+        if (s != HI_OK) return s;
+        if (i == 0) plan->anchor_stride = f[i].p.anchor_stride;
+        if (f[i].p.anchor_stride != plan->anchor_stride) return HI_EINVAL;
+        tiles += (uint64_t)G.g.ntiles;
+        if (f[i].p.eb_mode == HI_EB_REL) chunks += (uint64_t)((G.g.N + kBatchChunk - 1) / kBatchChunk);
+        if (f[i].p.autotune) {
+            samples += (uint64_t)G.m;
+            err += (uint64_t)G.m * G.L * G.cands.ncfg;
+        }
+    }
+    if (plan->anchor_stride != 8 && plan->anchor_stride != 16) return HI_EINVAL;
+    if (tiles > 0x7fffffffull || chunks > 0x7fffffffull || samples > 0x7fffffffull) return HI_EINVAL;
+    plan->n_fields = n;
+    plan->total_tiles = tiles;
+    plan->total_chunks = chunks;
+    plan->total_samples = samples;
+    plan->off_table = 256;
+    plan->off_prefix = align256(plan->off_table + sizeof(BatchField) * n);
+    plan->off_tickets = align256(plan->off_prefix + sizeof(uint32_t) * 3 * (n + 1));
+    plan->off_partials = align256(plan->off_tickets + sizeof(uint32_t) * 2 * n);
+    plan->off_err = align256(plan->off_partials + sizeof(float2) * chunks);
+    plan->ws_bytes = align256(plan->off_err + sizeof(double) * err);
+    return HI_OK;
+}
+
+static BatchLaunch batch_launch(const hi_batch_plan* plan, void* d_ws)
+{
+    char* ws = static_cast<char*>(d_ws);
+    const uint32_t n = plan->n_fields;
+    BatchLaunch b{};
+    b.fields = reinterpret_cast<const BatchField*>(ws + plan->off_table);
+    const uint32_t* pre = reinterpret_cast<const uint32_t*>(ws + plan->off_prefix);
+    b.tile_start = pre;
+    b.chunk_start = pre + (n + 1);
+    b.sample_start = pre + 2 * (n + 1);
+    b.queue = reinterpret_cast<uint32_t*>(ws);
+    b.n = (int)n;
+    b.total_tiles = (uint32_t)plan->total_tiles;
+    b.total_chunks = (uint32_t)plan->total_chunks;
+    b.total_samples = (uint32_t)plan->total_samples;
+    b.A = (int)plan->anchor_stride;
+    const uint32_t th = plan->tuning & 3u, bu = (plan->tuning >> 2) & 3u;
+    b.threads = th == 1 ? 64 : 128;
+    b.buffers = (bu == 2 && plan->all_tma) ? 2 : 1;
+    b.num_sms = num_sms();
+    return b;
+}
+
+hi_status hi_batch_query(uint32_t n, const hi_batch_field* h_fields, size_t* ws_bytes)
+{
+    std::vector<Geometry> geo;
+    hi_batch_plan plan;
+    const hi_status s = batch_layout(n, h_fields, &geo, &plan);
+    if (s != HI_OK) return s;
+    if (ws_bytes) *ws_bytes = (size_t)plan.ws_bytes;
+    return HI_OK;
+}
+
+hi_status hi_batch_prepare(uint32_t n, const hi_batch_field* h_fields, uint32_t tuning, void* d_ws,
+                           size_t ws_bytes, hi_batch_plan* h_plan, cudaStream_t stream)
+{
+    if ((tuning & ~0xFu) != 0 || (tuning & 3u) == 3u || ((tuning >> 2) & 3u) == 3u) return HI_EINVAL;
+    std::vector<Geometry> geo;
+    hi_batch_plan plan;
+    hi_status s = batch_layout(n, h_fields, &geo, &plan);
+    if (s != HI_OK) return s;
+    if (!d_ws || !aligned(d_ws, 256)) return HI_EINVAL;
+    if (ws_bytes < plan.ws_bytes) return HI_ENOMEM;
+    for (uint32_t i = 0; i < n; ++i) {
+        const hi_batch_field& f = h_fields[i];
+        if (!f.d_x || !f.d_codes || !f.d_anchors || !f.d_header) return HI_EINVAL;
+        if (f.out_cap > 0 && (!f.d_out_idx || !f.d_out_val)) return HI_EINVAL;
+        if (!aligned(f.d_x, 4) || !aligned(f.d_header, 8)) return HI_EINVAL;
+    }
+    plan.tuning = tuning;
+    char* ws = static_cast<char*>(d_ws);
+    const size_t host_bytes = plan.off_err;  // table, prefixes and tickets (partials / sums need no init)
+    std::vector<unsigned char> host(host_bytes, 0);
+    BatchField* table = reinterpret_cast<BatchField*>(host.data() + plan.off_table);
+    uint32_t* pre = reinterpret_cast<uint32_t*>(host.data() + plan.off_prefix);
+    uint32_t *ts = pre, *cs = pre + (n + 1), *ss = pre + 2 * (n + 1);
+    uint64_t tiles = 0, chunks = 0, samples = 0, err = 0;
+    bool all_tma = true;
+    int PX, CX;
+    pitches((int)plan.anchor_stride, &PX, &CX);
+    for (uint32_t i = 0; i < n; ++i) {
+        const hi_batch_field& f = h_fields[i];
+        const Geometry& G = geo[i];
+        BatchField& B = table[i];
+        new (&B) BatchField();
+        const bool tma = encode_box(&B.tmap, f.d_x, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, G.g, PX, G.A + 1);
+        all_tma = all_tma && tma;
+        B.g = G.g;
+        B.p = f.p;
+        B.x = f.d_x;
+        B.codes = f.d_codes;
+        B.anchors = f.d_anchors;
+        B.out_idx = f.d_out_idx;
+        B.out_val = f.d_out_val;
+        B.out_cap = f.out_cap;
+        B.hist = f.d_hist;
+        B.recon = f.d_recon;
+        B.hdr = f.d_header;
+        B.n_anchors = G.n_anchors;
+        B.cands = G.cands;
+        B.n_levels = (uint32_t)G.L;
+        B.tma_bytes = (uint32_t)(PX * (G.A + 1) * G.g.b0 * 4);
+        const int ch = G.A >= 16 ? 16 : 8;
+        B.flags = (tma ? kFlagTma : 0) | ((G.g.n[2] % ch == 0 && aligned(f.d_codes, 16)) ? kFlagVecCodes : 0);
+        B.m = f.p.autotune ? G.m : 0;
+        B.stride = G.stride;
+        B.nchunks = f.p.eb_mode == HI_EB_REL ? (uint32_t)((G.g.N + kBatchChunk - 1) / kBatchChunk) : 0u;
+        B.partials = reinterpret_cast<float2*>(ws + plan.off_partials) + chunks;
+        B.err = reinterpret_cast<double*>(ws + plan.off_err) + err;
+        B.tickets = reinterpret_cast<uint32_t*>(ws + plan.off_tickets) + 2 * i;
+        ts[i] = (uint32_t)tiles;
+        cs[i] = (uint32_t)chunks;
+        ss[i] = (uint32_t)samples;
+        tiles += (uint64_t)G.g.ntiles;
+        chunks += B.nchunks;
+        samples += (uint64_t)B.m;
+        err += (uint64_t)B.m * G.L * G.cands.ncfg;
+    }
+    ts[n] = (uint32_t)tiles;
+    cs[n] = (uint32_t)chunks;
+    ss[n] = (uint32_t)samples;
+    plan.all_tma = all_tma ? 1u : 0u;
+    cudaError_t e = cudaMemcpyAsync(ws, host.data(), host_bytes, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return HI_ECUDA;
+    e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return HI_ECUDA;
+    *h_plan = plan;
+    return HI_OK;
+}
+
+hi_status hi_compress_batch(const hi_batch_plan* h_plan, void* d_ws, cudaStream_t stream)
+{
+    if (!h_plan || !d_ws || h_plan->n_fields == 0) return HI_EINVAL;
+    const BatchLaunch b = batch_launch(h_plan, d_ws);
+    stage_event(0, stream);
+    if (launch_batch_prologue(b, stream) != cudaSuccess) return HI_ECUDA;
+    stage_event(1, stream);
+    if (launch_batch_range(b, stream) != cudaSuccess) return HI_ECUDA;
+    stage_event(2, stream);
+    if (launch_batch_tune(b, stream) != cudaSuccess) return HI_ECUDA;
+    stage_event(3, stream);
+    const hi_status s = cuda_status(launch_batch_compress(b, stream));
+    stage_event(4, stream);
+    return s;
+}
+
+hi_status hi_batch_tune_launch(hi_batch_plan* h_plan, void* d_ws, uint32_t reps, float* h_ms, cudaStream_t stream)
+{
+    if (!h_plan || !d_ws || reps == 0) return HI_EINVAL;
+    static const uint32_t kCand[4] = {2u | (1u << 2), 1u | (1u << 2), 2u | (2u << 2), 1u | (2u << 2)};
+    const uint32_t keep = h_plan->tuning;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return HI_ECUDA;
+    }
+    hi_status s = HI_OK;
+    float best = 0.0f;
+    uint32_t best_t = keep;
+    for (int c = 0; c < 4 && s == HI_OK; ++c) {
+        if (h_ms) h_ms[c] = 0.0f;
+        if (((kCand[c] >> 2) & 3u) == 2u && !h_plan->all_tma) continue;
+        h_plan->tuning = kCand[c];
+        s = hi_compress_batch(h_plan, d_ws, stream);  // warm-up
+        if (s != HI_OK) break;
+        if (cudaEventRecord(e0, stream) != cudaSuccess) s = HI_ECUDA;
+        for (uint32_t r = 0; r < reps && s == HI_OK; ++r) s = hi_compress_batch(h_plan, d_ws, stream);
+        if (s != HI_OK) break;
+        float ms = 0.0f;
+        if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            s = HI_ECUDA;
+            break;
+        }
+        ms /= (float)reps;
+        if (h_ms) h_ms[c] = ms;
+        if (best == 0.0f || ms < best) best = ms, best_t = kCand[c];
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h_plan->tuning = (s == HI_OK) ? best_t : keep;
+    return s;
+}
+
 hi_status hi_set_stage_events(void* const* events, uint32_t n)
 {
     if (!events) {
@@ -489,3 +695,6 @@ hi_status hi_header_read(const hi_header* d_header, hi_header* h_header, cudaStr
 
 static_assert(sizeof(hi_header) == 168, "hi_header layout");
 static_assert(sizeof(hi_params) == 80, "hi_params layout");
+static_assert(sizeof(hi_batch_field) == 152, "hi_batch_field layout");
+static_assert(sizeof(hi_batch_plan) == 120, "hi_batch_plan layout");
+static_assert(sizeof(hi::BatchField) % 64 == 0, "field records stay 64-byte aligned");

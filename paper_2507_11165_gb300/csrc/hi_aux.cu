@@ -7,149 +7,36 @@
 //     dimension sequence on uniformly sampled blocks, then the argmin.
 #include <cstdint>
 
-#include "hi_device.cuh"
-#include "hi_internal.h"
+#include "hi_aux_dev.cuh"
 
 namespace hi {
-
-// eps and the float32 constants the quantizer uses (device, IEEE double):
-//   eps = eb (absolute) or eb * (vmax - vmin) (relative; eb if the range is 0);
-//   eb_f = eps rounded toward zero (the largest float <= eps),
-//   ebx2_f = fl(2 eps), r_f = fl(1 / (2 eps)).
-__device__ void finalize_eps(hi_header* h, float vmin, float vmax)
-{
-    double eps;
-    if (h->eb_mode == HI_EB_ABS) {
-        eps = h->eb;
-    } else {
-        const double range = __dsub_rn((double)vmax, (double)vmin);
-        eps = (range > 0.0) ? __dmul_rn(h->eb, range) : h->eb;
-    }
-    const double two_eps = __dmul_rn(2.0, eps);
-    const float eb_f = __double2float_rz(eps);
-    const float ebx2_f = __double2float_rn(two_eps);
-    const float r_f = __double2float_rn(__ddiv_rn(1.0, two_eps));
-    h->eps = eps;
-    h->eb_f = eb_f;
-    h->ebx2_f = ebx2_f;
-    h->r_f = r_f;
-    h->vmin = vmin;
-    h->vmax = vmax;
-    const bool ok = (eps > 0.0) && (eps < INFINITY) && (eb_f > 0.0f) && (fabsf(ebx2_f) < INFINITY) &&
-                    (r_f > 0.0f) && (r_f < INFINITY);
-    if (!ok) set_status(&h->status, HI_EINVAL);
-}
 
 __global__ void k_prologue(hi_header* hdr, const hi_params p, uint64_t n_anchors, uint64_t out_cap,
                            uint32_t n_levels, uint32_t* hist, uint32_t* ticket, uint32_t* queue)
 {
-    const int tid = threadIdx.x;
-    if (hist)
-        for (int i = tid; i < 256; i += blockDim.x) hist[i] = 0;
-    if (tid == 0) {
-        hdr->magic = HI_MAGIC;
-        hdr->version = HI_VERSION;
-        for (int d = 0; d < 3; ++d) hdr->dims[d] = p.dims[d];
-        hdr->anchor_stride = p.anchor_stride;
-        hdr->eb_mode = p.eb_mode;
-        hdr->eb = p.eb;
-        hdr->status = 0;
-        hdr->n_outliers = 0;
-        hdr->out_cap = out_cap;
-        hdr->n_anchors = n_anchors;
-        hdr->n_levels = n_levels;
-        for (int l = 0; l < HI_MAX_LEVELS; ++l) hdr->level[l] = p.level[l];
-        for (int k = 0; k < 7; ++k) hdr->reserved[k] = 0;
-        if (ticket) ticket[0] = 0, ticket[2] = 0;  // range ticket, auto-tune ticket
-        if (queue) *queue = 0;
-        if (p.eb_mode == HI_EB_ABS) finalize_eps(hdr, 0.0f, 0.0f);
-    }
+    prologue_fill(hdr, p, n_anchors, out_cap, n_levels, hist, ticket, ticket ? ticket + 2 : nullptr, queue);
 }
-
-// A finite value (NaN and +-Inf are left out of the range).
-__device__ __forceinline__ bool finite_f(float v) { return fabsf(v) < INFINITY; }
 
 // Value range over the finite values: one grid-strided streaming read; the
 // last CTA to finish (ticket) folds the per-CTA partials and derives eps.
 __global__ void __launch_bounds__(512) k_range(const float* __restrict__ x, int64_t N, float2* partials,
                                                uint32_t* ticket, hi_header* hdr)
 {
-    float mn = INFINITY, mx = -INFINITY;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool vec = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
-    int64_t head = 0;
-    if (vec) {
-        const int64_t n4 = N / 4;
-        const float4* x4 = reinterpret_cast<const float4*>(x);
-        int64_t i = t0;
-        for (; i + 3 * stride < n4; i += 4 * stride) {  // four 16-byte loads in flight per thread
-            float4 f[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) f[u] = __ldcs(x4 + i + u * stride);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (finite_f(f[u].x)) mn = fminf(mn, f[u].x), mx = fmaxf(mx, f[u].x);
-                if (finite_f(f[u].y)) mn = fminf(mn, f[u].y), mx = fmaxf(mx, f[u].y);
-                if (finite_f(f[u].z)) mn = fminf(mn, f[u].z), mx = fmaxf(mx, f[u].z);
-                if (finite_f(f[u].w)) mn = fminf(mn, f[u].w), mx = fmaxf(mx, f[u].w);
-            }
-        }
-        for (; i < n4; i += stride) {
-            const float4 f = __ldcs(x4 + i);
-            if (finite_f(f.x)) mn = fminf(mn, f.x), mx = fmaxf(mx, f.x);
-            if (finite_f(f.y)) mn = fminf(mn, f.y), mx = fmaxf(mx, f.y);
-            if (finite_f(f.z)) mn = fminf(mn, f.z), mx = fmaxf(mx, f.z);
-            if (finite_f(f.w)) mn = fminf(mn, f.w), mx = fmaxf(mx, f.w);
-        }
-        head = n4 * 4;
-    }
-    for (int64_t i = head + t0; i < N; i += stride) {
-        const float f = x[i];
-        if (finite_f(f)) mn = fminf(mn, f), mx = fmaxf(mx, f);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    }
     __shared__ float s_mn[32], s_mx[32];
     __shared__ bool s_last;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (lane == 0) s_mn[warp] = mn, s_mx[warp] = mx;
-    __syncthreads();
+    float mn = INFINITY, mx = -INFINITY;
+    range_accum(x, 0, N, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x, mn, mx);
+    block_minmax(mn, mx, s_mn, s_mx);
     if (threadIdx.x == 0) {
-        for (int w = 1; w < nw; ++w) mn = fminf(mn, s_mn[w]), mx = fmaxf(mx, s_mx[w]);
         partials[blockIdx.x] = make_float2(mn, mx);
         __threadfence();
-        const uint32_t t = atomicAdd(ticket, 1u);
-        s_last = (t == gridDim.x - 1);
+        s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // the last CTA folds the partials (min / max are exact in any order)
-    mn = INFINITY, mx = -INFINITY;
-    for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x) {
-        const float2 pk = __ldcg(partials + k);
-        mn = fminf(mn, pk.x);
-        mx = fmaxf(mx, pk.y);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    }
-    __syncthreads();
-    if (lane == 0) s_mn[warp] = mn, s_mx[warp] = mx;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float a = INFINITY, b = -INFINITY;
-        for (int w = 0; w < nw; ++w) a = fminf(a, s_mn[w]), b = fmaxf(b, s_mx[w]);
-        if (!(a <= b)) a = 0.0f, b = 0.0f;  // no finite value
-        a = __fadd_rn(a, 0.0f);              // a signed zero is reported as +0
-        b = __fadd_rn(b, 0.0f);
-        finalize_eps(hdr, a, b);
-        *ticket = 0;
-    }
+    range_fold(partials, gridDim.x, hdr, s_mn, s_mx);
+    if (threadIdx.x == 0) *ticket = 0;
 }
 
 // Outlier values go to their place in the output before reconstruction reads
@@ -174,169 +61,15 @@ __global__ void k_scatter(const uint32_t* __restrict__ idx, const float* __restr
     }
 }
 
-// ---------------------------------------------------------------------------
-// Auto-tune: CTA (sample, candidate) computes, for every level, the sum of
-// |x - p| over that level's points of its sampled block, with every
-// prediction taken from the original values (no quantization), in the
-// candidate's pass order.  Each term is a float, summed in double: per line
-// into independent per-point accumulators (no long FP64 dependency chain),
-// then over the block in a fixed order, so the sums are deterministic run to
-// run.
-// ---------------------------------------------------------------------------
-template <int A, int S>
-__device__ __forceinline__ double tune_pass(const float* __restrict__ v, bool cubic, int d, int stq, int str,
-                                            const int e[3])
-{
-    using TG = TileGeom<A>;
-    constexpr int NDM = A / (2 * S);
-    const int q = (d == 0) ? 1 : 0, r = (d == 2) ? 1 : 2;
-    const int ed = d == 0 ? e[0] : (d == 1 ? e[1] : e[2]);
-    const int eq = q == 0 ? e[0] : e[1], er = r == 1 ? e[1] : e[2];
-    if (ed < S) return 0.0;
-    const int nd = (ed - S) / (2 * S) + 1;
-    const int nq = eq / stq + 1, nr = er / str + 1;
-    const int vpd = (d == 0 ? TG::PY : (d == 1 ? TG::PX : 1)) * S;
-    const int vpq = q == 0 ? TG::PY : TG::PX, vpr = r == 1 ? TG::PX : 1;
-    double acc = 0.0;
-    for (int line = threadIdx.x; line < nq * nr; line += blockDim.x) {
-        const int jq = line / nr, jr = line - jq * nr;
-        const int vb = jq * stq * vpq + jr * str * vpr;
-        float f[NDM + 1];
-#pragma unroll
-        for (int m = 0; m <= NDM; ++m) f[m] = (2 * m * S <= ed) ? v[vb + 2 * m * vpd] : 0.0f;
-        double part[NDM];
-#pragma unroll
-        for (int k = 0; k < NDM; ++k) {
-            part[k] = 0.0;
-            if (k < nd) {
-                const int c = (2 * k + 1) * S;
-                const bool have_r = c + S <= ed, have_r3 = c + 3 * S <= ed;
-                const float pr = predict(cubic, k >= 1, have_r, have_r3, k >= 1 ? f[k - 1] : 0.0f, f[k],
-                                         have_r ? f[k + 1] : 0.0f, (k + 2 <= NDM && have_r3) ? f[k + 2] : 0.0f);
-                part[k] = (double)fabsf(__fsub_rn(v[vb + (2 * k + 1) * vpd], pr));
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < NDM; ++k) acc += part[k];
-    }
-    return acc;
-}
-
-template <int A, int LV>
-__device__ __forceinline__ void tune_levels(const float* v, const hi_level& lv, const int e[3], double* acc)
-{
-    constexpr int S = 1 << LV;
-    const bool cubic = lv.interp == HI_CUBIC;
-    double a = 0.0;
-#pragma unroll
-    for (int p = 0; p < 3; ++p) {
-        const int d = lv.order[p];
-        const int q = (d == 0) ? 1 : 0, r = (d == 2) ? 1 : 2;
-        const int posq = (lv.order[0] == q) ? 0 : ((lv.order[1] == q) ? 1 : 2);
-        const int posr = (lv.order[0] == r) ? 0 : ((lv.order[1] == r) ? 1 : 2);
-        a += tune_pass<A, S>(v, cubic, d, (posq < p) ? S : 2 * S, (posr < p) ? S : 2 * S, e);
-    }
-    acc[LV] = a;
-    if constexpr (LV > 0) tune_levels<A, LV - 1>(v, lv, e, acc);
-}
-
 template <int A>
 __global__ void __launch_bounds__(256) k_tune(const __grid_constant__ CUtensorMap tmap, const FieldGeo g,
                                               const float* __restrict__ x, const TuneCands cands, int stride,
                                               double* __restrict__ err, uint32_t* ticket,
                                               hi_header* __restrict__ hdr, const uint32_t tma_bytes, const int use_tma)
 {
-    using TG = TileGeom<A>;
-    constexpr int L = TG::L;
     extern __shared__ __align__(128) unsigned char smem[];
-    float* v = reinterpret_cast<float*>(smem);
-    __shared__ double s_red[L][8];
-    __shared__ __align__(8) uint64_t s_mbar;
-
-    const int sample = blockIdx.x, c = blockIdx.y;
-    const int tile = sample * stride;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    int t[3], o[3], e[3];
-    tile_coords_rm(g, tile, t);
-    for (int d = 0; d < 3; ++d) {
-        o[d] = t[d] * A;
-        const int rem = (int)(g.n[d] - 1 - o[d]);
-        e[d] = (g.n[d] == 1) ? 0 : (rem < A ? rem : A);
-    }
-    if (use_tma) {  // one TMA box for the sampled tile
-        if (tid == 0) {
-            mbar_init(&s_mbar, 1);
-            fence_mbar_init();
-            mbar_arrive_expect_tx(&s_mbar, tma_bytes);
-            tma_load_3d(v, &tmap, o[2], o[1], o[0], &s_mbar);
-        }
-        __syncthreads();
-        const bool ok = mbar_wait(&s_mbar, 0, kSpinLimit);
-        if (!__syncthreads_and(ok)) {
-            if (tid == 0) set_status(&hdr->status, HI_ETIMEOUT);
-            return;
-        }
-    } else {
-        const int rows = (e[0] + 1) * (e[1] + 1);
-        for (int rr = warp; rr < rows; rr += (blockDim.x >> 5)) {
-            const int c0 = rr / (e[1] + 1), c1 = rr - c0 * (e[1] + 1);
-            const float* src = x + ((int64_t)(o[0] + c0) * g.n[1] + (o[1] + c1)) * g.n[2] + o[2];
-            for (int c2 = lane; c2 <= e[2]; c2 += 32) v[c0 * TG::PY + c1 * TG::PX + c2] = src[c2];
-        }
-        __syncthreads();
-    }
-
-    hi_level lv;
-    lv.interp = cands.interp[c];
-    lv.order[0] = cands.order[c][0];
-    lv.order[1] = cands.order[c][1];
-    lv.order[2] = cands.order[c][2];
-    double acc[L];
-    tune_levels<A, L - 1>(v, lv, e, acc);
-    // fixed-order reduction: warp butterfly, then warps in index order
-#pragma unroll
-    for (int l = 0; l < L; ++l) {
-        double a = acc[l];
-        for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
-        if (lane == 0) s_red[l][warp] = a;
-    }
-    __syncthreads();
-    if (tid < L) {
-        double a = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += s_red[tid][w];
-        err[((size_t)sample * L + tid) * cands.ncfg + c] = a;
-    }
-
-    // the last CTA to finish sums the samples and picks each level's candidate
-    __shared__ bool s_last;
-    __shared__ double s_tot[L * 12];
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    const int m = gridDim.x, ncfg = cands.ncfg;
-    for (int pr = warp; pr < L * ncfg; pr += (blockDim.x >> 5)) {  // one warp per (level, candidate)
-        const int l = pr / ncfg, cc = pr - l * ncfg;
-        double a = 0.0;
-        for (int k = lane; k < m; k += 32) a += __ldcg(err + ((size_t)k * L + l) * ncfg + cc);
-        for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
-        if (lane == 0) s_tot[pr] = a;
-    }
-    __syncthreads();
-    if (tid < L) {  // smallest sum, ties to the first candidate
-        int best = 0;
-        for (int cc = 1; cc < ncfg; ++cc)
-            if (s_tot[tid * ncfg + cc] < s_tot[tid * ncfg + best]) best = cc;
-        hi_level lv;
-        lv.interp = cands.interp[best];
-        lv.order[0] = cands.order[best][0];
-        lv.order[1] = cands.order[best][1];
-        lv.order[2] = cands.order[best][2];
-        hdr->level[tid] = lv;
-    }
-    if (tid == 0) *ticket = 0;
+    tune_block<A>(reinterpret_cast<float*>(smem), &tmap, g, x, cands, blockIdx.x, blockIdx.y, stride, gridDim.x, err,
+                  ticket, hdr, tma_bytes, use_tma != 0);
 }
 
 cudaError_t launch_prologue(hi_header* hdr, const hi_params& p, uint64_t n_anchors, uint64_t out_cap,

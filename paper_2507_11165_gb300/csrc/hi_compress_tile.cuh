@@ -1,0 +1,168 @@
+// hi_compress_tile.cuh -- one tile of the fused predict + quantize step
+// (Sec. 5.1.1-5.1.2, Sec. 5.2.1), shared by the single-field kernel and the
+// batched kernel: the level passes over a staged tile, then the epilogue that
+// stores the owned codes and anchors, appends the outliers and counts the
+// histogram.
+#pragma once
+
+#include "hi_passes.cuh"
+
+namespace hi {
+
+// Where one field's results go.  The single-field kernel passes its kernel
+// parameters by value; the batched kernel passes a view of the current
+// field's record in shared memory, read only after the level passes so that
+// no pointer stays in a register across them.
+struct CompressOut {
+    uint8_t* codes;
+    float* anchors;
+    uint32_t* out_idx;
+    float* out_val;
+    uint64_t out_cap;
+    float* recon;
+    hi_header* hdr;
+    bool vec_ok;   // code rows may be stored as vectors
+    bool hist_on;  // count the histogram
+};
+
+// The tile's floats are in v (reconstructed in place), its codes are staged
+// in cs; g, ti: the field and the tile; s_sel / s_lv: the level
+// configuration; full_ok: the field may take the compile-time full-tile
+// passes; out: a CompressOut or a reference to one in shared memory.
+template <int A, class Out>
+__device__ __forceinline__ void compress_tile(const FieldGeo& g, const TileInfo& ti, float* v, uint8_t* cs,
+                                              uint16_t* hc, uint32_t* s_hist, const int* s_sel,
+                                              const hi_level* s_lv, const Hot h, bool full_ok, const Out& out)
+{
+    using Lw = Lay<A>;
+    const int tid = threadIdx.x;
+    const bool full = full_ok && ti.e[0] == A && ti.e[1] == A && ti.e[2] == A;
+    if constexpr (HasFull<A>::value) {
+        if (full)
+            levels_full<A, TileGeom<A>::L - 1, true>(s_sel, v, cs, h);
+        else
+            levels_ragged<A, TileGeom<A>::L - 1, true>(s_lv, v, cs, h, ti);
+    } else {
+        levels_ragged<A, TileGeom<A>::L - 1, true>(s_lv, v, cs, h, ti);
+    }
+    const bool vec_ok = out.vec_ok, hist_on = out.hist_on;
+    uint8_t* __restrict__ const codes = out.codes;
+    float* __restrict__ const anchors = out.anchors;
+    uint32_t* __restrict__ const out_idx = out.out_idx;
+    float* __restrict__ const out_val = out.out_val;
+    const uint64_t out_cap = out.out_cap;
+    float* __restrict__ const recon_g = out.recon;
+    hi_header* __restrict__ const hdr = out.hdr;
+
+    // ---- epilogue: owned codes, histogram and outliers; recon; anchors
+    const int own0 = ti.own[0] + 1, own1 = ti.own[1] + 1, own2 = ti.own[2] + 1;
+    const int rows = own0 * own1;
+    const bool vec_codes = vec_ok && own2 == A && A >= 8;
+    if (vec_codes) {
+        constexpr int CH = (A >= 16) ? 4 : 2;  // words per global vector store
+        constexpr int NCH = (A >= 8) ? A / (4 * CH) : 1;
+        const bool square = own0 == A && own1 == A;  // rows decompose with shifts
+        const int items = rows * NCH;
+        for (int i0 = 0; i0 < items; i0 += blockDim.x) {
+            const int i = i0 + tid;
+            const bool act = i < items;
+            const int row = act ? i / NCH : 0, ch = act ? i - row * NCH : 0;
+            const int c0 = square ? row / A : row / own1;
+            const int c1 = row - c0 * (square ? A : own1);
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(cs + c0 * Lw::CYC + c1 * Lw::CXC) + ch * CH;
+            uint8_t* dst = codes + ((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2] +
+                           ch * CH * 4;
+            uint32_t w[4];
+            uint32_t z = 0;  // nonzero iff some code of the chunk is 0 (an outlier)
+#pragma unroll
+            for (int j = 0; j < CH; ++j) {
+                w[j] = src[j];
+                z |= (w[j] - 0x01010101u) & ~w[j] & 0x80808080u;
+            }
+            if (act) {
+                if constexpr (CH == 4)
+                    *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+                else
+                    *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
+            }
+            if (__any_sync(0xffffffffu, act && z != 0)) {
+#pragma unroll
+                for (int b = 0; b < 4 * CH; ++b) {
+                    const int code = (w[b >> 2] >> (8 * (b & 3))) & 0xff;
+                    outlier_append<A>(act && code == 0, c0 * Lw::PY + c1 * Lw::PX + ch * CH * 4 + b, v, hdr,
+                                      out_idx, out_val, out_cap, g, ti.o);
+                }
+            }
+            if (hist_on) {
+#pragma unroll
+                for (int b = 0; b < 4 * CH; ++b) hist_count(hc, s_hist, (w[b >> 2] >> (8 * (b & 3))) & 0xff, act);
+            }
+        }
+    } else {
+        const int items = rows * own2;
+        for (int i0 = 0; i0 < items; i0 += blockDim.x) {
+            const int i = i0 + tid;
+            const bool act = i < items;
+            const int row = act ? i / own2 : 0, c2 = act ? i - row * own2 : 0;
+            const int c0 = row / own1, c1 = row - c0 * own1;
+            const int code = cs[c0 * Lw::CYC + c1 * Lw::CXC + c2];
+            if (act)
+                codes[((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2] + c2] =
+                    (uint8_t)code;
+            if (hist_on) hist_count(hc, s_hist, code, act);
+            outlier_append<A>(act && code == 0, c0 * Lw::PY + c1 * Lw::PX + c2, v, hdr, out_idx, out_val, out_cap,
+                              g, ti.o);
+        }
+    }
+    if (recon_g) {
+        const int items = rows * own2;
+        for (int i = tid; i < items; i += blockDim.x) {
+            const int row = i / own2, c2 = i - row * own2;
+            const int c0 = row / own1, c1 = row - c0 * own1;
+            recon_g[((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2] + c2] =
+                v[c0 * Lw::PY + c1 * Lw::PX + c2];
+        }
+    }
+    if (tid < 8) {  // owned anchors, verbatim (Sec. 3.2)
+        const int a0 = (tid >> 2) & 1, a1 = (tid >> 1) & 1, a2 = tid & 1;
+        const int l0 = a0 * A, l1 = a1 * A, l2 = a2 * A;
+        if (l0 <= ti.own[0] && l1 <= ti.own[1] && l2 <= ti.own[2]) {
+            const int64_t ai = ((int64_t)(ti.o[0] / A + a0) * g.na[1] + (ti.o[1] / A + a1)) * g.na[2] +
+                               (ti.o[2] / A + a2);
+            anchors[ai] = v[l0 * Lw::PY + l1 * Lw::PX + l2];
+            if (hist_on) atomicSub(&s_hist[kRadius], 1u);  // anchors are not predicted
+        }
+    }
+}
+
+// Every kHistFoldTiles tiles a CTA folds its 16-bit histogram counters into
+// the shared histogram, before any of them can overflow: a thread counts at
+// most ceil(33^3 / 64) + 16 codes of a tile.
+constexpr int kHistFoldTiles = 64;
+
+// Fold the calling thread's counters into s_hist and clear them (whole warps).
+__device__ __forceinline__ void hist_fold(uint16_t* hc, uint32_t* s_hist)
+{
+    const int tid = threadIdx.x;
+    for (int k = 0; k < kHistBins; ++k) {
+        uint32_t c = hc[k * blockDim.x + tid];
+        hc[k * blockDim.x + tid] = 0;
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if ((tid & 31) == 0 && c) atomicAdd(&s_hist[kHistLo + k], c);
+    }
+}
+
+// Fold, add the CTA's histogram to hist_g and clear it (all threads).
+__device__ __forceinline__ void hist_flush(uint16_t* hc, uint32_t* s_hist, uint32_t* hist_g)
+{
+    hist_fold(hc, s_hist);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        const uint32_t c = s_hist[i];
+        if (c) atomicAdd(&hist_g[i], c);
+        s_hist[i] = 0;
+    }
+    __syncthreads();
+}
+
+}  // namespace hi

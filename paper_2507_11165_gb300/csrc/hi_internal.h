@@ -92,4 +92,55 @@ cudaError_t launch_tune(int A, const TuneLaunch& t, cudaStream_t st);
 
 constexpr int kRangeBlocks = 1024;
 
+// ---------------------------------------------------------------------------
+// Batches: many fields in one launch per stage.  The host writes one
+// BatchField per field into the workspace; every batched kernel finds the
+// field of a work item by binary search over a prefix array.
+// ---------------------------------------------------------------------------
+constexpr int64_t kBatchChunk = 1 << 18;  // points per range work item
+
+struct alignas(64) BatchField {
+    CUtensorMap tmap;  // the field as (PX, A+1, b0) float boxes (when flags & kFlagTma)
+    FieldGeo g;
+    hi_params p;
+    const float* x;
+    uint8_t* codes;
+    float* anchors;
+    uint32_t* out_idx;
+    float* out_val;
+    uint64_t out_cap;
+    uint32_t* hist;
+    float* recon;
+    hi_header* hdr;
+    uint64_t n_anchors;
+    float2* partials;   // range partials, one per chunk
+    double* err;        // auto-tune sums [m][L][ncfg]
+    uint32_t* tickets;  // [0] range, [1] auto-tune
+    TuneCands cands;
+    uint32_t n_levels;
+    uint32_t tma_bytes;
+    int flags;
+    int m, stride;       // auto-tune samples (m = 0: levels given)
+    uint32_t nchunks;    // range work items (0: absolute bound)
+};
+
+struct BatchLaunch {
+    const BatchField* fields;
+    const uint32_t* tile_start;    // [n + 1] first work item of each field in the tile queue
+    const uint32_t* chunk_start;   // [n + 1] same for range chunks
+    const uint32_t* sample_start;  // [n + 1] same for auto-tune samples
+    uint32_t* queue;               // tile queue counter
+    int n;
+    uint32_t total_tiles, total_chunks, total_samples;
+    int A;
+    int threads;
+    int buffers;  // 1 or 2 (2 only when every field is staged by TMA)
+    int num_sms;
+};
+
+cudaError_t launch_batch_prologue(const BatchLaunch& b, cudaStream_t st);
+cudaError_t launch_batch_range(const BatchLaunch& b, cudaStream_t st);
+cudaError_t launch_batch_tune(const BatchLaunch& b, cudaStream_t st);
+cudaError_t launch_batch_compress(const BatchLaunch& b, cudaStream_t st);
+
 }  // namespace hi

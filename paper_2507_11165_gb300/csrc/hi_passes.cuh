@@ -432,32 +432,54 @@ __device__ __forceinline__ void levels_ragged(const hi_level* s_lv, float* v, ui
 // ---------------------------------------------------------------------------
 // Staging
 // ---------------------------------------------------------------------------
+// Tiles that TMA cannot stage (a row pitch that is not a multiple of 16
+// bytes, an unaligned base): a warp per row; floats go by 4-byte cp.async,
+// so a thread's copies are all in flight at once; the caller synchronises.
 template <int A>
 __device__ void load_tile_plain(float* v, const float* __restrict__ x, const FieldGeo& g, const TileInfo& ti)
 {
     using Lw = Lay<A>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int rows = (ti.e[0] + 1) * (ti.e[1] + 1);
+    const int w1 = ti.e[1] + 1, rows = (ti.e[0] + 1) * w1;
     for (int rr = warp; rr < rows; rr += nw) {
-        const int c0 = rr / (ti.e[1] + 1);
-        const int c1 = rr - c0 * (ti.e[1] + 1);
+        const int c0 = rr / w1;
+        const int c1 = rr - c0 * w1;
         const float* src = x + ((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2];
-        for (int c2 = lane; c2 <= ti.e[2]; c2 += 32) v[c0 * Lw::PY + c1 * Lw::PX + c2] = src[c2];
+        for (int c2 = lane; c2 <= ti.e[2]; c2 += 32) cp_async4(v + c0 * Lw::PY + c1 * Lw::PX + c2, src + c2);
     }
+    cp_async_wait_all();
 }
 
+// Codes of such a tile: bytes, four rows in flight per warp.
 template <int A>
 __device__ void load_codes_plain(uint8_t* cs, const uint8_t* __restrict__ codes, const FieldGeo& g,
                                  const TileInfo& ti)
 {
     using Lw = Lay<A>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int rows = (ti.e[0] + 1) * (ti.e[1] + 1);
-    for (int rr = warp; rr < rows; rr += nw) {
-        const int c0 = rr / (ti.e[1] + 1);
-        const int c1 = rr - c0 * (ti.e[1] + 1);
-        const uint8_t* src = codes + ((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2];
-        for (int c2 = lane; c2 <= ti.e[2]; c2 += 32) cs[c0 * Lw::CYD + c1 * Lw::CXD + c2] = src[c2];
+    const int w1 = ti.e[1] + 1, rows = (ti.e[0] + 1) * w1;
+    for (int r0 = warp; r0 < rows; r0 += 4 * nw) {
+        for (int c2b = 0; c2b <= ti.e[2]; c2b += 32) {
+            const int c2 = c2b + lane;
+            uint8_t t[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int rr = r0 + u * nw;
+                t[u] = 0;
+                if (rr < rows && c2 <= ti.e[2]) {
+                    const int c0 = rr / w1, c1 = rr - c0 * w1;
+                    t[u] = codes[((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2] + c2];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int rr = r0 + u * nw;
+                if (rr < rows && c2 <= ti.e[2]) {
+                    const int c0 = rr / w1, c1 = rr - c0 * w1;
+                    cs[c0 * Lw::CYD + c1 * Lw::CXD + c2] = t[u];
+                }
+            }
+        }
     }
 }
 

@@ -52,9 +52,26 @@ class HiHeader(ctypes.Structure):
                 ("reserved", ctypes.c_uint32 * 7)]
 
 
+class HiBatchField(ctypes.Structure):
+    _fields_ = [("p", HiParams), ("d_x", ctypes.c_void_p), ("d_codes", ctypes.c_void_p),
+                ("d_anchors", ctypes.c_void_p), ("d_out_idx", ctypes.c_void_p), ("d_out_val", ctypes.c_void_p),
+                ("out_cap", ctypes.c_uint64), ("d_hist", ctypes.c_void_p), ("d_recon", ctypes.c_void_p),
+                ("d_header", ctypes.c_void_p)]
+
+
+class HiBatchPlan(ctypes.Structure):
+    _fields_ = [("n_fields", ctypes.c_uint32), ("anchor_stride", ctypes.c_uint32), ("tuning", ctypes.c_uint32),
+                ("all_tma", ctypes.c_uint32), ("total_tiles", ctypes.c_uint64), ("total_chunks", ctypes.c_uint64),
+                ("total_samples", ctypes.c_uint64), ("ws_bytes", ctypes.c_uint64), ("off_table", ctypes.c_uint64),
+                ("off_prefix", ctypes.c_uint64), ("off_tickets", ctypes.c_uint64),
+                ("off_partials", ctypes.c_uint64), ("off_err", ctypes.c_uint64),
+                ("reserved", ctypes.c_uint64 * 4)]
+
+
 HEADER_BYTES = ctypes.sizeof(HiHeader)
 SYMBOLS = ("hi_query", "hi_compress", "hi_decompress", "hi_autotune", "hi_autotune_errors", "hi_header_read",
-           "hi_status_str", "hi_version", "hi_set_stage_events", "hi_compress_static_ws")
+           "hi_status_str", "hi_version", "hi_set_stage_events", "hi_compress_static_ws", "hi_batch_query",
+           "hi_batch_prepare", "hi_compress_batch", "hi_batch_tune_launch")
 STATIC_WS_BYTES = 1 << 20  # HI_STATIC_WS_BYTES
 
 
@@ -81,6 +98,11 @@ def lib():
                                    ctypes.POINTER(u64), ctypes.POINTER(sz)]
             L.hi_compress.argtypes = [ctypes.POINTER(HiParams), P, P, P, P, P, u64, P, P, P, P, sz, P]
             L.hi_compress_static_ws.argtypes = [ctypes.POINTER(HiParams), P, P, P, P, P, u64, P, P, P, P]
+            BF, BP = ctypes.POINTER(HiBatchField), ctypes.POINTER(HiBatchPlan)
+            L.hi_batch_query.argtypes = [ctypes.c_uint32, BF, ctypes.POINTER(sz)]
+            L.hi_batch_prepare.argtypes = [ctypes.c_uint32, BF, ctypes.c_uint32, P, sz, BP, P]
+            L.hi_compress_batch.argtypes = [BP, P, P]
+            L.hi_batch_tune_launch.argtypes = [BP, P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_float), P]
             L.hi_decompress.argtypes = [ctypes.POINTER(HiParams), P, P, P, P, P, u64, P, P, P, sz, P]
             L.hi_autotune.argtypes = [ctypes.POINTER(HiParams), P, P, P, sz, P]
             L.hi_autotune_errors.argtypes = [ctypes.POINTER(HiParams), P, P, sz, P, P, P, P]
@@ -90,7 +112,8 @@ def lib():
             L.hi_status_str.restype = ctypes.c_char_p
             L.hi_version.restype = ctypes.c_uint32
             for f in ("hi_query", "hi_compress", "hi_decompress", "hi_autotune", "hi_autotune_errors",
-                      "hi_header_read", "hi_set_stage_events", "hi_compress_static_ws"):
+                      "hi_header_read", "hi_set_stage_events", "hi_compress_static_ws", "hi_batch_query",
+                      "hi_batch_prepare", "hi_compress_batch", "hi_batch_tune_launch"):
                 getattr(L, f).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -345,6 +368,88 @@ def decompress(c: Compressed, out=None, stream=None):
     if st != HI_OK:
         raise HiError(st, "hi_decompress (device)")
     return out
+
+
+# Launch shapes of the batched predict-quantize launch, in the order the
+# launch-shape tuner tries them (hi_params.tuning encoding).
+BATCH_SHAPES = ((128, 1), (64, 1), (128, 2), (64, 2))
+
+
+def tuning_code(threads, buffers):
+    return {64: 1, 128: 2}[threads] | ({1: 1, 2: 2}[buffers] << 2)
+
+
+class Batch:
+    """Many fields compressed together: one launch per stage for all of them
+    (hi_batch_prepare / hi_compress_batch).
+
+    ``xs``: contiguous float32 device tensors (shapes may differ); ``ebs``: one
+    bound per field (or one for all); the other arguments apply to every
+    field.  Buffers of each field are allocated here; ``compress()`` only
+    enqueues kernels, so it can be captured in a CUDA graph."""
+
+    def __init__(self, xs, ebs, mode="rel", anchor_stride=16, autotune=True, levels=None, out_caps=None,
+                 hist=True, recon=False, tuning=0):
+        n = len(xs)
+        if n == 0:
+            raise ValueError("empty batch")
+        if not isinstance(ebs, (list, tuple)):
+            ebs = [ebs] * n
+        modes = mode if isinstance(mode, (list, tuple)) else [mode] * n
+        self.xs = list(xs)
+        self.buffers = []
+        arr = (HiBatchField * n)()
+        for i, x in enumerate(self.xs):
+            if not x.is_cuda or x.dtype != torch.float32 or not x.is_contiguous():
+                raise ValueError("every field must be a contiguous float32 CUDA tensor")
+            p = make_params(x.shape, ebs[i], modes[i], anchor_stride, autotune, levels)
+            cap = None if out_caps is None else out_caps[i]
+            b = alloc(p, x.shape, x.device, cap, hist, recon)
+            self.buffers.append(b)
+            arr[i].p = p
+            arr[i].d_x = x.data_ptr()
+            arr[i].d_codes = b.codes.data_ptr()
+            arr[i].d_anchors = b.anchors.data_ptr()
+            arr[i].d_out_idx = b.out_idx.data_ptr()
+            arr[i].d_out_val = b.out_val.data_ptr()
+            arr[i].out_cap = b.out_cap
+            arr[i].d_hist = None if b.hist is None else b.hist.data_ptr()
+            arr[i].d_recon = None if b.recon is None else b.recon.data_ptr()
+            arr[i].d_header = b.header.data_ptr()
+        self.fields = arr
+        wsb = ctypes.c_size_t()
+        _check(lib().hi_batch_query(n, arr, ctypes.byref(wsb)), "hi_batch_query")
+        self.ws = torch.empty(max(256, wsb.value), dtype=torch.uint8, device=self.xs[0].device)
+        self.plan = HiBatchPlan()
+        _check(lib().hi_batch_prepare(n, arr, tuning, _ptr(self.ws), self.ws.numel(), ctypes.byref(self.plan),
+                                      _stream(None)), "hi_batch_prepare")
+
+    def __len__(self):
+        return len(self.xs)
+
+    def compress(self, stream=None):
+        """Enqueue the batch's compression (no sync)."""
+        _check(lib().hi_compress_batch(ctypes.byref(self.plan), _ptr(self.ws), _stream(stream)),
+               "hi_compress_batch")
+
+    def tune_launch(self, reps=3, stream=None):
+        """Time every launch shape, keep the fastest; returns {shape: ms}."""
+        ms = (ctypes.c_float * 4)()
+        _check(lib().hi_batch_tune_launch(ctypes.byref(self.plan), _ptr(self.ws), reps, ms, _stream(stream)),
+               "hi_batch_tune_launch")
+        return {BATCH_SHAPES[i]: float(ms[i]) for i in range(4) if ms[i] > 0}
+
+    @property
+    def shape(self):
+        t = self.plan.tuning
+        return ({1: 64, 2: 128}.get(t & 3, 128), {1: 1, 2: 2}.get((t >> 2) & 3, 1))
+
+    def set_shape(self, threads, buffers):
+        self.plan.tuning = tuning_code(threads, buffers)
+
+    def results(self, stream=None):
+        """Compressed records of every field (reads the headers; synchronises)."""
+        return [Compressed(b, read_header(b.header, stream)) for b in self.buffers]
 
 
 def estimate_cr(hist, n_out, n_anchors, n_points, header_bytes=None):

@@ -63,3 +63,27 @@ def test_host_calls_without_gpu(lib):
     p.level[0].interp = 7
     with pytest.raises(lib.HiError):
         lib.query(p)
+
+
+def test_batch_host_validation(lib):
+    import ctypes as C
+    assert C.sizeof(lib.HiBatchField) == 152 and C.sizeof(lib.HiBatchPlan) == 120
+    L = lib.lib()
+    arr = (lib.HiBatchField * 3)()
+    arr[0].p = lib.make_params((40, 50, 60), 1e-3, "rel", 16)
+    arr[1].p = lib.make_params((64, 64), 1e-3, "abs", 16)
+    arr[2].p = lib.make_params((1000,), 1e-3, "rel", 16)
+    ws = C.c_size_t()
+    assert L.hi_batch_query(3, arr, C.byref(ws)) == lib.HI_OK
+    # 256 B counters + 3 field records + prefixes + tickets + two range partials + auto-tune sums
+    assert ws.value % 256 == 0 and ws.value > 256 + 3 * 256
+    assert L.hi_batch_query(0, arr, C.byref(ws)) == lib.HI_EINVAL
+    arr[1].p = lib.make_params((64, 64), 1e-3, "abs", 8)  # mixed anchor strides
+    assert L.hi_batch_query(3, arr, C.byref(ws)) == lib.HI_EINVAL
+    for i in range(3):
+        arr[i].p.anchor_stride = 4  # batches take A = 8 or 16
+    assert L.hi_batch_query(3, arr, C.byref(ws)) == lib.HI_EINVAL
+    plan = lib.HiBatchPlan()
+    arr[0].p = lib.make_params((40, 50, 60), 1e-3, "rel", 16)
+    assert L.hi_batch_prepare(1, arr, 3, None, 0, C.byref(plan), None) == lib.HI_EINVAL  # bad tuning
+    assert L.hi_batch_prepare(1, arr, 0, None, 0, C.byref(plan), None) == lib.HI_EINVAL  # no workspace
