@@ -497,12 +497,15 @@ static hi_status batch_layout(uint32_t n, const hi_batch_field* f, std::vector<G
     plan->total_samples = samples;
     plan->off_table = 256;
     plan->off_prefix = align256(plan->off_table + sizeof(BatchField) * n);
-    plan->off_tickets = align256(plan->off_prefix + sizeof(uint32_t) * 3 * (n + 1));
+    plan->off_tickets = align256(plan->off_prefix + sizeof(uint32_t) * 4 * (n + 1));
     plan->off_partials = align256(plan->off_tickets + sizeof(uint32_t) * 2 * n);
     plan->off_err = align256(plan->off_partials + sizeof(float2) * chunks);
     plan->ws_bytes = align256(plan->off_err + sizeof(double) * err);
     return HI_OK;
 }
+
+// The plan keeps the number of head work items in its first reserved word.
+static uint32_t pre_total_head(const hi_batch_plan* plan) { return (uint32_t)plan->reserved[0]; }
 
 static BatchLaunch batch_launch(const hi_batch_plan* plan, void* d_ws)
 {
@@ -514,6 +517,8 @@ static BatchLaunch batch_launch(const hi_batch_plan* plan, void* d_ws)
     b.tile_start = pre;
     b.chunk_start = pre + (n + 1);
     b.sample_start = pre + 2 * (n + 1);
+    b.shell_start = pre + 3 * (n + 1);
+    b.total_head = pre_total_head(plan);
     b.queue = reinterpret_cast<uint32_t*>(ws);
     b.n = (int)n;
     b.total_tiles = (uint32_t)plan->total_tiles;
@@ -559,8 +564,8 @@ hi_status hi_batch_prepare(uint32_t n, const hi_batch_field* h_fields, uint32_t 
     std::vector<unsigned char> host(host_bytes, 0);
     BatchField* table = reinterpret_cast<BatchField*>(host.data() + plan.off_table);
     uint32_t* pre = reinterpret_cast<uint32_t*>(host.data() + plan.off_prefix);
-    uint32_t *ts = pre, *cs = pre + (n + 1), *ss = pre + 2 * (n + 1);
-    uint64_t tiles = 0, chunks = 0, samples = 0, err = 0;
+    uint32_t *ts = pre, *cs = pre + (n + 1), *ss = pre + 2 * (n + 1), *hs = pre + 3 * (n + 1);
+    uint64_t tiles = 0, chunks = 0, samples = 0, err = 0, head = 0, shell = 0;
     bool all_tma = true;
     int PX, CX;
     pitches((int)plan.anchor_stride, &PX, &CX);
@@ -588,13 +593,23 @@ hi_status hi_batch_prepare(uint32_t n, const hi_batch_field* h_fields, uint32_t 
         B.tma_bytes = (uint32_t)(PX * (G.A + 1) * G.g.b0 * 4);
         const int ch = G.A >= 16 ? 16 : 8;
         B.flags = (tma ? kFlagTma : 0) | ((G.g.n[2] % ch == 0 && aligned(f.d_codes, 16)) ? kFlagVecCodes : 0);
+        B.cur.out = CompressOut{f.d_codes, f.d_anchors, f.d_out_idx, f.d_out_val, f.out_cap, f.d_recon, f.d_header,
+                                (B.flags & kFlagVecCodes) != 0, f.d_hist != nullptr};
+        B.cur.g = G.g;
+        B.cur.x = f.d_x;
+        B.cur.hist = f.d_hist;
+        B.cur.flags = B.flags;
         B.m = f.p.autotune ? G.m : 0;
         B.stride = G.stride;
         B.nchunks = f.p.eb_mode == HI_EB_REL ? (uint32_t)((G.g.N + kBatchChunk - 1) / kBatchChunk) : 0u;
         B.partials = reinterpret_cast<float2*>(ws + plan.off_partials) + chunks;
         B.err = reinterpret_cast<double*>(ws + plan.off_err) + err;
         B.tickets = reinterpret_cast<uint32_t*>(ws + plan.off_tickets) + 2 * i;
-        ts[i] = (uint32_t)tiles;
+        B.nint = (uint32_t)G.g.ni[0] * (uint32_t)G.g.ni[1] * (uint32_t)G.g.ni[2];
+        ts[i] = (uint32_t)head;
+        hs[i] = (uint32_t)shell;
+        head += B.nint;
+        shell += (uint64_t)G.g.ntiles - B.nint;
         cs[i] = (uint32_t)chunks;
         ss[i] = (uint32_t)samples;
         tiles += (uint64_t)G.g.ntiles;
@@ -602,10 +617,12 @@ hi_status hi_batch_prepare(uint32_t n, const hi_batch_field* h_fields, uint32_t 
         samples += (uint64_t)B.m;
         err += (uint64_t)B.m * G.L * G.cands.ncfg;
     }
-    ts[n] = (uint32_t)tiles;
+    ts[n] = (uint32_t)head;
+    hs[n] = (uint32_t)shell;
     cs[n] = (uint32_t)chunks;
     ss[n] = (uint32_t)samples;
     plan.all_tma = all_tma ? 1u : 0u;
+    plan.reserved[0] = head;
     cudaError_t e = cudaMemcpyAsync(ws, host.data(), host_bytes, cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) return HI_ECUDA;
     e = cudaStreamSynchronize(stream);
@@ -624,6 +641,7 @@ hi_status hi_compress_batch(const hi_batch_plan* h_plan, void* d_ws, cudaStream_
     if (launch_batch_range(b, stream) != cudaSuccess) return HI_ECUDA;
     stage_event(2, stream);
     if (launch_batch_tune(b, stream) != cudaSuccess) return HI_ECUDA;
+    if (launch_batch_gather(b, stream) != cudaSuccess) return HI_ECUDA;
     stage_event(3, stream);
     const hi_status s = cuda_status(launch_batch_compress(b, stream));
     stage_event(4, stream);

@@ -78,51 +78,97 @@ __global__ void __launch_bounds__(256) k_batch_tune(const BatchField* __restrict
                   blockIdx.y, F.stride, F.m, F.err, &F.tickets[1], F.hdr, F.tma_bytes, (F.flags & kFlagTma) != 0);
 }
 
-// Thread 0 of a batched CTA, at the top of iteration `it` on work item
-// (f, lt) staged in v: takes the next work item from the queue, decodes its
-// field and tile into slot (it + 1) & 1, and starts the copies: with two
-// buffers the next tile's box into `other`; with one, this tile's box (the
-// buffer is free again) and an L2 prefetch of the next one.
+// After the auto-tuner: each field's constants, status and level
+// configuration from its header into its record.
+__global__ void k_batch_gather(BatchField* __restrict__ fields)
+{
+    BatchField& F = fields[blockIdx.x];
+    const hi_header* hdr = F.cur.out.hdr;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        F.cur.h.eb_f = hdr->eb_f;
+        F.cur.h.ebx2_f = hdr->ebx2_f;
+        F.cur.h.r_f = hdr->r_f;
+        const uint32_t st = hdr->status;
+        F.cur.skip = st != 0 && st != HI_ECAPACITY;
+    }
+    if (tid < HI_MAX_LEVELS) {
+        const hi_level lv = hdr->level[tid];
+        F.cur.lv[tid] = lv;
+        F.cur.sel[tid] = perm_sel(lv);
+    }
+}
+
+// Work item w -> (field, position in the field's queue order).  The head
+// tiles of every field (its whole 3D tiles) come first, then the rest of
+// every field: the CTAs in flight mostly run one kind of pass code.
+__device__ __forceinline__ int batch_locate(const BatchField* __restrict__ fields,
+                                            const uint32_t* __restrict__ head_start,
+                                            const uint32_t* __restrict__ shell_start, int n, uint32_t total_head,
+                                            uint32_t w, int* pos)
+{
+    if (w < total_head) {
+        const int f = find_field(head_start, n, w);
+        *pos = (int)(w - __ldg(head_start + f));
+        return f;
+    }
+    const uint32_t w2 = w - total_head;
+    const int f = find_field(shell_start, n, w2);
+    *pos = (int)(fields[f].nint + (w2 - __ldg(shell_start + f)));
+    return f;
+}
+
+// Asynchronous copy of a field's record into a shared-memory slot (thread 0).
+__device__ __forceinline__ void fetch_cur(BatchCur* dst, const BatchCur* src)
+{
+    static_assert(sizeof(BatchCur) % 16 == 0, "16-byte copies");
+    for (int k = 0; k < (int)(sizeof(BatchCur) / 16); ++k) cp_async16(reinterpret_cast<char*>(dst) + 16 * k,
+                                                                       reinterpret_cast<const char*>(src) + 16 * k);
+}
+
+// Thread 0 of a batched CTA, at iteration `it` on a tile of field f: takes
+// the next work item from the queue (in queue order the CTAs in flight work
+// on neighbouring tiles, which share faces and DRAM pages; that outweighs
+// the cost of changing field), decodes it into slot (it + 1) & 1, starts the
+// asynchronous copy of its field's record into `nslot` when that field is
+// not f, and starts its box: into `other` with two buffers, into L2 with one.
 template <int A>
-__device__ __forceinline__ void batch_schedule(const BatchField* __restrict__ fields,
-                                            const uint32_t* __restrict__ tile_start, int n, uint32_t total,
-                                            uint32_t* queue, int it, bool dbuf, int f, int lt, bool tma_here,
-                                            float* v, float* other, uint64_t* s_mbar, int* s_next, int* s_tf,
-                                            int* s_tl, int* s_tma, TileInfo* s_ti)
+__device__ __forceinline__ void batch_next(const BatchField* __restrict__ fields,
+                                           const uint32_t* __restrict__ head_start,
+                                           const uint32_t* __restrict__ shell_start, int n, uint32_t total_head,
+                                           uint32_t total, uint32_t* queue, int it, bool dbuf, int f, float* other,
+                                           uint64_t* s_mbar, int* s_next, int* s_tf, int* s_tma, uint32_t* s_tb,
+                                           TileInfo* s_ti, BatchCur* nslot)
 {
     const int buf = dbuf ? (it & 1) : 0;
     const uint32_t nx = gridDim.x + atomicAdd(queue, 1u);
     *s_next = (int)(nx < total ? nx : total);
-    int fn = -1, ln = 0;
-    if (nx < total) {
-        fn = find_field(tile_start, n, nx);
-        ln = (int)(nx - __ldg(tile_start + fn));
-        s_tf[(it + 1) & 1] = fn;
-        s_tl[(it + 1) & 1] = ln;
-        s_ti[(it + 1) & 1] = tile_info<A>(fields[fn].g, ln);
-        s_tma[(it + 1) & 1] = (fields[fn].flags & kFlagTma) != 0;
+    if (nx >= total) return;
+    int pos;
+    const int fn = batch_locate(fields, head_start, shell_start, n, total_head, nx, &pos);
+    const BatchField& F = fields[fn];
+    const TileInfo tn = tile_info<A>(F.g, pos);
+    const int nb = (it + 1) & 1;
+    const bool tma = (F.flags & kFlagTma) != 0;
+    s_tf[nb] = fn;
+    s_ti[nb] = tn;
+    s_tma[nb] = tma;
+    s_tb[nb] = F.tma_bytes;
+    if (fn != f) fetch_cur(nslot, &F.cur);
+    if (tma) {
+        if (dbuf) {
+            mbar_arrive_expect_tx(&s_mbar[buf ^ 1], F.tma_bytes);
+            tma_load_3d(other, &F.tmap, tn.o[2], tn.o[1], tn.o[0], &s_mbar[buf ^ 1]);
+        } else {
+            tma_prefetch_3d(&F.tmap, tn.o[2], tn.o[1], tn.o[0]);
+        }
     }
-    if (dbuf && fn >= 0 && (fields[fn].flags & kFlagTma))
-        tma_issue(other, &fields[fn].tmap, fields[fn].g, ln, A, &s_mbar[buf ^ 1], fields[fn].tma_bytes);
-    if (!dbuf && it > 0 && tma_here) tma_issue(v, &fields[f].tmap, fields[f].g, lt, A, &s_mbar[0], fields[f].tma_bytes);
-    if (!dbuf && fn >= 0 && (fields[fn].flags & kFlagTma)) tma_l2_prefetch(&fields[fn].tmap, fields[fn].g, ln, A);
 }
-
-// Per-field state of the field a CTA is working on (shared memory).
-struct BatchCur {
-    CompressOut out;
-    FieldGeo g;
-    const float* x;
-    uint32_t* hist;
-    Hot h;
-    int flags;
-    int skip;     // an earlier stage of this field failed: leave its outputs
-    int full_ok;  // every dim active: whole tiles take the compile-time passes
-};
 
 template <int A>
 __global__ void __launch_bounds__(kMaxThreads, 5)
-    k_compress_batch(const BatchField* __restrict__ fields, const uint32_t* __restrict__ tile_start, const int n,
+    k_compress_batch(const BatchField* __restrict__ fields, const uint32_t* __restrict__ head_start,
+                     const uint32_t* __restrict__ shell_start, const int n, const uint32_t total_head,
                      const uint32_t total, uint32_t* __restrict__ queue, const int dbuf_flag)
 {
     using Lw = Lay<A>;
@@ -135,13 +181,11 @@ __global__ void __launch_bounds__(kMaxThreads, 5)
     uint16_t* hc = reinterpret_cast<uint16_t*>(cs + round128((A + 1) * Lw::P * Lw::CXC));
     __shared__ uint32_t s_hist[256];
     __shared__ __align__(8) uint64_t s_mbar[2];
-    __shared__ hi_level s_lv[HI_MAX_LEVELS];
-    __shared__ int s_sel[HI_MAX_LEVELS];
-    __shared__ BatchCur s_cur;
+    __shared__ BatchCur s_cur[2];  // the current field's record; the next field's, arriving
     __shared__ int s_next;
-    __shared__ int s_tf[2];    // field of this work item and of the next
-    __shared__ int s_tl[2];    // its tile within the field (queue order)
-    __shared__ int s_tma[2];   // staged by TMA
+    __shared__ int s_tf[2];       // field of this work item and of the next
+    __shared__ int s_tma[2];      // staged by TMA
+    __shared__ uint32_t s_tb[2];  // bytes of its TMA box
     __shared__ TileInfo s_ti[2];
 
     const int tid = threadIdx.x;
@@ -152,63 +196,50 @@ __global__ void __launch_bounds__(kMaxThreads, 5)
         mbar_init(&s_mbar[1], 1);
         fence_mbar_init();
         if (blockIdx.x < total) {
-            const int f = find_field(tile_start, n, blockIdx.x);
+            int pos;
+            const int f = batch_locate(fields, head_start, shell_start, n, total_head, blockIdx.x, &pos);
             const BatchField& F = fields[f];
-            const int lt = (int)(blockIdx.x - __ldg(tile_start + f));
+            const TileInfo t0 = tile_info<A>(F.g, pos);
             s_tf[0] = f;
-            s_tl[0] = lt;
-            s_ti[0] = tile_info<A>(F.g, lt);
+            s_ti[0] = t0;
             s_tma[0] = (F.flags & kFlagTma) != 0;
-            if (s_tma[0]) tma_issue(vbuf0, &F.tmap, F.g, lt, A, &s_mbar[0], F.tma_bytes);
+            s_tb[0] = F.tma_bytes;
+            if (s_tma[0]) {
+                mbar_arrive_expect_tx(&s_mbar[0], F.tma_bytes);
+                tma_load_3d(vbuf0, &F.tmap, t0.o[2], t0.o[1], t0.o[0], &s_mbar[0]);
+            }
+            fetch_cur(&s_cur[0], &F.cur);
+            cp_async_wait_all();
         }
     }
     __syncthreads();
 
-    int cur = -1;
+    int cur = s_tf[0];
+    int sl = 0;       // slot of the current field's record
     uint32_t ph = 0;  // bit b: phase of buffer b's barrier
     int it = 0;
     for (uint32_t w = blockIdx.x; w < total; ++it) {
         const int buf = dbuf ? (it & 1) : 0;
         float* v = buf ? vbuf1 : vbuf0;
         const int f = s_tf[it & 1];
-        const int lt = s_tl[it & 1];
         const bool tma_here = s_tma[it & 1] != 0;
         const TileInfo ti = s_ti[it & 1];
-        if (tid == 0)
-            batch_schedule<A>(fields, tile_start, n, total, queue, it, dbuf, f, lt, tma_here, v, buf ? vbuf0 : vbuf1,
-                              s_mbar, &s_next, s_tf, s_tl, s_tma, s_ti);
-        if (f != cur) {  // a new field: flush the histogram of the last one, load this one
-            if (cur >= 0 && s_cur.hist) hist_flush(hc, s_hist, s_cur.hist);
+        if (tid == 0 && !dbuf && it > 0 && tma_here) {  // one buffer: it is free again
+            mbar_arrive_expect_tx(&s_mbar[0], s_tb[it & 1]);
+            tma_load_3d(v, &fields[f].tmap, ti.o[2], ti.o[1], ti.o[0], &s_mbar[0]);
+        }
+        if (f != cur) {  // a new field: flush the last one's histogram; its record is in the other slot
+            // (the last iteration's closing barrier ordered every count of it)
+            if (s_cur[sl].hist) hist_flush_to(hc, s_hist, s_cur[sl].hist);
+            if (tid == 0) cp_async_wait_all();
             __syncthreads();
-            if (tid == 0) {
-                const BatchField& F = fields[f];
-                s_cur.out.codes = F.codes;
-                s_cur.out.anchors = F.anchors;
-                s_cur.out.out_idx = F.out_idx;
-                s_cur.out.out_val = F.out_val;
-                s_cur.out.out_cap = F.out_cap;
-                s_cur.out.recon = F.recon;
-                s_cur.out.hdr = F.hdr;
-                s_cur.out.vec_ok = (F.flags & kFlagVecCodes) != 0;
-                s_cur.out.hist_on = F.hist != nullptr;
-                s_cur.g = F.g;
-                s_cur.x = F.x;
-                s_cur.hist = F.hist;
-                s_cur.h.eb_f = F.hdr->eb_f;
-                s_cur.h.ebx2_f = F.hdr->ebx2_f;
-                s_cur.h.r_f = F.hdr->r_f;
-                s_cur.flags = F.flags;
-                const uint32_t st = F.hdr->status;
-                s_cur.skip = st != 0 && st != HI_ECAPACITY;
-                s_cur.full_ok = HasFull<A>::value && F.g.n[0] > 1 && F.g.n[1] > 1 && F.g.n[2] > 1;
-            }
-            if (tid < HI_MAX_LEVELS) {
-                s_lv[tid] = fields[f].hdr->level[tid];
-                s_sel[tid] = perm_sel(s_lv[tid]);
-            }
-            __syncthreads();
+            sl ^= 1;
             cur = f;
         }
+        const BatchCur& C = s_cur[sl];
+        if (tid == 0)
+            batch_next<A>(fields, head_start, shell_start, n, total_head, total, queue, it, dbuf, f,
+                          buf ? vbuf0 : vbuf1, s_mbar, &s_next, s_tf, s_tma, s_tb, s_ti, &s_cur[sl ^ 1]);
         if (tid < 8) {  // anchors keep the zero-error code
             const int a0 = (tid >> 2) & 1, a1 = (tid >> 1) & 1, a2 = tid & 1;
             if (a0 * A <= ti.e[0] && a1 * A <= ti.e[1] && a2 * A <= ti.e[2])
@@ -218,24 +249,37 @@ __global__ void __launch_bounds__(kMaxThreads, 5)
             const bool ok = mbar_wait(&s_mbar[buf], (ph >> buf) & 1u, kSpinLimit);
             ph ^= 1u << buf;
             if (!__syncthreads_and(ok)) {
-                if (tid == 0) set_status(&s_cur.out.hdr->status, HI_ETIMEOUT);
+                if (tid == 0) set_status(&C.out.hdr->status, HI_ETIMEOUT);
                 if (dbuf && s_next < (int)total && s_tma[(it + 1) & 1])
                     mbar_wait(&s_mbar[buf ^ 1], (ph >> (buf ^ 1)) & 1u, kSpinLimit);
+                if (tid == 0) cp_async_wait_all();
                 return;
             }
         } else {
-            load_tile_plain<A>(v, s_cur.x, s_cur.g, ti);
+            load_tile_plain<A>(v, C.x, C.g, ti);
             __syncthreads();
+            const int nf = s_tf[(it + 1) & 1];
+            if (s_next < (int)total && !s_tma[(it + 1) & 1])
+                prefetch_rows_l2<A>(fields[nf].x, 4, fields[nf].g, s_ti[(it + 1) & 1]);
         }
         const int next = s_next;
-        if (!s_cur.skip)
-            compress_tile<A>(s_cur.g, ti, v, cs, hc, s_hist, s_sel, s_lv, s_cur.h, s_cur.full_ok != 0, s_cur.out);
+        if (!C.skip) {
+            const bool full_ok = HasFull<A>::value && C.g.n[0] > 1 && C.g.n[1] > 1 && C.g.n[2] > 1;
+            compress_tile<A>(C.g, ti, v, cs, hc, s_hist, C.sel, C.lv, C.h, full_ok, C.out);
+        }
         if ((it % kHistFoldTiles) == kHistFoldTiles - 1) hist_fold(hc, s_hist);
         fence_proxy_async_smem();
         __syncthreads();
         w = (uint32_t)next;
     }
-    if (cur >= 0 && s_cur.hist) hist_flush(hc, s_hist, s_cur.hist);
+    if (blockIdx.x < total && s_cur[sl].hist) hist_flush(hc, s_hist, s_cur[sl].hist);
+    if (tid == 0) cp_async_wait_all();
+}
+
+cudaError_t launch_batch_gather(const BatchLaunch& b, cudaStream_t st)
+{
+    k_batch_gather<<<b.n, 32, 0, st>>>(const_cast<BatchField*>(b.fields));
+    return cudaGetLastError();
 }
 
 cudaError_t launch_batch_prologue(const BatchLaunch& b, cudaStream_t st)
@@ -284,7 +328,8 @@ static cudaError_t launch_batch_compress_t(const BatchLaunch& b, cudaStream_t st
     int grid = 0;
     cudaError_t err = persistent_grid(kern, b.threads, smem, b.num_sms, (int)b.total_tiles, 0, &grid);
     if (err != cudaSuccess) return err;
-    kern<<<grid, b.threads, smem, st>>>(b.fields, b.tile_start, b.n, b.total_tiles, b.queue, dbuf ? 1 : 0);
+    kern<<<grid, b.threads, smem, st>>>(b.fields, b.tile_start, b.shell_start, b.n, b.total_head, b.total_tiles,
+                                        b.queue, dbuf ? 1 : 0);
     return cudaGetLastError();
 }
 

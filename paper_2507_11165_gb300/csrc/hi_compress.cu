@@ -73,12 +73,14 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
         float* v = buf ? vbuf1 : vbuf0;
         const TileInfo ti = s_ti[it & 1];
         if (tid == 0) {
+            // one buffer: this tile's copy first (the buffer is free again),
+            // before the queue's round trip
+            if (use_tma && !dbuf && it > 0) tma_issue(v, &tmap, g, tile, A, &s_mbar[0], tma_bytes);
             const int nx = (int)gridDim.x + (int)atomicAdd(queue, 1u);
             s_next = nx;
             if (nx < g.ntiles) s_ti[(it + 1) & 1] = tile_info<A>(g, nx);
             if (use_tma && dbuf && nx < g.ntiles)
                 tma_issue(buf ? vbuf0 : vbuf1, &tmap, g, nx, A, &s_mbar[buf ^ 1], tma_bytes);
-            if (use_tma && !dbuf && it > 0) tma_issue(v, &tmap, g, tile, A, &s_mbar[0], tma_bytes);
             // one buffer: the next tile waits in L2 until this one is done
             if (use_tma && !dbuf && nx < g.ntiles) tma_l2_prefetch(&tmap, g, nx, A);
         }
@@ -97,6 +99,7 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
         } else {
             load_tile_plain<A>(v, x, g, ti);
             __syncthreads();
+            if (s_next < g.ntiles) prefetch_rows_l2<A>(x, 4, g, s_ti[(it + 1) & 1]);
         }
         const int next = s_next;
         const CompressOut out{codes, anchors, out_idx, out_val, out_cap, recon_g, hdr, (flags & kFlagVecCodes) != 0,

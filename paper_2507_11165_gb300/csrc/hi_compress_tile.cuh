@@ -9,22 +9,6 @@
 
 namespace hi {
 
-// Where one field's results go.  The single-field kernel passes its kernel
-// parameters by value; the batched kernel passes a view of the current
-// field's record in shared memory, read only after the level passes so that
-// no pointer stays in a register across them.
-struct CompressOut {
-    uint8_t* codes;
-    float* anchors;
-    uint32_t* out_idx;
-    float* out_val;
-    uint64_t out_cap;
-    float* recon;
-    hi_header* hdr;
-    bool vec_ok;   // code rows may be stored as vectors
-    bool hist_on;  // count the histogram
-};
-
 // The tile's floats are in v (reconstructed in place), its codes are staged
 // in cs; g, ti: the field and the tile; s_sel / s_lv: the level
 // configuration; full_ok: the field may take the compile-time full-tile
@@ -98,6 +82,71 @@ __device__ __forceinline__ void compress_tile(const FieldGeo& g, const TileInfo&
                 for (int b = 0; b < 4 * CH; ++b) hist_count(hc, s_hist, (w[b >> 2] >> (8 * (b & 3))) & 0xff, act);
             }
         }
+    } else if ((own2 & 3) == 0 && own2 <= 32) {
+        // rows of whole 4-code words that cannot go out as 16-byte vectors
+        // (row pitch or base not 16-byte aligned): a word per thread step,
+        // stored as one word where the address allows, else as 4 bytes
+        const int wpr = own2 >> 2;
+        const int items = rows * wpr;
+        const float inv_wpr = 1.0f / (float)wpr, inv_own1 = 1.0f / (float)own1;
+        for (int i0 = 0; i0 < items; i0 += blockDim.x) {
+            const int i = i0 + tid;
+            const bool act = i < items;
+            const int ii = act ? i : 0;
+            const int row = (int)(((float)ii + 0.5f) * inv_wpr), k = ii - row * wpr;
+            const int c0 = (int)(((float)row + 0.5f) * inv_own1), c1 = row - c0 * own1;
+            const int vi = c0 * Lw::PY + c1 * Lw::PX + 4 * k;
+            const uint32_t w = *reinterpret_cast<const uint32_t*>(cs + c0 * Lw::CYC + c1 * Lw::CXC + 4 * k);
+            const int64_t gi = ((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2] + 4 * k;
+            if (act) {
+                uint8_t* dst = codes + gi;
+                if ((reinterpret_cast<uintptr_t>(dst) & 3u) == 0) {
+                    *reinterpret_cast<uint32_t*>(dst) = w;
+                } else {
+                    dst[0] = (uint8_t)w;
+                    dst[1] = (uint8_t)(w >> 8);
+                    dst[2] = (uint8_t)(w >> 16);
+                    dst[3] = (uint8_t)(w >> 24);
+                }
+                if (recon_g) {
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) recon_g[gi + b] = v[vi + b];
+                }
+            }
+            const uint32_t z = (w - 0x01010101u) & ~w & 0x80808080u;
+            if (__any_sync(0xffffffffu, act && z != 0)) {
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    outlier_append<A>(act && ((w >> (8 * b)) & 0xffu) == 0, vi + b, v, hdr, out_idx, out_val, out_cap,
+                                      g, ti.o);
+            }
+            if (hist_on) {
+#pragma unroll
+                for (int b = 0; b < 4; ++b) hist_count(hc, s_hist, (w >> (8 * b)) & 0xff, act);
+            }
+        }
+    } else if (own2 <= 32) {
+        // rows that are not stored as vectors: lanes over the columns, two
+        // rows per warp step when they are at most 16 wide
+        const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+        const bool two = own2 <= 16;
+        const int rpw = two ? 2 : 1;
+        const int sub = two ? (lane >> 4) : 0, col = two ? (lane & 15) : lane;
+        for (int r0 = warp * rpw; r0 < rows; r0 += nw * rpw) {
+            const int row = r0 + sub;
+            const bool act = row < rows && col < own2;
+            const int rr = act ? row : 0, c2 = act ? col : 0;
+            const int c0 = rr / own1, c1 = rr - c0 * own1;
+            const int code = cs[c0 * Lw::CYC + c1 * Lw::CXC + c2];
+            const int64_t gi = ((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2] + c2;
+            if (act) {
+                codes[gi] = (uint8_t)code;
+                if (recon_g) recon_g[gi] = v[c0 * Lw::PY + c1 * Lw::PX + c2];
+            }
+            if (hist_on) hist_count(hc, s_hist, code, act);
+            outlier_append<A>(act && code == 0, c0 * Lw::PY + c1 * Lw::PX + c2, v, hdr, out_idx, out_val, out_cap,
+                              g, ti.o);
+        }
     } else {
         const int items = rows * own2;
         for (int i0 = 0; i0 < items; i0 += blockDim.x) {
@@ -106,15 +155,17 @@ __device__ __forceinline__ void compress_tile(const FieldGeo& g, const TileInfo&
             const int row = act ? i / own2 : 0, c2 = act ? i - row * own2 : 0;
             const int c0 = row / own1, c1 = row - c0 * own1;
             const int code = cs[c0 * Lw::CYC + c1 * Lw::CXC + c2];
-            if (act)
-                codes[((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2] + c2] =
-                    (uint8_t)code;
+            if (act) {
+                const int64_t gi = ((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2] + c2;
+                codes[gi] = (uint8_t)code;
+                if (recon_g) recon_g[gi] = v[c0 * Lw::PY + c1 * Lw::PX + c2];
+            }
             if (hist_on) hist_count(hc, s_hist, code, act);
             outlier_append<A>(act && code == 0, c0 * Lw::PY + c1 * Lw::PX + c2, v, hdr, out_idx, out_val, out_cap,
                               g, ti.o);
         }
     }
-    if (recon_g) {
+    if (recon_g && vec_codes) {
         const int items = rows * own2;
         for (int i = tid; i < items; i += blockDim.x) {
             const int row = i / own2, c2 = i - row * own2;
@@ -145,10 +196,32 @@ __device__ __forceinline__ void hist_fold(uint16_t* hc, uint32_t* s_hist)
 {
     const int tid = threadIdx.x;
     for (int k = 0; k < kHistBins; ++k) {
-        uint32_t c = hc[k * blockDim.x + tid];
+        const uint32_t c = __reduce_add_sync(0xffffffffu, (uint32_t)hc[k * blockDim.x + tid]);
         hc[k * blockDim.x + tid] = 0;
-        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
         if ((tid & 31) == 0 && c) atomicAdd(&s_hist[kHistLo + k], c);
+    }
+}
+
+// Add the CTA's counts to hist_g and clear them, with no barrier of its own:
+// the hot bins of each warp go out straight from a warp reduction; the
+// shared bins are read after a barrier that followed their last update and
+// are next updated after a later one.  (The shared bin of code 128 may hold
+// a wrapped negative count, the anchors taken off; the sum in hist_g is
+// exact modulo 2^32.)
+__device__ __forceinline__ void hist_flush_to(uint16_t* hc, uint32_t* s_hist, uint32_t* hist_g)
+{
+    const int tid = threadIdx.x;
+    for (int k = 0; k < kHistBins; ++k) {
+        const uint32_t c = __reduce_add_sync(0xffffffffu, (uint32_t)hc[k * blockDim.x + tid]);
+        hc[k * blockDim.x + tid] = 0;
+        if ((tid & 31) == 0 && c) atomicAdd(&hist_g[kHistLo + k], c);
+    }
+    for (int i = tid; i < 256; i += blockDim.x) {
+        const uint32_t c = s_hist[i];
+        if (c) {
+            atomicAdd(&hist_g[i], c);
+            s_hist[i] = 0;
+        }
     }
 }
 

@@ -79,13 +79,14 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
         uint8_t* cs = buf ? cbuf1 : cbuf0;
         const TileInfo ti = s_ti[it & 1];
         if (tid == 0) {
+            // one buffer: this tile's copy first, before the queue's round trip
+            if (use_tma && !dbuf && it > 0) tma_issue(cs, &cmap, g, tile, A, &s_mbar[0], tma_bytes);
             const int nx = (int)gridDim.x + (int)atomicAdd(queue, 1u);
             s_next = nx;
             if (nx < g.ntiles) s_ti[(it + 1) & 1] = tile_info<A>(g, nx);
             s_rare.o[0] = ti.o[0], s_rare.o[1] = ti.o[1], s_rare.o[2] = ti.o[2];
             if (use_tma && dbuf && nx < g.ntiles)
                 tma_issue(buf ? cbuf0 : cbuf1, &cmap, g, nx, A, &s_mbar[buf ^ 1], tma_bytes);
-            if (use_tma && !dbuf && it > 0) tma_issue(cs, &cmap, g, tile, A, &s_mbar[0], tma_bytes);
             // one buffer: the next tile waits in L2 until this one is done
             if (use_tma && !dbuf && nx < g.ntiles) tma_l2_prefetch(&cmap, g, nx, A);
         }
@@ -104,6 +105,7 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
         } else {
             load_codes_plain<A>(cs, codes, g, ti);
             __syncthreads();
+            if (s_next < g.ntiles) prefetch_rows_l2<A>(codes, 1, g, s_ti[(it + 1) & 1]);
         }
         const int next = s_next;
         const float a_nxt = anchor_of<A>(g, anchors, next, s_ti[(it + 1) & 1]);  // in flight while this tile is reconstructed
@@ -132,6 +134,20 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
                 const float4 f4 = *reinterpret_cast<const float4*>(v + c0 * Lw::PY + c1 * Lw::PX + ch * 4);
                 *reinterpret_cast<float4*>(out + ((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] +
                                            ti.o[2] + ch * 4) = f4;
+            }
+        } else if (own2 <= 32) {
+            // lanes over the columns, two rows per warp step when they are at most 16 wide
+            const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+            const bool two = own2 <= 16;
+            const int rpw = two ? 2 : 1;
+            const int sub = two ? (lane >> 4) : 0, col = two ? (lane & 15) : lane;
+            for (int r0 = warp * rpw; r0 < rows; r0 += nw * rpw) {
+                const int row = r0 + sub;
+                if (row < rows && col < own2) {
+                    const int c0 = row / own1, c1 = row - c0 * own1;
+                    out[((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2] + col] =
+                        v[c0 * Lw::PY + c1 * Lw::PX + col];
+                }
             }
         } else {
             const int items = rows * own2;

@@ -126,6 +126,11 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ void fence_proxy_async_smem()
@@ -180,6 +185,12 @@ __device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* map, int x, i
                      reinterpret_cast<uint64_t>(map)),
                  "r"(x), "r"(y), "r"(z)
                  : "memory");
+}
+
+// Pull the cache line holding p into L2.
+__device__ __forceinline__ void prefetch_l2(const void* p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map)

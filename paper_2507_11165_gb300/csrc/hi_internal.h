@@ -19,6 +19,27 @@ enum : int {
     kFlagDoubleBuf = 8, // two tile buffers fit in shared memory: prefetch the next tile
 };
 
+// Quantizer constants every point needs (Eq. 1), passed by value.
+struct Hot {
+    float eb_f, ebx2_f, r_f;
+};
+
+// Where one field's results go.  The single-field kernel passes its kernel
+// parameters by value; the batched kernel passes a view of the current
+// field's record in shared memory, read only after the level passes so that
+// no pointer stays in a register across them.
+struct CompressOut {
+    uint8_t* codes;
+    float* anchors;
+    uint32_t* out_idx;
+    float* out_val;
+    uint64_t out_cap;
+    float* recon;
+    hi_header* hdr;
+    bool vec_ok;   // code rows may be stored as vectors
+    bool hist_on;  // count the histogram
+};
+
 struct CompressLaunch {
     CUtensorMap tmap;
     FieldGeo g;
@@ -99,8 +120,27 @@ constexpr int kRangeBlocks = 1024;
 // ---------------------------------------------------------------------------
 constexpr int64_t kBatchChunk = 1 << 18;  // points per range work item
 
+// What the predict-quantize kernel needs of a field: copied whole into
+// shared memory (16-byte asynchronous copies) when a CTA moves to the field.
+// The host fills the static part; after the auto-tuner, a gather launch
+// copies the constants, the status and the level configuration from the
+// field's header.
+struct alignas(16) BatchCur {
+    CompressOut out;
+    FieldGeo g;
+    const float* x;
+    uint32_t* hist;
+    Hot h;
+    int flags;
+    int skip;     // an earlier stage of this field failed: leave its outputs
+    int full_ok;  // every dim active: whole tiles take the compile-time passes
+    hi_level lv[HI_MAX_LEVELS];
+    int sel[HI_MAX_LEVELS];
+};
+
 struct alignas(64) BatchField {
     CUtensorMap tmap;  // the field as (PX, A+1, b0) float boxes (when flags & kFlagTma)
+    BatchCur cur;
     FieldGeo g;
     hi_params p;
     const float* x;
@@ -122,16 +162,19 @@ struct alignas(64) BatchField {
     int flags;
     int m, stride;       // auto-tune samples (m = 0: levels given)
     uint32_t nchunks;    // range work items (0: absolute bound)
+    uint32_t nint;       // tiles at the head of the field's queue order (whole 3D tiles first)
 };
 
 struct BatchLaunch {
     const BatchField* fields;
-    const uint32_t* tile_start;    // [n + 1] first work item of each field in the tile queue
+    const uint32_t* tile_start;    // [n + 1] first work item of each field's head tiles (nint of them)
+    const uint32_t* shell_start;   // [n + 1] same for the remaining tiles, after all head tiles
     const uint32_t* chunk_start;   // [n + 1] same for range chunks
     const uint32_t* sample_start;  // [n + 1] same for auto-tune samples
     uint32_t* queue;               // tile queue counter
     int n;
     uint32_t total_tiles, total_chunks, total_samples;
+    uint32_t total_head;  // work items of the head tiles
     int A;
     int threads;
     int buffers;  // 1 or 2 (2 only when every field is staged by TMA)
@@ -141,6 +184,7 @@ struct BatchLaunch {
 cudaError_t launch_batch_prologue(const BatchLaunch& b, cudaStream_t st);
 cudaError_t launch_batch_range(const BatchLaunch& b, cudaStream_t st);
 cudaError_t launch_batch_tune(const BatchLaunch& b, cudaStream_t st);
+cudaError_t launch_batch_gather(const BatchLaunch& b, cudaStream_t st);
 cudaError_t launch_batch_compress(const BatchLaunch& b, cudaStream_t st);
 
 }  // namespace hi

@@ -102,9 +102,6 @@ __device__ __forceinline__ int64_t global_index(const FieldGeo& g, const int o[3
 
 // Values every point needs, passed by value; the decompressor's rare outlier
 // read goes through shared memory so that no pass keeps it in registers.
-struct Hot {
-    float eb_f, ebx2_f, r_f;
-};
 
 struct Rare {
     const float* out;  // decompress: outlier values were scattered here beforehand
@@ -433,53 +430,166 @@ __device__ __forceinline__ void levels_ragged(const hi_level* s_lv, float* v, ui
 // Staging
 // ---------------------------------------------------------------------------
 // Tiles that TMA cannot stage (a row pitch that is not a multiple of 16
-// bytes, an unaligned base): a warp per row; floats go by 4-byte cp.async,
-// so a thread's copies are all in flight at once; the caller synchronises.
+// bytes, an unaligned base).
+//
+// 16-byte aligned base: a row of e2 + 1 floats starting at float offset s
+// is read as the aligned float4 chunks that cover it (one lane per chunk,
+// LPR lanes per row, U rows per lane in flight) and realigned against the
+// next lane's chunk; each lane stores one aligned float4 of the
+// shared-memory row (floats past e2 land in the row's padding).  Chunks that
+// would reach past the field's end are read float by float.
+// Otherwise: a warp per row, 4-byte cp.async per float.
+// The caller synchronises.
 template <int A>
 __device__ void load_tile_plain(float* v, const float* __restrict__ x, const FieldGeo& g, const TileInfo& ti)
 {
     using Lw = Lay<A>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int e2 = ti.e[2];
     const int w1 = ti.e[1] + 1, rows = (ti.e[0] + 1) * w1;
+    if ((reinterpret_cast<uintptr_t>(x) & 15u) == 0) {
+        constexpr int LPR = (A >= 32) ? 16 : 8;
+        constexpr int RPS = 32 / LPR;
+        constexpr int U = 3;
+        static_assert((3 + A) / 4 + 1 <= LPR, "row chunks");
+        static_assert((A / 4) * 4 + 3 < Lw::PX, "the last chunk of a row stays in its padding");
+        const int j = lane % LPR, sub = lane / LPR;
+        const float inv_w1 = 1.0f / (float)w1;
+        for (int r0 = warp * RPS + sub; r0 - sub < rows; r0 += nw * RPS * U) {
+            float4 cv[U];
+            int dv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int r = r0 + u * nw * RPS;
+                cv[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                dv[u] = 0;
+                if (r < rows) {
+                    const int c0 = (int)(((float)r + 0.5f) * inv_w1), c1 = r - c0 * w1;
+                    const int64_t si = ((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2];
+                    const int d = (int)(si & 3);
+                    dv[u] = d;
+                    const int64_t ci = si - d + 4 * j;  // first float of this lane's chunk
+                    if (4 * j <= d + e2) {
+                        if (ci + 4 <= g.N) {
+                            cv[u] = __ldg(reinterpret_cast<const float4*>(x + ci));
+                        } else {
+                            cv[u].x = x[ci];
+                            if (ci + 1 < g.N) cv[u].y = x[ci + 1];
+                            if (ci + 2 < g.N) cv[u].z = x[ci + 2];
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                float4 nx;
+                nx.x = __shfl_down_sync(0xffffffffu, cv[u].x, 1);
+                nx.y = __shfl_down_sync(0xffffffffu, cv[u].y, 1);
+                nx.z = __shfl_down_sync(0xffffffffu, cv[u].z, 1);
+                const int r = r0 + u * nw * RPS;
+                if (r < rows && 4 * j <= e2) {
+                    const int c0 = (int)(((float)r + 0.5f) * inv_w1), c1 = r - c0 * w1;
+                    const float4 a = cv[u];
+                    const int d = dv[u];
+                    float4 o;
+                    o.x = d == 0 ? a.x : (d == 1 ? a.y : (d == 2 ? a.z : a.w));
+                    o.y = d == 0 ? a.y : (d == 1 ? a.z : (d == 2 ? a.w : nx.x));
+                    o.z = d == 0 ? a.z : (d == 1 ? a.w : (d == 2 ? nx.x : nx.y));
+                    o.w = d == 0 ? a.w : (d == 1 ? nx.x : (d == 2 ? nx.y : nx.z));
+                    *reinterpret_cast<float4*>(v + c0 * Lw::PY + c1 * Lw::PX + 4 * j) = o;
+                }
+            }
+        }
+        return;
+    }
+    const int64_t rs = g.n[2], ps = g.n[1] * g.n[2];
+    const float* base = x + ((int64_t)ti.o[0] * g.n[1] + ti.o[1]) * g.n[2] + ti.o[2];
+    int c0 = warp / w1, c1 = warp - (warp / w1) * w1;
     for (int rr = warp; rr < rows; rr += nw) {
-        const int c0 = rr / w1;
-        const int c1 = rr - c0 * w1;
-        const float* src = x + ((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2];
-        for (int c2 = lane; c2 <= ti.e[2]; c2 += 32) cp_async4(v + c0 * Lw::PY + c1 * Lw::PX + c2, src + c2);
+        const float* src = base + c0 * ps + c1 * rs;
+        float* dst = v + c0 * Lw::PY + c1 * Lw::PX;
+        for (int c2 = lane; c2 <= e2; c2 += 32) cp_async4(dst + c2, src + c2);
+        c1 += nw;
+        while (c1 >= w1) c1 -= w1, ++c0;
     }
     cp_async_wait_all();
 }
 
-// Codes of such a tile: bytes, four rows in flight per warp.
+// Codes of such a tile.  A row of e2 + 1 bytes starting at an arbitrary
+// byte address is read as the aligned 4-byte words that cover it (one lane
+// per word, LPR lanes per row, U rows per lane in flight) and realigned with
+// a funnel shift against the next lane's word; each lane stores one aligned
+// word of the shared-memory row (the bytes past e2 land in the row's
+// padding).  Words that would reach outside [codes, codes + N) are read
+// byte by byte.
 template <int A>
 __device__ void load_codes_plain(uint8_t* cs, const uint8_t* __restrict__ codes, const FieldGeo& g,
                                  const TileInfo& ti)
 {
     using Lw = Lay<A>;
+    constexpr int LPR = (A >= 32) ? 16 : 8;  // lanes per row: (3 + A) / 4 + 1 words at most
+    constexpr int RPS = 32 / LPR;            // rows per warp step
+    constexpr int U = 4;                     // warp steps in flight
+    static_assert((3 + A) / 4 + 1 <= LPR, "row words");
+    static_assert((A / 4) * 4 + 3 < Lw::CXD, "the last word of a row stays in its padding");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int j = lane % LPR, sub = lane / LPR;
+    const int e2 = ti.e[2];
     const int w1 = ti.e[1] + 1, rows = (ti.e[0] + 1) * w1;
-    for (int r0 = warp; r0 < rows; r0 += 4 * nw) {
-        for (int c2b = 0; c2b <= ti.e[2]; c2b += 32) {
-            const int c2 = c2b + lane;
-            uint8_t t[4];
+    const float inv_w1 = 1.0f / (float)w1;
+    const uintptr_t lo = reinterpret_cast<uintptr_t>(codes), hi = lo + (uintptr_t)g.N;
+    for (int r0 = warp * RPS + sub; r0 - sub < rows; r0 += nw * RPS * U) {
+        uint32_t wv[U];
+        uint32_t dv[U];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int rr = r0 + u * nw;
-                t[u] = 0;
-                if (rr < rows && c2 <= ti.e[2]) {
-                    const int c0 = rr / w1, c1 = rr - c0 * w1;
-                    t[u] = codes[((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2] + c2];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int rr = r0 + u * nw;
-                if (rr < rows && c2 <= ti.e[2]) {
-                    const int c0 = rr / w1, c1 = rr - c0 * w1;
-                    cs[c0 * Lw::CYD + c1 * Lw::CXD + c2] = t[u];
+        for (int u = 0; u < U; ++u) {
+            const int r = r0 + u * nw * RPS;
+            wv[u] = 0u;
+            dv[u] = 0u;
+            if (r < rows) {
+                const int c0 = (int)(((float)r + 0.5f) * inv_w1), c1 = r - c0 * w1;
+                const uintptr_t a = lo + (uintptr_t)(((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] +
+                                                     ti.o[2]);
+                const uint32_t d = (uint32_t)(a & 3u);
+                dv[u] = d;
+                const uintptr_t w = a - d + 4u * (uint32_t)j;
+                if (4 * j <= (int)d + e2) {
+                    if (w >= lo && w + 4 <= hi) {
+                        wv[u] = __ldg(reinterpret_cast<const uint32_t*>(w));
+                    } else {
+                        uint32_t t = 0;
+                        for (int b = 0; b < 4; ++b)
+                            if (w + b >= lo && w + b < hi) t |= (uint32_t)(*reinterpret_cast<const uint8_t*>(w + b)) << (8 * b);
+                        wv[u] = t;
+                    }
                 }
             }
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t nxt = __shfl_down_sync(0xffffffffu, wv[u], 1);
+            const int r = r0 + u * nw * RPS;
+            if (r < rows && 4 * j <= e2) {
+                const int c0 = (int)(((float)r + 0.5f) * inv_w1), c1 = r - c0 * w1;
+                const uint32_t word = __funnelshift_r(wv[u], j + 1 < LPR ? nxt : 0u, 8 * dv[u]);
+                *reinterpret_cast<uint32_t*>(cs + c0 * Lw::CYD + c1 * Lw::CXD + 4 * j) = word;
+            }
+        }
+    }
+}
+
+// L2 prefetch of the rows of a tile that the plain loaders will read: the
+// first and last element of each row (elem bytes each).
+template <int A>
+__device__ __forceinline__ void prefetch_rows_l2(const void* base, int elem, const FieldGeo& g, const TileInfo& ti)
+{
+    const int w1 = ti.e[1] + 1, rows = (ti.e[0] + 1) * w1;
+    const char* b = static_cast<const char*>(base);
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        const int c0 = r / w1, c1 = r - c0 * w1;
+        const int64_t i = ((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2];
+        prefetch_l2(b + i * elem);
+        prefetch_l2(b + (i + ti.e[2]) * elem);
     }
 }
 
