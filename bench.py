@@ -530,6 +530,63 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+SERVE_METRIC = "serving: sustained input GB/s with p50/p99 latency (ms), Poisson 200 req/s, 40 GB budget"
+
+
+def run_serve(args):
+    """Serving workload: Poisson arrivals (200 / s), half compress of a
+    snapshot, half decompress of an earlier record; cubic sides log-uniform
+    in [64, 512]; rel eb from {1e-2, 1e-3, 1e-4, 1e-5}; admitted by slot
+    (8 streams) and a 40 GB device budget.  Snapshots are side^3 blocks of a
+    resident 512^3 field.  Also: the same requests all arriving at once
+    (saturation), and one slot only (no overlap) on the timed stream.  One
+    untimed burst of the whole stream first: the process is warm."""
+    import numpy as np
+    import torch
+
+    from paper_2507_11165_gb300 import fields, hi, serve
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    base = torch.from_numpy(fields.lognormal_grf(SHAPE, seed=SEED)).to(dev)
+    reqs = serve.make_requests(n=args.serve_requests, rate=200.0, seed=5, lo=64, hi=SHAPE[0])
+    warm = serve.make_requests(n=16, rate=1e6, seed=6, lo=64, hi=SHAPE[0])
+
+    def one(requests, slots, budget=40 * 10 ** 9):
+        ex = serve.GpuExecutor(base)
+        sv = serve.Server(ex, slots=slots, budget_bytes=budget)
+        t0 = time.perf_counter()
+        done = sv.run(requests)
+        wall = time.perf_counter() - t0
+        s = serve.summarize(done, wall)
+        s.update(peak_concurrency=sv.peak_concurrency, peak_bytes=sv.peak_bytes, slots=slots)
+        return s
+
+    burst = [serve.Request(r.id, 0.0, r.op, r.side, r.eb, r.seed, r.source) for r in reqs]
+    one(warm, 8)
+    one(burst, 8)  # a warm process: the allocator holds blocks of every size the stream asks for
+    with ClockSampler(0) as clk:
+        main = one(reqs, 8)
+    sat = one(burst, 8)
+    single = one(reqs, 1)
+    offered = sum(4 * r.side ** 3 for r in reqs) / max(r.t for r in reqs) / 1e9
+    line = dict(
+        metric=SERVE_METRIC, value=main["gbs"], unit="GB/s", n_gpus=1, steps=len(reqs), warmup=len(warm),
+        ms_per_step=1e3 * main["wall_s"] / len(reqs), higher_is_better=True, scaling="weak", vs_baseline=None,
+        dtype="f32", data="synthetic",
+        config=dict(workload="%d requests, Poisson 200/s (seed 5), 50%% compress / 50%% decompress of an earlier "
+                             "record, cubic sides log-uniform in [64, 512], rel eb from {1e-2,1e-3,1e-4,1e-5}, "
+                             "anchor stride 16, auto-tuned levels" % len(reqs),
+                    slots=8, budget_gb=40, snapshots="side^3 blocks of a resident 512^3 log-normal GRF",
+                    step="one request (value = input bytes of all requests / wall time of the run)"),
+        p50_ms=main["p50_ms"], p99_ms=main["p99_ms"], max_ms=main["max_ms"], offered_gbs=offered,
+        served=main, saturated=sat, one_slot=single,
+        gpu_launches=None,
+        clocks=clk.summary(),
+    )
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -540,9 +597,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-planes", type=int, default=512)
     ap.add_argument("--ref-planes", type=int, default=64)
-    ap.add_argument("--workload", default="single", choices=["single", "batch"],
-                    help="single: the 512^3 field (default); batch: 256 fields in one batched launch per stage")
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"],
+                    help="single: the 512^3 field (default); batch: 256 fields in one batched launch per stage; "
+                         "serve: a Poisson request stream through the continuous-batching loop")
     ap.add_argument("--batch-fields", type=int, default=256)
+    ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--shape", type=int, default=None,
                     help="cube side of a smaller field of the same recipe (profiling captures)")
     args = ap.parse_args()
@@ -555,6 +614,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_gpu(args)
 

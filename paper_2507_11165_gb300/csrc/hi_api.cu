@@ -196,12 +196,25 @@ void pitches(int A, int* PX, int* CX)
     }
 }
 
+constexpr int kMaxDevices = 64;
+
 int num_sms()
 {
+    static std::mutex mu;
+    static int cache[kMaxDevices] = {};
     int dev = 0, n = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (dev >= 0 && dev < kMaxDevices) {
+        std::lock_guard<std::mutex> lock(mu);
+        if (cache[dev] > 0) return cache[dev];
+    }
     if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
-    return n > 0 ? n : 1;
+    if (n < 1) n = 1;
+    if (dev >= 0 && dev < kMaxDevices) {
+        std::lock_guard<std::mutex> lock(mu);
+        cache[dev] = n;
+    }
+    return n;
 }
 
 int threads_for(const Geometry& G, uint32_t tuning)
@@ -218,8 +231,6 @@ int threads_for(const Geometry& G, uint32_t tuning)
 // Workspace of hi_compress_static_ws: one fixed array per device, part of
 // this library's device image, so that the call allocates nothing.
 static __device__ __align__(256) unsigned char g_static_ws[HI_STATIC_WS_BYTES];
-
-constexpr int kMaxDevices = 64;
 
 // Device address of g_static_ws on the current device, looked up once per
 // device; nullptr if the look-up fails.

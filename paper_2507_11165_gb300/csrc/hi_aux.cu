@@ -99,7 +99,7 @@ static cudaError_t launch_tune_t(const TuneLaunch& t, cudaStream_t st)
     using TG = TileGeom<A>;
     const size_t smem = (size_t)t.g.b0 * TG::P * TG::PX * 4;
     auto kern = k_tune<A>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_max_smem(kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<dim3(t.m, t.cands.ncfg), 256, smem, st>>>(t.tmap, t.g, t.x, t.cands, t.stride, t.err, t.ticket, t.hdr,
                                                      t.tma_bytes, t.use_tma ? 1 : 0);

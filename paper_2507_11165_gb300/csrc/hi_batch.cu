@@ -303,7 +303,7 @@ static cudaError_t launch_batch_tune_t(const BatchLaunch& b, cudaStream_t st)
     using TG = TileGeom<A>;
     const size_t smem = (size_t)(A + 1) * TG::P * TG::PX * 4;
     auto kern = k_batch_tune<A>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_max_smem(kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<dim3(b.total_samples, 12), 256, smem, st>>>(b.fields, b.sample_start, b.n);
     return cudaGetLastError();

@@ -8,6 +8,9 @@
 #pragma once
 
 #include <cstdint>
+#include <map>
+#include <mutex>
+#include <utility>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -30,6 +33,24 @@ __device__ __forceinline__ uint64_t global_ns()
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
+}
+
+// Raise a kernel's dynamic shared-memory limit to at least smem on the
+// current device; the runtime is asked only when a larger value is needed.
+template <typename K>
+static cudaError_t set_max_smem(K kern, size_t smem)
+{
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> done;
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& have = done[{dev, reinterpret_cast<const void*>(kern)}];
+    if (have >= smem) return cudaSuccess;
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err == cudaSuccess) have = smem;
+    return err;
 }
 
 // Block geometry for anchor stride A (Sec. 5.1.1): (A+1) points per active

@@ -31,6 +31,8 @@
 // counts the histogram.
 #pragma once
 #include <cstdint>
+#include <map>
+#include <mutex>
 
 #include "hi_device.cuh"
 #include "hi_internal.h"
@@ -682,13 +684,51 @@ static bool fits_double(K kern, size_t dyn_double)
     return dyn_double + fa.sharedSizeBytes <= (size_t)optin;
 }
 
+// Resident CTAs per SM of a kernel at a launch shape, asked of the runtime
+// once per (device, kernel, threads, shared memory) and kept: the queries
+// cost more host time than a launch.
+struct OccKey {
+    int dev;
+    const void* kern;
+    int threads;
+    size_t smem;
+    bool operator<(const OccKey& o) const
+    {
+        if (dev != o.dev) return dev < o.dev;
+        if (kern != o.kern) return kern < o.kern;
+        if (threads != o.threads) return threads < o.threads;
+        return smem < o.smem;
+    }
+};
+
+template <typename K>
+static cudaError_t ctas_per_sm(K kern, int threads, size_t smem, int* per_sm)
+{
+    static std::mutex mu;
+    static std::map<OccKey, int> cache;
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    const OccKey key{dev, reinterpret_cast<const void*>(kern), threads, smem};
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+        *per_sm = it->second;
+        return cudaSuccess;
+    }
+    err = set_max_smem(kern, smem);
+    if (err != cudaSuccess) return err;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, threads, smem);
+    if (err != cudaSuccess) return err;
+    cache[key] = *per_sm;
+    return cudaSuccess;
+}
+
 template <typename K>
 static cudaError_t persistent_grid(K kern, int threads, size_t smem, int num_sms, int ntiles, int max_ctas, int* grid)
 {
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
     int per_sm = 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    cudaError_t err = ctas_per_sm(kern, threads, smem, &per_sm);
     if (err != cudaSuccess) return err;
     if (per_sm < 1) per_sm = 1;
     int g = per_sm * num_sms;

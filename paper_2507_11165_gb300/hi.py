@@ -73,6 +73,7 @@ SYMBOLS = ("hi_query", "hi_compress", "hi_decompress", "hi_autotune", "hi_autotu
            "hi_status_str", "hi_version", "hi_set_stage_events", "hi_compress_static_ws", "hi_batch_query",
            "hi_batch_prepare", "hi_compress_batch", "hi_batch_tune_launch")
 STATIC_WS_BYTES = 1 << 20  # HI_STATIC_WS_BYTES
+DECOMPRESS_WS_BYTES = 256  # HI_DECOMPRESS_WS_BYTES
 
 
 class HiError(RuntimeError):
