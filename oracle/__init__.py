@@ -81,6 +81,7 @@ def _load():
             lib.hi_oracle_tune_samples.restype = i64
             lib.hi_oracle_tune_configs.argtypes = [P, P, P]
             lib.hi_oracle_tune_errors.argtypes = [P, ctypes.c_int, P, P, P]
+            lib.hi_oracle_tune_errors_tiles.argtypes = [P, ctypes.c_int, P, P, i64, P, P]
             lib.hi_oracle_tune_select.argtypes = [P, ctypes.c_int, P, P, P]
             lib.hi_oracle_trace.argtypes = [P, ctypes.c_int, P, P, P, P, P]
             _lib = lib
@@ -218,6 +219,20 @@ def tune_errors(x, A):
     nc = np.zeros(1, dtype=np.int32)
     _check(lib.hi_oracle_tune_errors(_p(_dims3(x.shape)), int(A), _p(x), _p(err), _p(nc)))
     return err[:L * int(nc[0])].reshape(L, int(nc[0]))
+
+
+def tune_errors_tiles(x, A, tiles):
+    """err[k, L, ncfg]: the terms of :func:`tune_errors` of block tiles[k]
+    (row-major block ids of x), one block at a time."""
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    L = n_levels(A)
+    t = np.ascontiguousarray(tiles, dtype=np.int64)
+    err = np.zeros(max(1, t.size) * L * 12, dtype=np.float64)
+    nc = np.zeros(1, dtype=np.int32)
+    _check(lib.hi_oracle_tune_errors_tiles(_p(_dims3(x.shape)), int(A), _p(x), _p(t), t.size, _p(err), _p(nc)))
+    n = int(nc[0])
+    return err[:t.size * L * n].reshape(t.size, L, n)
 
 
 def tune_select(shape, A, err):

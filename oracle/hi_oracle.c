@@ -819,6 +819,71 @@ done:
     return rc;
 }
 
+/* Per listed block (row-major block ids, in list order): err[(k * L + l) *
+ * ncfg + c] = sum of |x - p| over the points of level l of block tiles[k]
+ * under configuration c, predictions from original values -- the terms that
+ * hi_oracle_tune_errors adds up over its sampled blocks.  Lets ranks that
+ * hold parts of a field evaluate the global sample blocks they hold. */
+int hi_oracle_tune_errors_tiles(const int64_t dims[3], int A, const float* x, const int64_t* tiles,
+                                int64_t ntiles, double* err, int* ncfg_out)
+{
+    geom G;
+    block B;
+    block_mem M;
+    action act;
+    uint8_t cinterp[12], corder[36];
+    int64_t k, nblocks;
+    int ncfg, c, l, rc = geom_init(&G, dims, A);
+    if (rc) return rc;
+    nblocks = G.nb[0] * G.nb[1] * G.nb[2];
+    ncfg = hi_oracle_tune_configs(dims, cinterp, corder);
+    *ncfg_out = ncfg;
+    for (k = 0; k < ntiles * G.L * ncfg; k++) err[k] = 0.0;
+    if (block_mem_alloc(&M, A)) {
+        block_mem_free(&M);
+        return ORC_ENOMEM;
+    }
+    block_attach(&B, &M);
+    for (k = 0; k < ntiles; k++) {
+        const int64_t t = tiles[k];
+        int64_t t0, t1, t2;
+        if (t < 0 || t >= nblocks) {
+            rc = ORC_EINVAL;
+            goto done;
+        }
+        t0 = t / (G.nb[1] * G.nb[2]);
+        t1 = (t / G.nb[2]) % G.nb[1];
+        t2 = t % G.nb[2];
+        for (l = G.L - 1; l >= 0; l--) {
+            for (c = 0; c < ncfg; c++) {
+                int ll;
+                block_init(&B, &G, t0, t1, t2);
+                block_seed(&B, x, NULL, MODE_TUNE);
+                memset(&act, 0, sizeof act);
+                act.mode = MODE_TUNE;
+                for (ll = G.L - 1; ll > l; ll--) {
+                    run_level(&B, ll, cinterp[c], corder + 3 * c, &act);
+                    if (act.status) break;
+                }
+                if (act.status) {
+                    rc = act.status;
+                    goto done;
+                }
+                act.err = 0.0;
+                run_level(&B, l, cinterp[c], corder + 3 * c, &act);
+                if (act.status) {
+                    rc = act.status;
+                    goto done;
+                }
+                err[(k * G.L + l) * ncfg + c] = act.err;
+            }
+        }
+    }
+done:
+    block_mem_free(&M);
+    return rc;
+}
+
 /* Per level, the configuration with the smallest error; ties go to the
  * first in enumeration order. */
 int hi_oracle_tune_select(const int64_t dims[3], int A, const double* err, uint8_t* interp, uint8_t* order)
