@@ -125,7 +125,8 @@ HI_API hi_status hi_query(const hi_params* p, uint64_t* n_points, uint64_t* n_an
 /* Compress (Sec. 3.2, Sec. 5.1, Sec. 5.2.1).  Enqueues, in order: header
  * set-up; for HI_EB_REL the value range of d_x and eps = eb * (max - min)
  * (eps = eb if the range is 0); for autotune the per-level choice of spline
- * and dimension sequence on 0.2% of the blocks; then the fused
+ * and dimension sequence on 0.2% of the blocks (in one launch with the
+ * range when both are asked for: neither needs the other); then the fused
  * predict-quantize pass.
  *   d_x        [n_points] float32 input, 4-byte aligned (16 for the fast path)
  *   d_codes    [n_points] uint8 codes in the layout of d_x (anchors get 128)
@@ -262,8 +263,9 @@ HI_API hi_status hi_batch_prepare(uint32_t n, const hi_batch_field* h_fields, ui
                                   size_t ws_bytes, hi_batch_plan* h_plan, cudaStream_t stream);
 
 /* Compress every field of a prepared batch.  Enqueues four launches on
- * stream (header set-up; value range of every relative-bound field;
- * auto-tune of every auto-tuned field; predict-quantize of all tiles) and
+ * stream (header set-up; value range of every relative-bound field beside
+ * the auto-tuner of every auto-tuned field; the tuner's choices into the
+ * field records; predict-quantize of all tiles) and
  * nothing else: no host synchronisation, no memory copy.  The stage events
  * of hi_set_stage_events (0..4) are recorded as for hi_compress.  Calls that
  * share d_ws must not overlap. */
@@ -283,7 +285,9 @@ HI_API hi_status hi_batch_tune_launch(hi_batch_plan* h_plan, void* d_ws, uint32_
  * hi_compress / hi_decompress calls made by the calling host thread.
  * events[0..7] (cudaEvent_t handles created by the caller):
  *   hi_compress:   0 before header set-up, 1 before the range pass, 2 before
- *                  the auto-tuner, 3 before predict-quantize, 4 after it;
+ *                  the auto-tuner, 3 before predict-quantize, 4 after it
+ *                  (with both a relative bound and auto-tune, range and
+ *                  auto-tuner share one launch between events 1 and 2);
  *   hi_decompress: 5 before the outlier scatter, 6 before reconstruction,
  *                  7 after it.
  * A stage that does not run still records its event.  n must be 8; pass

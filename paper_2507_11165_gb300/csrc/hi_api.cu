@@ -2,7 +2,9 @@
 // workspace layout, TMA descriptors and the launch sequence of each call.
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -297,8 +299,7 @@ hi_status hi_query(const hi_params* p, uint64_t* n_points, uint64_t* n_anchors, 
     return HI_OK;
 }
 
-static hi_status enqueue_tune(const Geometry& G, const float* d_x, hi_header* d_header, void* d_ws,
-                              cudaStream_t stream)
+static TuneLaunch tune_launch(const Geometry& G, const float* d_x, hi_header* d_header, void* d_ws)
 {
     TuneLaunch t{};
     int PX, CX;
@@ -313,7 +314,13 @@ static hi_status enqueue_tune(const Geometry& G, const float* d_x, hi_header* d_
     t.err = reinterpret_cast<double*>(static_cast<char*>(d_ws) + kWsTune);
     t.ticket = reinterpret_cast<uint32_t*>(static_cast<char*>(d_ws) + kWsTuneTicket);
     t.hdr = d_header;
-    return cuda_status(launch_tune(G.A, t, stream));
+    return t;
+}
+
+static hi_status enqueue_tune(const Geometry& G, const float* d_x, hi_header* d_header, void* d_ws,
+                              cudaStream_t stream)
+{
+    return cuda_status(launch_tune(G.A, tune_launch(G, d_x, d_header, d_ws), stream));
 }
 
 hi_status hi_compress(const hi_params* p, const float* d_x, uint8_t* d_codes, float* d_anchors,
@@ -336,17 +343,29 @@ hi_status hi_compress(const hi_params* p, const float* d_x, uint8_t* d_codes, fl
         launch_prologue(d_header, *p, G.n_anchors, out_cap, (uint32_t)G.L, d_hist, ticket, queue, stream);
     if (e != cudaSuccess) return HI_ECUDA;
     stage_event(1, stream);
-    if (p->eb_mode == HI_EB_REL) {
+    if (p->eb_mode == HI_EB_REL && p->autotune) {
+        // one launch: the auto-tuner's blocks run beside the range pass (independent of each other)
         int nb = kRangeBlocks;
-        const int64_t need = (G.g.N + 4095) / 4096;
+        const int64_t need = (G.g.N + 2047) / 2048;
         if (need < nb) nb = (int)(need > 0 ? need : 1);
-        e = launch_range(d_x, G.g.N, reinterpret_cast<float2*>(ws + kWsPartials), nb, ticket, d_header, stream);
+        e = launch_range_tune(G.A, tune_launch(G, d_x, d_header, d_ws), reinterpret_cast<float2*>(ws + kWsPartials),
+                              nb, ticket, stream);
         if (e != cudaSuccess) return HI_ECUDA;
-    }
-    stage_event(2, stream);
-    if (p->autotune) {
-        s = enqueue_tune(G, d_x, d_header, d_ws, stream);
-        if (s != HI_OK) return s;
+        stage_event(2, stream);
+    } else {
+        if (p->eb_mode == HI_EB_REL) {
+            int nb = kRangeBlocks;
+            const int64_t need = (G.g.N + 4095) / 4096;
+            if (need < nb) nb = (int)(need > 0 ? need : 1);
+            e = launch_range(d_x, G.g.N, reinterpret_cast<float2*>(ws + kWsPartials), nb, ticket, d_header,
+                             stream);
+            if (e != cudaSuccess) return HI_ECUDA;
+        }
+        stage_event(2, stream);
+        if (p->autotune) {
+            s = enqueue_tune(G, d_x, d_header, d_ws, stream);
+            if (s != HI_OK) return s;
+        }
     }
     stage_event(3, stream);
     CompressLaunch c{};
@@ -572,9 +591,14 @@ hi_status hi_batch_prepare(uint32_t n, const hi_batch_field* h_fields, uint32_t 
     plan.tuning = tuning;
     char* ws = static_cast<char*>(d_ws);
     const size_t host_bytes = plan.off_err;  // table, prefixes and tickets (partials / sums need no init)
-    std::vector<unsigned char> host(host_bytes, 0);
-    BatchField* table = reinterpret_cast<BatchField*>(host.data() + plan.off_table);
-    uint32_t* pre = reinterpret_cast<uint32_t*>(host.data() + plan.off_prefix);
+    // host image of the table, aligned like the device copy
+    const size_t host_alloc = align256(host_bytes);
+    std::unique_ptr<unsigned char, void (*)(void*)> host(static_cast<unsigned char*>(std::aligned_alloc(256, host_alloc)),
+                                                         std::free);
+    if (!host) return HI_ENOMEM;
+    std::memset(host.get(), 0, host_alloc);
+    BatchField* table = reinterpret_cast<BatchField*>(host.get() + plan.off_table);
+    uint32_t* pre = reinterpret_cast<uint32_t*>(host.get() + plan.off_prefix);
     uint32_t *ts = pre, *cs = pre + (n + 1), *ss = pre + 2 * (n + 1), *hs = pre + 3 * (n + 1);
     uint64_t tiles = 0, chunks = 0, samples = 0, err = 0, head = 0, shell = 0;
     bool all_tma = true;
@@ -634,7 +658,7 @@ hi_status hi_batch_prepare(uint32_t n, const hi_batch_field* h_fields, uint32_t 
     ss[n] = (uint32_t)samples;
     plan.all_tma = all_tma ? 1u : 0u;
     plan.reserved[0] = head;
-    cudaError_t e = cudaMemcpyAsync(ws, host.data(), host_bytes, cudaMemcpyHostToDevice, stream);
+    cudaError_t e = cudaMemcpyAsync(ws, host.get(), host_bytes, cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) return HI_ECUDA;
     e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return HI_ECUDA;
@@ -649,9 +673,8 @@ hi_status hi_compress_batch(const hi_batch_plan* h_plan, void* d_ws, cudaStream_
     stage_event(0, stream);
     if (launch_batch_prologue(b, stream) != cudaSuccess) return HI_ECUDA;
     stage_event(1, stream);
-    if (launch_batch_range(b, stream) != cudaSuccess) return HI_ECUDA;
+    if (launch_batch_range_tune(b, stream) != cudaSuccess) return HI_ECUDA;
     stage_event(2, stream);
-    if (launch_batch_tune(b, stream) != cudaSuccess) return HI_ECUDA;
     if (launch_batch_gather(b, stream) != cudaSuccess) return HI_ECUDA;
     stage_event(3, stream);
     const hi_status s = cuda_status(launch_batch_compress(b, stream));
@@ -726,4 +749,4 @@ static_assert(sizeof(hi_header) == 168, "hi_header layout");
 static_assert(sizeof(hi_params) == 80, "hi_params layout");
 static_assert(sizeof(hi_batch_field) == 152, "hi_batch_field layout");
 static_assert(sizeof(hi_batch_plan) == 120, "hi_batch_plan layout");
-static_assert(sizeof(hi::BatchField) % 64 == 0, "field records stay 64-byte aligned");
+static_assert(sizeof(hi::BatchField) % 128 == 0, "field records stay 128-byte aligned");

@@ -22,21 +22,29 @@ __global__ void k_prologue(hi_header* hdr, const hi_params p, uint64_t n_anchors
 __global__ void __launch_bounds__(512) k_range(const float* __restrict__ x, int64_t N, float2* partials,
                                                uint32_t* ticket, hi_header* hdr)
 {
-    __shared__ float s_mn[32], s_mx[32];
-    __shared__ bool s_last;
-    float mn = INFINITY, mx = -INFINITY;
-    range_accum(x, 0, N, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x, mn, mx);
-    block_minmax(mn, mx, s_mn, s_mx);
-    if (threadIdx.x == 0) {
-        partials[blockIdx.x] = make_float2(mn, mx);
-        __threadfence();
-        s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    range_block(x, N, partials, blockIdx.x, gridDim.x, ticket, hdr);
+}
+
+// The value range and the auto-tuner in one launch: they do not depend on
+// each other (the tuner's errors are open-loop, without eps), and the
+// tuner's latency-bound blocks (first in the grid) run beside the range
+// pass's streaming read.  Blocks [0, m * ncfg): auto-tune (sample, candidate);
+// the next nb_range blocks: the range pass.
+template <int A>
+__global__ void __launch_bounds__(256) k_range_tune(const __grid_constant__ CUtensorMap tmap, const FieldGeo g,
+                                                    const float* __restrict__ x, const TuneCands cands, int stride,
+                                                    int m, double* __restrict__ err, uint32_t* tune_ticket,
+                                                    const uint32_t tma_bytes, const int use_tma, float2* partials,
+                                                    int nb_range, uint32_t* range_ticket, hi_header* hdr)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int ntune = m * cands.ncfg;
+    if ((int)blockIdx.x < ntune) {
+        tune_block<A>(reinterpret_cast<float*>(smem), &tmap, g, x, cands, (int)blockIdx.x / cands.ncfg,
+                      (int)blockIdx.x % cands.ncfg, stride, m, err, tune_ticket, hdr, tma_bytes, use_tma != 0);
+        return;
     }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    range_fold(partials, gridDim.x, hdr, s_mn, s_mx);
-    if (threadIdx.x == 0) *ticket = 0;
+    range_block(x, g.N, partials, (int)blockIdx.x - ntune, nb_range, range_ticket, hdr);
 }
 
 // Outlier values go to their place in the output before reconstruction reads
@@ -104,6 +112,34 @@ static cudaError_t launch_tune_t(const TuneLaunch& t, cudaStream_t st)
     kern<<<dim3(t.m, t.cands.ncfg), 256, smem, st>>>(t.tmap, t.g, t.x, t.cands, t.stride, t.err, t.ticket, t.hdr,
                                                      t.tma_bytes, t.use_tma ? 1 : 0);
     return cudaGetLastError();
+}
+
+template <int A>
+static cudaError_t launch_range_tune_t(const TuneLaunch& t, float2* partials, int nb_range, uint32_t* range_ticket,
+                                       cudaStream_t st)
+{
+    using TG = TileGeom<A>;
+    const size_t smem = (size_t)t.g.b0 * TG::P * TG::PX * 4;
+    auto kern = k_range_tune<A>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<t.m * t.cands.ncfg + nb_range, 256, smem, st>>>(t.tmap, t.g, t.x, t.cands, t.stride, t.m, t.err,
+                                                             t.ticket, t.tma_bytes, t.use_tma ? 1 : 0, partials,
+                                                             nb_range, range_ticket, t.hdr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_range_tune(int A, const TuneLaunch& t, float2* partials, int nb_range, uint32_t* range_ticket,
+                              cudaStream_t st)
+{
+    switch (A) {
+    case 2: return launch_range_tune_t<2>(t, partials, nb_range, range_ticket, st);
+    case 4: return launch_range_tune_t<4>(t, partials, nb_range, range_ticket, st);
+    case 8: return launch_range_tune_t<8>(t, partials, nb_range, range_ticket, st);
+    case 16: return launch_range_tune_t<16>(t, partials, nb_range, range_ticket, st);
+    case 32: return launch_range_tune_t<32>(t, partials, nb_range, range_ticket, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_tune(int A, const TuneLaunch& t, cudaStream_t st)

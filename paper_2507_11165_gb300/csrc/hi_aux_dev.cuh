@@ -147,6 +147,29 @@ __device__ __forceinline__ void range_fold(const float2* partials, uint32_t npar
     }
 }
 
+// One CTA `rb` of `nb` of a value-range pass over x[0, N): grid-strided
+// streaming read, its partial (min, max) to partials[rb]; the last CTA to
+// finish (ticket) folds the partials and derives eps into hdr.
+__device__ __forceinline__ void range_block(const float* __restrict__ x, int64_t N, float2* partials, int rb,
+                                            int nb, uint32_t* ticket, hi_header* hdr)
+{
+    __shared__ float s_mn[32], s_mx[32];
+    __shared__ bool s_last;
+    float mn = INFINITY, mx = -INFINITY;
+    range_accum(x, 0, N, (int64_t)rb * blockDim.x + threadIdx.x, (int64_t)nb * blockDim.x, mn, mx);
+    block_minmax(mn, mx, s_mn, s_mx);
+    if (threadIdx.x == 0) {
+        partials[rb] = make_float2(mn, mx);
+        __threadfence();
+        s_last = atomicAdd(ticket, 1u) == (uint32_t)nb - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    range_fold(partials, nb, hdr, s_mn, s_mx);
+    if (threadIdx.x == 0) *ticket = 0;
+}
+
 // ---------------------------------------------------------------------------
 // Auto-tune: a CTA (sample, candidate) computes, for every level, the sum of
 // |x - p| over that level's points of its sampled block, with every
@@ -227,7 +250,7 @@ __device__ __forceinline__ void tune_block(float* v, const CUtensorMap* tmap, co
 {
     using TG = TileGeom<A>;
     constexpr int L = TG::L;
-    __shared__ double s_red[L][8];
+    __shared__ double s_red[L][16];  // up to 512 threads
     __shared__ __align__(8) uint64_t s_mbar;
     __shared__ bool s_last;
     __shared__ double s_tot[L * 12];

@@ -33,13 +33,15 @@ __global__ void k_batch_prologue(const BatchField* __restrict__ fields, uint32_t
 }
 
 // Value range of every relative-bound field: work item = kBatchChunk points
-// of one field; the last item of a field to finish folds its partials.
-__global__ void __launch_bounds__(512) k_batch_range(const BatchField* __restrict__ fields,
-                                                     const uint32_t* __restrict__ chunk_start, int n, uint32_t total)
+// of one field, items first, first + step, ...; the last item of a field to
+// finish folds its partials.
+__device__ __forceinline__ void batch_range_items(const BatchField* __restrict__ fields,
+                                                  const uint32_t* __restrict__ chunk_start, int n, uint32_t total,
+                                                  uint32_t first, uint32_t step)
 {
     __shared__ float s_mn[32], s_mx[32];
     __shared__ bool s_last;
-    for (uint32_t c = blockIdx.x; c < total; c += gridDim.x) {
+    for (uint32_t c = first; c < total; c += step) {
         const int f = find_field(chunk_start, n, c);
         const BatchField& F = fields[f];
         const uint32_t k = c - __ldg(chunk_start + f);
@@ -63,19 +65,27 @@ __global__ void __launch_bounds__(512) k_batch_range(const BatchField* __restric
     }
 }
 
-// Auto-tune of every field that asks for it: blockIdx.x = a sample of some
-// field, blockIdx.y = candidate (beyond the field's count: nothing to do).
+// Value range and auto-tune of every field in one launch (neither needs the
+// other: the tuner's errors are open-loop, without eps).  Blocks [0, ntune):
+// auto-tune, block = (a sample of some field, candidate; beyond the field's
+// candidate count: nothing to do); the next nb_range blocks: the range items.
 template <int A>
-__global__ void __launch_bounds__(256) k_batch_tune(const BatchField* __restrict__ fields,
-                                                    const uint32_t* __restrict__ sample_start, int n)
+__global__ void __launch_bounds__(256) k_batch_range_tune(const BatchField* __restrict__ fields,
+                                                          const uint32_t* __restrict__ sample_start,
+                                                          const uint32_t* __restrict__ chunk_start, int n,
+                                                          uint32_t ntune, uint32_t total_chunks, uint32_t nb_range)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    const int f = find_field(sample_start, n, blockIdx.x);
-    const BatchField& F = fields[f];
-    if ((int)blockIdx.y >= F.cands.ncfg) return;
-    if (F.hdr->status != 0) return;  // the range stage failed: keep the given levels
-    tune_block<A>(reinterpret_cast<float*>(smem), &F.tmap, F.g, F.x, F.cands, blockIdx.x - __ldg(sample_start + f),
-                  blockIdx.y, F.stride, F.m, F.err, &F.tickets[1], F.hdr, F.tma_bytes, (F.flags & kFlagTma) != 0);
+    if (blockIdx.x < ntune) {
+        const uint32_t smp = blockIdx.x / 12, c = blockIdx.x % 12;
+        const int f = find_field(sample_start, n, smp);
+        const BatchField& F = fields[f];
+        if ((int)c >= F.cands.ncfg) return;
+        tune_block<A>(reinterpret_cast<float*>(smem), &F.tmap, F.g, F.x, F.cands, smp - __ldg(sample_start + f), c,
+                      F.stride, F.m, F.err, &F.tickets[1], F.hdr, F.tma_bytes, (F.flags & kFlagTma) != 0);
+        return;
+    }
+    batch_range_items(fields, chunk_start, n, total_chunks, blockIdx.x - ntune, nb_range);
 }
 
 // After the auto-tuner: each field's constants, status and level
@@ -288,33 +298,28 @@ cudaError_t launch_batch_prologue(const BatchLaunch& b, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_range(const BatchLaunch& b, cudaStream_t st)
-{
-    if (b.total_chunks == 0) return cudaSuccess;
-    uint32_t grid = (uint32_t)b.num_sms * 4;
-    if (grid > b.total_chunks) grid = b.total_chunks;
-    k_batch_range<<<grid, 512, 0, st>>>(b.fields, b.chunk_start, b.n, b.total_chunks);
-    return cudaGetLastError();
-}
-
 template <int A>
-static cudaError_t launch_batch_tune_t(const BatchLaunch& b, cudaStream_t st)
+static cudaError_t launch_batch_range_tune_t(const BatchLaunch& b, cudaStream_t st)
 {
     using TG = TileGeom<A>;
-    const size_t smem = (size_t)(A + 1) * TG::P * TG::PX * 4;
-    auto kern = k_batch_tune<A>;
+    const size_t smem = b.total_samples ? (size_t)(A + 1) * TG::P * TG::PX * 4 : 0;
+    auto kern = k_batch_range_tune<A>;
     cudaError_t e = set_max_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<dim3(b.total_samples, 12), 256, smem, st>>>(b.fields, b.sample_start, b.n);
+    uint32_t nb_range = (uint32_t)b.num_sms * 8;
+    if (nb_range > b.total_chunks) nb_range = b.total_chunks;
+    const uint32_t ntune = b.total_samples * 12;
+    kern<<<ntune + nb_range, 256, smem, st>>>(b.fields, b.sample_start, b.chunk_start, b.n, ntune, b.total_chunks,
+                                             nb_range);
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_tune(const BatchLaunch& b, cudaStream_t st)
+cudaError_t launch_batch_range_tune(const BatchLaunch& b, cudaStream_t st)
 {
-    if (b.total_samples == 0) return cudaSuccess;
+    if (b.total_samples == 0 && b.total_chunks == 0) return cudaSuccess;
     switch (b.A) {
-    case 8: return launch_batch_tune_t<8>(b, st);
-    case 16: return launch_batch_tune_t<16>(b, st);
+    case 8: return launch_batch_range_tune_t<8>(b, st);
+    case 16: return launch_batch_range_tune_t<16>(b, st);
     default: return cudaErrorInvalidValue;
     }
 }

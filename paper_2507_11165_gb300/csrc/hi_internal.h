@@ -110,6 +110,8 @@ struct TuneLaunch {
     bool use_tma;
 };
 cudaError_t launch_tune(int A, const TuneLaunch& t, cudaStream_t st);
+cudaError_t launch_range_tune(int A, const TuneLaunch& t, float2* partials, int nb_range, uint32_t* range_ticket,
+                              cudaStream_t st);
 
 constexpr int kRangeBlocks = 1024;
 
@@ -138,7 +140,7 @@ struct alignas(16) BatchCur {
     int sel[HI_MAX_LEVELS];
 };
 
-struct alignas(64) BatchField {
+struct alignas(128) BatchField {
     CUtensorMap tmap;  // the field as (PX, A+1, b0) float boxes (when flags & kFlagTma)
     BatchCur cur;
     FieldGeo g;
@@ -182,8 +184,7 @@ struct BatchLaunch {
 };
 
 cudaError_t launch_batch_prologue(const BatchLaunch& b, cudaStream_t st);
-cudaError_t launch_batch_range(const BatchLaunch& b, cudaStream_t st);
-cudaError_t launch_batch_tune(const BatchLaunch& b, cudaStream_t st);
+cudaError_t launch_batch_range_tune(const BatchLaunch& b, cudaStream_t st);
 cudaError_t launch_batch_gather(const BatchLaunch& b, cudaStream_t st);
 cudaError_t launch_batch_compress(const BatchLaunch& b, cudaStream_t st);
 
