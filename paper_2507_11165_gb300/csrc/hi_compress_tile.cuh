@@ -70,12 +70,12 @@ __device__ __forceinline__ void compress_tile(const FieldGeo& g, const TileInfo&
                     *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
             }
             if (__any_sync(0xffffffffu, act && z != 0)) {
+                uint32_t zm[CH];  // 0x80 in each byte that is zero (exact, no borrow between bytes)
 #pragma unroll
-                for (int b = 0; b < 4 * CH; ++b) {
-                    const int code = (w[b >> 2] >> (8 * (b & 3))) & 0xff;
-                    outlier_append<A>(act && code == 0, c0 * Lw::PY + c1 * Lw::PX + ch * CH * 4 + b, v, hdr,
-                                      out_idx, out_val, out_cap, g, ti.o);
-                }
+                for (int j = 0; j < CH; ++j)
+                    zm[j] = act ? ~(((w[j] & 0x7f7f7f7fu) + 0x7f7f7f7fu) | w[j]) & 0x80808080u : 0u;
+                outliers_append_words<A, CH>(zm, c0 * Lw::PY + c1 * Lw::PX + ch * CH * 4, v, hdr, out_idx, out_val,
+                                             out_cap, g, ti.o);
             }
             if (hist_on) {
 #pragma unroll
@@ -115,10 +115,9 @@ __device__ __forceinline__ void compress_tile(const FieldGeo& g, const TileInfo&
             }
             const uint32_t z = (w - 0x01010101u) & ~w & 0x80808080u;
             if (__any_sync(0xffffffffu, act && z != 0)) {
-#pragma unroll
-                for (int b = 0; b < 4; ++b)
-                    outlier_append<A>(act && ((w >> (8 * b)) & 0xffu) == 0, vi + b, v, hdr, out_idx, out_val, out_cap,
-                                      g, ti.o);
+                uint32_t zm[1];
+                zm[0] = act ? ~(((w & 0x7f7f7f7fu) + 0x7f7f7f7fu) | w) & 0x80808080u : 0u;
+                outliers_append_words<A, 1>(zm, vi, v, hdr, out_idx, out_val, out_cap, g, ti.o);
             }
             if (hist_on) {
 #pragma unroll

@@ -119,7 +119,8 @@ __device__ __forceinline__ float dequantize(int code, float p, float ebx2_f)
 // First error wins.
 __device__ __forceinline__ void set_status(uint32_t* status, uint32_t code)
 {
-    if (status) atomicCAS(status, 0u, code);
+    // first error wins; once one is recorded, later callers only read
+    if (status && *reinterpret_cast<volatile uint32_t*>(status) == 0u) atomicCAS(status, 0u, code);
 }
 
 // ---------------------------------------------------------------------------

@@ -640,6 +640,51 @@ __device__ __forceinline__ void outlier_append(bool is_out, int vi, const float*
     }
 }
 
+// Outliers of NW 4-byte code words per lane (all lanes of the warp call
+// it): zm[j] has 0x80 in each byte of word j whose code is 0; the codes
+// stand at float offsets vi0 + 4 j + byte in the tile.  The warp reserves its
+// slots with one atomic (a prefix sum over the lanes' counts) and each lane
+// writes its own outliers.
+template <int A, int NW>
+__device__ __forceinline__ void outliers_append_words(const uint32_t* zm, int vi0, const float* v, hi_header* hdr,
+                                                      uint32_t* out_idx, float* out_val, uint64_t out_cap,
+                                                      const FieldGeo& g, const int o[3])
+{
+    const int lane = threadIdx.x & 31;
+    int cnt = 0;
+#pragma unroll
+    for (int j = 0; j < NW; ++j) cnt += __popc(zm[j]);
+    int incl = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned long long base = 0;
+    if (lane == 31) base = atomicAdd(reinterpret_cast<unsigned long long*>(&hdr->n_outliers), (unsigned long long)total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    unsigned long long pos = base + (unsigned long long)(incl - cnt);
+    bool over = false;
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+        uint32_t m = zm[j];
+        while (m) {
+            const int bit = __ffs(m) - 1;  // 7, 15, 23 or 31
+            m &= m - 1;
+            const int vi = vi0 + 4 * j + (bit >> 3);
+            if (pos < out_cap) {
+                out_idx[pos] = (uint32_t)global_index<A>(g, o, vi);
+                out_val[pos] = v[vi];
+            } else {
+                over = true;
+            }
+            ++pos;
+        }
+    }
+    if (over) set_status(&hdr->status, HI_ECAPACITY);
+}
+
 // Histogram: codes 120..135 (the bulk at any practical error bound) go to
 // per-thread 16-bit counters laid out bin-major, so that a warp's updates hit
 // 32 consecutive half-words (no bank conflict, no atomics); other codes go
