@@ -355,7 +355,7 @@ def run_gpu(args):
             dtype="f32", data="synthetic",
             config=dict(workload=WORKLOAD, shape=list(SHAPE), eb_mode="rel", eb=EB, anchor_stride=A,
                         l2="input 512 MiB and outputs exceed the 126 MB L2: no flush between steps",
-                        step="compress (setup, range, autotune, predict_quantize) + decompress (scatter, "
+                        step="compress (setup, range + autotune in one launch, predict_quantize) + decompress (scatter, "
                              "reconstruct)", parallelism="replicas" if ws > 1 else "single"),
             compress_gbs=bytes_in / ((st["setup"] + st["range"] + st["autotune"] + st["predict_quantize"])
                                      * 1e-3) / 1e9,
@@ -373,7 +373,7 @@ def run_gpu(args):
                          bit_rate=est["bit_rate"],
                          levels=[(int(h.level[l].interp), list(h.level[l].order)) for l in range(h.n_levels)]),
             e2e=e2e,
-            gpu_launches=6 * args.steps,  # setup, range, autotune, predict-quantize, scatter, reconstruct
+            gpu_launches=5 * args.steps,  # setup, range + auto-tune (one launch), predict-quantize, scatter, reconstruct
             cpu_baseline=cpu,
             clocks=clocks,
         )
@@ -524,7 +524,7 @@ def run_batch(args):
         roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
                       peak_kind=peak_kind, alg_bytes_per_step=alg,
                       note="whole step: range read 4 B/pt + predict-quantize 5 B/pt"),
-        gpu_launches=4 * steps,
+        gpu_launches=4 * steps,  # setup, range + auto-tune, gather, predict-quantize
         clocks=clk.summary(),
     )
     print(json.dumps(line), flush=True)
