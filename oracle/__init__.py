@@ -36,6 +36,7 @@ CFLAGS = ["-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast
           "-fno-tree-vectorize", "-fno-finite-math-only"]
 
 LINEAR, CUBIC = 0, 1
+MD_LINEAR, MD_CUBIC = 2, 3  # multi-dimensional interpolation scheme (Sec. 5.1.2)
 RADIUS = 128
 ABS, REL = 0, 1
 
@@ -204,8 +205,8 @@ def tune_samples(shape, A):
 
 def tune_configs(shape):
     """Candidate (interp, order) per level in enumeration order."""
-    ci = np.zeros(12, dtype=np.uint8)
-    co = np.zeros(36, dtype=np.uint8)
+    ci = np.zeros(14, dtype=np.uint8)
+    co = np.zeros(42, dtype=np.uint8)
     n = _load().hi_oracle_tune_configs(_p(_dims3(shape)), _p(ci), _p(co))
     return [(int(ci[k]), tuple(int(v) for v in co[3 * k:3 * k + 3])) for k in range(n)]
 
@@ -215,7 +216,7 @@ def tune_errors(x, A):
     lib = _load()
     x = np.ascontiguousarray(x, dtype=np.float32)
     L = n_levels(A)
-    err = np.zeros(L * 12, dtype=np.float64)
+    err = np.zeros(L * 14, dtype=np.float64)
     nc = np.zeros(1, dtype=np.int32)
     _check(lib.hi_oracle_tune_errors(_p(_dims3(x.shape)), int(A), _p(x), _p(err), _p(nc)))
     return err[:L * int(nc[0])].reshape(L, int(nc[0]))
@@ -228,7 +229,7 @@ def tune_errors_tiles(x, A, tiles):
     x = np.ascontiguousarray(x, dtype=np.float32)
     L = n_levels(A)
     t = np.ascontiguousarray(tiles, dtype=np.int64)
-    err = np.zeros(max(1, t.size) * L * 12, dtype=np.float64)
+    err = np.zeros(max(1, t.size) * L * 14, dtype=np.float64)
     nc = np.zeros(1, dtype=np.int32)
     _check(lib.hi_oracle_tune_errors_tiles(_p(_dims3(x.shape)), int(A), _p(x), _p(t), t.size, _p(err), _p(nc)))
     n = int(nc[0])

@@ -59,6 +59,8 @@
 
 #define ORC_LINEAR 0
 #define ORC_CUBIC 1
+#define ORC_MD_LINEAR 2 /* multi-dimensional interpolation, linear splines */
+#define ORC_MD_CUBIC 3  /* multi-dimensional interpolation, cubic splines  */
 #define ORC_RADIUS 128
 #define ORC_MAX_LEVELS 8
 
@@ -201,6 +203,18 @@ static int stencil_case(int interp, int have_l3, int have_r, int have_r3)
     return 0;
 }
 
+/* Order of the stencil predict_line uses, for the multi-dimensional scheme's
+ * "highest spline order" rule: 3 cubic, 2 quadratic, 1 linear (midpoint or
+ * extrapolation), 0 copy. */
+static int stencil_order(int interp, int have_l3, int have_r, int have_r3)
+{
+    if (!have_r) return have_l3 ? 1 : 0;
+    if (interp == ORC_LINEAR) return 1;
+    if (have_l3 && have_r3) return 3;
+    if (have_l3 || have_r3) return 2;
+    return 1;
+}
+
 /* Linear quantization of the prediction error (Sec. 5.2.1).  Returns the
  * code (1..255, or 0 for an outlier) and stores the reconstructed value. */
 static int quantize(float x, float p, float eb_f, float ebx2_f, float r_f, float* xr_out)
@@ -278,6 +292,141 @@ typedef struct {
     int8_t* t_case;
     int status;
 } action;
+
+/* The prediction pr of point c (local index li) is final: quantize it
+ * (compress), rebuild from the code (decompress) or add |x - pr| (tune), and
+ * record the trace; the point becomes known. */
+static void apply_point(block* B, const int c[3], int li, float pr, int l, int dir, int kc, action* act)
+{
+    if (act->mode == MODE_COMPRESS) {
+        float xr;
+        int k = quantize(B->orig[li], pr, act->eb_f, act->ebx2_f, act->r_f, &xr);
+        B->code[li] = (uint8_t)k;
+        B->rec[li] = xr;
+    } else if (act->mode == MODE_DECOMPRESS) {
+        int64_t g = gindex(B->G, B->o[0] + c[0], B->o[1] + c[1], B->o[2] + c[2]);
+        int k = act->g_codes[g];
+        B->code[li] = (uint8_t)k;
+        if (k == 0) {
+            if (!act->g_outhas[g]) {
+                act->status = ORC_ECORRUPT;
+                return;
+            }
+            B->rec[li] = act->g_outval[g];
+        } else {
+            B->rec[li] = pr + (float)(k - ORC_RADIUS) * act->ebx2_f;
+        }
+    } else {
+        float x = B->orig[li];
+        act->err += (double)fabsf(x - pr);
+    }
+    if (act->t_lvl) {
+        int64_t g = gindex(B->G, B->o[0] + c[0], B->o[1] + c[1], B->o[2] + c[2]);
+        if (act->t_lvl[g] >= 0 && (act->t_lvl[g] != l || act->t_dir[g] != dir || act->t_case[g] != kc)) {
+            act->status = ORC_EFACE;
+            return;
+        }
+        act->t_lvl[g] = (int8_t)l;
+        act->t_dir[g] = (int8_t)dir;
+        act->t_case[g] = (int8_t)kc;
+    }
+    B->known[li] = 1;
+}
+
+/* The 1D stencil of point c along dim d at stride s: availability, the
+ * known-before-use check, the values (from `src`) and the prediction.
+ * Returns 0, or ORC_ETRAVERSAL. */
+static int line_predict(const block* B, const float* src, const int c[3], int d, int s, int interp, float* pr,
+                        int* kc, int* ord)
+{
+    int cd = c[d], e = B->e[d];
+    int have_l3 = (cd - 3 * s) >= 0;
+    int have_r = (cd + s) <= e;
+    int have_r3 = (cd + 3 * s) <= e;
+    int cm[3];
+    float a = 0.0f, b, u = 0.0f, v = 0.0f;
+    int lb, la = -1, lu = -1, lv = -1;
+    memcpy(cm, c, sizeof cm);
+    cm[d] = cd - s;
+    lb = lidx(B, cm[0], cm[1], cm[2]);
+    if (have_r) {
+        cm[d] = cd + s;
+        lu = lidx(B, cm[0], cm[1], cm[2]);
+    }
+    if (have_l3) {
+        cm[d] = cd - 3 * s;
+        la = lidx(B, cm[0], cm[1], cm[2]);
+    }
+    if (have_r3) {
+        cm[d] = cd + 3 * s;
+        lv = lidx(B, cm[0], cm[1], cm[2]);
+    }
+    if (!B->known[lb] || (lu >= 0 && !B->known[lu]) || (la >= 0 && !B->known[la]) || (lv >= 0 && !B->known[lv]))
+        return ORC_ETRAVERSAL;
+    b = src[lb];
+    if (lu >= 0) u = src[lu];
+    if (la >= 0) a = src[la];
+    if (lv >= 0) v = src[lv];
+    *pr = predict_line(interp, have_l3, have_r, have_r3, a, b, u, v);
+    *kc = stencil_case(interp, have_l3, have_r, have_r3);
+    *ord = stencil_order(interp, have_l3, have_r, have_r3);
+    return ORC_OK;
+}
+
+/* Multi-dimensional interpolation of level l (Sec. 5.1.2, parallelized
+ * multi-dimensional interpolation; reading in the design notes): the level's
+ * points, those whose coordinates are all multiples of s with at least one
+ * odd multiple, are taken in three phases by the number k of odd-multiple
+ * coordinates (1, then 2, then 3).  A point is interpolated along each of
+ * its k odd dims with that dim's 1D stencil (the same cases as the 1D
+ * scheme); only the interpolations of the highest order among them count,
+ * and the prediction is their mean, summed in increasing dim order
+ * (one: itself; two: sum * 0.5; three: sum / 3).  Its stencil nodes have
+ * k - 1 odd coordinates, so they are known from the phase before. */
+static void run_level_md(block* B, int l, int interp, action* act)
+{
+    int s = 1 << l;
+    int k, d, c[3];
+    const float* src = (act->mode == MODE_TUNE) ? B->orig : B->rec;
+    for (k = 1; k <= 3; k++) {
+        for (c[0] = 0; c[0] <= B->e[0]; c[0] += s)
+            for (c[1] = 0; c[1] <= B->e[1]; c[1] += s)
+                for (c[2] = 0; c[2] <= B->e[2]; c[2] += s) {
+                    float p[3], pr, sum = 0.0f;
+                    int ord[3], kc[3], odd[3], nodd = 0, best = -1, n = 0, mask = 0, li;
+                    for (d = 0; d < 3; d++)
+                        if (c[d] % (2 * s) == s) odd[nodd++] = d;
+                    if (nodd != k) continue;
+                    li = lidx(B, c[0], c[1], c[2]);
+                    if (B->known[li]) {
+                        act->status = ORC_EREVISIT;
+                        return;
+                    }
+                    for (d = 0; d < nodd; d++) {
+                        if (line_predict(B, src, c, odd[d], s, interp, &p[d], &kc[d], &ord[d])) {
+                            act->status = ORC_ETRAVERSAL;
+                            return;
+                        }
+                        if (ord[d] > best) best = ord[d];
+                    }
+                    for (d = 0; d < nodd; d++)
+                        if (ord[d] == best) {
+                            sum = (n == 0) ? p[d] : sum + p[d];
+                            mask |= 1 << odd[d];
+                            n++;
+                        }
+                    if (n == 1)
+                        pr = sum;
+                    else if (n == 2)
+                        pr = sum * 0.5f;
+                    else
+                        pr = sum / 3.0f;
+                    /* trace: dir = 3 + the mask of the averaged dims, case = their order */
+                    apply_point(B, c, li, pr, l, 3 + mask, best, act);
+                    if (act->status) return;
+                }
+    }
+}
 
 /* Every point c of the block with
  *   c[d_p] = s mod 2s,  c[d_q] = 0 mod s (q < p),  c[d_q] = 0 mod 2s (q > p)
@@ -428,7 +577,7 @@ static int check_levels(int L, const uint8_t* interp, const uint8_t* order)
     int l;
     for (l = 0; l < L; l++) {
         int seen = 0, q;
-        if (interp[l] != ORC_LINEAR && interp[l] != ORC_CUBIC) return ORC_EINVAL;
+        if (interp[l] > ORC_MD_CUBIC) return ORC_EINVAL;
         for (q = 0; q < 3; q++) {
             if (order[3 * l + q] > 2) return ORC_EINVAL;
             seen |= 1 << order[3 * l + q];
@@ -439,11 +588,21 @@ static int check_levels(int L, const uint8_t* interp, const uint8_t* order)
 }
 
 /* Run every level of one block, from the coarsest to the finest. */
+/* One level under its configuration: the 1D dimension sequence, or the
+ * multi-dimensional scheme (with linear or cubic splines). */
+static void run_level_any(block* B, int l, int interp, const uint8_t order[3], action* act)
+{
+    if (interp == ORC_MD_LINEAR || interp == ORC_MD_CUBIC)
+        run_level_md(B, l, interp == ORC_MD_CUBIC ? ORC_CUBIC : ORC_LINEAR, act);
+    else
+        run_level(B, l, interp, order, act);
+}
+
 static int block_run(block* B, const uint8_t* interp, const uint8_t* order, action* act)
 {
     int l;
     for (l = B->G->L - 1; l >= 0; l--) {
-        run_level(B, l, interp[l], order + 3 * l, act);
+        run_level_any(B, l, interp[l], order + 3 * l, act);
         if (act->status) return act->status;
     }
     if (!block_complete(B)) return ORC_EMISSED;
@@ -698,9 +857,12 @@ int64_t hi_oracle_tune_samples(const int64_t dims[3], int A)
     return m;
 }
 
-/* Candidate configurations of one level, in enumeration order: cubic before
- * linear; within each, the permutations of the active dims in lexicographic
- * order, inactive dims appended in ascending order.  Returns the count. */
+/* Candidate configurations of one level, in enumeration order: the 1D
+ * scheme, cubic before linear, within each the permutations of the active
+ * dims in lexicographic order (inactive dims appended in ascending order);
+ * then, with two or more active dims, the multi-dimensional scheme, cubic
+ * before linear (its order field is the first permutation, unused).
+ * Returns the count (at most 14). */
 int hi_oracle_tune_configs(const int64_t dims[3], uint8_t* interp_out, uint8_t* order_out)
 {
     int act[3], na = 0, inact[3], ni = 0, d, i, cnt = 0, sp;
@@ -750,6 +912,14 @@ int hi_oracle_tune_configs(const int64_t dims[3], uint8_t* interp_out, uint8_t* 
             cnt++;
         }
     }
+    if (na >= 2) {
+        for (sp = 0; sp < 2; sp++) {
+            int q;
+            interp_out[cnt] = (uint8_t)(sp == 0 ? ORC_MD_CUBIC : ORC_MD_LINEAR);
+            for (q = 0; q < 3; q++) order_out[3 * cnt + q] = order_out[q];
+            cnt++;
+        }
+    }
     return cnt;
 }
 
@@ -762,7 +932,7 @@ int hi_oracle_tune_errors(const int64_t dims[3], int A, const float* x, double* 
     block B;
     block_mem M;
     action act;
-    uint8_t cinterp[12], corder[36];
+    uint8_t cinterp[14], corder[42];
     uint8_t lvl_interp[ORC_MAX_LEVELS], lvl_order[3 * ORC_MAX_LEVELS];
     int64_t m, stride, k, nblocks;
     int ncfg, c, l, rc = geom_init(&G, dims, A);
@@ -797,7 +967,7 @@ int hi_oracle_tune_errors(const int64_t dims[3], int A, const float* x, double* 
                 memset(&act, 0, sizeof act);
                 act.mode = MODE_TUNE;
                 for (ll = G.L - 1; ll > l; ll--) {
-                    run_level(&B, ll, lvl_interp[ll], lvl_order + 3 * ll, &act);
+                    run_level_any(&B, ll, lvl_interp[ll], lvl_order + 3 * ll, &act);
                     if (act.status) break;
                 }
                 if (act.status) {
@@ -805,7 +975,7 @@ int hi_oracle_tune_errors(const int64_t dims[3], int A, const float* x, double* 
                     goto done;
                 }
                 act.err = 0.0;
-                run_level(&B, l, cinterp[c], corder + 3 * c, &act);
+                run_level_any(&B, l, cinterp[c], corder + 3 * c, &act);
                 if (act.status) {
                     rc = act.status;
                     goto done;
@@ -831,7 +1001,7 @@ int hi_oracle_tune_errors_tiles(const int64_t dims[3], int A, const float* x, co
     block B;
     block_mem M;
     action act;
-    uint8_t cinterp[12], corder[36];
+    uint8_t cinterp[14], corder[42];
     int64_t k, nblocks;
     int ncfg, c, l, rc = geom_init(&G, dims, A);
     if (rc) return rc;
@@ -862,7 +1032,7 @@ int hi_oracle_tune_errors_tiles(const int64_t dims[3], int A, const float* x, co
                 memset(&act, 0, sizeof act);
                 act.mode = MODE_TUNE;
                 for (ll = G.L - 1; ll > l; ll--) {
-                    run_level(&B, ll, cinterp[c], corder + 3 * c, &act);
+                    run_level_any(&B, ll, cinterp[c], corder + 3 * c, &act);
                     if (act.status) break;
                 }
                 if (act.status) {
@@ -870,7 +1040,7 @@ int hi_oracle_tune_errors_tiles(const int64_t dims[3], int A, const float* x, co
                     goto done;
                 }
                 act.err = 0.0;
-                run_level(&B, l, cinterp[c], corder + 3 * c, &act);
+                run_level_any(&B, l, cinterp[c], corder + 3 * c, &act);
                 if (act.status) {
                     rc = act.status;
                     goto done;
@@ -888,7 +1058,7 @@ done:
  * first in enumeration order. */
 int hi_oracle_tune_select(const int64_t dims[3], int A, const double* err, uint8_t* interp, uint8_t* order)
 {
-    uint8_t cinterp[12], corder[36];
+    uint8_t cinterp[14], corder[42];
     int ncfg = hi_oracle_tune_configs(dims, cinterp, corder);
     int L = ilog2_exact(A), l, c, q;
     if (L < 1) return ORC_EINVAL;

@@ -382,10 +382,14 @@ def test_tune_samples(oracle_mod):
 
 
 def test_tune_configs(oracle_mod):
+    """1D sequences (cubic, then linear, permutations in lexicographic order),
+    then the multi-dimensional scheme (cubic, then linear) with two or more
+    active dims."""
     got = oracle_mod.tune_configs((4, 5, 6))
     perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
-    assert got == [(1, p) for p in perms] + [(0, p) for p in perms]
-    assert oracle_mod.tune_configs((7, 9)) == [(1, (1, 2, 0)), (1, (2, 1, 0)), (0, (1, 2, 0)), (0, (2, 1, 0))]
+    assert got == [(1, p) for p in perms] + [(0, p) for p in perms] + [(3, (0, 1, 2)), (2, (0, 1, 2))]
+    assert oracle_mod.tune_configs((7, 9)) == [(1, (1, 2, 0)), (1, (2, 1, 0)), (0, (1, 2, 0)), (0, (2, 1, 0)),
+                                               (3, (1, 2, 0)), (2, (1, 2, 0))]
     assert oracle_mod.tune_configs((9,)) == [(1, (2, 0, 1)), (0, (2, 0, 1))]
 
 
@@ -423,10 +427,14 @@ def test_tune_errors_bruteforce(oracle_mod, shape, A):
 
 
 def test_tune_select_argmin(oracle_mod):
-    err = np.array([[3.0, 1.0, 1.0, 2.0], [0.0, 0.0, 0.0, 0.0]])
+    # 2D: 4 one-dimensional candidates, then multi-dimensional cubic and linear
+    err = np.array([[3.0, 1.0, 1.0, 2.0, 5.0, 4.0], [0.0] * 6])
     interp, order = oracle_mod.tune_select((7, 9), 4, err)
     assert list(interp) == [1, 1]
     assert [tuple(o) for o in order] == [(2, 1, 0), (1, 2, 0)]
+    err = np.array([[3.0, 1.0, 1.0, 2.0, 0.5, 4.0], [2.0, 2.0, 2.0, 2.0, 2.0, 1.0]])
+    interp, order = oracle_mod.tune_select((7, 9), 4, err)
+    assert list(interp) == [3, 2]
 
 
 # --------------------------------------------------------------------------
@@ -464,3 +472,101 @@ def test_quantizer_boundaries(oracle_mod):
             assert abs(out["recon"][1] - v) < 0.5
         else:
             assert out["recon"][1] == v
+
+
+# --------------------------------------------------------------------------
+# Multi-dimensional interpolation scheme (Sec. 5.1.2)
+# --------------------------------------------------------------------------
+MD_SHAPES = [((9, 9, 9), 8), ((10, 7, 13), 8), ((17, 17, 17), 16), ((33, 20, 5), 16), ((12, 30), 4),
+             ((5, 6, 7), 2), ((20, 19), 8)]
+
+
+def _md_levels(rng, L, shape, p_md=0.6):
+    """Random per-level configurations, each level multi-dimensional with probability p_md."""
+    interp, order = _random_levels(rng, L, shape)
+    for l in range(L):
+        if rng.uniform() < p_md:
+            interp[l] = bf.MD_LINEAR + int(rng.integers(0, 2))
+    return interp, order
+
+
+@pytest.mark.parametrize("shape,A", MD_SHAPES)
+def test_md_trace_matches_bruteforce(oracle_mod, shape, A):
+    """Level, averaged dims and their stencil order of every point, against the
+    brute force built from the phase definition (points with 1, 2, 3 odd
+    coordinates; the highest-order stencils averaged)."""
+    rng = np.random.default_rng(31)
+    L = oracle_mod.n_levels(A)
+    for _ in range(4):
+        interp, order = _md_levels(rng, L, shape)
+        lvl, d, k = oracle_mod.trace(shape, A, interp, order)
+        bl, bd, bk = bf.trace(shape, A, interp, order)
+        assert np.array_equal(lvl, bl) and np.array_equal(d, bd) and np.array_equal(k, bk)
+    for spline in (0, 1):
+        assert bf.md_check_causality(shape, A, [spline] * L) == 0
+
+
+@pytest.mark.parametrize("shape,A", [((17, 17, 17), 16), ((17, 33, 9), 8), ((33, 65), 16), ((9, 9, 9), 4)])
+def test_md_linear_field_all_zero_codes(oracle_mod, shape, A):
+    """Every stencil is exact for a linear field, so is every mean of them."""
+    x = _linear_field(shape)
+    L = oracle_mod.n_levels(A)
+    c = oracle_mod.eps_constants(x, oracle_mod.ABS, 0.25)
+    for spline in (bf.MD_LINEAR, bf.MD_CUBIC):
+        interp = np.full(L, spline, dtype=np.uint8)
+        order = np.tile(np.array([0, 1, 2], dtype=np.uint8), (L, 1))
+        out = oracle_mod.compress(x, A, interp, order, c)
+        assert np.all(out["codes"] == 128)
+        assert np.array_equal(out["recon"].view(np.uint32), x.view(np.uint32))
+
+
+@pytest.mark.parametrize("shape,A", [((17, 9, 10), 8), ((9, 9, 9), 8), ((13, 21), 4), ((6, 11, 7), 4)])
+def test_md_codes_equal_exact_mean_residual(oracle_mod, shape, A):
+    """Integer polynomial fields times 96: every 1D prediction is a multiple of
+    6, so means of two and of three are exact integers, the closed loop is
+    lossless at 2*eps = 1 and each code is 128 + (x - the exact mean of the
+    highest-order predictions), or 0 out of range.  A wrong phase, a wrong
+    choice of averaged dims or a wrong mean moves codes."""
+    rng = np.random.default_rng(17)
+    L = oracle_mod.n_levels(A)
+    x = (_int_poly(shape, rng, deg=2, scale=1).astype(np.float64) * 96).astype(np.float32)
+    c = oracle_mod.eps_constants(x, oracle_mod.ABS, 0.5)
+    for _ in range(3):
+        interp, order = _md_levels(rng, L, shape, p_md=1.0)
+        out = oracle_mod.compress(x, A, interp, order, c)
+        assert np.array_equal(out["recon"].view(np.uint32), x.view(np.uint32))
+        res = bf.open_loop_residuals(x, A, interp, order)
+        codes = out["codes"].reshape(bf.dims3(shape))
+        for g, r in res.items():
+            assert r.denominator == 1
+            want = 128 + int(r) if abs(r) <= 127 else 0
+            assert codes[g] == want, (g, r, codes[g])
+
+
+def test_md_mean_of_two_and_three(oracle_mod):
+    """Hand values on one 3x3x3 block (A = 2, one level, linear splines) of
+    f = x*y*z + x*y: the point (1,1,1) averages three midpoint predictions,
+    (1,1,0) two; with 2*eps = 1 the codes are 128 + x - mean."""
+    n = 3
+    g = np.meshgrid(*[np.arange(n, dtype=np.float64)] * 3, indexing="ij")
+    f = (g[0] * g[1] * g[2] + g[0] * g[1]) * 6.0
+    x = f.astype(np.float32)
+    c = oracle_mod.eps_constants(x, oracle_mod.ABS, 0.5)
+    interp = np.array([bf.MD_LINEAR], dtype=np.uint8)
+    order = np.array([[0, 1, 2]], dtype=np.uint8)
+    out = oracle_mod.compress(x, 2, interp, order, c)
+    codes = out["codes"].astype(int) - 128
+    # (1,0,0): along x only: (f(0,0,0) + f(2,0,0)) / 2 = 0 = f -> 0
+    assert codes[1, 0, 0] == 0
+    # (1,1,0): x and y midpoints of f = 6xy at z = 0: along x (0,1,0)=0,(2,1,0)=12 -> 6;
+    # along y (1,0,0)=0,(1,2,0)=12 -> 6; mean 6 = f(1,1,0) -> 0
+    assert codes[1, 1, 0] == 0
+    # (1,1,1): f = 6xyz + 6xy; along x: (f(0,1,1) + f(2,1,1))/2 = (0 + 24)/2 = 12,
+    # along y: (f(1,0,1) + f(1,2,1))/2 = (0 + 24)/2 = 12, along z: (f(1,1,0) + f(1,1,2))/2 = (6 + 18)/2 = 12;
+    # mean 12 = f(1,1,1) -> 0
+    assert codes[1, 1, 1] == 0
+    # f = 6 x^2 y: at (1,1,0): along x (0 + 24)/2 = 12 vs f = 6 -> residual -6;
+    # along y (0 + 12)/2 = 6 -> 0; both linear: mean 9 -> code -3
+    x2 = (6.0 * g[0] ** 2 * g[1]).astype(np.float32)
+    out = oracle_mod.compress(x2, 2, interp, order, oracle_mod.eps_constants(x2, oracle_mod.ABS, 0.5))
+    assert int(out["codes"][1, 1, 0]) - 128 == 6 - 9
