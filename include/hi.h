@@ -60,7 +60,12 @@ typedef enum {
 } hi_status;
 
 enum { HI_EB_ABS = 0, HI_EB_REL = 1 };
-enum { HI_LINEAR = 0, HI_CUBIC = 1 };
+/* Interpolation of a level: 1D splines along the level's dimension sequence
+ * (Sec. 5.1.2, Fig. 4a), or the multi-dimensional scheme (Sec. 5.1.2,
+ * Fig. 4b: points with 1, 2, 3 odd coordinates in turn, the mean of the
+ * highest-order 1D interpolations along their odd dims; the order field is
+ * then unused but must still be a permutation). */
+enum { HI_LINEAR = 0, HI_CUBIC = 1, HI_MD_LINEAR = 2, HI_MD_CUBIC = 3 };
 
 #define HI_MAX_LEVELS 8
 #define HI_MAGIC 0x48693235u /* "Hi25" */
@@ -70,7 +75,7 @@ enum { HI_LINEAR = 0, HI_CUBIC = 1 };
  * the spline and the sequence of dimensions of its 1D passes.  order[] is a
  * permutation of {0,1,2}; passes along inactive dims are empty. */
 typedef struct {
-    uint8_t interp;   /* HI_LINEAR or HI_CUBIC */
+    uint8_t interp;   /* HI_LINEAR, HI_CUBIC, HI_MD_LINEAR or HI_MD_CUBIC */
     uint8_t order[3]; /* dimension sequence, 0 = slowest */
 } hi_level;
 
@@ -80,7 +85,9 @@ typedef struct {
     double eb;              /* error bound: absolute, or relative to max - min    */
     uint32_t eb_mode;       /* HI_EB_ABS or HI_EB_REL (Sec. 6.1.4)                */
     uint32_t anchor_stride; /* A: 2, 4, 8, 16 or 32 (Sec. 5.1.1 uses 16)          */
-    uint32_t autotune;      /* 1: choose level[] on the device (Sec. 5.1.3)       */
+    uint32_t autotune;      /* 1: choose level[] on the device among the 1D       */
+                            /* sequences (Sec. 5.1.3); 2: also the multi-        */
+                            /* dimensional scheme; 0: use level[] as given        */
     uint32_t tuning;        /* launch shape, 0 = library default; else bits 0-1:  */
                             /* threads per CTA (1: 64, 2: 128), bits 2-3: tile    */
                             /* buffers (1: one, 2: two, prefetching)              */
@@ -193,8 +200,10 @@ HI_API hi_status hi_decompress(const hi_params* p, const hi_header* d_header, co
 /* Auto-tune only (Sec. 5.1.3): writes the chosen level[] and n_levels into
  * d_header (other fields untouched).  Uniformly sampled blocks (every
  * (n_blocks / m)-th, m = max(1, round(0.002 n_points / A^d))); per level and
- * per candidate (cubic before linear, dimension sequences in lexicographic
- * order) the sum of |x - p| with predictions from the original values; the
+ * per candidate (1D: cubic before linear, dimension sequences in
+ * lexicographic order; then, for autotune = 2 and two or more active dims,
+ * the multi-dimensional scheme, cubic before linear: up to 14) the sum of
+ * |x - p| with predictions from the original values; the
  * smallest sum wins, ties to the first candidate.  Uses the same workspace
  * as hi_compress. */
 HI_API hi_status hi_autotune(const hi_params* p, const float* d_x, hi_header* d_header, void* d_ws, size_t ws_bytes,

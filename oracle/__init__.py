@@ -80,10 +80,10 @@ def _load():
                                                  P, i64, P]
             lib.hi_oracle_tune_samples.argtypes = [P, ctypes.c_int]
             lib.hi_oracle_tune_samples.restype = i64
-            lib.hi_oracle_tune_configs.argtypes = [P, P, P]
-            lib.hi_oracle_tune_errors.argtypes = [P, ctypes.c_int, P, P, P]
-            lib.hi_oracle_tune_errors_tiles.argtypes = [P, ctypes.c_int, P, P, i64, P, P]
-            lib.hi_oracle_tune_select.argtypes = [P, ctypes.c_int, P, P, P]
+            lib.hi_oracle_tune_configs.argtypes = [P, ctypes.c_int, P, P]
+            lib.hi_oracle_tune_errors.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, P]
+            lib.hi_oracle_tune_errors_tiles.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, i64, P, P]
+            lib.hi_oracle_tune_select.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, P]
             lib.hi_oracle_trace.argtypes = [P, ctypes.c_int, P, P, P, P, P]
             _lib = lib
     return _lib
@@ -203,26 +203,27 @@ def tune_samples(shape, A):
     return int(_load().hi_oracle_tune_samples(_p(_dims3(shape)), int(A)))
 
 
-def tune_configs(shape):
-    """Candidate (interp, order) per level in enumeration order."""
+def tune_configs(shape, md=False):
+    """Candidate (interp, order) per level in enumeration order (md: with the
+    multi-dimensional scheme's two candidates)."""
     ci = np.zeros(14, dtype=np.uint8)
     co = np.zeros(42, dtype=np.uint8)
-    n = _load().hi_oracle_tune_configs(_p(_dims3(shape)), _p(ci), _p(co))
+    n = _load().hi_oracle_tune_configs(_p(_dims3(shape)), int(bool(md)), _p(ci), _p(co))
     return [(int(ci[k]), tuple(int(v) for v in co[3 * k:3 * k + 3])) for k in range(n)]
 
 
-def tune_errors(x, A):
+def tune_errors(x, A, md=False):
     """err[L, ncfg]: open-loop sum |x - p| per level and candidate (Sec. 5.1.3)."""
     lib = _load()
     x = np.ascontiguousarray(x, dtype=np.float32)
     L = n_levels(A)
     err = np.zeros(L * 14, dtype=np.float64)
     nc = np.zeros(1, dtype=np.int32)
-    _check(lib.hi_oracle_tune_errors(_p(_dims3(x.shape)), int(A), _p(x), _p(err), _p(nc)))
+    _check(lib.hi_oracle_tune_errors(_p(_dims3(x.shape)), int(A), int(bool(md)), _p(x), _p(err), _p(nc)))
     return err[:L * int(nc[0])].reshape(L, int(nc[0]))
 
 
-def tune_errors_tiles(x, A, tiles):
+def tune_errors_tiles(x, A, tiles, md=False):
     """err[k, L, ncfg]: the terms of :func:`tune_errors` of block tiles[k]
     (row-major block ids of x), one block at a time."""
     lib = _load()
@@ -231,18 +232,19 @@ def tune_errors_tiles(x, A, tiles):
     t = np.ascontiguousarray(tiles, dtype=np.int64)
     err = np.zeros(max(1, t.size) * L * 14, dtype=np.float64)
     nc = np.zeros(1, dtype=np.int32)
-    _check(lib.hi_oracle_tune_errors_tiles(_p(_dims3(x.shape)), int(A), _p(x), _p(t), t.size, _p(err), _p(nc)))
+    _check(lib.hi_oracle_tune_errors_tiles(_p(_dims3(x.shape)), int(A), int(bool(md)), _p(x), _p(t), t.size,
+                                           _p(err), _p(nc)))
     n = int(nc[0])
     return err[:t.size * L * n].reshape(t.size, L, n)
 
 
-def tune_select(shape, A, err):
+def tune_select(shape, A, err, md=False):
     lib = _load()
     L = n_levels(A)
     err = np.ascontiguousarray(err, dtype=np.float64)
     interp = np.zeros(L, dtype=np.uint8)
     order = np.zeros((L, 3), dtype=np.uint8)
-    _check(lib.hi_oracle_tune_select(_p(_dims3(shape)), int(A), _p(err), _p(interp), _p(order)))
+    _check(lib.hi_oracle_tune_select(_p(_dims3(shape)), int(A), int(bool(md)), _p(err), _p(interp), _p(order)))
     return interp, order
 
 

@@ -860,10 +860,10 @@ int64_t hi_oracle_tune_samples(const int64_t dims[3], int A)
 /* Candidate configurations of one level, in enumeration order: the 1D
  * scheme, cubic before linear, within each the permutations of the active
  * dims in lexicographic order (inactive dims appended in ascending order);
- * then, with two or more active dims, the multi-dimensional scheme, cubic
- * before linear (its order field is the first permutation, unused).
- * Returns the count (at most 14). */
-int hi_oracle_tune_configs(const int64_t dims[3], uint8_t* interp_out, uint8_t* order_out)
+ * then, when with_md is set and two or more dims are active, the
+ * multi-dimensional scheme, cubic before linear (its order field is the
+ * first permutation, unused).  Returns the count (at most 14). */
+int hi_oracle_tune_configs(const int64_t dims[3], int with_md, uint8_t* interp_out, uint8_t* order_out)
 {
     int act[3], na = 0, inact[3], ni = 0, d, i, cnt = 0, sp;
     int perms[6][3], np = 0;
@@ -912,7 +912,7 @@ int hi_oracle_tune_configs(const int64_t dims[3], uint8_t* interp_out, uint8_t* 
             cnt++;
         }
     }
-    if (na >= 2) {
+    if (with_md && na >= 2) {
         for (sp = 0; sp < 2; sp++) {
             int q;
             interp_out[cnt] = (uint8_t)(sp == 0 ? ORC_MD_CUBIC : ORC_MD_LINEAR);
@@ -926,7 +926,7 @@ int hi_oracle_tune_configs(const int64_t dims[3], uint8_t* interp_out, uint8_t* 
 /* err[l * ncfg + c]: sum over the sampled blocks of |x - p| for the points
  * of level l under configuration c, predictions from original values.
  * The sampled blocks are every (nblocks / m)-th block, starting at block 0. */
-int hi_oracle_tune_errors(const int64_t dims[3], int A, const float* x, double* err, int* ncfg_out)
+int hi_oracle_tune_errors(const int64_t dims[3], int A, int with_md, const float* x, double* err, int* ncfg_out)
 {
     geom G;
     block B;
@@ -940,7 +940,7 @@ int hi_oracle_tune_errors(const int64_t dims[3], int A, const float* x, double* 
     nblocks = G.nb[0] * G.nb[1] * G.nb[2];
     m = hi_oracle_tune_samples(dims, A);
     stride = nblocks / m;
-    ncfg = hi_oracle_tune_configs(dims, cinterp, corder);
+    ncfg = hi_oracle_tune_configs(dims, with_md, cinterp, corder);
     *ncfg_out = ncfg;
     for (k = 0; k < G.L * ncfg; k++) err[k] = 0.0;
     if (block_mem_alloc(&M, A)) {
@@ -994,7 +994,7 @@ done:
  * under configuration c, predictions from original values -- the terms that
  * hi_oracle_tune_errors adds up over its sampled blocks.  Lets ranks that
  * hold parts of a field evaluate the global sample blocks they hold. */
-int hi_oracle_tune_errors_tiles(const int64_t dims[3], int A, const float* x, const int64_t* tiles,
+int hi_oracle_tune_errors_tiles(const int64_t dims[3], int A, int with_md, const float* x, const int64_t* tiles,
                                 int64_t ntiles, double* err, int* ncfg_out)
 {
     geom G;
@@ -1006,7 +1006,7 @@ int hi_oracle_tune_errors_tiles(const int64_t dims[3], int A, const float* x, co
     int ncfg, c, l, rc = geom_init(&G, dims, A);
     if (rc) return rc;
     nblocks = G.nb[0] * G.nb[1] * G.nb[2];
-    ncfg = hi_oracle_tune_configs(dims, cinterp, corder);
+    ncfg = hi_oracle_tune_configs(dims, with_md, cinterp, corder);
     *ncfg_out = ncfg;
     for (k = 0; k < ntiles * G.L * ncfg; k++) err[k] = 0.0;
     if (block_mem_alloc(&M, A)) {
@@ -1056,10 +1056,10 @@ done:
 
 /* Per level, the configuration with the smallest error; ties go to the
  * first in enumeration order. */
-int hi_oracle_tune_select(const int64_t dims[3], int A, const double* err, uint8_t* interp, uint8_t* order)
+int hi_oracle_tune_select(const int64_t dims[3], int A, int with_md, const double* err, uint8_t* interp, uint8_t* order)
 {
     uint8_t cinterp[14], corder[42];
-    int ncfg = hi_oracle_tune_configs(dims, cinterp, corder);
+    int ncfg = hi_oracle_tune_configs(dims, with_md, cinterp, corder);
     int L = ilog2_exact(A), l, c, q;
     if (L < 1) return ORC_EINVAL;
     for (l = 0; l < L; l++) {

@@ -36,7 +36,7 @@ int ilog2_pow2(uint32_t A)
 
 // Candidates of one level (Sec. 5.1.3): cubic before linear; permutations of
 // the active dims in lexicographic order with inactive dims appended.
-TuneCands make_cands(const uint64_t dims[3])
+TuneCands make_cands(const uint64_t dims[3], bool with_md)
 {
     TuneCands tc{};
     int act[3], na = 0, ina[3], ni = 0;
@@ -72,6 +72,13 @@ TuneCands make_cands(const uint64_t dims[3])
             tc.interp[c] = (uint8_t)(sp == 0 ? HI_CUBIC : HI_LINEAR);
             for (int k = 0; k < 3; ++k) tc.order[c][k] = (uint8_t)perms[i][k];
         }
+    if (with_md && na >= 2) {  // the multi-dimensional scheme, cubic before linear (order field: the first sequence)
+        for (int sp = 0; sp < 2; ++sp) {
+            const int c = tc.ncfg++;
+            tc.interp[c] = (uint8_t)(sp == 0 ? HI_MD_CUBIC : HI_MD_LINEAR);
+            for (int k = 0; k < 3; ++k) tc.order[c][k] = (uint8_t)perms[0][k];
+        }
+    }
     return tc;
 }
 
@@ -82,7 +89,7 @@ hi_status make_geometry(const hi_params* p, Geometry* G)
     if (L < 0) return HI_EINVAL;
     if (!(p->eb > 0.0) || !std::isfinite(p->eb)) return HI_EINVAL;
     if (p->eb_mode != HI_EB_ABS && p->eb_mode != HI_EB_REL) return HI_EINVAL;
-    if (p->autotune > 1) return HI_EINVAL;
+    if (p->autotune > 2) return HI_EINVAL;
     const int A = (int)p->anchor_stride;
     G->A = A;
     G->L = L;
@@ -104,7 +111,7 @@ hi_status make_geometry(const hi_params* p, Geometry* G)
     if (!p->autotune) {
         for (int l = 0; l < L; ++l) {
             const hi_level& lv = p->level[l];
-            if (lv.interp != HI_LINEAR && lv.interp != HI_CUBIC) return HI_EINVAL;
+            if (lv.interp > HI_MD_CUBIC) return HI_EINVAL;
             int seen = 0;
             for (int k = 0; k < 3; ++k) {
                 if (lv.order[k] > 2) return HI_EINVAL;
@@ -131,7 +138,7 @@ hi_status make_geometry(const hi_params* p, Geometry* G)
     if (m > (long long)nt) m = (long long)nt;
     G->m = (int)m;
     G->stride = (int)(nt / (uint64_t)m);
-    G->cands = make_cands(p->dims);
+    G->cands = make_cands(p->dims, p->autotune == 2);
     return HI_OK;
 }
 
@@ -144,7 +151,7 @@ constexpr size_t kWsTune = kWsPartials + sizeof(float2) * kRangeBlocks;
 size_t workspace_bytes(const Geometry& G)
 {
     static_assert(kWsTune >= HI_DECOMPRESS_WS_BYTES, "workspace layout");
-    return kWsTune + sizeof(double) * (size_t)G.m * G.L * 12;
+    return kWsTune + sizeof(double) * (size_t)G.m * G.L * (size_t)G.cands.ncfg;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode()
@@ -464,7 +471,7 @@ hi_status hi_autotune(const hi_params* p, const float* d_x, hi_header* d_header,
 {
     Geometry G;
     hi_params q = *p;
-    q.autotune = 1;
+    if (q.autotune == 0) q.autotune = 1;
     hi_status s = make_geometry(&q, &G);
     if (s != HI_OK) return s;
     if (!d_x || !d_header || !d_ws || !aligned(d_ws, 8)) return HI_EINVAL;
@@ -479,7 +486,7 @@ hi_status hi_autotune_errors(const hi_params* p, const void* d_ws, double* h_err
 {
     Geometry G;
     hi_params q = *p;
-    q.autotune = 1;
+    if (q.autotune == 0) q.autotune = 1;
     hi_status s = make_geometry(&q, &G);
     if (s != HI_OK) return s;
     if (m) *m = (uint32_t)G.m;

@@ -218,10 +218,73 @@ __device__ __forceinline__ double tune_pass(const float* __restrict__ v, bool cu
     return acc;
 }
 
+// Open-loop error of the multi-dimensional scheme at stride S (the same
+// phases and means as level_md, predictions from the original values).
+template <int A>
+__device__ __noinline__ double tune_md(const float* __restrict__ v, int S, bool cubic, const int e0, const int e1,
+                                       const int e2)
+{
+    using TG = TileGeom<A>;
+    const int e[3] = {e0, e1, e2};
+    const int act = (e0 > 0 ? 1 : 0) | (e1 > 0 ? 2 : 0) | (e2 > 0 ? 4 : 0);
+    double acc = 0.0;
+    for (int m = 1; m < 8; ++m) {
+        if (m & ~act) continue;
+        int n[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            n[d] = ((m >> d) & 1) ? (e[d] >= S ? (e[d] - S) / (2 * S) + 1 : 0) : e[d] / (2 * S) + 1;
+        const int total = n[0] * n[1] * n[2];
+        for (int i = threadIdx.x; i < total; i += blockDim.x) {
+            const int j2 = i % n[2], r = i / n[2];
+            const int j1 = r % n[1], j0 = r / n[1];
+            const int jj[3] = {j0, j1, j2};
+            int c[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) c[d] = ((m >> d) & 1) ? (2 * jj[d] + 1) * S : 2 * jj[d] * S;
+            const int vi = c[0] * TG::PY + c[1] * TG::PX + c[2];
+            float p[3];
+            int o[3];
+            int best = -1;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                p[d] = 0.0f;
+                o[d] = -1;
+                if (!((m >> d) & 1)) continue;
+                const int st = (d == 0 ? TG::PY : (d == 1 ? TG::PX : 1)) * S;
+                const bool have_r = c[d] + S <= e[d], have_l3 = c[d] >= 3 * S, have_r3 = c[d] + 3 * S <= e[d];
+                const float b = v[vi - st];
+                const float u = have_r ? v[vi + st] : 0.0f;
+                const float a = have_l3 ? v[vi - 3 * st] : 0.0f;
+                const float w = have_r3 ? v[vi + 3 * st] : 0.0f;
+                p[d] = predict(cubic, have_l3, have_r, have_r3, a, b, u, w);
+                o[d] = !have_r ? (have_l3 ? 1 : 0) : (!cubic ? 1 : ((have_l3 && have_r3) ? 3 : ((have_l3 || have_r3) ? 2 : 1)));
+                best = o[d] > best ? o[d] : best;
+            }
+            float sum = 0.0f;
+            int cnt = 0;
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                if (o[d] == best) {
+                    sum = cnt == 0 ? p[d] : __fadd_rn(sum, p[d]);
+                    ++cnt;
+                }
+            const float pr = cnt == 1 ? sum : (cnt == 2 ? __fmul_rn(sum, 0.5f) : __fdiv_rn(sum, 3.0f));
+            acc += (double)fabsf(__fsub_rn(v[vi], pr));
+        }
+    }
+    return acc;
+}
+
 template <int A, int LV>
 __device__ __forceinline__ void tune_levels(const float* v, const hi_level& lv, const int e[3], double* acc)
 {
     constexpr int S = 1 << LV;
+    if (lv.interp == HI_MD_LINEAR || lv.interp == HI_MD_CUBIC) {
+        acc[LV] = tune_md<A>(v, S, lv.interp == HI_MD_CUBIC, e[0], e[1], e[2]);
+        if constexpr (LV > 0) tune_levels<A, LV - 1>(v, lv, e, acc);
+        return;
+    }
     const bool cubic = lv.interp == HI_CUBIC;
     double a = 0.0;
 #pragma unroll
@@ -253,7 +316,7 @@ __device__ __forceinline__ void tune_block(float* v, const CUtensorMap* tmap, co
     __shared__ double s_red[L][16];  // up to 512 threads
     __shared__ __align__(8) uint64_t s_mbar;
     __shared__ bool s_last;
-    __shared__ double s_tot[L * 12];
+    __shared__ double s_tot[L * kMaxCands];
 
     const int tile = sample * stride;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;

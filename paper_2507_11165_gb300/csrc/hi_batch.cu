@@ -68,7 +68,8 @@ __device__ __forceinline__ void batch_range_items(const BatchField* __restrict__
 // Value range and auto-tune of every field in one launch (neither needs the
 // other: the tuner's errors are open-loop, without eps).  Blocks [0, ntune):
 // auto-tune, block = (a sample of some field, candidate; beyond the field's
-// candidate count: nothing to do); the next nb_range blocks: the range items.
+// candidate count: nothing to do), kMaxCands blocks per sample; the next
+// nb_range blocks: the range items.
 template <int A>
 __global__ void __launch_bounds__(256) k_batch_range_tune(const BatchField* __restrict__ fields,
                                                           const uint32_t* __restrict__ sample_start,
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(256) k_batch_range_tune(const BatchField* __re
 {
     extern __shared__ __align__(128) unsigned char smem[];
     if (blockIdx.x < ntune) {
-        const uint32_t smp = blockIdx.x / 12, c = blockIdx.x % 12;
+        const uint32_t smp = blockIdx.x / kMaxCands, c = blockIdx.x % kMaxCands;
         const int f = find_field(sample_start, n, smp);
         const BatchField& F = fields[f];
         if ((int)c >= F.cands.ncfg) return;
@@ -308,7 +309,7 @@ static cudaError_t launch_batch_range_tune_t(const BatchLaunch& b, cudaStream_t 
     if (e != cudaSuccess) return e;
     uint32_t nb_range = (uint32_t)b.num_sms * 8;
     if (nb_range > b.total_chunks) nb_range = b.total_chunks;
-    const uint32_t ntune = b.total_samples * 12;
+    const uint32_t ntune = b.total_samples * kMaxCands;
     kern<<<ntune + nb_range, 256, smem, st>>>(b.fields, b.sample_start, b.chunk_start, b.n, ntune, b.total_chunks,
                                              nb_range);
     return cudaGetLastError();

@@ -78,12 +78,15 @@ struct DecompressLaunch {
     int max_ctas;
 };
 
-// Auto-tune candidates of one level.
+// Auto-tune candidates of one level: the 1D sequences, then the
+// multi-dimensional scheme (two or more active dims).
+constexpr int kMaxCands = 14;
+
 struct TuneCands {
     int ncfg;
     int nperm;
-    uint8_t interp[12];
-    uint8_t order[12][3];
+    uint8_t interp[kMaxCands];
+    uint8_t order[kMaxCands][3];
 };
 
 cudaError_t launch_compress(int A, const CompressLaunch& c, cudaStream_t st);

@@ -328,7 +328,86 @@ __device__ HI_LEVEL_FN void level_full(float* v, uint8_t* cs, const Hot h)
     __syncthreads();
 }
 
-// sel = 2 * perm + cubic; perm: 0 (0,1,2) 1 (0,2,1) 2 (1,0,2) 3 (1,2,0) 4 (2,0,1) 5 (2,1,0)
+// ---------------------------------------------------------------------------
+// Multi-dimensional interpolation (Sec. 5.1.2): the level's points are taken
+// in three phases by the number of their coordinates that are odd multiples
+// of S (1, 2, then 3); a point is interpolated along each of its odd dims
+// with that dim's 1D stencil, and the prediction is the mean of the
+// interpolations of the highest order (cubic 3, quadratic 2, linear 1,
+// copy 0), summed in increasing dim order: one as is, two times 0.5, three
+// divided by 3.  Run-time extents; one block barrier per phase.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int stencil_order(bool cubic, bool have_l3, bool have_r, bool have_r3)
+{
+    if (!have_r) return have_l3 ? 1 : 0;
+    if (!cubic) return 1;
+    if (have_l3 && have_r3) return 3;
+    return (have_l3 || have_r3) ? 2 : 1;
+}
+
+template <int A, bool COMP>
+__device__ __noinline__ void level_md(int S, bool cubic, float* v, uint8_t* cs, const Hot h, int e0, int e1, int e2)
+{
+    using Lw = Lay<A>;
+    constexpr int CX = COMP ? Lw::CXC : Lw::CXD, CY = COMP ? Lw::CYC : Lw::CYD;
+    const int e[3] = {e0, e1, e2};
+    const int act = (e0 > 0 ? 1 : 0) | (e1 > 0 ? 2 : 0) | (e2 > 0 ? 4 : 0);  // extent 0: inactive dim
+    for (int k = 1; k <= 3; ++k) {
+        for (int m = 1; m < 8; ++m) {
+            if (__popc(m) != k || (m & ~act)) continue;
+            int n[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                n[d] = ((m >> d) & 1) ? (e[d] >= S ? (e[d] - S) / (2 * S) + 1 : 0) : e[d] / (2 * S) + 1;
+            const int total = n[0] * n[1] * n[2];
+            for (int i = threadIdx.x; i < total; i += blockDim.x) {
+                const int j2 = i % n[2], r = i / n[2];
+                const int j1 = r % n[1], j0 = r / n[1];
+                const int jj[3] = {j0, j1, j2};
+                int c[3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) c[d] = ((m >> d) & 1) ? (2 * jj[d] + 1) * S : 2 * jj[d] * S;
+                const int vi = c[0] * Lw::PY + c[1] * Lw::PX + c[2];
+                float p[3];
+                int o[3];
+                int best = -1;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    p[d] = 0.0f;
+                    o[d] = -1;
+                    if (!((m >> d) & 1)) continue;
+                    const int st = (d == 0 ? Lw::PY : (d == 1 ? Lw::PX : 1)) * S;
+                    const bool have_r = c[d] + S <= e[d], have_l3 = c[d] >= 3 * S, have_r3 = c[d] + 3 * S <= e[d];
+                    const float b = v[vi - st];
+                    const float u = have_r ? v[vi + st] : 0.0f;
+                    const float a = have_l3 ? v[vi - 3 * st] : 0.0f;
+                    const float w = have_r3 ? v[vi + 3 * st] : 0.0f;
+                    p[d] = predict(cubic, have_l3, have_r, have_r3, a, b, u, w);
+                    o[d] = stencil_order(cubic, have_l3, have_r, have_r3);
+                    best = o[d] > best ? o[d] : best;
+                }
+                float sum = 0.0f;
+                int cnt = 0;
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+                    if (o[d] == best) {
+                        sum = cnt == 0 ? p[d] : __fadd_rn(sum, p[d]);
+                        ++cnt;
+                    }
+                const float pr = cnt == 1 ? sum : (cnt == 2 ? __fmul_rn(sum, 0.5f) : __fdiv_rn(sum, 3.0f));
+                const int ci = c[0] * CY + c[1] * CX + c[2];
+                if constexpr (COMP)
+                    v[vi] = point_compress(h, v[vi], pr, cs + ci);
+                else
+                    v[vi] = point_decompress<A>(h, cs[ci], pr, vi);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// sel = 2 * perm + cubic; perm: 0 (0,1,2) 1 (0,2,1) 2 (1,0,2) 3 (1,2,0) 4 (2,0,1) 5 (2,1,0);
+// 12 / 13: the multi-dimensional scheme with linear / cubic splines
 template <int A, int S, bool COMP>
 __device__ __forceinline__ void level_dispatch(int sel, float* v, uint8_t* cs, const Hot h)
 {
@@ -344,7 +423,9 @@ __device__ __forceinline__ void level_dispatch(int sel, float* v, uint8_t* cs, c
     case 8: level_full<A, S, 2, 0, 1, false, COMP>(v, cs, h); break;
     case 9: level_full<A, S, 2, 0, 1, true, COMP>(v, cs, h); break;
     case 10: level_full<A, S, 2, 1, 0, false, COMP>(v, cs, h); break;
-    default: level_full<A, S, 2, 1, 0, true, COMP>(v, cs, h); break;
+    case 11: level_full<A, S, 2, 1, 0, true, COMP>(v, cs, h); break;
+    case 12: level_md<A, COMP>(S, false, v, cs, h, A, A, A); break;
+    default: level_md<A, COMP>(S, true, v, cs, h, A, A, A); break;
     }
 }
 
@@ -357,6 +438,8 @@ __device__ __forceinline__ void levels_full(const int* s_sel, float* v, uint8_t*
 
 __device__ __forceinline__ int perm_sel(const hi_level& lv)
 {
+    if (lv.interp == HI_MD_LINEAR) return 12;
+    if (lv.interp == HI_MD_CUBIC) return 13;
     const int a = lv.order[0], b = lv.order[1];
     const int p = (a == 0) ? (b == 1 ? 0 : 1) : (a == 1) ? (b == 0 ? 2 : 3) : (b == 0 ? 4 : 5);
     return 2 * p + (lv.interp == HI_CUBIC ? 1 : 0);
@@ -399,6 +482,10 @@ __device__ HI_LEVEL_FN void level_ragged(const hi_level lv, float* v, uint8_t* c
                                           int e2)
 {
     constexpr int S = 1 << LV;
+    if (lv.interp == HI_MD_LINEAR || lv.interp == HI_MD_CUBIC) {
+        level_md<A, COMP>(S, lv.interp == HI_MD_CUBIC, v, cs, h, e0, e1, e2);
+        return;
+    }
     const bool cubic = lv.interp == HI_CUBIC;
     const int e[3] = {e0, e1, e2};
     for (int p = 0; p < 3; ++p) {

@@ -27,6 +27,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libhi.so")
 HI_OK, HI_EINVAL, HI_ENOMEM, HI_ECAPACITY, HI_ECUDA, HI_ETIMEOUT, HI_ECORRUPT = range(7)
 EB_ABS, EB_REL = 0, 1
 LINEAR, CUBIC = 0, 1
+MD_LINEAR, MD_CUBIC = 2, 3  # multi-dimensional interpolation scheme (Sec. 5.1.2)
 MAX_LEVELS = 8
 MAGIC = 0x48693235
 RADIUS = 128
@@ -160,7 +161,7 @@ def make_params(shape, eb, mode="rel", anchor_stride=16, autotune=True, levels=N
     p.eb = float(eb)
     p.eb_mode = EB_REL if mode in ("rel", EB_REL) else EB_ABS
     p.anchor_stride = int(anchor_stride)
-    p.autotune = 1 if autotune else 0
+    p.autotune = 2 if autotune == 2 else (1 if autotune else 0)  # 2: with the multi-dimensional scheme
     p.tuning = {0: 0, 64: 1, 128: 2}[int(threads)] | ({0: 0, 1: 1, 2: 2}[int(buffers)] << 2)
     L = max(1, int(anchor_stride).bit_length() - 1)
     if levels is None:

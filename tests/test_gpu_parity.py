@@ -92,6 +92,15 @@ CASES = [
     ((1, 1, 1), 8, 1e-3, 1, "random"),
     ((37, 41, 43), 16, 1e-3, 1, "random"),           # n2 % 4 != 0: plain-load path
     ((48, 48, 52), 16, 1e-5, 1, "random"),           # many outliers
+    # the multi-dimensional scheme (Sec. 5.1.2), mixed with 1D levels
+    ((70, 45, 53), 16, 1e-3, 1, "md"),
+    ((33, 33, 33), 16, 1e-4, 1, "md"),
+    ((40, 36, 44), 8, 1e-2, 1, "md"),
+    ((257, 301), 16, 1e-3, 1, "md"),
+    ((37, 41, 43), 16, 1e-3, 1, "md"),               # plain-load path
+    ((31, 29, 30), 4, 1e-3, 1, "md"),
+    ((50, 40, 70), 32, 1e-3, 1, "md"),
+    ((64, 64, 64), 8, 1e-3, 1, "md_all"),
 ]
 
 
@@ -107,12 +116,16 @@ def _cfg(oracle, shape, A, spec, rng):
         return oracle.levels(L, oracle.CUBIC, (0, 1, 2))
     if spec == "linear":
         return oracle.levels(L, oracle.LINEAR, (2, 1, 0))
+    if spec == "md_all":
+        return oracle.levels(L, oracle.MD_CUBIC, (0, 1, 2))
     n3 = (1,) * (3 - len(shape)) + tuple(shape)
     act = [d for d in range(3) if n3[d] > 1]
     interp = rng.integers(0, 2, size=L).astype(np.uint8)
     order = np.zeros((L, 3), dtype=np.uint8)
     for l in range(L):
         order[l] = list(rng.permutation(act)) + [d for d in range(3) if d not in act]
+        if spec == "md" and rng.uniform() < 0.6:
+            interp[l] = oracle.MD_LINEAR + int(rng.integers(0, 2))
     return interp, order
 
 
@@ -234,18 +247,20 @@ def test_determinism(hi):
 # --------------------------------------------------------------------------
 # Auto-tune (Sec. 5.1.3)
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("shape,A", [((64, 64, 64), 8), ((96, 112, 80), 16), ((300, 500), 16), ((5000,), 8),
-                                     ((100, 120, 90), 4)])
-def test_autotune_parity(oracle_mod, hi, shape, A):
+@pytest.mark.parametrize("shape,A,md", [((64, 64, 64), 8, False), ((96, 112, 80), 16, False), ((300, 500), 16, False),
+                                        ((5000,), 8, False), ((100, 120, 90), 4, False), ((96, 112, 80), 16, True),
+                                        ((300, 500), 16, True), ((64, 64, 64), 8, True)])
+def test_autotune_parity(oracle_mod, hi, shape, A, md):
+    """md: candidates include the multi-dimensional scheme (autotune = 2)."""
     x = fields.lognormal_grf(shape, seed=7) if len(shape) == 3 else fields.bumps_field(shape, seed=7)
-    p, b, h = run_gpu(hi, x, A, 1e-3, 1, autotune=True)
+    p, b, h = run_gpu(hi, x, A, 1e-3, 1, autotune=2 if md else True)
     assert h.status == 0
     gerr = hi.autotune_errors(b)  # [m, L, ncfg]
-    oerr = oracle_mod.tune_errors(x, A)  # [L, ncfg]
+    oerr = oracle_mod.tune_errors(x, A, md=md)  # [L, ncfg]
     assert gerr.shape[0] == oracle_mod.tune_samples(shape, A)
     tot = gerr.sum(axis=0)
     np.testing.assert_allclose(tot, oerr, rtol=1e-9, atol=1e-12)
-    cfgs = oracle_mod.tune_configs(shape)
+    cfgs = oracle_mod.tune_configs(shape, md=md)
     L = oracle_mod.n_levels(A)
     for l in range(L):
         chosen = (int(h.level[l].interp), tuple(h.level[l].order))

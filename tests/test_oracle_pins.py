@@ -382,23 +382,26 @@ def test_tune_samples(oracle_mod):
 
 
 def test_tune_configs(oracle_mod):
-    """1D sequences (cubic, then linear, permutations in lexicographic order),
-    then the multi-dimensional scheme (cubic, then linear) with two or more
-    active dims."""
-    got = oracle_mod.tune_configs((4, 5, 6))
+    """1D sequences (cubic, then linear, permutations in lexicographic order);
+    with md, then the multi-dimensional scheme (cubic, then linear) when two
+    or more dims are active."""
     perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
-    assert got == [(1, p) for p in perms] + [(0, p) for p in perms] + [(3, (0, 1, 2)), (2, (0, 1, 2))]
-    assert oracle_mod.tune_configs((7, 9)) == [(1, (1, 2, 0)), (1, (2, 1, 0)), (0, (1, 2, 0)), (0, (2, 1, 0)),
-                                               (3, (1, 2, 0)), (2, (1, 2, 0))]
-    assert oracle_mod.tune_configs((9,)) == [(1, (2, 0, 1)), (0, (2, 0, 1))]
+    one_d = [(1, p) for p in perms] + [(0, p) for p in perms]
+    assert oracle_mod.tune_configs((4, 5, 6)) == one_d
+    assert oracle_mod.tune_configs((4, 5, 6), md=True) == one_d + [(3, (0, 1, 2)), (2, (0, 1, 2))]
+    two_d = [(1, (1, 2, 0)), (1, (2, 1, 0)), (0, (1, 2, 0)), (0, (2, 1, 0))]
+    assert oracle_mod.tune_configs((7, 9)) == two_d
+    assert oracle_mod.tune_configs((7, 9), md=True) == two_d + [(3, (1, 2, 0)), (2, (1, 2, 0))]
+    assert oracle_mod.tune_configs((9,)) == oracle_mod.tune_configs((9,), md=True) == [(1, (2, 0, 1)), (0, (2, 0, 1))]
 
 
-@pytest.mark.parametrize("shape,A", [((40, 33, 35), 16), ((64, 64, 64), 8), ((100, 120), 16), ((300,), 8)])
-def test_tune_errors_bruteforce(oracle_mod, shape, A):
+@pytest.mark.parametrize("shape,A,md", [((40, 33, 35), 16, False), ((64, 64, 64), 8, True), ((100, 120), 16, True),
+                                        ((300,), 8, False), ((40, 33, 35), 16, True)])
+def test_tune_errors_bruteforce(oracle_mod, shape, A, md):
     x = fields.bumps_field(shape, seed=13)
-    err = oracle_mod.tune_errors(x, A)
+    err = oracle_mod.tune_errors(x, A, md=md)
     L = oracle_mod.n_levels(A)
-    cfgs = oracle_mod.tune_configs(shape)
+    cfgs = oracle_mod.tune_configs(shape, md=md)
     m = oracle_mod.tune_samples(shape, A)
     nb = oracle_mod.block_grid(shape, A)
     nblocks = int(np.prod(nb))
@@ -428,12 +431,12 @@ def test_tune_errors_bruteforce(oracle_mod, shape, A):
 
 def test_tune_select_argmin(oracle_mod):
     # 2D: 4 one-dimensional candidates, then multi-dimensional cubic and linear
-    err = np.array([[3.0, 1.0, 1.0, 2.0, 5.0, 4.0], [0.0] * 6])
+    err = np.array([[3.0, 1.0, 1.0, 2.0], [0.0] * 4])
     interp, order = oracle_mod.tune_select((7, 9), 4, err)
     assert list(interp) == [1, 1]
     assert [tuple(o) for o in order] == [(2, 1, 0), (1, 2, 0)]
     err = np.array([[3.0, 1.0, 1.0, 2.0, 0.5, 4.0], [2.0, 2.0, 2.0, 2.0, 2.0, 1.0]])
-    interp, order = oracle_mod.tune_select((7, 9), 4, err)
+    interp, order = oracle_mod.tune_select((7, 9), 4, err, md=True)
     assert list(interp) == [3, 2]
 
 

@@ -33,7 +33,7 @@ def test_static_scratch_size_limits(hi):
 def test_static_scratch_rejects_large_field(hi):
     """A field whose workspace exceeds the fixed scratch is refused on the host
     before anything is enqueued or any pointer is looked at."""
-    p = hi.make_params((2 * 10 ** 7,), 1e-3, "rel", 2)
+    p = hi.make_params((10 ** 8,), 1e-3, "rel", 2)
     assert hi.query(p)["ws_bytes"] > hi.STATIC_WS_BYTES
     rc = hi.lib().hi_compress_static_ws(ctypes.byref(p), None, None, None, None, None, 0, None, None, None, None)
     assert rc == hi.HI_ENOMEM
