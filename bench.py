@@ -212,7 +212,7 @@ def run_gpu(args):
     x_host = fields.lognormal_grf(SHAPE, seed=SEED)
     N = x_host.size
     x = torch.from_numpy(x_host).to(dev)
-    p = hi.make_params(SHAPE, EB, "rel", A, autotune=True)
+    p = hi.make_params(SHAPE, EB, "rel", A, autotune=2 if args.md else True)
     b = hi.alloc(p, SHAPE, dev, hist=True, recon=False)
     out = torch.empty(SHAPE, dtype=torch.float32, device=dev)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
@@ -601,12 +601,16 @@ def main():
                     help="single: the 512^3 field (default); batch: 256 fields in one batched launch per stage; "
                          "serve: a Poisson request stream through the continuous-batching loop")
     ap.add_argument("--batch-fields", type=int, default=256)
+    ap.add_argument("--md", action="store_true",
+                    help="single: auto-tune over the 1D sequences and the multi-dimensional scheme")
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--shape", type=int, default=None,
                     help="cube side of a smaller field of the same recipe (profiling captures)")
     args = ap.parse_args()
+    global SHAPE, WORKLOAD
+    if args.md:
+        WORKLOAD = WORKLOAD.replace("auto-tuned levels", "auto-tuned levels incl. the multi-dimensional scheme")
     if args.shape:
-        global SHAPE, WORKLOAD
         SHAPE = (args.shape,) * 3
         WORKLOAD = WORKLOAD.replace("512^3", "%d^3" % args.shape)
         args.cpu_planes = min(args.cpu_planes, args.shape)

@@ -406,6 +406,75 @@ __device__ __noinline__ void level_md(int S, bool cubic, float* v, uint8_t* cs, 
     }
 }
 
+// The multi-dimensional scheme on a whole 3D tile: the points whose odd
+// dims are the set M, everything known at compile time (counts, divisions,
+// stencil cases: along an odd dim with NO odd positions, position j has
+// f(c-3S) when j >= 1 and f(c+3S) when j <= NO - 2; f(c+S) always).
+template <int A, int S, int M, bool CUBIC, bool COMP>
+__device__ __forceinline__ void md_set_full(float* v, uint8_t* cs, const Hot h)
+{
+    using Lw = Lay<A>;
+    constexpr int CX = COMP ? Lw::CXC : Lw::CXD, CY = COMP ? Lw::CYC : Lw::CYD;
+    constexpr int NO = A / (2 * S), NE = A / (2 * S) + 1;
+    constexpr int N0 = (M & 1) ? NO : NE, N1 = (M & 2) ? NO : NE, N2 = (M & 4) ? NO : NE;
+    constexpr int TOTAL = N0 * N1 * N2;
+    for (int i = threadIdx.x; i < TOTAL; i += blockDim.x) {
+        const int j2 = i % N2, r = i / N2;
+        const int j1 = r % N1, j0 = r / N1;
+        const int c0 = (M & 1) ? (2 * j0 + 1) * S : 2 * j0 * S;
+        const int c1 = (M & 2) ? (2 * j1 + 1) * S : 2 * j1 * S;
+        const int c2 = (M & 4) ? (2 * j2 + 1) * S : 2 * j2 * S;
+        const int vi = c0 * Lw::PY + c1 * Lw::PX + c2;
+        const int jd[3] = {j0, j1, j2};
+        float p[3];
+        int o[3];
+        int best = -1;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            p[d] = 0.0f;
+            o[d] = -1;
+            if (!((M >> d) & 1)) continue;
+            const int st = (d == 0 ? Lw::PY : (d == 1 ? Lw::PX : 1)) * S;
+            const bool l3 = CUBIC && jd[d] >= 1, r3 = CUBIC && jd[d] <= NO - 2;
+            const float b = v[vi - st], u = v[vi + st];
+            const float a = l3 ? v[vi - 3 * st] : 0.0f;
+            const float w = r3 ? v[vi + 3 * st] : 0.0f;
+            p[d] = predict(CUBIC, l3, true, r3, a, b, u, w);
+            o[d] = !CUBIC ? 1 : ((l3 && r3) ? 3 : ((l3 || r3) ? 2 : 1));
+            best = o[d] > best ? o[d] : best;
+        }
+        float sum = 0.0f;
+        int cnt = 0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            if (o[d] == best) {
+                sum = cnt == 0 ? p[d] : __fadd_rn(sum, p[d]);
+                ++cnt;
+            }
+        const float pr = cnt == 1 ? sum : (cnt == 2 ? __fmul_rn(sum, 0.5f) : __fdiv_rn(sum, 3.0f));
+        const int ci = c0 * CY + c1 * CX + c2;
+        if constexpr (COMP)
+            v[vi] = point_compress(h, v[vi], pr, cs + ci);
+        else
+            v[vi] = point_decompress<A>(h, cs[ci], pr, vi);
+    }
+}
+
+template <int A, int S, bool CUBIC, bool COMP>
+__device__ HI_LEVEL_FN void level_md_full(float* v, uint8_t* cs, const Hot h)
+{
+    md_set_full<A, S, 1, CUBIC, COMP>(v, cs, h);  // one odd dim
+    md_set_full<A, S, 2, CUBIC, COMP>(v, cs, h);
+    md_set_full<A, S, 4, CUBIC, COMP>(v, cs, h);
+    __syncthreads();
+    md_set_full<A, S, 3, CUBIC, COMP>(v, cs, h);  // two
+    md_set_full<A, S, 5, CUBIC, COMP>(v, cs, h);
+    md_set_full<A, S, 6, CUBIC, COMP>(v, cs, h);
+    __syncthreads();
+    md_set_full<A, S, 7, CUBIC, COMP>(v, cs, h);  // three
+    __syncthreads();
+}
+
 // sel = 2 * perm + cubic; perm: 0 (0,1,2) 1 (0,2,1) 2 (1,0,2) 3 (1,2,0) 4 (2,0,1) 5 (2,1,0);
 // 12 / 13: the multi-dimensional scheme with linear / cubic splines
 template <int A, int S, bool COMP>
@@ -424,8 +493,8 @@ __device__ __forceinline__ void level_dispatch(int sel, float* v, uint8_t* cs, c
     case 9: level_full<A, S, 2, 0, 1, true, COMP>(v, cs, h); break;
     case 10: level_full<A, S, 2, 1, 0, false, COMP>(v, cs, h); break;
     case 11: level_full<A, S, 2, 1, 0, true, COMP>(v, cs, h); break;
-    case 12: level_md<A, COMP>(S, false, v, cs, h, A, A, A); break;
-    default: level_md<A, COMP>(S, true, v, cs, h, A, A, A); break;
+    case 12: level_md_full<A, S, false, COMP>(v, cs, h); break;
+    default: level_md_full<A, S, true, COMP>(v, cs, h); break;
     }
 }
 
