@@ -48,12 +48,21 @@ class Done:
         return self.t_done - self.t_arrival
 
 
-def device_bytes(op: str, side: int) -> int:
+def outlier_capacity(side: int, eb: float) -> int:
+    """Outlier slots of a compress request: an eighth of the points, all of
+    them at bounds of 1e-5 and below (where a quarter of a turbulent field
+    can be outliers); a request that still overflows runs once more with the
+    exact count."""
+    n = side ** 3
+    return n if eb <= 1e-5 else max(4096, n // 8)
+
+
+def device_bytes(op: str, side: int, eb: float = 1e-3) -> int:
     """Device bytes a request holds while in flight (its own buffers)."""
     n = side ** 3
     if op == "compress":
-        # snapshot, codes, outlier list (capacity n / 8), anchors, header, workspace
-        return 4 * n + n + n + 4 * (n // 64 + 1) + 1024 + (1 << 16)
+        # snapshot, codes, outlier list, anchors, header, workspace
+        return 4 * n + n + 8 * outlier_capacity(side, eb) + 4 * (n // 64 + 1) + 1024 + (1 << 16)
     # reconstructed field (the record it reads is held by its compress request)
     return 4 * n + 1024
 
@@ -116,7 +125,7 @@ class Server:
                 n += 1
         return n
 
-    def run(self, requests: List[Request], idle_sleep: float = 50e-6) -> List[Done]:
+    def run(self, requests: List[Request], idle_sleep: float = 0.0) -> List[Done]:
         """Serve the requests (sorted by arrival); returns one Done per request."""
         pending = collections.deque(sorted(requests, key=lambda r: r.t))
         t0 = self.clock()
@@ -133,7 +142,7 @@ class Server:
                     # its record was dropped (or failed): serve it as a compress of the same snapshot
                     req = dataclasses.replace(req, op="compress")
                     pending[0] = req
-                need = device_bytes(req.op, req.side)
+                need = device_bytes(req.op, req.side, req.eb)
                 slot = self._free_slot()
                 if slot is None or not self._fits(need):
                     if not self.in_flight and not self._fits(need):
@@ -224,7 +233,11 @@ class GpuExecutor:
     simulation writing it), then runs hi_compress; its record (codes,
     anchors, outliers, header) is kept for later decompress requests.  A
     decompress request runs hi_decompress of a kept record into a new field.
-    Completion is a CUDA event after the last kernel."""
+    Completion is a CUDA event after the last kernel.
+
+    Buffers come from per-shape pools and go back once their last reader has
+    completed: a kept record stays until it is dropped and no decompress of
+    it is in flight."""
 
     def __init__(self, base, anchor_stride=16, keep_outputs=False, device=None):
         import torch
@@ -236,10 +249,14 @@ class GpuExecutor:
         self.A = anchor_stride
         self.dev = base.device if device is None else device
         self.streams = {}
-        self.kept = {}      # compress id -> (Buffers, shape)
+        self.kept = {}      # compress id -> Buffers of its record
+        self.readers = {}   # compress id -> decompress requests of it in flight
+        self.dropped = set()
         self.outputs = {}   # request id -> result tensors (when keep_outputs)
         self.keep_outputs = keep_outputs
         self.t0_event = None
+        self.pool = collections.defaultdict(list)  # (kind, shape, cap) -> free buffers
+        self.params = {}
 
     def start(self):
         self.t0_event = self.torch.cuda.Event(enable_timing=True)
@@ -253,6 +270,27 @@ class GpuExecutor:
             self.streams[slot] = self.torch.cuda.Stream(device=self.dev)
         return self.streams[slot]
 
+    def _get(self, key, make):
+        free = self.pool[key]
+        return free.pop() if free else make()
+
+    def _put(self, key, obj):
+        self.pool[key].append(obj)
+
+    @staticmethod
+    def _copy_record(b):
+        """A copy of a finished record (tests compare it with the same request run alone)."""
+        import types
+        return types.SimpleNamespace(codes=b.codes.clone(), anchors=b.anchors.clone(), hist=b.hist.clone(),
+                                     header=b.header.clone(), out_idx=b.out_idx.clone(),
+                                     out_val=b.out_val.clone(), out_cap=b.out_cap, shape=b.shape)
+
+    def _params(self, shape, eb):
+        key = (shape, eb)
+        if key not in self.params:
+            self.params[key] = self.hi.make_params(shape, eb, "rel", self.A, autotune=True)
+        return self.params[key]
+
     def snapshot_view(self, req):
         B = self.base.shape[0]
         s = req.side
@@ -263,29 +301,32 @@ class GpuExecutor:
         torch, hi = self.torch, self.hi
         st = self._stream(slot)
         shape = (req.side,) * 3
-        n = req.side ** 3
         with torch.cuda.stream(st):
             if req.op == "compress":
-                x = torch.empty(shape, dtype=torch.float32, device=self.dev)
+                cap = outlier_capacity(req.side, req.eb)
+                x = self._get(("x", shape), lambda: torch.empty(shape, dtype=torch.float32, device=self.dev))
                 x.copy_(self.snapshot_view(req))
-                p = hi.make_params(shape, req.eb, "rel", self.A, autotune=True)
-                b = hi.alloc(p, shape, self.dev, out_cap=max(4096, n // 8), hist=True, recon=False)
+                p = self._params(shape, req.eb)
+                b = self._get(("rec", shape, cap),
+                              lambda: hi.alloc(p, shape, self.dev, out_cap=cap, hist=True, recon=False))
+                b.params = p
                 hi.compress_into(x, b, stream=st)
-                hdr = torch.empty(hi.HEADER_BYTES, dtype=torch.uint8, pin_memory=True)
+                hdr = self._get(("hdr",), lambda: torch.empty(hi.HEADER_BYTES, dtype=torch.uint8, pin_memory=True))
                 hdr.copy_(b.header, non_blocking=True)
                 ev = torch.cuda.Event(enable_timing=True)
                 ev.record(st)
-                return dict(req=req, x=x, b=b, hdr=hdr, ev=ev, st=st, p=p)
+                return dict(req=req, x=x, b=b, cap=cap, hdr=hdr, ev=ev, st=st, p=p)
             b = self.kept[req.source]
-            out = torch.empty(b.shape, dtype=torch.float32, device=self.dev)
-            status = torch.zeros(1, dtype=torch.int32, device=self.dev)
-            ws = torch.empty(hi.DECOMPRESS_WS_BYTES, dtype=torch.uint8, device=self.dev)  # its own tile queue
-            hi.decompress_into(b, out, status, stream=st, ws=ws)
-            sh = torch.empty(1, dtype=torch.int32, pin_memory=True)
+            self.readers[req.source] = self.readers.get(req.source, 0) + 1
+            out = self._get(("out", shape), lambda: torch.empty(shape, dtype=torch.float32, device=self.dev))
+            status = self._get(("st",), lambda: torch.zeros(1, dtype=torch.int32, device=self.dev))
+            ws = self._get(("ws",), lambda: torch.empty(hi.DECOMPRESS_WS_BYTES, dtype=torch.uint8, device=self.dev))
+            hi.decompress_into(b, out, status, stream=st, ws=ws)  # its own tile queue
+            sh = self._get(("sh",), lambda: torch.empty(1, dtype=torch.int32, pin_memory=True))
             sh.copy_(status, non_blocking=True)
             ev = torch.cuda.Event(enable_timing=True)
             ev.record(st)
-            return dict(req=req, out=out, sh=sh, ev=ev, ws=ws)
+            return dict(req=req, out=out, stat_t=status, sh=sh, ev=ev, ws=ws)
 
     def poll(self, h):
         if not h["ev"].query():
@@ -299,12 +340,14 @@ class GpuExecutor:
                 # more outliers than the first capacity: once more with the exact count
                 torch, hi = self.torch, self.hi
                 with torch.cuda.stream(h["st"]):
+                    self._put(("rec", h["x"].shape, h["cap"]), h["b"])
                     b = hi.alloc(h["p"], h["x"].shape, self.dev, out_cap=int(hd.n_outliers), hist=True, recon=False)
                     hi.compress_into(h["x"], b, stream=h["st"])
                     h["hdr"].copy_(b.header, non_blocking=True)
                     h["ev"] = torch.cuda.Event(enable_timing=True)
                     h["ev"].record(h["st"])
                 h["b"] = b
+                h["cap"] = None  # not a pooled size
                 h["retried"] = True
                 return None
         else:
@@ -312,23 +355,49 @@ class GpuExecutor:
         h["status"] = st
         return (t, st)
 
+    def _recycle_record(self, rid):
+        b = self.kept.pop(rid, None)
+        self.dropped.discard(rid)
+        self.readers.pop(rid, None)
+        if b is not None and getattr(b, "pool_key", None) is not None:
+            self._put(b.pool_key, b)
+
     def release(self, h):
         req = h["req"]
+        shape = (req.side,) * 3
         if req.op == "compress":
+            self._put(("x", shape), h["x"])
+            self._put(("hdr",), h["hdr"])
+            b = h["b"]
+            b.pool_key = ("rec", shape, h["cap"]) if h["cap"] is not None else None
             if h.get("status", 1) == 0:
-                self.kept[req.id] = h["b"]
+                self.kept[req.id] = b
+            elif b.pool_key is not None:
+                self._put(b.pool_key, b)
             if self.keep_outputs:
-                self.outputs[req.id] = h["b"]
-        elif self.keep_outputs:
-            self.outputs[req.id] = h["out"]
+                self.outputs[req.id] = self._copy_record(b)
+        else:
+            if self.keep_outputs:
+                self.outputs[req.id] = h["out"].clone()
+            self._put(("out", shape), h["out"])
+            self._put(("st",), h["stat_t"])
+            self._put(("ws",), h["ws"])
+            self._put(("sh",), h["sh"])
+            left = self.readers.get(req.source, 1) - 1
+            self.readers[req.source] = left
+            if left == 0 and req.source in self.dropped:
+                self._recycle_record(req.source)
         h.clear()
 
     def record_bytes(self, req):
         n = req.side ** 3
-        return n + n + 4 * (n // 64 + 1) + 1024
+        return n + 8 * outlier_capacity(req.side, req.eb) + 4 * (n // 64 + 1) + 1024
 
     def drop_record(self, rid):
-        self.kept.pop(rid, None)
+        if self.readers.get(rid, 0) > 0:
+            self.dropped.add(rid)  # recycled when its last decompress completes
+        else:
+            self._recycle_record(rid)
 
 
 def make_requests(n=2000, rate=200.0, seed=5, lo=64, hi=512):
