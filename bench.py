@@ -601,13 +601,17 @@ def main():
                     help="single: the 512^3 field (default); batch: 256 fields in one batched launch per stage; "
                          "serve: a Poisson request stream through the continuous-batching loop")
     ap.add_argument("--batch-fields", type=int, default=256)
+    ap.add_argument("--eb", type=float, default=None, help="single: another relative bound (the sweep 1e-2 / 1e-4)")
     ap.add_argument("--md", action="store_true",
                     help="single: auto-tune over the 1D sequences and the multi-dimensional scheme")
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--shape", type=int, default=None,
                     help="cube side of a smaller field of the same recipe (profiling captures)")
     args = ap.parse_args()
-    global SHAPE, WORKLOAD
+    global SHAPE, WORKLOAD, EB
+    if args.eb:
+        EB = args.eb
+        WORKLOAD = WORKLOAD.replace("rel eb 1e-3", "rel eb %g" % EB)
     if args.md:
         WORKLOAD = WORKLOAD.replace("auto-tuned levels", "auto-tuned levels incl. the multi-dimensional scheme")
     if args.shape:

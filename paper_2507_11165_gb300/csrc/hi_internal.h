@@ -56,7 +56,7 @@ struct CompressLaunch {
     uint32_t tma_bytes;
     int flags;
     int threads;
-    int buffers;   // 0 = two when they fit, 1 = one, 2 = two
+    int buffers;   // 2: two tile buffers when they fit; otherwise one
     int num_sms;
     int max_ctas;  // 0 = occupancy-limited persistent grid
 };

@@ -99,6 +99,19 @@ def test_batch_equals_single_A8_fixed_levels(hi):
     _batch_vs_single(hi, mix, 8, False)
 
 
+def test_batch_equals_single_multidimensional(hi):
+    """Auto-tune over the 1D sequences and the multi-dimensional scheme
+    (autotune = 2): the batched kernel runs the same levels per field."""
+    mix = [((37, 45, 70), 1e-3, "rel"), ((64, 64, 64), 1e-3, "rel"), ((33, 33, 33), 1e-4, "rel"),
+           ((20, 300), 1e-3, "rel"), ((81, 97, 112), 1e-3, "rel"), ((50, 47, 63), 1e-2, "rel")]
+    bat, singles, xs = _batch_vs_single(hi, mix, 16, 2)
+    picked = set()
+    for b in bat.buffers:
+        h = hi.read_header(b.header)
+        picked |= {int(h.level[l].interp) for l in range(4)}
+    assert picked & {hi.MD_LINEAR, hi.MD_CUBIC}  # the scheme was chosen somewhere
+
+
 def test_batch_against_oracle(oracle_mod, hi):
     mix = [((37, 45, 70), 1e-3, "rel"), ((33, 33, 33), 1e-4, "rel")]
     xs = _inputs(mix, seed0=20)
