@@ -25,11 +25,16 @@ __global__ void __launch_bounds__(512) k_range(const float* __restrict__ x, int6
     range_block(x, N, partials, blockIdx.x, gridDim.x, ticket, hdr);
 }
 
+// A field's auto-tune samples are each split over this many blocks (the
+// candidates of a sample dealt out round robin): enough blocks to run beside
+// the range pass, each tile loaded by few of them.
+constexpr int kTuneGroups = 4;
+
 // The value range and the auto-tuner in one launch: they do not depend on
 // each other (the tuner's errors are open-loop, without eps), and the
 // tuner's latency-bound blocks (first in the grid) run beside the range
-// pass's streaming read.  Blocks [0, m * ncfg): auto-tune (sample, candidate);
-// the next nb_range blocks: the range pass.
+// pass's streaming read.  Blocks [0, m * kTuneGroups): auto-tune, a sample
+// and a group of candidates each; the next nb_range blocks: the range pass.
 template <int A>
 __global__ void __launch_bounds__(256) k_range_tune(const __grid_constant__ CUtensorMap tmap, const FieldGeo g,
                                                     const float* __restrict__ x, const TuneCands cands, int stride,
@@ -38,13 +43,13 @@ __global__ void __launch_bounds__(256) k_range_tune(const __grid_constant__ CUte
                                                     int nb_range, uint32_t* range_ticket, hi_header* hdr)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    const int ntune = m * cands.ncfg;
-    if ((int)blockIdx.x < ntune) {
-        tune_block<A>(reinterpret_cast<float*>(smem), &tmap, g, x, cands, (int)blockIdx.x / cands.ncfg,
-                      (int)blockIdx.x % cands.ncfg, stride, m, err, tune_ticket, hdr, tma_bytes, use_tma != 0);
+    if ((int)blockIdx.x < m * kTuneGroups) {
+        tune_sample<A>(reinterpret_cast<float*>(smem), &tmap, g, x, cands, blockIdx.x / kTuneGroups,
+                       blockIdx.x % kTuneGroups, kTuneGroups, stride, m, err, tune_ticket, hdr, tma_bytes,
+                       use_tma != 0);
         return;
     }
-    range_block(x, g.N, partials, (int)blockIdx.x - ntune, nb_range, range_ticket, hdr);
+    range_block(x, g.N, partials, (int)blockIdx.x - m * kTuneGroups, nb_range, range_ticket, hdr);
 }
 
 // Outlier values go to their place in the output before reconstruction reads
@@ -76,8 +81,9 @@ __global__ void __launch_bounds__(256) k_tune(const __grid_constant__ CUtensorMa
                                               hi_header* __restrict__ hdr, const uint32_t tma_bytes, const int use_tma)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    tune_block<A>(reinterpret_cast<float*>(smem), &tmap, g, x, cands, blockIdx.x, blockIdx.y, stride, gridDim.x, err,
-                  ticket, hdr, tma_bytes, use_tma != 0);
+    tune_sample<A>(reinterpret_cast<float*>(smem), &tmap, g, x, cands, blockIdx.x / kTuneGroups,
+                   blockIdx.x % kTuneGroups, kTuneGroups, stride, gridDim.x / kTuneGroups, err, ticket, hdr, tma_bytes,
+                   use_tma != 0);
 }
 
 cudaError_t launch_prologue(hi_header* hdr, const hi_params& p, uint64_t n_anchors, uint64_t out_cap,
@@ -109,8 +115,8 @@ static cudaError_t launch_tune_t(const TuneLaunch& t, cudaStream_t st)
     auto kern = k_tune<A>;
     cudaError_t e = set_max_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<dim3(t.m, t.cands.ncfg), 256, smem, st>>>(t.tmap, t.g, t.x, t.cands, t.stride, t.err, t.ticket, t.hdr,
-                                                     t.tma_bytes, t.use_tma ? 1 : 0);
+    kern<<<t.m * kTuneGroups, 256, smem, st>>>(t.tmap, t.g, t.x, t.cands, t.stride, t.err, t.ticket, t.hdr,
+                                               t.tma_bytes, t.use_tma ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -123,7 +129,7 @@ static cudaError_t launch_range_tune_t(const TuneLaunch& t, float2* partials, in
     auto kern = k_range_tune<A>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<t.m * t.cands.ncfg + nb_range, 256, smem, st>>>(t.tmap, t.g, t.x, t.cands, t.stride, t.m, t.err,
+    kern<<<t.m * kTuneGroups + nb_range, 256, smem, st>>>(t.tmap, t.g, t.x, t.cands, t.stride, t.m, t.err,
                                                              t.ticket, t.tma_bytes, t.use_tma ? 1 : 0, partials,
                                                              nb_range, range_ticket, t.hdr);
     return cudaGetLastError();

@@ -300,16 +300,18 @@ __device__ __forceinline__ void tune_levels(const float* v, const hi_level& lv, 
 }
 
 // One auto-tune block: sample `sample` (of m, every stride-th tile in
-// row-major order) under candidate c; its per-level sums go to
-// err[sample][l][c].  The last of the m * ncfg blocks of the field (ticket)
-// sums over the samples and writes each level's argmin to hdr->level (ties
-// to the first candidate), then resets the ticket.  v: (A+1)^3 floats of
-// dynamic shared memory.
+// row-major order) is loaded once and candidates group, group + groups, ...
+// are evaluated on it in turn; the per-level sums go to
+// err[sample][l][c].  The last of the field's m * groups blocks (ticket) sums
+// over the samples and writes each level's argmin to hdr->level (ties to the
+// first candidate), then resets the ticket.  v: (A+1)^3 floats of dynamic
+// shared memory.
 template <int A>
-__device__ __forceinline__ void tune_block(float* v, const CUtensorMap* tmap, const FieldGeo& g,
-                                           const float* __restrict__ x, const TuneCands& cands, int sample, int c,
-                                           int stride, int m, double* __restrict__ err, uint32_t* ticket,
-                                           hi_header* __restrict__ hdr, uint32_t tma_bytes, bool use_tma)
+__device__ __forceinline__ void tune_sample(float* v, const CUtensorMap* tmap, const FieldGeo& g,
+                                            const float* __restrict__ x, const TuneCands& cands, int sample,
+                                            int group, int groups, int stride, int m, double* __restrict__ err,
+                                            uint32_t* ticket, hi_header* __restrict__ hdr, uint32_t tma_bytes,
+                                            bool use_tma)
 {
     using TG = TileGeom<A>;
     constexpr int L = TG::L;
@@ -351,32 +353,35 @@ __device__ __forceinline__ void tune_block(float* v, const CUtensorMap* tmap, co
         __syncthreads();
     }
 
-    hi_level lv;
-    lv.interp = cands.interp[c];
-    lv.order[0] = cands.order[c][0];
-    lv.order[1] = cands.order[c][1];
-    lv.order[2] = cands.order[c][2];
-    double acc[L];
-    tune_levels<A, L - 1>(v, lv, e, acc);
-    // fixed-order reduction: warp butterfly, then warps in index order
-#pragma unroll
-    for (int l = 0; l < L; ++l) {
-        double a = acc[l];
-        for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
-        if (lane == 0) s_red[l][warp] = a;
-    }
-    __syncthreads();
     const int ncfg = cands.ncfg;
-    if (tid < L) {
-        double a = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += s_red[tid][w];
-        err[((size_t)sample * L + tid) * ncfg + c] = a;
+    for (int c = group; c < ncfg; c += groups) {
+        hi_level lv;
+        lv.interp = cands.interp[c];
+        lv.order[0] = cands.order[c][0];
+        lv.order[1] = cands.order[c][1];
+        lv.order[2] = cands.order[c][2];
+        double acc[L];
+        tune_levels<A, L - 1>(v, lv, e, acc);
+        // fixed-order reduction: warp butterfly, then warps in index order
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            double a = acc[l];
+            for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+            if (lane == 0) s_red[l][warp] = a;
+        }
+        __syncthreads();
+        if (tid < L) {
+            double a = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += s_red[tid][w];
+            err[((size_t)sample * L + tid) * ncfg + c] = a;
+        }
+        __syncthreads();  // s_red is reused by the next candidate
     }
 
     // the last block of the field sums the samples and picks each level's candidate
     __threadfence();
     __syncthreads();
-    if (tid == 0) s_last = atomicAdd(ticket, 1u) == (uint32_t)(m * ncfg) - 1;
+    if (tid == 0) s_last = atomicAdd(ticket, 1u) == (uint32_t)(m * groups) - 1;
     __syncthreads();
     if (!s_last) return;
     __threadfence();

@@ -67,9 +67,8 @@ __device__ __forceinline__ void batch_range_items(const BatchField* __restrict__
 
 // Value range and auto-tune of every field in one launch (neither needs the
 // other: the tuner's errors are open-loop, without eps).  Blocks [0, ntune):
-// auto-tune, block = (a sample of some field, candidate; beyond the field's
-// candidate count: nothing to do), kMaxCands blocks per sample; the next
-// nb_range blocks: the range items.
+// auto-tune, one sample of some field each; the next nb_range blocks: the
+// range items.
 template <int A>
 __global__ void __launch_bounds__(256) k_batch_range_tune(const BatchField* __restrict__ fields,
                                                           const uint32_t* __restrict__ sample_start,
@@ -78,12 +77,10 @@ __global__ void __launch_bounds__(256) k_batch_range_tune(const BatchField* __re
 {
     extern __shared__ __align__(128) unsigned char smem[];
     if (blockIdx.x < ntune) {
-        const uint32_t smp = blockIdx.x / kMaxCands, c = blockIdx.x % kMaxCands;
-        const int f = find_field(sample_start, n, smp);
+        const int f = find_field(sample_start, n, blockIdx.x);
         const BatchField& F = fields[f];
-        if ((int)c >= F.cands.ncfg) return;
-        tune_block<A>(reinterpret_cast<float*>(smem), &F.tmap, F.g, F.x, F.cands, smp - __ldg(sample_start + f), c,
-                      F.stride, F.m, F.err, &F.tickets[1], F.hdr, F.tma_bytes, (F.flags & kFlagTma) != 0);
+        tune_sample<A>(reinterpret_cast<float*>(smem), &F.tmap, F.g, F.x, F.cands, blockIdx.x - __ldg(sample_start + f),
+                       0, 1, F.stride, F.m, F.err, &F.tickets[1], F.hdr, F.tma_bytes, (F.flags & kFlagTma) != 0);
         return;
     }
     batch_range_items(fields, chunk_start, n, total_chunks, blockIdx.x - ntune, nb_range);
@@ -309,7 +306,7 @@ static cudaError_t launch_batch_range_tune_t(const BatchLaunch& b, cudaStream_t 
     if (e != cudaSuccess) return e;
     uint32_t nb_range = (uint32_t)b.num_sms * 8;
     if (nb_range > b.total_chunks) nb_range = b.total_chunks;
-    const uint32_t ntune = b.total_samples * kMaxCands;
+    const uint32_t ntune = b.total_samples;
     kern<<<ntune + nb_range, 256, smem, st>>>(b.fields, b.sample_start, b.chunk_start, b.n, ntune, b.total_chunks,
                                              nb_range);
     return cudaGetLastError();
