@@ -85,6 +85,7 @@ def _load():
             lib.hi_oracle_tune_errors_tiles.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, i64, P, P]
             lib.hi_oracle_tune_select.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, P]
             lib.hi_oracle_trace.argtypes = [P, ctypes.c_int, P, P, P, P, P]
+            lib.hi_oracle_reorder_index.argtypes = [P, ctypes.c_int, P]
             _lib = lib
     return _lib
 
@@ -290,3 +291,34 @@ def full_compress(x, A, interp, order, eb_mode, eb):
     out.update(col)
     out["consts"] = consts
     return out
+
+
+# ---------------------------------------------------------------------------
+# Quantization-code reordering (Sec. 5.2.2, Eq. 3)
+# ---------------------------------------------------------------------------
+def reorder_index(shape, A):
+    """I(x, y, z) of Eq. 3 for every point of the field, in row-major order
+    (int64, one entry per point): codes grouped by interpolation level,
+    coarsest (the anchors) first, row-major within a level."""
+    lib = _load()
+    d = _dims3(shape)
+    n_levels(A)
+    out = np.empty(int(np.prod(d)), dtype=np.int64)
+    _check(lib.hi_oracle_reorder_index(_p(d), int(A), _p(out)))
+    return out
+
+
+def reorder_codes(codes, A):
+    """The code array (any 1-3D shape) as the 1D sequence of Eq. 3."""
+    codes = np.ascontiguousarray(codes)
+    idx = reorder_index(codes.shape, A)
+    seq = np.empty(codes.size, dtype=codes.dtype)
+    seq[idx] = codes.reshape(-1)
+    return seq
+
+
+def unreorder_codes(seq, shape, A):
+    """Inverse of reorder_codes: the code array of ``shape`` from its sequence."""
+    idx = reorder_index(shape, A)
+    return np.asarray(seq).reshape(-1)[idx].reshape(tuple(int(s) for s in shape))
+

@@ -1117,3 +1117,65 @@ int hi_oracle_trace(const int64_t dims[3], int A, const uint8_t* interp, const u
     block_mem_free(&M);
     return rc;
 }
+
+/* ---------------------------------------------------------------------------
+ * Quantization-code reordering (Sec. 5.2.2, Eq. 3).
+ *
+ * The code of the point (x, y, z) (x slowest; dims dx, dy, dz) goes to
+ * position I(x, y, z) of a 1D sequence in which the codes of each
+ * interpolation level lie together, coarser levels first.  The level of a
+ * point is the largest l <= log2 A such that 2^l divides x, y and z;
+ * prefix(l) = fx(l) fy(l) fz(l) is the number of points on coarser levels,
+ * with f(0) = floor((d + 1) / 2) and f(k + 1) = floor((f(k) + 1) / 2), and
+ * prefix(log2 A) = 0.
+ *
+ * Reading: Eq. 3 spells out the rank within a level for l = 0 on the global
+ * grid -- the row-major index x dy dz + y dz + z minus the number of points
+ * with three even coordinates that precede it.  For 0 < l < log2 A the same
+ * rank is taken on the stride-2^l subgrid (coordinates x / 2^l, ..., whose
+ * dims are f(l - 1)), which is the reading under which prefix(l) counts the
+ * coarser points; the anchors (l = log2 A) come first, in the row-major
+ * order of the anchor grid.
+ *
+ * I[p] for every point p in row-major order.
+ * ------------------------------------------------------------------------- */
+static int64_t half_up(int64_t d) { return (d + 1) / 2; }  /* floor((d + 1) / 2) */
+
+int hi_oracle_reorder_index(const int64_t dims[3], int A, int64_t* I)
+{
+    const int L = ilog2_exact(A);
+    if (L < 1 || L > 6) return 1;
+    for (int d = 0; d < 3; ++d)
+        if (dims[d] < 1) return 1;
+    /* sub[l][d]: points per dim of the stride-2^l grid; sub[0] = dims, and
+       sub[l + 1] = f(l) of Eq. 3 */
+    int64_t sub[8][3];
+    for (int d = 0; d < 3; ++d) {
+        sub[0][d] = dims[d];
+        for (int l = 0; l < L; ++l) sub[l + 1][d] = half_up(sub[l][d]);
+    }
+    int64_t prefix[8];
+    for (int l = 0; l < L; ++l) prefix[l] = sub[l + 1][0] * sub[l + 1][1] * sub[l + 1][2];
+    prefix[L] = 0;
+    int64_t p = 0;
+    for (int64_t x = 0; x < dims[0]; ++x)
+        for (int64_t y = 0; y < dims[1]; ++y)
+            for (int64_t z = 0; z < dims[2]; ++z, ++p) {
+                int l = 0;
+                while (l < L) {
+                    const int64_t s = (int64_t)1 << (l + 1);
+                    if (x % s != 0 || y % s != 0 || z % s != 0) break;
+                    ++l;
+                }
+                const int64_t xs = x >> l, ys = y >> l, zs = z >> l;
+                const int64_t Dy = sub[l][1], Dz = sub[l][2];
+                int64_t rank = xs * Dy * Dz + ys * Dz + zs;
+                if (l < L) {
+                    rank -= half_up(xs) * half_up(Dy) * half_up(Dz);
+                    if (xs % 2 == 0) rank -= half_up(ys) * half_up(Dz);
+                    if (xs % 2 == 0 && ys % 2 == 0) rank -= half_up(zs);
+                }
+                I[p] = prefix[l] + rank;
+            }
+    return 0;
+}
