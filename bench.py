@@ -281,6 +281,29 @@ def run_gpu(args):
     kname = {"predict_quantize": "k_compress", "reconstruct": "k_decompress"}[dom]
     traffic = traffic_record(kname)
 
+    # quantization-code reordering (Sec. 5.2.2, Eq. 3) of this step's codes and back, each timed on
+    # its own (not part of the step: decompression reads the row-major codes); 2N bytes per direction
+    seq = torch.empty(N, dtype=torch.uint8, device=dev)
+    back = torch.empty(N, dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        hi.reorder_codes(b.codes, p, out=seq, stream=stream)
+        hi.unreorder_codes(seq, p, out=back, stream=stream)
+    rev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(10)]
+    for e in rev:
+        e[0].record(stream)
+        hi.reorder_codes(b.codes, p, out=seq, stream=stream)
+        e[1].record(stream)
+        hi.unreorder_codes(seq, p, out=back, stream=stream)
+        e[2].record(stream)
+    torch.cuda.synchronize()
+    assert torch.equal(back, b.codes)
+    f_ms = statistics.median(e[0].elapsed_time(e[1]) for e in rev)
+    i_ms = statistics.median(e[1].elapsed_time(e[2]) for e in rev)
+    reorder = dict(kernel="k_reorder", forward_ms=f_ms, inverse_ms=i_ms, alg_bytes=2 * N,
+                   forward_gbs=2 * N / (f_ms * 1e-3) / 1e9, inverse_gbs=2 * N / (i_ms * 1e-3) / 1e9,
+                   forward_frac=2 * N / (f_ms * 1e-3) / 1e9 / peak, inverse_frac=2 * N / (i_ms * 1e-3) / 1e9 / peak)
+    del seq, back
+
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     e2e = None
     if not args.no_e2e:
@@ -372,6 +395,7 @@ def run_gpu(args):
                          n_outliers=n_out, entropy_bits=est["entropy_bits"], cr_est=est["cr"],
                          bit_rate=est["bit_rate"],
                          levels=[(int(h.level[l].interp), list(h.level[l].order)) for l in range(h.n_levels)]),
+            reorder=reorder,
             e2e=e2e,
             gpu_launches=5 * args.steps,  # setup, range + auto-tune (one launch), predict-quantize, scatter, reconstruct
             cpu_baseline=cpu,

@@ -303,6 +303,30 @@ HI_API hi_status hi_batch_tune_launch(hi_batch_plan* h_plan, void* d_ws, uint32_
  * events = NULL to switch recording off.  No GPU work of its own. */
 HI_API hi_status hi_set_stage_events(void* const* events, uint32_t n);
 
+/* Quantization-code reordering (Sec. 5.2.2, Eq. 3).  The code of the point
+ * (x, y, z) of the field (x slowest) moves to position I(x, y, z) of a 1D
+ * sequence in which the codes of each interpolation level lie together:
+ * the anchors first (in row-major order of the anchor grid), then level
+ * log2(A) - 1, ..., level 0, row-major within a level.  The level of a
+ * point is the largest l <= log2 A with 2^l dividing all its coordinates.
+ * The paper writes the within-level rank for level 0 on the global grid;
+ * for coarser levels the library takes the same rank on the stride-2^l
+ * subgrid (the reading under which Eq. 3's prefix(l) counts the coarser
+ * points).  The codes are those of hi_compress; the reordering feeds a
+ * lossless coder and is not needed by hi_decompress, which reads the
+ * row-major array.
+ *   hi_reorder_codes:   d_seq[I(x, y, z)] = d_codes[x][y][z]
+ *   hi_unreorder_codes: d_codes[x][y][z] = d_seq[I(x, y, z)]
+ * p: the field's parameters (only dims and anchor_stride matter, but p
+ * must be valid for hi_compress).  d_codes and d_seq: n_points bytes each
+ * of device memory owned by the caller; they must not overlap.  Enqueued
+ * on stream, asynchronous, nothing allocated.  Returns HI_EINVAL for a
+ * NULL pointer, invalid parameters or overlapping buffers (nothing
+ * enqueued), HI_ECUDA if the launch fails. */
+HI_API hi_status hi_reorder_codes(const hi_params* p, const uint8_t* d_codes, uint8_t* d_seq, cudaStream_t stream);
+HI_API hi_status hi_unreorder_codes(const hi_params* p, const uint8_t* d_seq, uint8_t* d_codes,
+                                    cudaStream_t stream);
+
 /* Copy the device header to the host (synchronises the stream). */
 HI_API hi_status hi_header_read(const hi_header* d_header, hi_header* h_header, cudaStream_t stream);
 

@@ -742,6 +742,30 @@ hi_status hi_set_stage_events(void* const* events, uint32_t n)
     return HI_OK;
 }
 
+static hi_status reorder_call(const hi_params* p, const uint8_t* src, uint8_t* dst, bool inverse,
+                              cudaStream_t stream)
+{
+    Geometry G;
+    if (!p || !src || !dst) return HI_EINVAL;
+    hi_status s = make_geometry(p, &G);
+    if (s != HI_OK) return s;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(src), b = reinterpret_cast<uintptr_t>(dst);
+    const uintptr_t n = (uintptr_t)G.g.N;
+    if (a < b + n && b < a + n) return HI_EINVAL;  // overlapping buffers
+    const ReorderGeo R = make_reorder_geo(G.g.n, G.L);
+    return cuda_status(launch_reorder(R, src, dst, inverse, num_sms(), stream));
+}
+
+hi_status hi_reorder_codes(const hi_params* p, const uint8_t* d_codes, uint8_t* d_seq, cudaStream_t stream)
+{
+    return reorder_call(p, d_codes, d_seq, false, stream);
+}
+
+hi_status hi_unreorder_codes(const hi_params* p, const uint8_t* d_seq, uint8_t* d_codes, cudaStream_t stream)
+{
+    return reorder_call(p, d_seq, d_codes, true, stream);
+}
+
 hi_status hi_header_read(const hi_header* d_header, hi_header* h_header, cudaStream_t stream)
 {
     if (!d_header || !h_header) return HI_EINVAL;

@@ -191,4 +191,20 @@ cudaError_t launch_batch_range_tune(const BatchLaunch& b, cudaStream_t st);
 cudaError_t launch_batch_gather(const BatchLaunch& b, cudaStream_t st);
 cudaError_t launch_batch_compress(const BatchLaunch& b, cudaStream_t st);
 
+// Quantization-code reordering (Sec. 5.2.2, Eq. 3): per level l = 0..L, the
+// stride-2^l grid's points along d1 and d2 (D), their halves rounded up (H)
+// and the first sequence position of the level (prefix; the anchors, l = L,
+// start at 0).
+struct ReorderGeo {
+    uint32_t n0, n1, n2;
+    uint32_t segs;  // row segments per row
+    int L;
+    uint32_t D1[HI_MAX_LEVELS], D2[HI_MAX_LEVELS];
+    uint32_t H1[HI_MAX_LEVELS], H2[HI_MAX_LEVELS];
+    uint32_t prefix[HI_MAX_LEVELS];
+};
+ReorderGeo make_reorder_geo(const int64_t n[3], int L);
+cudaError_t launch_reorder(const ReorderGeo& G, const uint8_t* src, uint8_t* dst, bool inverse, int num_sms,
+                           cudaStream_t st);
+
 }  // namespace hi

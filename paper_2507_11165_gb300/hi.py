@@ -109,6 +109,8 @@ def lib():
             L.hi_autotune.argtypes = [ctypes.POINTER(HiParams), P, P, P, sz, P]
             L.hi_autotune_errors.argtypes = [ctypes.POINTER(HiParams), P, P, sz, P, P, P, P]
             L.hi_header_read.argtypes = [P, ctypes.POINTER(HiHeader), P]
+            L.hi_reorder_codes.argtypes = [ctypes.POINTER(HiParams), P, P, P]
+            L.hi_unreorder_codes.argtypes = [ctypes.POINTER(HiParams), P, P, P]
             L.hi_set_stage_events.argtypes = [P, ctypes.c_uint32]
             L.hi_status_str.argtypes = [ctypes.c_int]
             L.hi_status_str.restype = ctypes.c_char_p
@@ -283,6 +285,25 @@ def decompress_into(b: Buffers, out, status=None, stream=None, ws=None):
                              _ptr(b.out_idx), _ptr(b.out_val), b.out_cap, _ptr(out), _ptr(status), _ptr(w),
                              w.numel(), _stream(stream))
     _check(rc, "hi_decompress")
+
+
+def reorder_codes(codes, p, out=None, stream=None):
+    """hi_reorder_codes: the uint8 device code array of the field of ``p`` as
+    the level-grouped sequence of Sec. 5.2.2, Eq. 3 (a new 1D tensor unless
+    ``out`` is given; no sync)."""
+    if out is None:
+        out = torch.empty(codes.numel(), dtype=torch.uint8, device=codes.device)
+    _check(lib().hi_reorder_codes(ctypes.byref(p), _ptr(codes), _ptr(out), _stream(stream)), "hi_reorder_codes")
+    return out
+
+
+def unreorder_codes(seq, p, out=None, stream=None):
+    """hi_unreorder_codes: the row-major code array back from its sequence
+    (a new 1D tensor unless ``out`` is given; no sync)."""
+    if out is None:
+        out = torch.empty(seq.numel(), dtype=torch.uint8, device=seq.device)
+    _check(lib().hi_unreorder_codes(ctypes.byref(p), _ptr(seq), _ptr(out), _stream(stream)), "hi_unreorder_codes")
+    return out
 
 
 def autotune_errors(b: Buffers, stream=None):
