@@ -299,7 +299,11 @@ def run_gpu(args):
     assert torch.equal(back, b.codes)
     f_ms = statistics.median(e[0].elapsed_time(e[1]) for e in rev)
     i_ms = statistics.median(e[1].elapsed_time(e[2]) for e in rev)
-    reorder = dict(kernel="k_reorder", forward_ms=f_ms, inverse_ms=i_ms, alg_bytes=2 * N,
+    rows_path = SHAPE[-1] % 16 == 0 and SHAPE[-1] <= 4096  # staged rows (buffers from torch: aligned)
+    reorder = dict(kernel="k_reorder_rows" if rows_path else "k_reorder", forward_ms=f_ms, inverse_ms=i_ms,
+                   alg_bytes=2 * N,
+                   traffic_fwd=traffic_record("k_reorder_rows_fwd") if rows_path else None,
+                   traffic_inv=traffic_record("k_reorder_rows_inv") if rows_path else None,
                    forward_gbs=2 * N / (f_ms * 1e-3) / 1e9, inverse_gbs=2 * N / (i_ms * 1e-3) / 1e9,
                    forward_frac=2 * N / (f_ms * 1e-3) / 1e9 / peak, inverse_frac=2 * N / (i_ms * 1e-3) / 1e9 / peak)
     del seq, back

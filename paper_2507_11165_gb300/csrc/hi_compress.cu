@@ -81,8 +81,6 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
             if (nx < g.ntiles) s_ti[(it + 1) & 1] = tile_info<A>(g, nx);
             if (use_tma && dbuf && nx < g.ntiles)
                 tma_issue(buf ? vbuf0 : vbuf1, &tmap, g, nx, A, &s_mbar[buf ^ 1], tma_bytes);
-            // one buffer: the next tile waits in L2 until this one is done
-            if (use_tma && !dbuf && nx < g.ntiles) tma_l2_prefetch(&tmap, g, nx, A);
         }
         if (tid < 8) {  // anchors keep the zero-error code
             const int a0 = (tid >> 2) & 1, a1 = (tid >> 1) & 1, a2 = tid & 1;

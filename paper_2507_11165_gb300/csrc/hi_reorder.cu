@@ -76,6 +76,126 @@ __global__ void __launch_bounds__(256) k_reorder(const uint8_t* __restrict__ src
     }
 }
 
+// ---------------------------------------------------------------------------
+// Rows of 16-byte multiples (both buffers 16-byte aligned): a warp stages a
+// row of the row-major side in shared memory and moves it run by run.  The
+// points of row (x, y) fall into at most L + 1 runs of consecutive sequence
+// positions: on the stride-2^l subgrid (row coordinates xs = x >> l,
+// ys = y >> l, points zs in [0, D2[l])), if xs or ys is odd every point of
+// the row is on level l, in order; if both are even the odd zs are on level
+// l, in order, and the even zs go on to level l + 1; at l = L every point is
+// an anchor.  Run j-th position B + j holds row element z = zb + zst * j.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kRowMax = 4096;  // longest row the staged path takes (bytes)
+constexpr int kRowWarps = 8;
+
+struct Run {
+    uint32_t B, cnt, zb, zst;
+};
+
+// The runs of row (x, y), in level order; returns how many (<= L + 1).
+__device__ __forceinline__ int row_runs(const ReorderGeo& G, uint32_t x, uint32_t y, Run* r)
+{
+    int n = 0;
+    for (int l = 0;; ++l) {
+        const uint32_t xs = x >> l, ys = y >> l;
+        const uint32_t row_rank = (xs * G.D1[l] + ys) * G.D2[l];
+        if (l == G.L) {
+            r[n++] = Run{G.prefix[l] + row_rank, G.D2[l], 0u, 1u << l};
+            return n;
+        }
+        uint32_t before = half_up(xs) * G.H1[l] * G.H2[l];
+        if ((xs & 1u) == 0) before += half_up(ys) * G.H2[l];
+        if ((xs | ys) & 1u) {
+            r[n++] = Run{G.prefix[l] + row_rank - before, G.D2[l], 0u, 1u << l};
+            return n;
+        }
+        if (G.D2[l] >= 2) r[n++] = Run{G.prefix[l] + row_rank - before, G.D2[l] / 2, 1u << l, 2u << l};
+    }
+}
+
+// seq[B + j] = row[zb + zst j] for a run: aligned 4-byte words, single bytes
+// at the run's ends.  sw: the staged row as words (one word of padding).
+__device__ __forceinline__ void run_store(const uint32_t* sw, const uint8_t* sb, uint8_t* __restrict__ seq,
+                                          const Run& R, uint32_t lane)
+{
+    const uint32_t head = min((4u - (R.B & 3u)) & 3u, R.cnt);
+    const uint32_t nw = (R.cnt - head) >> 2;
+    const uint32_t tail0 = head + 4 * nw;
+    if (lane < head) seq[R.B + lane] = sb[R.zb + R.zst * lane];
+    if (lane < R.cnt - tail0) seq[R.B + tail0 + lane] = sb[R.zb + R.zst * (tail0 + lane)];
+    uint32_t* dst = reinterpret_cast<uint32_t*>(seq + R.B + head);
+    if (R.zst == 1) {
+        for (uint32_t m = lane; m < nw; m += 32) {
+            const uint32_t z = R.zb + head + 4 * m;
+            dst[m] = __funnelshift_r(sw[z >> 2], sw[(z >> 2) + 1], 8 * (z & 3u));
+        }
+    } else {
+        for (uint32_t m = lane; m < nw; m += 32) {
+            const uint32_t z = R.zb + R.zst * (head + 4 * m);
+            dst[m] = (uint32_t)sb[z] | ((uint32_t)sb[z + R.zst] << 8) | ((uint32_t)sb[z + 2 * R.zst] << 16) |
+                     ((uint32_t)sb[z + 3 * R.zst] << 24);
+        }
+    }
+}
+
+// row[zb + zst j] = seq[B + j] for a run, into the staged row.
+__device__ __forceinline__ void run_load(uint8_t* sb, const uint8_t* __restrict__ seq, const Run& R, uint32_t lane)
+{
+    if (R.zst == 1 && R.zb == 0 && (R.cnt & 3u) == 0) {
+        // whole words of the row: each from the two aligned sequence words it straddles
+        const uint32_t* sq = reinterpret_cast<const uint32_t*>(seq) + (R.B >> 2);
+        const uint32_t sh = 8 * (R.B & 3u);
+        uint32_t* sw = reinterpret_cast<uint32_t*>(sb);
+        for (uint32_t k = lane; k < (R.cnt >> 2); k += 32) {
+            const uint32_t w0 = __ldg(sq + k);
+            sw[k] = sh ? __funnelshift_r(w0, __ldg(sq + k + 1), sh) : w0;
+        }
+        return;
+    }
+    const uint32_t a0 = R.B & ~3u;  // aligned words covering [B, B + cnt)
+    const uint32_t nw = (R.B + R.cnt - a0 + 3) >> 2;
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(seq + a0);
+    for (uint32_t m = lane; m < nw; m += 32) {
+        const uint32_t w = __ldg(src + m);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const uint32_t j = a0 + 4 * m + t - R.B;  // wraps for bytes before B
+            if (j < R.cnt) sb[R.zb + R.zst * j] = (uint8_t)(w >> (8 * t));
+        }
+    }
+}
+
+template <bool INV>
+__global__ void __launch_bounds__(kRowWarps * 32) k_reorder_rows(const uint8_t* __restrict__ src,
+                                                                uint8_t* __restrict__ dst, const ReorderGeo G)
+{
+    extern __shared__ __align__(16) unsigned char rsm[];
+    const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+    const uint32_t pitch = G.n2 + 16;  // one word of padding for the funnel shift, 16-byte rows
+    uint8_t* sb = rsm + wib * pitch;
+    const uint32_t* sw = reinterpret_cast<const uint32_t*>(sb);
+    const uint32_t rows = G.n0 * G.n1;
+    const uint32_t nv = G.n2 >> 4;
+    for (uint32_t row = blockIdx.x * kRowWarps + wib; row < rows; row += gridDim.x * kRowWarps) {
+        const uint32_t x = row / G.n1, y = row - x * G.n1;
+        Run R[HI_MAX_LEVELS];
+        const int nr = row_runs(G, x, y, R);
+        if constexpr (!INV) {
+            const uint4* s16 = reinterpret_cast<const uint4*>(src + (size_t)row * G.n2);
+            for (uint32_t c = lane; c < nv; c += 32) reinterpret_cast<uint4*>(sb)[c] = __ldg(s16 + c);
+            __syncwarp();
+            for (int k = 0; k < nr; ++k) run_store(sw, sb, dst, R[k], lane);
+        } else {
+            for (int k = 0; k < nr; ++k) run_load(sb, src, R[k], lane);
+            __syncwarp();
+            uint4* d16 = reinterpret_cast<uint4*>(dst + (size_t)row * G.n2);
+            for (uint32_t c = lane; c < nv; c += 32) d16[c] = reinterpret_cast<const uint4*>(sb)[c];
+        }
+        __syncwarp();  // the staged row is reused by the next row
+    }
+}
+
 ReorderGeo make_reorder_geo(const int64_t n[3], int L)
 {
     ReorderGeo G{};
@@ -96,6 +216,20 @@ ReorderGeo make_reorder_geo(const int64_t n[3], int L)
 cudaError_t launch_reorder(const ReorderGeo& G, const uint8_t* src, uint8_t* dst, bool inverse, int num_sms,
                            cudaStream_t st)
 {
+    const bool rows_ok = G.n2 % 16 == 0 && G.n2 <= kRowMax && (reinterpret_cast<uintptr_t>(src) & 15) == 0 &&
+                         (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
+    if (rows_ok) {
+        const uint32_t rows = G.n0 * G.n1;
+        const size_t smem = (size_t)kRowWarps * (G.n2 + 16);
+        const uint32_t want = (rows + kRowWarps - 1) / kRowWarps;
+        const uint32_t cap = (uint32_t)num_sms * 8;
+        const int grid = (int)(want < cap ? want : cap);
+        if (inverse)
+            k_reorder_rows<true><<<grid, kRowWarps * 32, smem, st>>>(src, dst, G);
+        else
+            k_reorder_rows<false><<<grid, kRowWarps * 32, smem, st>>>(src, dst, G);
+        return cudaGetLastError();
+    }
     const uint64_t items = (uint64_t)G.n0 * G.n1 * G.segs;
     const uint64_t want = (items + 7) / 8;  // 8 warps per block
     const int grid = (int)(want < (uint64_t)num_sms * 8 ? (want ? want : 1) : (uint64_t)num_sms * 8);

@@ -17,7 +17,10 @@ pytestmark = pytest.mark.gpu
 
 CASES = [((9, 9, 9), 8), ((10, 7, 13), 8), ((17, 17, 17), 16), ((33, 20, 5), 16), ((12, 30), 4),
          ((21,), 4), ((5, 1, 19), 8), ((2, 3, 4), 2), ((1, 1, 1), 8), ((40,), 32), ((70, 45, 1100), 16),
-         ((3, 2500), 8), ((5000,), 2), ((65, 64, 63), 32), ((1, 1, 3000), 16)]
+         ((3, 2500), 8), ((5000,), 2), ((65, 64, 63), 32), ((1, 1, 3000), 16),
+         # rows of 16-byte multiples (at most 4096): the staged-row path
+         ((9, 9, 16), 8), ((33, 20, 48), 16), ((12, 64), 4), ((5, 7, 4096), 32), ((2, 3, 16), 2),
+         ((1, 1, 16), 16), ((3, 5, 32), 2), ((16,), 16), ((40, 1, 160), 8), ((31, 17, 4080), 16)]
 
 
 @pytest.fixture(scope="module")
@@ -44,6 +47,24 @@ def test_reorder_matches_oracle(hi, oracle_mod, shape, A):
     # the inverse alone, from the oracle's sequence
     back2 = hi.unreorder_codes(torch.from_numpy(ref).cuda(), p)
     assert np.array_equal(back2.cpu().numpy().reshape(shape), oracle_mod.unreorder_codes(ref, shape, A))
+
+
+@pytest.mark.parametrize("shape,A", [((9, 9, 16), 8), ((33, 20, 48), 16), ((10, 7, 13), 8)])
+def test_reorder_unaligned_buffers(hi, oracle_mod, shape, A):
+    """Buffers off a 16-byte boundary take the general path: same sequence."""
+    rng = np.random.default_rng(7)
+    c = rng.integers(0, 256, size=shape, dtype=np.uint8)
+    n = c.size
+    p = hi.make_params(shape, 1e-3, "rel", A, autotune=False)
+    src = torch.zeros(n + 8, dtype=torch.uint8, device="cuda")
+    dst = torch.zeros(n + 8, dtype=torch.uint8, device="cuda")
+    src[3:3 + n] = torch.from_numpy(c.reshape(-1)).cuda()
+    hi.reorder_codes(src[3:3 + n], p, out=dst[5:5 + n])
+    back = torch.zeros(n + 8, dtype=torch.uint8, device="cuda")
+    hi.unreorder_codes(dst[5:5 + n], p, out=back[1:1 + n])
+    torch.cuda.synchronize()
+    assert np.array_equal(dst[5:5 + n].cpu().numpy(), oracle_mod.reorder_codes(c, A))
+    assert np.array_equal(back[1:1 + n].cpu().numpy().reshape(shape), c)
 
 
 def test_reorder_of_compressed_codes(hi, oracle_mod):
