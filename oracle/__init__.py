@@ -46,7 +46,7 @@ _lib = None
 ERRORS = {
     1: "invalid argument", 2: "out of memory", 10: "stencil point read before it was known",
     11: "point predicted twice", 12: "point never predicted", 13: "blocks disagree on a shared face",
-    14: "code 0 without an outlier value",
+    14: "code 0 without an outlier value", 15: "corrupt lossless stream",
 }
 
 
@@ -86,6 +86,10 @@ def _load():
             lib.hi_oracle_tune_select.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, P]
             lib.hi_oracle_trace.argtypes = [P, ctypes.c_int, P, P, P, P, P]
             lib.hi_oracle_reorder_index.argtypes = [P, ctypes.c_int, P]
+            lib.hi_oracle_tp_bound.argtypes = [i64]
+            lib.hi_oracle_tp_bound.restype = i64
+            lib.hi_oracle_tp_encode.argtypes = [P, i64, P, i64, P]
+            lib.hi_oracle_tp_decode.argtypes = [P, i64, P, i64]
             _lib = lib
     return _lib
 
@@ -321,4 +325,34 @@ def unreorder_codes(seq, shape, A):
     """Inverse of reorder_codes: the code array of ``shape`` from its sequence."""
     idx = reorder_index(shape, A)
     return np.asarray(seq).reshape(-1)[idx].reshape(tuple(int(s) for s in shape))
+
+
+# ---------------------------------------------------------------------------
+# Throughput-mode lossless pipeline TCMS1-BIT1-RRE1 (Sec. 5.2.3)
+# ---------------------------------------------------------------------------
+TP_CHUNK = 16384
+
+
+def tp_bound(n):
+    """Largest stream tp_encode can produce for n input bytes."""
+    return int(_load().hi_oracle_tp_bound(int(n)))
+
+
+def tp_encode(data):
+    """The TCMS1-BIT1-RRE1 stream (uint8 array) of a byte sequence."""
+    lib = _load()
+    data = np.ascontiguousarray(data, dtype=np.uint8).reshape(-1)
+    out = np.zeros(tp_bound(data.size), dtype=np.uint8)
+    ln = np.zeros(1, dtype=np.int64)
+    _check(lib.hi_oracle_tp_encode(_p(data), data.size, _p(out), out.size, _p(ln)))
+    return out[: int(ln[0])].copy()
+
+
+def tp_decode(stream, n):
+    """The n bytes a TCMS1-BIT1-RRE1 stream encodes."""
+    lib = _load()
+    stream = np.ascontiguousarray(stream, dtype=np.uint8).reshape(-1)
+    out = np.zeros(int(n), dtype=np.uint8)
+    _check(lib.hi_oracle_tp_decode(_p(stream), stream.size, _p(out), int(n)))
+    return out
 

@@ -1179,3 +1179,196 @@ int hi_oracle_reorder_index(const int64_t dims[3], int A, int64_t* I)
             }
     return 0;
 }
+
+/* ---------------------------------------------------------------------------
+ * Throughput-mode lossless pipeline TCMS1-BIT1-RRE1 (Sec. 5.2.3) over a byte
+ * sequence (the reordered codes).  The paper names the stages and what each
+ * does; chunking, bit-plane order, recursion depth and the container are
+ * not given, so this format is a reading:
+ *
+ *   stream   = u64 n | u32 chunk (16384) | u32 nchunks | u32 size[nchunks]
+ *              | zero padding to 16 bytes | payloads, each padded to 16
+ *   size[k]  = padded payload bytes; bit 31 set: the chunk is stored raw
+ *   chunk k  = bytes [16384 k, min(16384 (k + 1), n)), m of them
+ *   TCMS1    t = (b << 1) ^ (b >> 7) on the byte read as a signed int8
+ *              (two's complement -> magnitude-sign; code 128 -> 0xff)
+ *   BIT1     t zero-padded to m' = m rounded up to 64; plane p = 0..7 holds
+ *              bit 7 - p of every element: byte j of a plane has element
+ *              8 j + b at bit b; planes in order, m' / 8 bytes each
+ *   RRE1     over a byte string v of length L: bitmap bit i = (v[i] !=
+ *              v[i - 1]) with v[-1] = 0, byte j of the bitmap holding bits
+ *              8 j .. 8 j + 7 (LSB first), ceil(L / 8) bytes; kept = the
+ *              bytes whose bit is set, in order.  Levels: v_0 = the shuffled
+ *              chunk, v_{r+1} = bitmap of v_r, until a level has L_R <= 64
+ *              bytes, which is stored as is.
+ *   payload  = v_R | kept_{R-1} | ... | kept_0 (decodable front to back);
+ *              if that is longer than m the chunk is stored raw (m bytes).
+ * ------------------------------------------------------------------------- */
+#define TP_CHUNK 16384
+#define TP_RAW 0x80000000u
+
+static uint8_t tcms1(uint8_t b) { return (uint8_t)((b << 1) ^ ((b & 0x80) ? 0xff : 0x00)); }
+static uint8_t tcms1_inv(uint8_t t) { return (uint8_t)((t >> 1) ^ ((t & 1) ? 0xff : 0x00)); }
+
+/* RRE of v[0..L): bitmap into bm (ceil(L/8) bytes), kept bytes into kept; returns their count */
+static int64_t rre_level(const uint8_t* v, int64_t L, uint8_t* bm, uint8_t* kept)
+{
+    int64_t nk = 0;
+    memset(bm, 0, (size_t)((L + 7) / 8));
+    for (int64_t i = 0; i < L; ++i) {
+        const uint8_t prev = i ? v[i - 1] : 0;
+        if (v[i] != prev) {
+            bm[i / 8] |= (uint8_t)(1u << (i % 8));
+            kept[nk++] = v[i];
+        }
+    }
+    return nk;
+}
+
+static int64_t tp_chunk_encode(const uint8_t* s, int64_t m, uint8_t* out /* >= m + 64 */, int* raw)
+{
+    const int64_t mp = (m + 63) / 64 * 64;
+    uint8_t* t = calloc((size_t)mp, 1);
+    uint8_t* u = calloc((size_t)mp, 1);
+    /* levels */
+    uint8_t* lv[8];
+    uint8_t* kept[8];
+    int64_t L[8], nk[8];
+    if (!t || !u) { free(t); free(u); return -1; }
+    for (int64_t i = 0; i < m; ++i) t[i] = tcms1(s[i]);
+    const int64_t pl = mp / 8;
+    for (int p = 0; p < 8; ++p)
+        for (int64_t e = 0; e < mp; ++e)
+            if ((t[e] >> (7 - p)) & 1) u[p * pl + e / 8] |= (uint8_t)(1u << (e % 8));
+    lv[0] = u;
+    L[0] = mp;
+    int R = 0;
+    while (L[R] > 64) {
+        lv[R + 1] = malloc((size_t)((L[R] + 7) / 8));
+        kept[R] = malloc((size_t)L[R]);
+        L[R + 1] = (L[R] + 7) / 8;
+        nk[R] = rre_level(lv[R], L[R], lv[R + 1], kept[R]);
+        ++R;
+    }
+    int64_t total = L[R];
+    for (int r = 0; r < R; ++r) total += nk[r];
+    int64_t len;
+    if (total > m) {
+        memcpy(out, s, (size_t)m);
+        len = m;
+        *raw = 1;
+    } else {
+        int64_t o = 0;
+        memcpy(out + o, lv[R], (size_t)L[R]);
+        o += L[R];
+        for (int r = R - 1; r >= 0; --r) {
+            memcpy(out + o, kept[r], (size_t)nk[r]);
+            o += nk[r];
+        }
+        len = o;
+        *raw = 0;
+    }
+    for (int r = 0; r < R; ++r) { free(lv[r + 1]); free(kept[r]); }
+    free(t);
+    free(u);
+    return len;
+}
+
+static int64_t tp_header_bytes(int64_t nchunks) { return (16 + 4 * nchunks + 15) / 16 * 16; }
+
+/* Upper bound of the stream size for n input bytes. */
+int64_t hi_oracle_tp_bound(int64_t n)
+{
+    const int64_t nc = (n + TP_CHUNK - 1) / TP_CHUNK;
+    return tp_header_bytes(nc) + nc * 16 + n + 15;
+}
+
+int hi_oracle_tp_encode(const uint8_t* in, int64_t n, uint8_t* out, int64_t cap, int64_t* out_len)
+{
+    if (n < 0 || (n && !in) || !out || !out_len) return 1;
+    const int64_t nc = (n + TP_CHUNK - 1) / TP_CHUNK;
+    if (cap < hi_oracle_tp_bound(n)) return 1;
+    memset(out, 0, (size_t)tp_header_bytes(nc));
+    memcpy(out, &n, 8);
+    const uint32_t ch = TP_CHUNK, nc32 = (uint32_t)nc;
+    memcpy(out + 8, &ch, 4);
+    memcpy(out + 12, &nc32, 4);
+    int64_t o = tp_header_bytes(nc);
+    uint8_t* buf = malloc(TP_CHUNK + 64);
+    if (!buf) return 2;
+    for (int64_t k = 0; k < nc; ++k) {
+        const int64_t m = (k + 1) * TP_CHUNK <= n ? TP_CHUNK : n - k * TP_CHUNK;
+        int raw = 0;
+        const int64_t len = tp_chunk_encode(in + k * TP_CHUNK, m, buf, &raw);
+        if (len < 0) { free(buf); return 2; }
+        const int64_t pad = (len + 15) / 16 * 16;
+        memcpy(out + o, buf, (size_t)len);
+        memset(out + o + len, 0, (size_t)(pad - len));
+        const uint32_t sz = (uint32_t)pad | (raw ? TP_RAW : 0u);
+        memcpy(out + 16 + 4 * k, &sz, 4);
+        o += pad;
+    }
+    free(buf);
+    *out_len = o;
+    return 0;
+}
+
+int hi_oracle_tp_decode(const uint8_t* in, int64_t len, uint8_t* out, int64_t n)
+{
+    if (len < 16 || !in || (n && !out)) return 1;
+    int64_t n_s;
+    uint32_t ch, nc;
+    memcpy(&n_s, in, 8);
+    memcpy(&ch, in + 8, 4);
+    memcpy(&nc, in + 12, 4);
+    if (n_s != n || ch != TP_CHUNK || (int64_t)nc != (n + TP_CHUNK - 1) / TP_CHUNK) return 15;
+    int64_t o = tp_header_bytes(nc);
+    if (o > len) return 15;
+    uint8_t* lv[9];
+    for (int r = 0; r < 9; ++r) lv[r] = malloc(TP_CHUNK + 64);
+    int rc = 0;
+    for (int64_t k = 0; k < (int64_t)nc && rc == 0; ++k) {
+        uint32_t sz;
+        memcpy(&sz, in + 16 + 4 * k, 4);
+        const int64_t pad = sz & ~TP_RAW;
+        const int64_t m = (k + 1) * TP_CHUNK <= n ? TP_CHUNK : n - k * TP_CHUNK;
+        if (o + pad > len) { rc = 15; break; }
+        const uint8_t* p = in + o;
+        if (sz & TP_RAW) {
+            if (pad < m) { rc = 15; break; }
+            memcpy(out + k * TP_CHUNK, p, (size_t)m);
+        } else {
+            const int64_t mp = (m + 63) / 64 * 64;
+            int64_t L[9];
+            L[0] = mp;
+            int R = 0;
+            while (L[R] > 64) { L[R + 1] = (L[R] + 7) / 8; ++R; }
+            int64_t q = 0;
+            if (L[R] > pad) { rc = 15; break; }
+            memcpy(lv[R], p, (size_t)L[R]);
+            q = L[R];
+            for (int r = R - 1; r >= 0 && rc == 0; --r) {
+                /* v_r from its bitmap v_{r+1} and the kept bytes */
+                uint8_t prev = 0;
+                for (int64_t i = 0; i < L[r]; ++i) {
+                    if ((lv[r + 1][i / 8] >> (i % 8)) & 1) {
+                        if (q >= pad) { rc = 15; break; }
+                        prev = p[q++];
+                    }
+                    lv[r][i] = prev;
+                }
+            }
+            if (rc) break;
+            const int64_t pl = mp / 8;
+            for (int64_t e = 0; e < m; ++e) {
+                uint8_t t = 0;
+                for (int pp = 0; pp < 8; ++pp)
+                    t |= (uint8_t)(((lv[0][pp * pl + e / 8] >> (e % 8)) & 1) << (7 - pp));
+                out[k * TP_CHUNK + e] = tcms1_inv(t);
+            }
+        }
+        o += pad;
+    }
+    for (int r = 0; r < 9; ++r) free(lv[r]);
+    return rc;
+}
