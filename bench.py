@@ -306,7 +306,35 @@ def run_gpu(args):
                    traffic_inv=traffic_record("k_reorder_rows_inv") if rows_path else None,
                    forward_gbs=2 * N / (f_ms * 1e-3) / 1e9, inverse_gbs=2 * N / (i_ms * 1e-3) / 1e9,
                    forward_frac=2 * N / (f_ms * 1e-3) / 1e9 / peak, inverse_frac=2 * N / (i_ms * 1e-3) / 1e9 / peak)
-    del seq, back
+    # throughput-mode lossless pipeline TCMS1-BIT1-RRE1 (Sec. 5.2.3) on the reordered codes: a real
+    # compressed size beside the entropy estimate; timed on its own, not part of the step
+    hi.reorder_codes(b.codes, p, out=seq, stream=stream)
+    codec = hi.TpCodec(N, dev)
+    for _ in range(2):
+        codec.encode_into(seq, stream=stream)
+        torch.cuda.synchronize()
+        s_len = int(codec.len.item())
+        codec.decode_into(codec.stream_buf, s_len, back, stream=stream)
+    tev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(5)]
+    for e in tev:
+        e[0].record(stream)
+        codec.encode_into(seq, stream=stream)
+        e[1].record(stream)
+        codec.decode_into(codec.stream_buf, s_len, back, stream=stream)
+        e[2].record(stream)
+    torch.cuda.synchronize()
+    assert int(codec.status.item()) == 0 and torch.equal(back, seq) and int(codec.len.item()) == s_len
+    te_ms = statistics.median(e[0].elapsed_time(e[1]) for e in tev)
+    td_ms = statistics.median(e[1].elapsed_time(e[2]) for e in tev)
+    n_out_tp = int(hi.read_header(b.header).n_outliers)
+    rec_bytes = s_len + 8 * n_out_tp + 4 * int(b.anchors.numel()) + hi.HEADER_BYTES
+    lossless_tp = dict(pipeline="TCMS1-BIT1-RRE1", kernels=["k_tp_encode_chunks", "k_tp_scan", "k_tp_gather",
+                                                            "k_tp_decode_chunks"],
+                       encode_ms=te_ms, decode_ms=td_ms, encode_gbs_of_codes=N / (te_ms * 1e-3) / 1e9,
+                       decode_gbs_of_codes=N / (td_ms * 1e-3) / 1e9, stream_bytes=s_len,
+                       codes_ratio=N / s_len, record_bytes=rec_bytes, cr=4.0 * N / rec_bytes,
+                       launches_encode=3, launches_decode=2)
+    del seq, back, codec
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -400,6 +428,7 @@ def run_gpu(args):
                          bit_rate=est["bit_rate"],
                          levels=[(int(h.level[l].interp), list(h.level[l].order)) for l in range(h.n_levels)]),
             reorder=reorder,
+            lossless_tp=lossless_tp,
             e2e=e2e,
             gpu_launches=5 * args.steps,  # setup, range + auto-tune (one launch), predict-quantize, scatter, reconstruct
             cpu_baseline=cpu,

@@ -327,6 +327,42 @@ HI_API hi_status hi_reorder_codes(const hi_params* p, const uint8_t* d_codes, ui
 HI_API hi_status hi_unreorder_codes(const hi_params* p, const uint8_t* d_seq, uint8_t* d_codes,
                                     cudaStream_t stream);
 
+/* Throughput-mode lossless pipeline TCMS1-BIT1-RRE1 (Sec. 5.2.3): a byte
+ * sequence (normally the output of hi_reorder_codes) into a self-describing
+ * stream, and back.  Stages, per 16 KiB chunk: TCMS1 maps each byte, read as
+ * a signed int8, to magnitude-sign form ((b << 1) ^ (b >> 7); the zero
+ * residual 128 becomes 0xff); BIT1 transposes the chunk into 8 bit planes
+ * (most significant first, zero-padded to a multiple of 64 elements); RRE1
+ * keeps the bytes that differ from their predecessor plus a bitmap of them,
+ * and compresses the bitmap the same way until it is at most 64 bytes.  The
+ * paper names the stages only; the chunking, plane order, recursion depth
+ * and container are this library's reading:
+ *   stream = u64 n | u32 16384 | u32 nchunks | u32 size[nchunks] | zero
+ *            padding to 16 bytes | payloads, each padded to 16 bytes;
+ *   size[k] = padded payload bytes, bit 31 set when chunk k is stored raw
+ *            (its encoding would not be shorter);
+ *   payload = the top bitmap level, then the kept bytes of each level below
+ *            it, top down.
+ * hi_tp_query: *max_stream_bytes = the largest stream for n input bytes;
+ *   *ws_bytes = the workspace both calls need (either pointer may be NULL).
+ * hi_tp_encode: d_in (n bytes) -> d_out (16-byte aligned, out_cap >=
+ *   max_stream_bytes, not overlapping d_in); the stream length is written to
+ *   *d_len (device uint64).  d_ws: ws_bytes >= hi_tp_query's, 16-byte
+ *   aligned.  Three launches on stream, no sync.
+ * hi_tp_decode: d_in (a stream of in_len bytes, 16-byte aligned) -> d_out
+ *   (n bytes, the length the stream was made from).  A stream that does not
+ *   match n or whose table or payloads are inconsistent sets HI_ECORRUPT in
+ *   *d_status (may be NULL) and leaves the affected chunks unwritten.  Two
+ *   launches on stream, no sync.
+ * All three return HI_EINVAL for NULL or misaligned pointers, short
+ * buffers, a too-small workspace or n >= 2^44 (nothing enqueued), HI_ECUDA
+ * if a launch fails. */
+HI_API hi_status hi_tp_query(uint64_t n, uint64_t* max_stream_bytes, size_t* ws_bytes);
+HI_API hi_status hi_tp_encode(const uint8_t* d_in, uint64_t n, uint8_t* d_out, uint64_t out_cap, uint64_t* d_len,
+                              void* d_ws, size_t ws_bytes, cudaStream_t stream);
+HI_API hi_status hi_tp_decode(const uint8_t* d_in, uint64_t in_len, uint8_t* d_out, uint64_t n, uint32_t* d_status,
+                              void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
 /* Copy the device header to the host (synchronises the stream). */
 HI_API hi_status hi_header_read(const hi_header* d_header, hi_header* h_header, cudaStream_t stream);
 

@@ -207,4 +207,12 @@ ReorderGeo make_reorder_geo(const int64_t n[3], int L);
 cudaError_t launch_reorder(const ReorderGeo& G, const uint8_t* src, uint8_t* dst, bool inverse, int num_sms,
                            cudaStream_t st);
 
+// Throughput-mode lossless pipeline TCMS1-BIT1-RRE1 (Sec. 5.2.3).
+size_t tp_ws_bytes(uint64_t n);
+uint64_t tp_stream_bound(uint64_t n);
+cudaError_t launch_tp_encode(const uint8_t* in, uint64_t n, uint8_t* out, uint64_t* len, void* ws, int num_sms,
+                             cudaStream_t st);
+cudaError_t launch_tp_decode(const uint8_t* in, uint64_t in_len, uint64_t n, uint8_t* out, uint32_t* status, void* ws,
+                             int num_sms, cudaStream_t st);
+
 }  // namespace hi

@@ -110,6 +110,9 @@ def lib():
             L.hi_autotune_errors.argtypes = [ctypes.POINTER(HiParams), P, P, sz, P, P, P, P]
             L.hi_header_read.argtypes = [P, ctypes.POINTER(HiHeader), P]
             L.hi_reorder_codes.argtypes = [ctypes.POINTER(HiParams), P, P, P]
+            L.hi_tp_query.argtypes = [u64, ctypes.POINTER(u64), ctypes.POINTER(sz)]
+            L.hi_tp_encode.argtypes = [P, u64, P, u64, P, P, sz, P]
+            L.hi_tp_decode.argtypes = [P, u64, P, u64, P, P, sz, P]
             L.hi_unreorder_codes.argtypes = [ctypes.POINTER(HiParams), P, P, P]
             L.hi_set_stage_events.argtypes = [P, ctypes.c_uint32]
             L.hi_status_str.argtypes = [ctypes.c_int]
@@ -304,6 +307,35 @@ def unreorder_codes(seq, p, out=None, stream=None):
         out = torch.empty(seq.numel(), dtype=torch.uint8, device=seq.device)
     _check(lib().hi_unreorder_codes(ctypes.byref(p), _ptr(seq), _ptr(out), _stream(stream)), "hi_unreorder_codes")
     return out
+
+
+def tp_query(n):
+    """(largest stream bytes, workspace bytes) of the TCMS1-BIT1-RRE1 pipeline for n input bytes."""
+    mx, ws = ctypes.c_uint64(), ctypes.c_size_t()
+    _check(lib().hi_tp_query(int(n), ctypes.byref(mx), ctypes.byref(ws)), "hi_tp_query")
+    return mx.value, ws.value
+
+
+class TpCodec:
+    """Device buffers for hi_tp_encode / hi_tp_decode of n-byte sequences."""
+
+    def __init__(self, n, device):
+        self.n = int(n)
+        mx, ws = tp_query(self.n)
+        self.stream_buf = torch.empty(mx, dtype=torch.uint8, device=device)
+        self.ws = torch.empty(max(ws, 16), dtype=torch.uint8, device=device)
+        self.len = torch.zeros(1, dtype=torch.int64, device=device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+
+    def encode_into(self, data, stream=None):
+        """Enqueue the encoding of ``data`` (n bytes, device) into ``stream_buf``; length in ``self.len``."""
+        _check(lib().hi_tp_encode(_ptr(data), self.n, _ptr(self.stream_buf), self.stream_buf.numel(),
+                                  _ptr(self.len), _ptr(self.ws), self.ws.numel(), _stream(stream)), "hi_tp_encode")
+
+    def decode_into(self, stream_bytes, in_len, out, stream=None):
+        """Enqueue the decoding of a stream of ``in_len`` bytes into ``out`` (n bytes); status in ``self.status``."""
+        _check(lib().hi_tp_decode(_ptr(stream_bytes), int(in_len), _ptr(out), self.n, _ptr(self.status),
+                                  _ptr(self.ws), self.ws.numel(), _stream(stream)), "hi_tp_decode")
 
 
 def autotune_errors(b: Buffers, stream=None):
