@@ -64,113 +64,97 @@ __host__ __device__ constexpr uint32_t tp_level_off(int r)
 constexpr uint32_t kTpLevelBytes = tp_level_off(kTpMaxLevels);
 static_assert(kTpLevelBytes < 20 * 1024, "level buffers");
 
-__device__ __forceinline__ uint8_t tcms1(uint32_t b) { return (uint8_t)((b << 1) ^ ((b & 0x80u) ? 0xffu : 0u)); }
-__device__ __forceinline__ uint8_t tcms1_inv(uint32_t t) { return (uint8_t)((t >> 1) ^ ((t & 1u) ? 0xffu : 0u)); }
+// Four bytes at a time: TCMS1 on each byte of w, and its inverse.
+__device__ __forceinline__ uint32_t tcms1_4(uint32_t w)
+{
+    return ((w << 1) & 0xfefefefeu) ^ (((w >> 7) & 0x01010101u) * 0xffu);
+}
+__device__ __forceinline__ uint32_t tcms1_inv_4(uint32_t t)
+{
+    return ((t >> 1) & 0x7f7f7f7fu) ^ ((t & 0x01010101u) * 0xffu);
+}
 
-// Block sum of one value per warp (lane 0's), returned to every thread.
-__device__ __forceinline__ uint32_t block_sum_warps(uint32_t v, uint32_t* s_red)
+// 8x8 bit transpose (Hacker's Delight, transpose8 with 64-bit delta swaps):
+// bit 8 i + j of x goes to bit 8 j + i.  With byte i = element i, byte j of
+// the result holds bit j of every element, element i at bit i.
+__device__ __forceinline__ uint64_t transpose8(uint64_t x)
+{
+    uint64_t t = (x ^ (x >> 7)) & 0x00aa00aa00aa00aaull;
+    x = x ^ t ^ (t << 7);
+    t = (x ^ (x >> 14)) & 0x0000cccc0000ccccull;
+    x = x ^ t ^ (t << 14);
+    t = (x ^ (x >> 28)) & 0x00000000f0f0f0f0ull;
+    return x ^ t ^ (t << 28);
+}
+
+// Bit k (k < 4) set when byte k of w differs from the byte before it (prev:
+// the word before w).  Nonzero bytes of the xor are found exactly (no carry
+// between bytes) and their top bits gathered by one multiply.
+__device__ __forceinline__ uint32_t diff_flags4(uint32_t w, uint32_t prev)
+{
+    const uint32_t d = w ^ __funnelshift_l(prev, w, 8);
+    const uint32_t nz = (((d & 0x7f7f7f7fu) + 0x7f7f7f7fu) | d) & 0x80808080u;
+    return (((nz >> 7) * 0x00204081u) >> 21) & 0xfu;
+}
+
+// Flags of positions a .. a + 4 W - 1 of level v (bit i: v[a + i] differs
+// from its predecessor, v[-1] = 0), cleared at and past L.  a is a multiple
+// of 4 W.
+template <int W>
+__device__ __forceinline__ uint64_t range_flags(const uint8_t* v, uint32_t a, uint32_t L)
+{
+    uint32_t prev = a ? (uint32_t)v[a - 1] << 24 : 0u;
+    uint64_t f = 0;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        const uint32_t w = reinterpret_cast<const uint32_t*>(v + a)[k];
+        f |= (uint64_t)diff_flags4(w, prev) << (4 * k);
+        prev = w;
+    }
+    if (a + 4 * W > L) {
+        const uint32_t valid = L > a ? L - a : 0u;
+        f &= valid >= 64 ? ~0ull : ((1ull << valid) - 1ull);
+    }
+    return f;
+}
+
+// Exclusive prefix over the block of one count per thread; *total = the sum.
+__device__ __forceinline__ uint32_t block_exscan(uint32_t c, uint32_t* s_red, uint32_t* total)
 {
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (lane == 0) s_red[warp] = v;
-    __syncthreads();
-    uint32_t t = 0;
-    for (uint32_t w = 0; w < nw; ++w) t += s_red[w];
-    __syncthreads();
-    return t;
-}
-
-// Exclusive prefix (over warps, in warp order) of one value per warp.
-__device__ __forceinline__ uint32_t block_prefix_warps(uint32_t v, uint32_t* s_red)
-{
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    if (lane == 0) s_red[warp] = v;
-    __syncthreads();
-    uint32_t t = 0;
-    for (uint32_t w = 0; w < warp; ++w) t += s_red[w];
-    __syncthreads();
-    return t;
-}
-
-// Bits of group g (positions 32 g .. 32 g + 31) that lie below L.
-__device__ __forceinline__ uint32_t valid_bits(uint32_t g, uint32_t L)
-{
-    const uint32_t lo = 32 * g;
-    return (L >= lo + 32) ? 0xffffffffu : ((L > lo) ? ((1u << (L - lo)) - 1u) : 0u);
-}
-
-// Set bits of the bitmap bm over positions [0, L) (all threads).
-__device__ uint32_t bitmap_count(const uint8_t* bm, uint32_t L, uint32_t* s_red)
-{
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const uint32_t* bw = reinterpret_cast<const uint32_t*>(bm);
-    uint32_t c = 0;
-    for (uint32_t g = warp * 32 + lane; g < (L + 31) / 32; g += nw * 32) c += __popc(bw[g] & valid_bits(g, L));
-    c = __reduce_add_sync(0xffffffffu, c);
-    return block_sum_warps(c, s_red);
-}
-
-// RRE bitmap of v[0..L) into bm (whole words; bits past L are 0); returns
-// the number of set bits (all threads).
-__device__ uint32_t rre_bitmap(const uint8_t* v, uint32_t L, uint8_t* bm, uint32_t* s_red)
-{
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const uint32_t groups = (L + 31) / 32;
-    uint32_t cnt = 0;
-    for (uint32_t g = warp; g < groups; g += nw) {
-        const uint32_t i = 32 * g + lane;
-        const bool f = i < L && v[i] != (i ? v[i - 1] : 0);
-        const uint32_t w = __ballot_sync(0xffffffffu, f);
-        if (lane == 0) reinterpret_cast<uint32_t*>(bm)[g] = w;
-        cnt += __popc(w);
+    uint32_t incl = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= (uint32_t)d) incl += t;
     }
-    return block_sum_warps(cnt, s_red);
-}
-
-// Each warp's contiguous share of the groups of 32 positions.
-__device__ __forceinline__ void warp_groups(uint32_t groups, uint32_t* g0, uint32_t* g1)
-{
-    const uint32_t warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const uint32_t per = (groups + nw - 1) / nw;
-    *g0 = min(warp * per, groups);
-    *g1 = min(*g0 + per, groups);
-}
-
-// The kept bytes of v (bitmap bm) in order to dst (global).
-__device__ void rre_compact(const uint8_t* v, uint32_t L, const uint8_t* bm, uint8_t* __restrict__ dst,
-                            uint32_t* s_red)
-{
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t* bw = reinterpret_cast<const uint32_t*>(bm);
-    uint32_t g0, g1;
-    warp_groups((L + 31) / 32, &g0, &g1);
-    uint32_t c = 0;
-    for (uint32_t g = g0; g < g1; ++g) c += __popc(bw[g] & valid_bits(g, L));
-    uint32_t base = block_prefix_warps(c, s_red);
-    for (uint32_t g = g0; g < g1; ++g) {
-        const uint32_t w = bw[g] & valid_bits(g, L);
-        if ((w >> lane) & 1u) dst[base + __popc(w & ((1u << lane) - 1u))] = v[32 * g + lane];
-        base += __popc(w);
+    if (lane == 31) s_red[warp] = incl;
+    __syncthreads();
+    uint32_t before = 0, tot = 0;
+    for (uint32_t w = 0; w < nw; ++w) {
+        const uint32_t v = s_red[w];
+        before += (w < warp) ? v : 0u;
+        tot += v;
     }
+    __syncthreads();
+    *total = tot;
+    return before + incl - c;
 }
 
-// v[0..L) from its bitmap bm and kept bytes src[0..):  v[i] = the kept byte of
-// rank popcount(bm[0..i]), 0 before the first.
-__device__ void rre_expand(uint8_t* v, uint32_t L, const uint8_t* bm, const uint8_t* src, uint32_t* s_red)
+// Level r of a chunk: a thread covers 64 positions at level 0, 8 above.
+__device__ __forceinline__ uint32_t level_span(int r) { return r == 0 ? 64u : 8u; }
+
+// Bitmap bits of level r's positions [a, a + span) read from the level
+// above (bitmap buffer bm), cleared at and past L.
+__device__ __forceinline__ uint64_t level_bits(const uint8_t* bm, int r, uint32_t t, uint32_t L)
 {
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t* bw = reinterpret_cast<const uint32_t*>(bm);
-    uint32_t g0, g1;
-    warp_groups((L + 31) / 32, &g0, &g1);
-    uint32_t c = 0;
-    for (uint32_t g = g0; g < g1; ++g) c += __popc(bw[g] & valid_bits(g, L));
-    uint32_t base = block_prefix_warps(c, s_red);
-    for (uint32_t g = g0; g < g1; ++g) {
-        const uint32_t w = bw[g] & valid_bits(g, L);
-        const uint32_t r = base + __popc(w & ((2u << lane) - 1u));
-        const uint32_t i = 32 * g + lane;
-        if (i < L) v[i] = r ? src[r - 1] : (uint8_t)0;
-        base += __popc(w);
+    const uint32_t a = level_span(r) * t;
+    uint64_t f = (r == 0) ? reinterpret_cast<const uint64_t*>(bm)[t] : (uint64_t)bm[t];
+    if (a + level_span(r) > L) {
+        const uint32_t valid = L > a ? L - a : 0u;
+        f &= valid >= 64 ? ~0ull : ((1ull << valid) - 1ull);
     }
+    return f;
 }
 
 __global__ void __launch_bounds__(kTpThreads) k_tp_encode_chunks(const uint8_t* __restrict__ in, uint64_t n,
@@ -179,49 +163,96 @@ __global__ void __launch_bounds__(kTpThreads) k_tp_encode_chunks(const uint8_t* 
 {
     extern __shared__ __align__(16) unsigned char tsm[];
     __shared__ uint32_t s_red[kTpThreads / 32];
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t t = threadIdx.x;
+    uint8_t* sin = tsm + kTpLevelBytes;  // the chunk's input, then its payload
     for (uint32_t k = blockIdx.x; k < nchunks; k += gridDim.x) {
         const uint8_t* s = in + (uint64_t)k * kTpChunk;
         const uint32_t m = (uint32_t)min((uint64_t)kTpChunk, n - (uint64_t)k * kTpChunk);
         const TpLevels T = tp_levels(m);
+        const uint32_t mp = T.L[0];
+        if ((reinterpret_cast<uintptr_t>(s) & 15u) == 0) {
+            for (uint32_t i = t; i < m / 16; i += blockDim.x)
+                reinterpret_cast<uint4*>(sin)[i] = __ldg(reinterpret_cast<const uint4*>(s) + i);
+            for (uint32_t i = m / 16 * 16 + t; i < m; i += blockDim.x) sin[i] = s[i];
+        } else {
+            for (uint32_t i = t; i < m; i += blockDim.x) sin[i] = s[i];
+        }
+        for (uint32_t i = m + t; i < mp; i += blockDim.x) sin[i] = 0;  // TCMS1(0) = 0: the zero padding
+        __syncthreads();
+        // TCMS1 + BIT1: elements 64 t .. 64 t + 63 -> bytes 8 t .. 8 t + 7 of each plane
         uint8_t* u = tsm + tp_level_off(0);
-        const uint32_t pl = T.L[0] / 8;
-        // TCMS1 + BIT1: plane p, bytes 4 g .. 4 g + 3 = ballot of bit 7 - p over elements 32 g ..
-        for (uint32_t g = warp; g < T.L[0] / 32; g += nw) {
-            const uint32_t e = 32 * g + lane;
-            const uint32_t t = e < m ? tcms1(s[e]) : 0u;
+        const uint32_t pl = mp / 8;
+        if (64 * t < mp) {
+            uint64_t tr[8];
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                const uint2 w = reinterpret_cast<const uint2*>(sin + 64 * t)[g];
+                tr[g] = transpose8((uint64_t)tcms1_4(w.x) | ((uint64_t)tcms1_4(w.y) << 32));
+            }
 #pragma unroll
             for (int p = 0; p < 8; ++p) {
-                const uint32_t w = __ballot_sync(0xffffffffu, (t >> (7 - p)) & 1u);
-                if (lane == (uint32_t)p) reinterpret_cast<uint32_t*>(u + p * pl)[g] = w;
+                const int b = 7 - p;  // byte of each transposed group holding plane p
+                uint32_t h[8];
+#pragma unroll
+                for (int g = 0; g < 8; ++g) h[g] = (uint32_t)(tr[g] >> (b >= 4 ? 32 : 0));
+                const uint32_t sel = (uint32_t)(b & 3) | ((uint32_t)(4 + (b & 3)) << 4);
+                const uint32_t lo = __byte_perm(__byte_perm(h[0], h[1], sel), __byte_perm(h[2], h[3], sel), 0x5410);
+                const uint32_t hi = __byte_perm(__byte_perm(h[4], h[5], sel), __byte_perm(h[6], h[7], sel), 0x5410);
+                reinterpret_cast<uint2*>(u + p * pl)[t] = make_uint2(lo, hi);
             }
         }
         __syncthreads();
+        // RRE1 bitmaps, level by level
         uint32_t cnt[kTpMaxLevels];
-        uint32_t total = 0;
+        uint32_t total = T.L[T.R];
         for (int r = 0; r < T.R; ++r) {
-            cnt[r] = rre_bitmap(tsm + tp_level_off(r), T.L[r], tsm + tp_level_off(r + 1), s_red);
-            total += cnt[r];
+            const uint8_t* v = tsm + tp_level_off(r);
+            uint8_t* bm = tsm + tp_level_off(r + 1);
+            const uint32_t span = level_span(r);
+            uint64_t f = 0;
+            if (span * t < T.L[r]) {
+                if (r == 0) {
+                    f = range_flags<16>(v, 64 * t, T.L[r]);
+                    reinterpret_cast<uint64_t*>(bm)[t] = f;
+                } else {
+                    f = range_flags<2>(v, 8 * t, T.L[r]);
+                    bm[t] = (uint8_t)f;
+                }
+            }
+            uint32_t c_tot;
+            block_exscan((uint32_t)__popcll(f), s_red, &c_tot);
+            cnt[r] = c_tot;
+            total += c_tot;
         }
-        total += T.L[T.R];
         uint8_t* slot = slots + (uint64_t)k * kTpSlot;
-        uint32_t len;
-        if (total > m) {
-            for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) slot[i] = s[i];
-            len = m;
-        } else {
+        const bool raw = total > m;
+        uint32_t len = m;
+        if (!raw) {
+            // payload in sin: top level, then the kept bytes of each level below it
             const uint8_t* top = tsm + tp_level_off(T.R);
-            for (uint32_t i = threadIdx.x; i < T.L[T.R]; i += blockDim.x) slot[i] = top[i];
+            for (uint32_t i = t; i < T.L[T.R]; i += blockDim.x) sin[i] = top[i];
             uint32_t off = T.L[T.R];
             for (int r = T.R - 1; r >= 0; --r) {
-                rre_compact(tsm + tp_level_off(r), T.L[r], tsm + tp_level_off(r + 1), slot + off, s_red);
-                off += cnt[r];
+                const uint8_t* v = tsm + tp_level_off(r);
+                const uint32_t a = level_span(r) * t;
+                uint64_t f = (a < T.L[r]) ? level_bits(tsm + tp_level_off(r + 1), r, t, T.L[r]) : 0ull;
+                uint32_t c_tot;
+                uint32_t pos = off + block_exscan((uint32_t)__popcll(f), s_red, &c_tot);
+                while (f) {
+                    const int i = __ffsll((long long)f) - 1;
+                    f &= f - 1;
+                    sin[pos++] = v[a + i];
+                }
+                off += c_tot;
             }
             len = off;
         }
         const uint32_t pad = (len + 15) / 16 * 16;
-        for (uint32_t i = len + threadIdx.x; i < pad; i += blockDim.x) slot[i] = 0;
-        if (threadIdx.x == 0) sizes[k] = pad | (total > m ? kTpRaw : 0u);
+        for (uint32_t i = len + t; i < pad; i += blockDim.x) sin[i] = 0;
+        __syncthreads();
+        for (uint32_t i = t; i < pad / 16; i += blockDim.x)
+            reinterpret_cast<uint4*>(slot)[i] = reinterpret_cast<const uint4*>(sin)[i];
+        if (t == 0) sizes[k] = pad | (raw ? kTpRaw : 0u);
         __syncthreads();  // shared buffers are reused by the next chunk
     }
 }
@@ -288,7 +319,7 @@ __global__ void __launch_bounds__(256) k_tp_gather(const uint8_t* __restrict__ s
 // Decode, a CTA per chunk; offsets from k_tp_scan over the stream's size
 // table.  A stream that does not fit its header, size table or levels sets
 // HI_ECORRUPT and leaves those chunks' bytes unwritten.
-__global__ void __launch_bounds__(kTpThreads) k_tp_decode_chunks(const uint8_t* __restrict__ in, uint64_t in_len,
+__global__ void __launch_bounds__(kTpThreads, 4) k_tp_decode_chunks(const uint8_t* __restrict__ in, uint64_t in_len,
                                                                  uint64_t n, uint32_t nchunks,
                                                                  const uint64_t* __restrict__ offsets,
                                                                  uint8_t* __restrict__ out,
@@ -296,16 +327,17 @@ __global__ void __launch_bounds__(kTpThreads) k_tp_decode_chunks(const uint8_t* 
 {
     extern __shared__ __align__(16) unsigned char tsm[];
     __shared__ uint32_t s_red[kTpThreads / 32];
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t t = threadIdx.x;
     const bool hdr_ok = reinterpret_cast<const uint64_t*>(in)[0] == n &&
                         reinterpret_cast<const uint32_t*>(in)[2] == kTpChunk &&
                         reinterpret_cast<const uint32_t*>(in)[3] == nchunks;
     if (!hdr_ok) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(status, HI_ECORRUPT);
+        if (blockIdx.x == 0 && t == 0) set_status(status, HI_ECORRUPT);
         return;
     }
     uint8_t* pay = tsm + kTpLevelBytes;
     const uint64_t hb = tp_header_bytes(nchunks);
+    const bool vec_out = (reinterpret_cast<uintptr_t>(out) & 7u) == 0;
     for (uint32_t k = blockIdx.x; k < nchunks; k += gridDim.x) {
         const uint32_t sz = reinterpret_cast<const uint32_t*>(in + 16)[k];
         const uint32_t pad = sz & ~kTpRaw;
@@ -316,54 +348,88 @@ __global__ void __launch_bounds__(kTpThreads) k_tp_decode_chunks(const uint8_t* 
         if (raw) ok = ok && pad >= m;
         uint8_t* o = out + (uint64_t)k * kTpChunk;
         if (!ok) {
-            if (threadIdx.x == 0) set_status(status, HI_ECORRUPT);
+            if (t == 0) set_status(status, HI_ECORRUPT);
             continue;
         }
         const uint8_t* p = in + off;
         if (raw) {
-            for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) o[i] = p[i];
+            for (uint32_t i = t; i < m; i += blockDim.x) o[i] = p[i];
             continue;
         }
-        for (uint32_t i = threadIdx.x; i < pad / 16; i += blockDim.x)
+        for (uint32_t i = t; i < pad / 16; i += blockDim.x)
             reinterpret_cast<uint4*>(pay)[i] = reinterpret_cast<const uint4*>(p)[i];
         const TpLevels T = tp_levels(m);
-        uint8_t* top = tsm + tp_level_off(T.R);
         if (T.L[T.R] > pad) {
-            if (threadIdx.x == 0) set_status(status, HI_ECORRUPT);
+            if (t == 0) set_status(status, HI_ECORRUPT);
             __syncthreads();
             continue;
         }
         __syncthreads();
-        for (uint32_t i = threadIdx.x; i < T.L[T.R]; i += blockDim.x) top[i] = pay[i];
+        uint8_t* top = tsm + tp_level_off(T.R);
+        for (uint32_t i = t; i < T.L[T.R]; i += blockDim.x) top[i] = pay[i];
         __syncthreads();
         uint32_t q = T.L[T.R];
         bool good = true;
         for (int r = T.R - 1; r >= 0; --r) {
-            const uint8_t* bm = tsm + tp_level_off(r + 1);
-            const uint32_t c = bitmap_count(bm, T.L[r], s_red);
-            if (q + c > pad) {
+            uint8_t* v = tsm + tp_level_off(r);
+            const uint32_t span = level_span(r), a = span * t;
+            const uint64_t f = (a < T.L[r]) ? level_bits(tsm + tp_level_off(r + 1), r, t, T.L[r]) : 0ull;
+            uint32_t c_tot;
+            uint32_t rank = block_exscan((uint32_t)__popcll(f), s_red, &c_tot);
+            if (q + c_tot > pad) {
                 good = false;
                 break;
             }
-            rre_expand(tsm + tp_level_off(r), T.L[r], bm, pay + q, s_red);
-            q += c;
+            if (a < T.L[r]) {
+                // v[a + i] = the kept byte of rank (set bits at or before a + i), 0 before the first
+                for (uint32_t w0 = 0; w0 < span; w0 += 4) {
+                    uint32_t word = 0;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        rank += (uint32_t)((f >> (w0 + b)) & 1ull);
+                        const uint32_t val = rank ? pay[q + rank - 1] : 0u;
+                        word |= val << (8 * b);
+                    }
+                    reinterpret_cast<uint32_t*>(v + a)[w0 / 4] = word;
+                }
+            }
+            q += c_tot;
             __syncthreads();
         }
         if (!good) {
-            if (threadIdx.x == 0) set_status(status, HI_ECORRUPT);
+            if (t == 0) set_status(status, HI_ECORRUPT);
             __syncthreads();
             continue;
         }
-        // bit planes back to bytes, then magnitude-sign back to two's complement
+        // bit planes back to bytes (the transpose is its own inverse), then TCMS1 back
         const uint8_t* u = tsm + tp_level_off(0);
         const uint32_t pl = T.L[0] / 8;
-        for (uint32_t g = warp; g < T.L[0] / 32; g += nw) {
-            uint32_t t = 0;
+        if (64 * t < T.L[0]) {
+            uint32_t qlo[8], qhi[8];
 #pragma unroll
-            for (int pp = 0; pp < 8; ++pp)
-                t |= ((reinterpret_cast<const uint32_t*>(u + pp * pl)[g] >> lane) & 1u) << (7 - pp);
-            const uint32_t e = 32 * g + lane;
-            if (e < m) o[e] = tcms1_inv(t);
+            for (int pp = 0; pp < 8; ++pp) {
+                const uint2 w = reinterpret_cast<const uint2*>(u + pp * pl)[t];
+                qlo[pp] = w.x, qhi[pp] = w.y;
+            }
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                // byte 7 - p of group g's transposed word = byte g of plane p's 8 bytes
+                uint32_t h[8];
+#pragma unroll
+                for (int pp = 0; pp < 8; ++pp) h[7 - pp] = g < 4 ? qlo[pp] : qhi[pp];
+                const uint32_t sel = (uint32_t)(g & 3) | ((uint32_t)(4 + (g & 3)) << 4);
+                const uint32_t lo = __byte_perm(__byte_perm(h[0], h[1], sel), __byte_perm(h[2], h[3], sel), 0x5410);
+                const uint32_t hi = __byte_perm(__byte_perm(h[4], h[5], sel), __byte_perm(h[6], h[7], sel), 0x5410);
+                const uint64_t x = transpose8((uint64_t)lo | ((uint64_t)hi << 32));
+                const uint32_t e0 = tcms1_inv_4((uint32_t)x), e1 = tcms1_inv_4((uint32_t)(x >> 32));
+                const uint32_t e = 64 * t + 8 * g;
+                if (vec_out && e + 8 <= m) {
+                    reinterpret_cast<uint2*>(o + e)[0] = make_uint2(e0, e1);
+                } else {
+                    for (int b = 0; b < 8; ++b)
+                        if (e + b < m) o[e + b] = (uint8_t)((b < 4 ? e0 : e1) >> (8 * (b & 3)));
+                }
+            }
         }
         __syncthreads();
     }
@@ -383,7 +449,7 @@ uint64_t tp_stream_bound(uint64_t n)
 
 static int tp_grid(uint32_t nchunks, int num_sms)
 {
-    const uint32_t cap = (uint32_t)num_sms * 4;
+    const uint32_t cap = (uint32_t)num_sms * 6;  // 6 CTAs of ~36 KB shared memory per SM
     return (int)(nchunks < cap ? (nchunks ? nchunks : 1) : cap);
 }
 
@@ -397,7 +463,8 @@ cudaError_t launch_tp_encode(const uint8_t* in, uint64_t n, uint8_t* out, uint64
     uint8_t* slots = reinterpret_cast<uint8_t*>(offsets + nc);
     slots = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(slots) + 15) & ~(uintptr_t)15);
     if (nc) {
-        k_tp_encode_chunks<<<tp_grid(nc, num_sms), kTpThreads, kTpLevelBytes, st>>>(in, n, slots, sizes, nc);
+        k_tp_encode_chunks<<<tp_grid(nc, num_sms), kTpThreads, kTpLevelBytes + kTpChunk, st>>>(in, n, slots, sizes,
+                                                                                              nc);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
