@@ -616,7 +616,7 @@ def run_serve(args):
         done = sv.run(requests)
         wall = time.perf_counter() - t0
         s = serve.summarize(done, wall)
-        s.update(peak_concurrency=sv.peak_concurrency, peak_bytes=sv.peak_bytes, slots=slots)
+        s.update(peak_concurrency=sv.peak_concurrency, peak_bytes=sv.peak_bytes, slots=slots, launches=ex.launches)
         return s
 
     burst = [serve.Request(r.id, 0.0, r.op, r.side, r.eb, r.seed, r.source) for r in reqs]
@@ -638,7 +638,7 @@ def run_serve(args):
                     step="one request (value = input bytes of all requests / wall time of the run)"),
         p50_ms=main["p50_ms"], p99_ms=main["p99_ms"], max_ms=main["max_ms"], offered_gbs=offered,
         served=main, saturated=sat, one_slot=single,
-        gpu_launches=None,
+        gpu_launches=main["launches"],  # compress 3 (+3 on a capacity re-run), decompress 2 per request
         clocks=clk.summary(),
     )
     print(json.dumps(line), flush=True)

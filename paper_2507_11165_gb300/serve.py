@@ -257,6 +257,7 @@ class GpuExecutor:
         self.t0_event = None
         self.pool = collections.defaultdict(list)  # (kind, shape, cap) -> free buffers
         self.params = {}
+        self.launches = 0  # library kernels enqueued
 
     def start(self):
         self.t0_event = self.torch.cuda.Event(enable_timing=True)
@@ -311,6 +312,7 @@ class GpuExecutor:
                               lambda: hi.alloc(p, shape, self.dev, out_cap=cap, hist=True, recon=False))
                 b.params = p
                 hi.compress_into(x, b, stream=st)
+                self.launches += 3  # set-up, range + auto-tune (one launch), predict-quantize
                 hdr = self._get(("hdr",), lambda: torch.empty(hi.HEADER_BYTES, dtype=torch.uint8, pin_memory=True))
                 hdr.copy_(b.header, non_blocking=True)
                 ev = torch.cuda.Event(enable_timing=True)
@@ -322,6 +324,7 @@ class GpuExecutor:
             status = self._get(("st",), lambda: torch.zeros(1, dtype=torch.int32, device=self.dev))
             ws = self._get(("ws",), lambda: torch.empty(hi.DECOMPRESS_WS_BYTES, dtype=torch.uint8, device=self.dev))
             hi.decompress_into(b, out, status, stream=st, ws=ws)  # its own tile queue
+            self.launches += 2  # outlier scatter, reconstruct
             sh = self._get(("sh",), lambda: torch.empty(1, dtype=torch.int32, pin_memory=True))
             sh.copy_(status, non_blocking=True)
             ev = torch.cuda.Event(enable_timing=True)
@@ -343,6 +346,7 @@ class GpuExecutor:
                     self._put(("rec", h["x"].shape, h["cap"]), h["b"])
                     b = hi.alloc(h["p"], h["x"].shape, self.dev, out_cap=int(hd.n_outliers), hist=True, recon=False)
                     hi.compress_into(h["x"], b, stream=h["st"])
+                    self.launches += 3
                     h["hdr"].copy_(b.header, non_blocking=True)
                     h["ev"] = torch.cuda.Event(enable_timing=True)
                     h["ev"].record(h["st"])
