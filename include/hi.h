@@ -327,6 +327,19 @@ HI_API hi_status hi_reorder_codes(const hi_params* p, const uint8_t* d_codes, ui
 HI_API hi_status hi_unreorder_codes(const hi_params* p, const uint8_t* d_seq, uint8_t* d_codes,
                                     cudaStream_t stream);
 
+/* The value range of the value-range-relative bound (Sec. 6.1.4) alone:
+ * the min and the max over the finite values of d_x go to d_header->vmin /
+ * vmax (0 and 0 when there is none), with the header's eps and float32
+ * constants derived from them as hi_compress would.  For a field processed
+ * in parts (out of core, or one part per GPU): the parts' ranges combine
+ * into the field's, whose eps each part then takes as an absolute bound.
+ * p: the part's parameters, eb_mode HI_EB_REL.  d_ws: at least
+ * HI_DECOMPRESS_WS_BYTES + 8 KiB (hi_query's ws_bytes always suffices).
+ * Two launches on stream, no sync; HI_EINVAL / HI_ENOMEM / HI_ECUDA as for
+ * hi_compress. */
+HI_API hi_status hi_value_range(const hi_params* p, const float* d_x, hi_header* d_header, void* d_ws,
+                                size_t ws_bytes, cudaStream_t stream);
+
 /* Throughput-mode lossless pipeline TCMS1-BIT1-RRE1 (Sec. 5.2.3): a byte
  * sequence (normally the output of hi_reorder_codes) into a self-describing
  * stream, and back.  Stages, per 16 KiB chunk: TCMS1 maps each byte, read as

@@ -766,6 +766,27 @@ hi_status hi_unreorder_codes(const hi_params* p, const uint8_t* d_seq, uint8_t* 
     return reorder_call(p, d_seq, d_codes, true, stream);
 }
 
+hi_status hi_value_range(const hi_params* p, const float* d_x, hi_header* d_header, void* d_ws, size_t ws_bytes,
+                         cudaStream_t stream)
+{
+    Geometry G;
+    hi_status s = make_geometry(p, &G);
+    if (s != HI_OK) return s;
+    if (p->eb_mode != HI_EB_REL || !d_x || !d_header || !d_ws) return HI_EINVAL;
+    if (!aligned(d_x, 4) || !aligned(d_ws, 8) || !aligned(d_header, 8)) return HI_EINVAL;
+    if (ws_bytes < kWsTune) return HI_ENOMEM;
+    char* ws = static_cast<char*>(d_ws);
+    uint32_t* ticket = reinterpret_cast<uint32_t*>(ws + kWsTicket);
+    uint32_t* queue = reinterpret_cast<uint32_t*>(ws + kWsQueue);
+    cudaError_t e = launch_prologue(d_header, *p, G.n_anchors, 0, (uint32_t)G.L, nullptr, ticket, queue, stream);
+    if (e != cudaSuccess) return HI_ECUDA;
+    int nb = kRangeBlocks;
+    const int64_t need = (G.g.N + 4095) / 4096;
+    if (need < nb) nb = (int)(need > 0 ? need : 1);
+    return cuda_status(
+        launch_range(d_x, G.g.N, reinterpret_cast<float2*>(ws + kWsPartials), nb, ticket, d_header, stream));
+}
+
 hi_status hi_tp_query(uint64_t n, uint64_t* max_stream_bytes, size_t* ws_bytes)
 {
     if (n >= (1ull << 44)) return HI_EINVAL;

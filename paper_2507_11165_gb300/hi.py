@@ -111,6 +111,7 @@ def lib():
             L.hi_header_read.argtypes = [P, ctypes.POINTER(HiHeader), P]
             L.hi_reorder_codes.argtypes = [ctypes.POINTER(HiParams), P, P, P]
             L.hi_tp_query.argtypes = [u64, ctypes.POINTER(u64), ctypes.POINTER(sz)]
+            L.hi_value_range.argtypes = [ctypes.POINTER(HiParams), P, P, P, sz, P]
             L.hi_tp_encode.argtypes = [P, u64, P, u64, P, P, sz, P]
             L.hi_tp_decode.argtypes = [P, u64, P, u64, P, P, sz, P]
             L.hi_unreorder_codes.argtypes = [ctypes.POINTER(HiParams), P, P, P]
@@ -307,6 +308,16 @@ def unreorder_codes(seq, p, out=None, stream=None):
         out = torch.empty(seq.numel(), dtype=torch.uint8, device=seq.device)
     _check(lib().hi_unreorder_codes(ctypes.byref(p), _ptr(seq), _ptr(out), _stream(stream)), "hi_unreorder_codes")
     return out
+
+
+RANGE_WS_BYTES = DECOMPRESS_WS_BYTES + 8192
+
+
+def value_range_into(x, p, header, ws, stream=None):
+    """Enqueue hi_value_range of device tensor ``x`` (parameters ``p``, relative bound): the min and max
+    of its finite values into the device ``header`` (no sync)."""
+    _check(lib().hi_value_range(ctypes.byref(p), _ptr(x), _ptr(header), _ptr(ws), ws.numel(), _stream(stream)),
+           "hi_value_range")
 
 
 def tp_query(n):

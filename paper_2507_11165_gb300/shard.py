@@ -128,3 +128,115 @@ def compress_in_sequence(x, eb: float, A: int, parts: int, levels, mode: str = "
     return dict(codes=torch.cat(codes, 0), anchors=torch.cat(anchors, 0).reshape(-1),
                 out_idx=torch.cat(oidx), out_val=torch.cat(oval), hist=hist, eps=eps,
                 eb_f=cst.eb_f, ebx2_f=cst.ebx2_f, r_f=cst.r_f, vmin=vmin, vmax=vmax)
+
+
+def compress_out_of_core(x_host, eb: float, A: int, levels, mode: str = "rel", shard_blocks: int = 8,
+                         device=None):
+    """Compress a 3D float32 field held in host memory (a CPU tensor; pinned
+    memory lets the copies overlap the kernels) on one GPU, a shard of
+    ``shard_blocks`` block planes along d0 (plus the next shard's first
+    plane) at a time: the device holds two shards, never the field.  The
+    shards' value ranges (hi_value_range) give the field's eps first; then
+    each shard is compressed at that absolute bound while the next one is
+    uploaded.  Returns host arrays equal to a whole-field compression with
+    the same level configuration: dict(codes, anchors, out_idx, out_val,
+    hist, eps, eb_f, ebx2_f, r_f, vmin, vmax)."""
+    import numpy as np
+    import torch
+
+    from . import hi
+
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    n0, n1, n2 = (int(v) for v in x_host.shape)
+    plane = n1 * n2
+    nb0 = 1 if n0 == 1 else (n0 - 1 + A - 1) // A
+    plan = shard_bounds(n0, A, max(1, -(-nb0 // max(1, shard_blocks))))
+    max_planes = max(sh["read_hi"] - sh["own_lo"] for sh in plan)
+    comp = torch.cuda.current_stream(dev)
+    copy = torch.cuda.Stream(dev)
+    bufs = [torch.empty(max_planes * plane, dtype=torch.float32, device=dev) for _ in range(2)]
+    ready = [torch.cuda.Event() for _ in range(2)]
+    free = [torch.cuda.Event() for _ in range(2)]
+    for e in free:
+        e.record(comp)
+    flat = x_host.reshape(-1)
+
+    def upload(i, lo, hi_):
+        k = i % 2
+        copy.wait_event(free[k])
+        with torch.cuda.stream(copy):
+            n = (hi_ - lo) * plane
+            bufs[k][:n].copy_(flat[lo * plane:hi_ * plane], non_blocking=True)
+            ready[k].record(copy)
+        return bufs[k][:n].view(hi_ - lo, n1, n2)
+
+    # pass 1: the field's value range from the shards' own planes
+    vmin, vmax = math.inf, -math.inf
+    if mode == "rel":
+        ws = torch.empty(hi.RANGE_WS_BYTES, dtype=torch.uint8, device=dev)
+        parts = []
+        nxt = upload(0, plan[0]["own_lo"], plan[0]["own_hi"])
+        for i, sh in enumerate(plan):
+            xs = nxt
+            comp.wait_event(ready[i % 2])
+            p = hi.make_params(tuple(xs.shape), eb, "rel", A, autotune=False, levels=levels)
+            hdr = torch.empty(hi.HEADER_BYTES, dtype=torch.uint8, device=dev)
+            hi.value_range_into(xs, p, hdr, ws)
+            parts.append((hdr, torch.isfinite(xs).any()))  # a shard without finite values adds nothing
+            free[i % 2].record(comp)
+            if i + 1 < len(plan):
+                nxt = upload(i + 1, plan[i + 1]["own_lo"], plan[i + 1]["own_hi"])
+        for hdr, fin in parts:
+            if bool(fin.item()):
+                h = hi.read_header(hdr)
+                vmin, vmax = min(vmin, float(h.vmin)), max(vmax, float(h.vmax))
+        if vmin > vmax:
+            vmin = vmax = 0.0
+    eps = eps_from_range(mode, eb, vmin, vmax)
+
+    # pass 2: each shard with its halo plane at the absolute bound eps
+    codes = np.empty(n0 * plane, dtype=np.uint8)
+    anchors, oidx, oval = [], [], []
+    hist = np.zeros(256, dtype=np.int64)
+    amask = torch.zeros((n1, n2), dtype=torch.bool, device=dev)
+    amask[::A, ::A] = True
+    cst = None
+    nxt = upload(0, plan[0]["own_lo"], plan[0]["read_hi"])
+    for i, sh in enumerate(plan):
+        xs = nxt
+        comp.wait_event(ready[i % 2])
+        p = hi.make_params(tuple(xs.shape), eps, "abs", A, autotune=False, levels=levels)
+        cap = max(1024, xs.numel() // 16)
+        b = hi.alloc(p, tuple(xs.shape), dev, out_cap=cap, hist=True, recon=False)
+        hi.compress_into(xs, b)
+        h = hi.read_header(b.header)  # also orders the results before the next upload reuses the buffer
+        if h.status == hi.HI_ECAPACITY:  # more outliers than the first guess: once more with the count
+            b = hi.alloc(p, tuple(xs.shape), dev, out_cap=int(h.n_outliers), hist=True, recon=False)
+            hi.compress_into(xs, b)
+            h = hi.read_header(b.header)
+        if h.status != 0:
+            raise hi.HiError(h.status, "shard %d" % sh["k"])
+        free[i % 2].record(comp)
+        if i + 1 < len(plan):
+            nxt = upload(i + 1, plan[i + 1]["own_lo"], plan[i + 1]["read_hi"])
+        cst = h
+        nown = sh["own_hi"] - sh["own_lo"]
+        codes[sh["own_lo"] * plane:sh["own_hi"] * plane] = b.codes[:nown * plane].cpu().numpy()
+        ash = ((xs.shape[0] - 1) // A + 1, (n1 - 1) // A + 1, (n2 - 1) // A + 1)
+        an = b.anchors[:int(np.prod(ash))].view(ash)
+        anchors.append((an if sh["last"] else an[:-1]).cpu().numpy())
+        k = int(h.n_outliers)
+        idx = b.out_idx[:k].to(torch.int64) & 0xFFFFFFFF
+        keep = idx < nown * plane
+        oidx.append((idx[keep] + sh["own_lo"] * plane).cpu().numpy())
+        oval.append(b.out_val[:k][keep].cpu().numpy())
+        hs = b.hist.to(torch.int64)
+        if not sh["last"]:  # the halo plane's non-anchor codes belong to the next shard
+            top = b.codes[nown * plane:(nown + 1) * plane].view(n1, n2).to(torch.int64)
+            hs = hs - torch.bincount(top[~amask], minlength=256)
+        hist += hs.cpu().numpy()
+    torch.cuda.current_stream(dev).synchronize()
+    return dict(codes=codes.reshape(n0, n1, n2), anchors=np.concatenate(anchors, 0).reshape(-1),
+                out_idx=np.concatenate(oidx), out_val=np.concatenate(oval), hist=hist, eps=eps,
+                eb_f=cst.eb_f, ebx2_f=cst.ebx2_f, r_f=cst.r_f, vmin=vmin, vmax=vmax)
+

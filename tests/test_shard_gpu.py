@@ -38,3 +38,35 @@ def test_shards_in_sequence_equal_the_whole_field(hi, shape, A, parts, eb):
     assert torch.equal(m["hist"], c.hist.to(torch.int64))
     if eb <= 1e-5:
         assert c.n_outliers > 0
+
+
+@pytest.mark.parametrize("shape,A,blocks,eb,mode,nan_slab", [((150, 64, 72), 16, 2, 1e-3, "rel", True),
+                                                             ((101, 40, 36), 8, 3, 1e-5, "rel", False),
+                                                             ((70, 33, 52), 16, 1, 1e-3, "abs", False),
+                                                             ((40, 17, 20), 16, 8, 1e-3, "rel", False)])
+def test_out_of_core_equals_the_whole_field(hi, shape, A, blocks, eb, mode, nan_slab):
+    """A host-resident field compressed two shards at a time on the device
+    (value ranges first, then each shard with its halo plane at the field's
+    eps) gives the whole-field record; a shard with no finite value at all
+    leaves the range alone and re-runs with the exact outlier count."""
+    xn = fields.lognormal_grf(shape, seed=32)
+    xn[5, 3, 7] = np.inf
+    xn[-1, -2, -3] = np.nan
+    if nan_slab:
+        xn[:blocks * A] = np.nan
+    L = A.bit_length() - 1
+    levels = [(l % 2, (2, 1, 0) if l % 2 else (0, 2, 1)) for l in range(L)]
+    m = shard.compress_out_of_core(torch.from_numpy(xn).pin_memory(), eb, A, levels, mode=mode, shard_blocks=blocks)
+    c = hi.compress(torch.from_numpy(xn).cuda(), eb, mode, A, autotune=False, levels=levels, out_cap=xn.size)
+    assert c.h.status == 0
+    assert m["eps"] == c.h.eps
+    assert np.float32(m["eb_f"]) == np.float32(c.h.eb_f) and np.float32(m["r_f"]) == np.float32(c.h.r_f)
+    assert np.array_equal(m["codes"], c.codes.cpu().numpy().reshape(shape))
+    assert np.array_equal(m["anchors"].view(np.uint32), c.anchors.cpu().numpy().view(np.uint32))
+    idx, val = c.outliers
+    idx = idx.cpu().numpy().view(np.uint32).astype(np.int64)
+    val = val.cpu().numpy()
+    oa, ob = np.argsort(m["out_idx"]), np.argsort(idx)
+    assert np.array_equal(m["out_idx"][oa], idx[ob])
+    assert np.array_equal(m["out_val"][oa].view(np.uint32), val[ob].view(np.uint32))
+    assert np.array_equal(m["hist"], c.hist.cpu().numpy().view(np.uint32).astype(np.int64))
