@@ -644,6 +644,58 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+OOC_METRIC = "out-of-core compress: input GB/s of a host-resident field, two shards on the device"
+
+
+def run_ooc(args):
+    """A field held in pinned host memory compressed on one GPU two shards at
+    a time (value ranges, then each shard with its halo plane at the field's
+    eps, the next shard uploading meanwhile), merged into host arrays; the
+    record is checked against the whole field compressed on the device."""
+    import numpy as np
+    import torch
+
+    from paper_2507_11165_gb300 import fields, hi, shard
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    x_np = fields.lognormal_grf(SHAPE, seed=SEED)
+    x_host = torch.from_numpy(x_np).pin_memory()
+    blocks = 4
+    c = hi.compress(torch.from_numpy(x_np).to(dev), EB, "rel", A, autotune=True, out_cap=x_np.size // 8)
+    levels = [(int(c.h.level[l].interp), tuple(int(v) for v in c.h.level[l].order)) for l in range(c.h.n_levels)]
+    ref_codes = c.codes.cpu().numpy().reshape(SHAPE)
+    ref_hist = c.hist.cpu().numpy().view(np.uint32).astype(np.int64)
+    del c
+    torch.cuda.empty_cache()
+    for _ in range(max(1, args.warmup)):
+        shard.compress_out_of_core(x_host, EB, A, levels, shard_blocks=blocks)
+    steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            m = shard.compress_out_of_core(x_host, EB, A, levels, shard_blocks=blocks)
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - t0) / steps
+    exact = bool(np.array_equal(m["codes"], ref_codes)) and bool(np.array_equal(m["hist"], ref_hist))
+    nb0 = (SHAPE[0] - 1 + A - 1) // A
+    line = dict(
+        metric=OOC_METRIC, value=4.0 * x_np.size / wall / 1e9, unit="GB/s", n_gpus=1, steps=steps,
+        warmup=max(1, args.warmup), ms_per_step=1e3 * wall, higher_is_better=True, scaling="weak",
+        vs_baseline=None, dtype="f32", data="synthetic",
+        config=dict(workload=WORKLOAD + ", held in pinned host memory", shards=-(-nb0 // blocks),
+                    shard_planes=blocks * A + 1, levels="the whole-field auto-tuner's choice",
+                    step="value ranges of the shards + compression of each shard, results copied to host arrays "
+                         "(host wall clock)"),
+        bit_exact_vs_whole_field=exact,
+        # per shard: set-up + range (hi_value_range), then set-up + predict-quantize (absolute bound)
+        gpu_launches=steps * (-(-nb0 // blocks)) * 4,
+        clocks=clk.summary(),
+    )
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -654,7 +706,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-planes", type=int, default=512)
     ap.add_argument("--ref-planes", type=int, default=64)
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"],
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "ooc"],
                     help="single: the 512^3 field (default); batch: 256 fields in one batched launch per stage; "
                          "serve: a Poisson request stream through the continuous-batching loop")
     ap.add_argument("--batch-fields", type=int, default=256)
@@ -681,6 +733,8 @@ def main():
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "ooc":
+        run_ooc(args)
     else:
         run_gpu(args)
 
