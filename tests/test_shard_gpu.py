@@ -70,3 +70,33 @@ def test_out_of_core_equals_the_whole_field(hi, shape, A, blocks, eb, mode, nan_
     assert np.array_equal(m["out_idx"][oa], idx[ob])
     assert np.array_equal(m["out_val"][oa].view(np.uint32), val[ob].view(np.uint32))
     assert np.array_equal(m["hist"], c.hist.cpu().numpy().view(np.uint32).astype(np.int64))
+
+
+@pytest.mark.parametrize("shape", [(64, 48, 40), (1, 1, 1000), (7, 300)])
+def test_value_range_matches_oracle(hi, oracle_mod, shape):
+    """hi_value_range: the min and max over the finite values and the
+    constants derived from them, as the oracle derives them (Eq. 1,
+    relative bound); an all-non-finite part reports 0 and 0."""
+    xn = fields.lognormal_grf(shape, seed=41)
+    flat = xn.reshape(-1)
+    flat[::97] = np.nan
+    flat[5] = -np.inf
+    flat[11] = np.inf
+    x = torch.from_numpy(xn).cuda()
+    p = hi.make_params(shape, 1e-3, "rel", 16, autotune=False)
+    ws = torch.empty(hi.RANGE_WS_BYTES, dtype=torch.uint8, device="cuda")
+    hdr = torch.empty(hi.HEADER_BYTES, dtype=torch.uint8, device="cuda")
+    hi.value_range_into(x, p, hdr, ws)
+    h = hi.read_header(hdr)
+    fin = flat[np.isfinite(flat)]
+    assert np.float32(h.vmin) == fin.min() and np.float32(h.vmax) == fin.max()
+    cst = oracle_mod.eps_constants(xn, 1, 1e-3)
+    assert h.eps == cst["eps"]
+    assert np.float32(h.eb_f) == cst["eb_f"] and np.float32(h.ebx2_f) == cst["ebx2_f"]
+    assert np.float32(h.r_f) == cst["r_f"]
+    hi.value_range_into(torch.full(shape, float("nan"), device="cuda"), p, hdr, ws)
+    h = hi.read_header(hdr)
+    assert float(h.vmin) == 0.0 and float(h.vmax) == 0.0
+    small = torch.empty(hi.RANGE_WS_BYTES - 8, dtype=torch.uint8, device="cuda")
+    with pytest.raises(RuntimeError):
+        hi.value_range_into(x, p, hdr, small)
