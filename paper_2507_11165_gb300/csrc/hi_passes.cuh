@@ -202,28 +202,28 @@ __device__ __forceinline__ void pass_cols(float* __restrict__ v, uint8_t* __rest
             line_point<A, COMP>(v, cs, h, vb + (2 * NDM - 1) * VPD, cb + (2 * NDM - 1) * CPD,
                                 predict(CUBIC, true, true, false, fb, fu, fv, 0.0f));
         }
-        return;
-    }
-    for (int line = threadIdx.x; line < nl; line += blockDim.x) {
-        const int jq = line_q<RT>(line, nr, inv_nr), jr = line - jq * nr;
-        const int cq = jq * stq, cr = jr * str;
-        const int vb = cq * VPQ + cr, cb = cq * CPQ + cr;
-        float f[NDM + 1];  // known nodes at even multiples of S along D
+    } else {
+        for (int line = threadIdx.x; line < nl; line += blockDim.x) {
+            const int jq = line_q<RT>(line, nr, inv_nr), jr = line - jq * nr;
+            const int cq = jq * stq, cr = jr * str;
+            const int vb = cq * VPQ + cr, cb = cq * CPQ + cr;
+            float f[NDM + 1];  // known nodes at even multiples of S along D
 #pragma unroll
-        for (int m = 0; m <= NDM; ++m) f[m] = (2 * m * S <= ed) ? v[vb + 2 * m * VPD] : 0.0f;
+            for (int m = 0; m <= NDM; ++m) f[m] = (2 * m * S <= ed) ? v[vb + 2 * m * VPD] : 0.0f;
 #pragma unroll
-        for (int k = 0; k < NDM; ++k) {
-            if (k >= nd) break;
-            const int c = (2 * k + 1) * S;
-            const bool have_r = c + S <= ed;
-            const bool have_r3 = c + 3 * S <= ed;
-            const float pr = predict(CUBIC, k >= 1, have_r, have_r3, k >= 1 ? f[k - 1] : 0.0f, f[k],
-                                     have_r ? f[k + 1] : 0.0f, (k + 2 <= NDM && have_r3) ? f[k + 2] : 0.0f);
-            const int vi = vb + (2 * k + 1) * VPD;
-            if constexpr (COMP) {
-                v[vi] = point_compress(h, v[vi], pr, cs + cb + (2 * k + 1) * CPD);
-            } else {
-                v[vi] = point_decompress<A>(h, cs[cb + (2 * k + 1) * CPD], pr, vi);
+            for (int k = 0; k < NDM; ++k) {
+                if (k >= nd) break;
+                const int c = (2 * k + 1) * S;
+                const bool have_r = c + S <= ed;
+                const bool have_r3 = c + 3 * S <= ed;
+                const float pr = predict(CUBIC, k >= 1, have_r, have_r3, k >= 1 ? f[k - 1] : 0.0f, f[k],
+                                         have_r ? f[k + 1] : 0.0f, (k + 2 <= NDM && have_r3) ? f[k + 2] : 0.0f);
+                const int vi = vb + (2 * k + 1) * VPD;
+                if constexpr (COMP) {
+                    v[vi] = point_compress(h, v[vi], pr, cs + cb + (2 * k + 1) * CPD);
+                } else {
+                    v[vi] = point_decompress<A>(h, cs[cb + (2 * k + 1) * CPD], pr, vi);
+                }
             }
         }
     }

@@ -13,12 +13,14 @@
 //           level has at most 64 bytes, which is stored as is
 //   payload = top level | kept of the levels below, top down; raw (m bytes)
 //             when that would be longer than m.
-// Encoding: a CTA per chunk (bit planes by warp ballots, bitmaps by
-// ballots, kept bytes placed by per-warp popcount prefixes) into a scratch
-// slot per chunk; a scan of the sizes; a gather of the payloads.  Decoding:
-// the scan, then a CTA per chunk expanding the levels top down (the byte at
-// i is the kept byte of rank popcount(bitmap[0..i])) and transposing the
-// bit planes back.
+// Encoding: a CTA per chunk, a thread per 64 bytes of it -- the transform
+// four bytes at a time, an 8x8 bit transpose per 8 elements for the bit
+// planes, changed-byte flags from byte-exact compares for the bitmaps, kept
+// bytes placed by a block prefix sum into the payload staged in shared
+// memory -- into a scratch slot per chunk; a scan of the sizes; a gather of
+// the payloads.  Decoding: the scan, then a CTA per chunk expanding the
+// levels top down (the byte at i is the kept byte of rank popcount(bitmap
+// [0..i])) and transposing the bit planes back.
 #include "hi_internal.h"
 #include "hi_device.cuh"
 
@@ -203,7 +205,6 @@ __global__ void __launch_bounds__(kTpThreads) k_tp_encode_chunks(const uint8_t* 
         }
         __syncthreads();
         // RRE1 bitmaps, level by level
-        uint32_t cnt[kTpMaxLevels];
         uint32_t total = T.L[T.R];
         for (int r = 0; r < T.R; ++r) {
             const uint8_t* v = tsm + tp_level_off(r);
@@ -221,7 +222,6 @@ __global__ void __launch_bounds__(kTpThreads) k_tp_encode_chunks(const uint8_t* 
             }
             uint32_t c_tot;
             block_exscan((uint32_t)__popcll(f), s_red, &c_tot);
-            cnt[r] = c_tot;
             total += c_tot;
         }
         uint8_t* slot = slots + (uint64_t)k * kTpSlot;
