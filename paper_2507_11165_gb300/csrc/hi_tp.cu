@@ -121,24 +121,29 @@ __device__ __forceinline__ uint64_t range_flags(const uint8_t* v, uint32_t a, ui
 }
 
 // Exclusive prefix over the block of one count per thread; *total = the sum.
-__device__ __forceinline__ uint32_t block_exscan(uint32_t c, uint32_t* s_red, uint32_t* total)
+// s_red holds two arrays of a word per warp, used by alternate calls
+// (parity): a call writes the array that the previous call did not read,
+// and every thread has finished reading the one before that when it
+// reaches the previous call's barrier, so one barrier per call suffices.
+__device__ __forceinline__ uint32_t block_exscan(uint32_t c, uint32_t* s_red, int& parity, uint32_t* total)
 {
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t* part = s_red + (parity ? kTpThreads / 32 : 0);
+    parity ^= 1;
     uint32_t incl = c;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         const uint32_t t = __shfl_up_sync(0xffffffffu, incl, d);
         if (lane >= (uint32_t)d) incl += t;
     }
-    if (lane == 31) s_red[warp] = incl;
+    if (lane == 31) part[warp] = incl;
     __syncthreads();
     uint32_t before = 0, tot = 0;
     for (uint32_t w = 0; w < nw; ++w) {
-        const uint32_t v = s_red[w];
+        const uint32_t v = part[w];
         before += (w < warp) ? v : 0u;
         tot += v;
     }
-    __syncthreads();
     *total = tot;
     return before + incl - c;
 }
@@ -164,7 +169,8 @@ __global__ void __launch_bounds__(kTpThreads) k_tp_encode_chunks(const uint8_t* 
                                                                  uint32_t* __restrict__ sizes, uint32_t nchunks)
 {
     extern __shared__ __align__(16) unsigned char tsm[];
-    __shared__ uint32_t s_red[kTpThreads / 32];
+    __shared__ uint32_t s_red[2 * (kTpThreads / 32)];
+    int parity = 0;
     const uint32_t t = threadIdx.x;
     uint8_t* sin = tsm + kTpLevelBytes;  // the chunk's input, then its payload
     for (uint32_t k = blockIdx.x; k < nchunks; k += gridDim.x) {
@@ -221,7 +227,7 @@ __global__ void __launch_bounds__(kTpThreads) k_tp_encode_chunks(const uint8_t* 
                 }
             }
             uint32_t c_tot;
-            block_exscan((uint32_t)__popcll(f), s_red, &c_tot);
+            block_exscan((uint32_t)__popcll(f), s_red, parity, &c_tot);
             total += c_tot;
         }
         uint8_t* slot = slots + (uint64_t)k * kTpSlot;
@@ -237,7 +243,7 @@ __global__ void __launch_bounds__(kTpThreads) k_tp_encode_chunks(const uint8_t* 
                 const uint32_t a = level_span(r) * t;
                 uint64_t f = (a < T.L[r]) ? level_bits(tsm + tp_level_off(r + 1), r, t, T.L[r]) : 0ull;
                 uint32_t c_tot;
-                uint32_t pos = off + block_exscan((uint32_t)__popcll(f), s_red, &c_tot);
+                uint32_t pos = off + block_exscan((uint32_t)__popcll(f), s_red, parity, &c_tot);
                 while (f) {
                     const int i = __ffsll((long long)f) - 1;
                     f &= f - 1;
@@ -326,7 +332,8 @@ __global__ void __launch_bounds__(kTpThreads, 4) k_tp_decode_chunks(const uint8_
                                                                  uint32_t* __restrict__ status)
 {
     extern __shared__ __align__(16) unsigned char tsm[];
-    __shared__ uint32_t s_red[kTpThreads / 32];
+    __shared__ uint32_t s_red[2 * (kTpThreads / 32)];
+    int parity = 0;
     const uint32_t t = threadIdx.x;
     const bool hdr_ok = reinterpret_cast<const uint64_t*>(in)[0] == n &&
                         reinterpret_cast<const uint32_t*>(in)[2] == kTpChunk &&
@@ -375,7 +382,7 @@ __global__ void __launch_bounds__(kTpThreads, 4) k_tp_decode_chunks(const uint8_
             const uint32_t span = level_span(r), a = span * t;
             const uint64_t f = (a < T.L[r]) ? level_bits(tsm + tp_level_off(r + 1), r, t, T.L[r]) : 0ull;
             uint32_t c_tot;
-            uint32_t rank = block_exscan((uint32_t)__popcll(f), s_red, &c_tot);
+            uint32_t rank = block_exscan((uint32_t)__popcll(f), s_red, parity, &c_tot);
             if (q + c_tot > pad) {
                 good = false;
                 break;
