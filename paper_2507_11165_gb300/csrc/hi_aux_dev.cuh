@@ -339,7 +339,10 @@ __device__ __forceinline__ void tune_sample(float* v, const CUtensorMap* tmap, c
         __syncthreads();
         const bool ok = mbar_wait(&s_mbar, 0, kSpinLimit);
         if (!__syncthreads_and(ok)) {
+            // the copy may still be in flight: stay until it lands
             if (tid == 0) set_status(&hdr->status, HI_ETIMEOUT);
+            drain_wait(&s_mbar, 0);
+            __syncthreads();
             return;
         }
     } else {

@@ -257,10 +257,13 @@ __global__ void __launch_bounds__(kMaxThreads, 5)
             const bool ok = mbar_wait(&s_mbar[buf], (ph >> buf) & 1u, kSpinLimit);
             ph ^= 1u << buf;
             if (!__syncthreads_and(ok)) {
+                // copies this CTA issued may still be in flight: stay until they land
                 if (tid == 0) set_status(&C.out.hdr->status, HI_ETIMEOUT);
+                drain_wait(&s_mbar[buf], ((ph >> buf) & 1u) ^ 1u);
                 if (dbuf && s_next < (int)total && s_tma[(it + 1) & 1])
-                    mbar_wait(&s_mbar[buf ^ 1], (ph >> (buf ^ 1)) & 1u, kSpinLimit);
+                    drain_wait(&s_mbar[buf ^ 1], (ph >> (buf ^ 1)) & 1u);
                 if (tid == 0) cp_async_wait_all();
+                __syncthreads();
                 return;
             }
         } else {

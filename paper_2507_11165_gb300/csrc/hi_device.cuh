@@ -177,8 +177,10 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t b
                  : "memory");
 }
 
-// Bounded wait on the given phase parity; false when the bound ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint32_t limit)
+// Bounded wait on the given phase parity; false when the bound ran out
+// (limit_ns of the global timer, or `limit` polls).
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint32_t limit,
+                                          uint64_t limit_ns = kWaitLimitNs)
 {
     const uint32_t a = smem_addr(mbar);
     uint64_t t0 = 0;
@@ -194,11 +196,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint3
         if (done) return true;
         if (it == 0) {
             t0 = global_ns();
-        } else if ((it & 15) == 0 && global_ns() - t0 > kWaitLimitNs) {
+        } else if ((it & 15) == 0 && global_ns() - t0 > limit_ns) {
             return false;
         }
     }
     return false;
+}
+
+// After a wait gave up: a bulk copy issued on this barrier may still write
+// into the CTA's shared memory, so the CTA stays until the phase completes,
+// bounded by ten times the usual limit (past that the copy engine is not
+// answering and nothing the kernel does can make the memory safe).
+__device__ __forceinline__ void drain_wait(uint64_t* mbar, uint32_t parity)
+{
+    (void)mbar_wait(mbar, parity, kSpinLimit, 10 * kWaitLimitNs);
 }
 
 // 3D tiled TMA load of one box into shared memory, completing on mbar.
