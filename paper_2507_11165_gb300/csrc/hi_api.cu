@@ -122,11 +122,10 @@ hi_status make_geometry(const hi_params* p, Geometry* G)
     }
     G->g.N = (int64_t)N;
     G->g.ntiles = (int)nt;
-    // whole 3D tiles first in the queue when the field's far faces are ragged
-    for (int d = 0; d < 3; ++d) {
-        const bool ragged = p->dims[d] > 1 && (p->dims[d] - 1) % (uint64_t)A != 0;
-        G->g.ni[d] = G->g.nb[d] - ((nact == 3 && ragged) ? 1 : 0);
-    }
+    // 3D fields: the tiles below the last block along every dim first in the
+    // queue (whole tiles that own no upper face: the pipelined kernels' fast
+    // tiles), then the last blocks, face by face
+    for (int d = 0; d < 3; ++d) G->g.ni[d] = G->g.nb[d] - (nact == 3 ? 1 : 0);
     G->g.b0 = (p->dims[0] > 1) ? A + 1 : 1;
     G->n_anchors = na_all;
     G->ndim_active = nact;
@@ -400,7 +399,9 @@ hi_status hi_compress(const hi_params* p, const float* d_x, uint8_t* d_codes, fl
     c.buffers = (int)((p->tuning >> 2) & 3u);
     c.num_sms = num_sms();
     c.max_ctas = 0;
-    s = cuda_status(launch_compress(G.A, c, stream));
+    // 3D fields that TMA stages, at the default launch shape: the pipelined kernel
+    const bool pipe = tma && (G.A == 8 || G.A == 16) && G.ndim_active == 3 && p->tuning == 0;
+    s = cuda_status(pipe ? launch_compress_pipe(G.A, c, stream) : launch_compress(G.A, c, stream));
     stage_event(4, stream);
     return s;
 }

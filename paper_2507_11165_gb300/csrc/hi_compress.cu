@@ -3,7 +3,6 @@
 // persistent CTAs take tiles from a queue, stage them with TMA and run
 // compress_tile (hi_compress_tile.cuh) on each.
 #include "hi_compress_tile.cuh"
-#include "hi_fast.cuh"
 
 namespace hi {
 
@@ -65,14 +64,7 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
     __syncthreads();
     const bool full_ok = HasFull<A>::value && g.n[0] > 1 && g.n[1] > 1 && g.n[2] > 1;
 
-    // tiles after each CTA's first come from a queue in ascending order: the
-    // load stays balanced (edge tiles cost more) and neighbouring tiles, which
-    // share faces, are in flight together
-    const FastC fc = fast_consts(h);
-    const bool fast_ok = blockDim.x == kMaxThreads;  // the fast passes are laid out for this CTA size
-    uint32_t hacc = 0;  // fast tiles: histogram bins 126..129, a byte each
-    int nfast = 0, nslow = 0;
-    bool issued = false;  // this tile's copy was issued at the end of the previous one
+    int nslow = 0;
 
     // tiles after each CTA's first come from a queue in ascending order: the
     // load stays balanced (edge tiles cost more) and neighbouring tiles, which
@@ -82,20 +74,17 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
         const int buf = dbuf ? (it & 1) : 0;
         float* v = buf ? vbuf1 : vbuf0;
         const TileInfo ti = s_ti[it & 1];
-        const bool fast = fast_ok && fast_tile<A>(full_ok, ti);
         if (tid == 0) {
             // one buffer: this tile's copy first (the buffer is free again),
             // before the queue's round trip
-            if (use_tma && !dbuf && it > 0 && !issued) tma_issue(v, &tmap, g, tile, A, &s_mbar[0], tma_bytes);
+            if (use_tma && !dbuf && it > 0) tma_issue(v, &tmap, g, tile, A, &s_mbar[0], tma_bytes);
             const int nx = (int)gridDim.x + (int)atomicAdd(queue, 1u);
             s_next = nx;
             if (nx < g.ntiles) s_ti[(it + 1) & 1] = tile_info<A>(g, nx);
             if (use_tma && dbuf && nx < g.ntiles)
                 tma_issue(buf ? vbuf0 : vbuf1, &tmap, g, nx, A, &s_mbar[buf ^ 1], tma_bytes);
         }
-        if (fast) {
-            if (tid == 0) cs[0] = (uint8_t)kRadius;  // the owned anchor keeps the zero-error code
-        } else if (tid < 8) {  // anchors keep the zero-error code
+        if (tid < 8) {  // anchors keep the zero-error code
             const int a0 = (tid >> 2) & 1, a1 = (tid >> 1) & 1, a2 = tid & 1;
             if (a0 * A <= ti.e[0] && a1 * A <= ti.e[1] && a2 * A <= ti.e[2])
                 cs[a0 * A * Lw::CYC + a1 * A * Lw::CXC + a2 * A] = (uint8_t)kRadius;
@@ -117,39 +106,7 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
             if (s_next < g.ntiles) prefetch_rows_l2<A>(x, 4, g, s_ti[(it + 1) & 1]);
         }
         const int next = s_next;
-        issued = false;
-        if constexpr (HasFull<A>::value) {
-            if (fast) {
-                const bool bad = flevels<A, TileGeom<A>::L - 1, true, kMaxThreads>(s_sel, v, cs, fc, h);
-                fence_proxy_async_smem();
-                const bool any_out = __syncthreads_or(bad);
-                // the tile buffer is free once the owned anchor is read, unless the
-                // reconstruction is an output; outlier values are read from the field
-                const bool early = use_tma && !dbuf && recon_g == nullptr && next < g.ntiles;
-                if (tid == 0) {
-                    const float a = v[0];
-                    const int64_t ai = ((int64_t)(ti.o[0] / A) * g.na[1] + ti.o[1] / A) * g.na[2] + ti.o[2] / A;
-                    anchors[ai] = a;
-                    if (hist_on) atomicSub(&s_hist[kRadius], 1u);  // the anchor is not predicted
-                    if (early) {
-                        fence_proxy_async_smem();
-                        tma_issue(v, &tmap, g, next, A, &s_mbar[0], tma_bytes);
-                    }
-                }
-                issued = early;
-                fast_codes_out<A, kMaxThreads>(g, ti, cs, codes, (flags & kFlagVecCodes) != 0, hist_on, hacc, s_hist);
-                if (any_out) fast_outliers<A, kMaxThreads>(g, ti, cs, x, hdr, out_idx, out_val, out_cap);
-                if (recon_g) {
-                    for (int i = tid; i < A * A * A; i += blockDim.x) {
-                        const int c0 = i / (A * A), c1 = (i / A) % A, c2 = i % A;
-                        recon_g[((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2] + c2] =
-                            v[c0 * Lw::PY + c1 * Lw::PX + c2];
-                    }
-                }
-                if (hist_on && ++nfast % kFastFlush == 0) fast_hist_flush(hacc, s_hist);
-            }
-        }
-        if (!fast) {
+        {
             const CompressOut out{codes, anchors, out_idx, out_val, out_cap, recon_g, hdr,
                                   (flags & kFlagVecCodes) != 0, hist_on};
             compress_tile<A>(g, ti, v, cs, hc, s_hist, s_sel, s_lv, h, full_ok, out);
@@ -161,7 +118,6 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
         __syncthreads();
         tile = next;
     }
-    if (hist_on) fast_hist_flush(hacc, s_hist);
     if (hist_on) hist_flush(hc, s_hist, hist_g);
 }
 

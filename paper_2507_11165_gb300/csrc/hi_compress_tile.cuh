@@ -41,6 +41,8 @@ __device__ __forceinline__ void compress_tile(const FieldGeo& g, const TileInfo&
     // ---- epilogue: owned codes, histogram and outliers; recon; anchors
     const int own0 = ti.own[0] + 1, own1 = ti.own[1] + 1, own2 = ti.own[2] + 1;
     const int rows = own0 * own1;
+    constexpr bool kHot = A <= 16;  // register histogram (see hist_hot)
+    uint32_t hacc = 0;
     const bool vec_codes = vec_ok && own2 == A && A >= 8;
     if (vec_codes) {
         constexpr int CH = (A >= 16) ? 4 : 2;  // words per global vector store
@@ -78,8 +80,12 @@ __device__ __forceinline__ void compress_tile(const FieldGeo& g, const TileInfo&
                                              out_cap, g, ti.o);
             }
             if (hist_on) {
-#pragma unroll
-                for (int b = 0; b < 4 * CH; ++b) hist_count(hc, s_hist, (w[b >> 2] >> (8 * (b & 3))) & 0xff, act);
+                if constexpr (kHot) {
+                    for (int j = 0; j < CH; ++j) hist_hot4(w[j], act, hacc, s_hist);
+                } else {
+                    for (int b = 0; b < 4 * CH; ++b)
+                        hist_count(hc, s_hist, (w[b >> 2] >> (8 * (b & 3))) & 0xff, act);
+                }
             }
         }
     } else if ((own2 & 3) == 0 && own2 <= 32) {
@@ -120,8 +126,11 @@ __device__ __forceinline__ void compress_tile(const FieldGeo& g, const TileInfo&
                 outliers_append_words<A, 1>(zm, vi, v, hdr, out_idx, out_val, out_cap, g, ti.o);
             }
             if (hist_on) {
-#pragma unroll
-                for (int b = 0; b < 4; ++b) hist_count(hc, s_hist, (w >> (8 * b)) & 0xff, act);
+                if constexpr (kHot) {
+                    hist_hot4(w, act, hacc, s_hist);
+                } else {
+                    for (int b = 0; b < 4; ++b) hist_count(hc, s_hist, (w >> (8 * b)) & 0xff, act);
+                }
             }
         }
     } else if (own2 <= 32) {
@@ -142,7 +151,12 @@ __device__ __forceinline__ void compress_tile(const FieldGeo& g, const TileInfo&
                 codes[gi] = (uint8_t)code;
                 if (recon_g) recon_g[gi] = v[c0 * Lw::PY + c1 * Lw::PX + c2];
             }
-            if (hist_on) hist_count(hc, s_hist, code, act);
+            if (hist_on) {
+                if constexpr (kHot)
+                    hist_hot((uint32_t)code, act, hacc, s_hist);
+                else
+                    hist_count(hc, s_hist, code, act);
+            }
             outlier_append<A>(act && code == 0, c0 * Lw::PY + c1 * Lw::PX + c2, v, hdr, out_idx, out_val, out_cap,
                               g, ti.o);
         }
@@ -159,10 +173,18 @@ __device__ __forceinline__ void compress_tile(const FieldGeo& g, const TileInfo&
                 codes[gi] = (uint8_t)code;
                 if (recon_g) recon_g[gi] = v[c0 * Lw::PY + c1 * Lw::PX + c2];
             }
-            if (hist_on) hist_count(hc, s_hist, code, act);
+            if (hist_on) {
+                if constexpr (kHot)
+                    hist_hot((uint32_t)code, act, hacc, s_hist);
+                else
+                    hist_count(hc, s_hist, code, act);
+            }
             outlier_append<A>(act && code == 0, c0 * Lw::PY + c1 * Lw::PX + c2, v, hdr, out_idx, out_val, out_cap,
                               g, ti.o);
         }
+    }
+    if constexpr (kHot) {
+        if (hist_on) hist_hot_flush(hacc, s_hist);
     }
     if (recon_g && vec_codes) {
         const int items = rows * own2;

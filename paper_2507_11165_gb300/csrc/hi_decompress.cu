@@ -2,7 +2,7 @@
 // 2507.11165, Eq. 1, Sec. 3.2): staged code tiles, the level passes
 // (hi_passes.cuh) and the epilogue that stores the owned values.
 #define HI_LEVEL_FN __noinline__
-#include "hi_fast.cuh"
+#include "hi_passes.cuh"
 
 namespace hi {
 
@@ -72,21 +72,15 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
 
     // the 8 corner anchors of a tile, loaded one tile ahead by threads 0..7
     float a_cur = anchor_of<A>(g, anchors, blockIdx.x, s_ti[0]);
-    const FastC fc = fast_consts(h);
-    const bool fast_ok = blockDim.x == kMaxThreads;  // the fast passes are laid out for this CTA size
-    __shared__ int s_zero;  // the staged code tile holds an outlier code
-    if (tid == 0) s_zero = 0;
-    bool issued = false;  // this tile's copy was issued at the end of the previous one
 
     int it = 0;
     for (int tile = blockIdx.x; tile < g.ntiles; ++it) {
         const int buf = dbuf ? (it & 1) : 0;
         uint8_t* cs = buf ? cbuf1 : cbuf0;
         const TileInfo ti = s_ti[it & 1];
-        const bool cand = fast_ok && fast_tile<A>(full_ok, ti);
         if (tid == 0) {
             // one buffer: this tile's copy first, before the queue's round trip
-            if (use_tma && !dbuf && it > 0 && !issued) tma_issue(cs, &cmap, g, tile, A, &s_mbar[0], tma_bytes);
+            if (use_tma && !dbuf && it > 0) tma_issue(cs, &cmap, g, tile, A, &s_mbar[0], tma_bytes);
             const int nx = (int)gridDim.x + (int)atomicAdd(queue, 1u);
             s_next = nx;
             if (nx < g.ntiles) s_ti[(it + 1) & 1] = tile_info<A>(g, nx);
@@ -103,7 +97,6 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
         }
         if (use_tma) {
             const bool ok = mbar_wait(&s_mbar[buf], dbuf ? ((it >> 1) & 1) : (it & 1), kSpinLimit);
-            if (ok && cand && tile_has_zero_code<A, kMaxThreads>(cs)) s_zero = 1;
             if (!__syncthreads_and(ok)) {
                 // the copies this CTA issued may still be in flight: record the
                 // status and stay until they have landed (or a longer bound ends)
@@ -116,28 +109,11 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
         } else {
             load_codes_plain<A>(cs, codes, g, ti);
             __syncthreads();
-            if (cand && tile_has_zero_code<A, kMaxThreads>(cs)) s_zero = 1;
-            __syncthreads();
             if (s_next < g.ntiles) prefetch_rows_l2<A>(codes, 1, g, s_ti[(it + 1) & 1]);
         }
         const int next = s_next;
         const float a_nxt = anchor_of<A>(g, anchors, next, s_ti[(it + 1) & 1]);  // in flight while this tile is reconstructed
-        const bool fast = cand && s_zero == 0;
-        issued = false;
-        if constexpr (HasFull<A>::value) {
-            if (fast) {
-                // tiles without outlier codes: packed passes with no outlier checks
-                (void)flevels<A, TileGeom<A>::L - 1, false, kMaxThreads>(s_sel, v, cs, fc, h);
-                fence_proxy_async_smem();
-                __syncthreads();
-                // the codes are consumed: the next tile's copy overlaps the epilogue
-                if (use_tma && !dbuf && next < g.ntiles) {
-                    if (tid == 0) tma_issue(cs, &cmap, g, next, A, &s_mbar[0], tma_bytes);
-                    issued = true;
-                }
-            }
-        }
-        if (!fast) {
+        {
             const bool full = full_ok && ti.e[0] == A && ti.e[1] == A && ti.e[2] == A;
             if constexpr (HasFull<A>::value) {
                 if (full)
@@ -148,7 +124,6 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
                 levels_ragged<A, TileGeom<A>::L - 1, false>(s_lv, v, cs, h, ti);
             }
         }
-        if (tid == 0) s_zero = 0;  // read by every thread above, before the last barrier
 
         // ---- epilogue: owned reconstructed values
         const int own0 = ti.own[0] + 1, own1 = ti.own[1] + 1, own2 = ti.own[2] + 1;

@@ -32,6 +32,12 @@
 
 #include "hi_passes.cuh"
 
+// Level functions of the fast passes: out of line unless the including
+// kernel has the registers to take them inline.
+#ifndef HI_FAST_FN
+#define HI_FAST_FN __noinline__
+#endif
+
 namespace hi {
 
 // ---------------------------------------------------------------------------
@@ -63,6 +69,45 @@ __device__ __forceinline__ float2 p_mul(float2 a, float2 b)
     return make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y));
 }
 __device__ __forceinline__ float2 p_dup(float c) { return make_float2(c, c); }
+
+// A group of threads that runs the passes of one tile together: its size T,
+// the calling thread's index in it (its threads are FIRST .. FIRST + T - 1 of
+// the CTA) and its barrier: BAR = 0 the whole CTA (__syncthreads), BAR < 0 one
+// warp (__syncwarp), BAR > 0 the named barrier BAR over the group's T threads.
+template <int N, int FIRST, int BAR>
+struct Grp {
+    static constexpr int T = N;
+    __device__ __forceinline__ static int tid() { return (int)threadIdx.x - FIRST; }
+    __device__ __forceinline__ static void sync()
+    {
+        if constexpr (BAR == 0)
+            __syncthreads();
+        else if constexpr (BAR < 0)
+            __syncwarp();
+        else
+            asm volatile("bar.sync %0, %1;" ::"n"(BAR), "n"(N) : "memory");
+    }
+    // barrier with an OR over the group's predicates
+    __device__ __forceinline__ static bool sync_or(bool p)
+    {
+        if constexpr (BAR == 0) {
+            return __syncthreads_or(p) != 0;
+        } else if constexpr (BAR < 0) {
+            return __any_sync(0xffffffffu, p);
+        } else {
+            uint32_t r;
+            asm volatile(
+                "{\n\t.reg .pred pi, po;\n\t"
+                "setp.ne.u32 pi, %1, 0;\n\t"
+                "barrier.red.or.pred po, %2, %3, pi;\n\t"
+                "selp.u32 %0, 1, 0, po;\n\t}"
+                : "=r"(r)
+                : "r"((uint32_t)p), "n"(BAR), "n"(N)
+                : "memory");
+            return r != 0;
+        }
+    }
+};
 
 // Rounding addend whose low mantissa byte is the code: fl(t + M) = M + rint(t)
 // for |t| < 2^22 - 128 (unit spacing in [2^23, 2^24), M even, so ties go to
@@ -317,7 +362,7 @@ __host__ __device__ constexpr int fstep(int d)
 }
 
 // One pass (dim D, pass P of the level's sequence) over a whole tile by T threads.
-template <int A, int S, int P, int D0, int D1, int D2, bool CUBIC, bool COMP, int T>
+template <int A, int S, int P, int D0, int D1, int D2, bool CUBIC, bool COMP, class G>
 __device__ __forceinline__ void fpass(float* __restrict__ v, uint8_t* __restrict__ cs, const FastC& c, bool& bad)
 {
     using FL = FLay<A, COMP>;
@@ -336,8 +381,8 @@ __device__ __forceinline__ void fpass(float* __restrict__ v, uint8_t* __restrict
         constexpr int NS = (NQ + 1) / 2;
         constexpr int NI = NV + NS;
 #pragma unroll
-        for (int r0 = 0; r0 < NI; r0 += T) {
-            const int it = r0 + (int)threadIdx.x;
+        for (int r0 = 0; r0 < NI; r0 += G::T) {
+            const int it = r0 + G::tid();
             if (it < NV) {
                 const int jq = it / NPR, i2 = 2 * (it - jq * NPR);
                 const int va = jq * VQ + i2, ka = jq * KQ + i2;
@@ -353,8 +398,8 @@ __device__ __forceinline__ void fpass(float* __restrict__ v, uint8_t* __restrict
     } else {
         constexpr int NH = (NL + 1) / 2;  // pairs: line i with line i + NH
 #pragma unroll
-        for (int r0 = 0; r0 < NH; r0 += T) {
-            const int it = r0 + (int)threadIdx.x;
+        for (int r0 = 0; r0 < NH; r0 += G::T) {
+            const int it = r0 + G::tid();
             if (it < NH) {
                 const int la = it, lb = (it + NH < NL) ? it + NH : it;
                 const int qa = la / NR, qb = lb / NR;
@@ -376,7 +421,7 @@ __device__ __forceinline__ void fpass(float* __restrict__ v, uint8_t* __restrict
 // path's code layout: the points whose odd dims are the set M (see
 // md_set_full); codes of owned points only.  Scalar arithmetic: the points of
 // a phase do not share a stencil case.
-template <int A, int S, int M, bool CUBIC, bool COMP>
+template <int A, int S, int M, bool CUBIC, bool COMP, class G>
 __device__ __forceinline__ void md_set_owned(float* v, uint8_t* cs, const Hot h, bool& bad)
 {
     using Lw = Lay<A>;
@@ -384,7 +429,7 @@ __device__ __forceinline__ void md_set_owned(float* v, uint8_t* cs, const Hot h,
     constexpr int NO = A / (2 * S), NE = A / (2 * S) + 1;
     constexpr int N0 = (M & 1) ? NO : NE, N1 = (M & 2) ? NO : NE, N2 = (M & 4) ? NO : NE;
     constexpr int TOTAL = N0 * N1 * N2;
-    for (int i = threadIdx.x; i < TOTAL; i += blockDim.x) {
+    for (int i = G::tid(); i < TOTAL; i += G::T) {
         const int j2 = i % N2, r = i / N2;
         const int j1 = r % N1, j0 = r / N1;
         const int c0 = (M & 1) ? (2 * j0 + 1) * S : 2 * j0 * S;
@@ -431,69 +476,156 @@ __device__ __forceinline__ void md_set_owned(float* v, uint8_t* cs, const Hot h,
     }
 }
 
-template <int A, int S, bool CUBIC, bool COMP>
-__device__ __noinline__ bool md_full_owned(float* v, uint8_t* cs, const Hot h)
+template <int A, int S, bool CUBIC, bool COMP, class G>
+__device__ HI_FAST_FN bool md_full_owned(float* v, uint8_t* cs, const Hot h)
 {
     bool bad = false;
-    md_set_owned<A, S, 1, CUBIC, COMP>(v, cs, h, bad);  // one odd dim
-    md_set_owned<A, S, 2, CUBIC, COMP>(v, cs, h, bad);
-    md_set_owned<A, S, 4, CUBIC, COMP>(v, cs, h, bad);
-    __syncthreads();
-    md_set_owned<A, S, 3, CUBIC, COMP>(v, cs, h, bad);  // two
-    md_set_owned<A, S, 5, CUBIC, COMP>(v, cs, h, bad);
-    md_set_owned<A, S, 6, CUBIC, COMP>(v, cs, h, bad);
-    __syncthreads();
-    md_set_owned<A, S, 7, CUBIC, COMP>(v, cs, h, bad);  // three
+    md_set_owned<A, S, 1, CUBIC, COMP, G>(v, cs, h, bad);  // one odd dim
+    md_set_owned<A, S, 2, CUBIC, COMP, G>(v, cs, h, bad);
+    md_set_owned<A, S, 4, CUBIC, COMP, G>(v, cs, h, bad);
+    G::sync();
+    md_set_owned<A, S, 3, CUBIC, COMP, G>(v, cs, h, bad);  // two
+    md_set_owned<A, S, 5, CUBIC, COMP, G>(v, cs, h, bad);
+    md_set_owned<A, S, 6, CUBIC, COMP, G>(v, cs, h, bad);
+    G::sync();
+    md_set_owned<A, S, 7, CUBIC, COMP, G>(v, cs, h, bad);  // three
     return bad;
 }
 
-// One level: three passes with a barrier after the first two (the caller
-// places the one after the third).  Returns whether a point of this thread
-// was an outlier (compression).
-template <int A, int S, int D0, int D1, int D2, bool CUBIC, bool COMP, int T>
-__device__ __noinline__ bool flevel(float* v, uint8_t* cs, const FastC c)
+// One level: three passes with a barrier of the group after the first two
+// (the caller places the one after the third).  Returns whether a point of
+// this thread was an outlier (compression).
+template <int A, int S, int D0, int D1, int D2, bool CUBIC, bool COMP, class G>
+__device__ HI_FAST_FN bool flevel(float* v, uint8_t* cs, const FastC c)
 {
     bool bad = false;
-    fpass<A, S, 0, D0, D1, D2, CUBIC, COMP, T>(v, cs, c, bad);
-    __syncthreads();
-    fpass<A, S, 1, D0, D1, D2, CUBIC, COMP, T>(v, cs, c, bad);
-    __syncthreads();
-    fpass<A, S, 2, D0, D1, D2, CUBIC, COMP, T>(v, cs, c, bad);
+    fpass<A, S, 0, D0, D1, D2, CUBIC, COMP, G>(v, cs, c, bad);
+    G::sync();
+    fpass<A, S, 1, D0, D1, D2, CUBIC, COMP, G>(v, cs, c, bad);
+    G::sync();
+    fpass<A, S, 2, D0, D1, D2, CUBIC, COMP, G>(v, cs, c, bad);
     return bad;
 }
 
 // sel = 2 * perm + cubic (perm: 0 (0,1,2) 1 (0,2,1) 2 (1,0,2) 3 (1,2,0) 4 (2,0,1) 5 (2,1,0));
 // 12 / 13: the multi-dimensional scheme with linear / cubic splines
-template <int A, int S, bool COMP, int T>
+template <int A, int S, bool COMP, class G>
 __device__ __forceinline__ bool flevel_dispatch(int sel, float* v, uint8_t* cs, const FastC& c, const Hot h)
 {
     switch (sel) {
-    case 0: return flevel<A, S, 0, 1, 2, false, COMP, T>(v, cs, c);
-    case 1: return flevel<A, S, 0, 1, 2, true, COMP, T>(v, cs, c);
-    case 2: return flevel<A, S, 0, 2, 1, false, COMP, T>(v, cs, c);
-    case 3: return flevel<A, S, 0, 2, 1, true, COMP, T>(v, cs, c);
-    case 4: return flevel<A, S, 1, 0, 2, false, COMP, T>(v, cs, c);
-    case 5: return flevel<A, S, 1, 0, 2, true, COMP, T>(v, cs, c);
-    case 6: return flevel<A, S, 1, 2, 0, false, COMP, T>(v, cs, c);
-    case 7: return flevel<A, S, 1, 2, 0, true, COMP, T>(v, cs, c);
-    case 8: return flevel<A, S, 2, 0, 1, false, COMP, T>(v, cs, c);
-    case 9: return flevel<A, S, 2, 0, 1, true, COMP, T>(v, cs, c);
-    case 10: return flevel<A, S, 2, 1, 0, false, COMP, T>(v, cs, c);
-    case 11: return flevel<A, S, 2, 1, 0, true, COMP, T>(v, cs, c);
-    case 12: return md_full_owned<A, S, false, COMP>(v, cs, h);
-    default: return md_full_owned<A, S, true, COMP>(v, cs, h);
+    case 0: return flevel<A, S, 0, 1, 2, false, COMP, G>(v, cs, c);
+    case 1: return flevel<A, S, 0, 1, 2, true, COMP, G>(v, cs, c);
+    case 2: return flevel<A, S, 0, 2, 1, false, COMP, G>(v, cs, c);
+    case 3: return flevel<A, S, 0, 2, 1, true, COMP, G>(v, cs, c);
+    case 4: return flevel<A, S, 1, 0, 2, false, COMP, G>(v, cs, c);
+    case 5: return flevel<A, S, 1, 0, 2, true, COMP, G>(v, cs, c);
+    case 6: return flevel<A, S, 1, 2, 0, false, COMP, G>(v, cs, c);
+    case 7: return flevel<A, S, 1, 2, 0, true, COMP, G>(v, cs, c);
+    case 8: return flevel<A, S, 2, 0, 1, false, COMP, G>(v, cs, c);
+    case 9: return flevel<A, S, 2, 0, 1, true, COMP, G>(v, cs, c);
+    case 10: return flevel<A, S, 2, 1, 0, false, COMP, G>(v, cs, c);
+    case 11: return flevel<A, S, 2, 1, 0, true, COMP, G>(v, cs, c);
+    case 12: return md_full_owned<A, S, false, COMP, G>(v, cs, h);
+    default: return md_full_owned<A, S, true, COMP, G>(v, cs, h);
     }
 }
 
-// All levels of a whole tile, coarsest first, with a barrier between levels
-// and none after the last pass.  Returns this thread's outlier flag.
-template <int A, int LV, bool COMP, int T>
+// Levels HI .. LO of a whole tile, coarsest first, with a group barrier
+// between levels and none after the last pass.  Returns this thread's
+// outlier flag.
+template <int A, int HI, int LO, bool COMP, class G>
 __device__ __forceinline__ bool flevels(const int* s_sel, float* v, uint8_t* cs, const FastC& c, const Hot h)
 {
-    bool bad = flevel_dispatch<A, (1 << LV), COMP, T>(s_sel[LV], v, cs, c, h);
-    if constexpr (LV > 0) {
-        __syncthreads();
-        bad = flevels<A, LV - 1, COMP, T>(s_sel, v, cs, c, h) || bad;
+    bool bad = flevel_dispatch<A, (1 << HI), COMP, G>(s_sel[HI], v, cs, c, h);
+    if constexpr (HI > LO) {
+        G::sync();
+        bad = flevels<A, HI - 1, LO, COMP, G>(s_sel, v, cs, c, h) || bad;
+    }
+    return bad;
+}
+
+// ---------------------------------------------------------------------------
+// Coarse levels by a small group: one line per thread, scalar arithmetic.  A
+// coarse pass has a few dozen lines of one to four points; single lines keep
+// more of the group's lanes busy than line pairs would.
+// ---------------------------------------------------------------------------
+template <int A, int S, int P, int D0, int D1, int D2, bool CUBIC, bool COMP, class G>
+__device__ __forceinline__ void spass(float* __restrict__ v, uint8_t* __restrict__ cs, const Hot h, bool& bad)
+{
+    using FL = FLay<A, COMP>;
+    constexpr int D = (P == 0) ? D0 : (P == 1 ? D1 : D2);
+    constexpr int Q = (D == 0) ? 1 : 0, R = (D == 2) ? 1 : 2;
+    constexpr int STQ = fstep<D0, D1, D2, P, S>(Q), STR = fstep<D0, D1, D2, P, S>(R);
+    constexpr int NQ = A / STQ + 1, NR = A / STR + 1, NL = NQ * NR;
+    constexpr int NDM = A / (2 * S);
+    constexpr int VD = FL::v(D) * S, KD = FL::k(D) * S;
+    for (int l = G::tid(); l < NL; l += G::T) {
+        const int jq = l / NR, jr = l - (l / NR) * NR;
+        const int cq = jq * STQ, cr = jr * STR;
+        const int vb = cq * FL::v(Q) + cr * FL::v(R), kb = cq * FL::k(Q) + cr * FL::k(R);
+        const bool own = cq < A && cr < A;
+        float f[NDM + 1];
+#pragma unroll
+        for (int m = 0; m <= NDM; ++m) f[m] = v[vb + 2 * m * VD];
+#pragma unroll
+        for (int k = 0; k < NDM; ++k) {
+            const float pr = predict(CUBIC, k >= 1, true, k <= NDM - 2, f[k >= 1 ? k - 1 : 0], f[k], f[k + 1],
+                                     f[k + 2 <= NDM ? k + 2 : NDM]);
+            const int vi = vb + (2 * k + 1) * VD;
+            if constexpr (COMP) {
+                float xr;
+                const int code = quantize(v[vi], pr, h.eb_f, h.ebx2_f, h.r_f, xr);
+                v[vi] = xr;
+                bad = bad || code == 0;
+                if (own) cs[kb + (2 * k + 1) * KD] = (uint8_t)code;
+            } else {
+                v[vi] = dequantize(cs[kb + (2 * k + 1) * KD], pr, h.ebx2_f);
+            }
+        }
+    }
+}
+
+template <int A, int S, int D0, int D1, int D2, bool CUBIC, bool COMP, class G>
+__device__ HI_FAST_FN bool slevel(float* v, uint8_t* cs, const Hot h)
+{
+    bool bad = false;
+    spass<A, S, 0, D0, D1, D2, CUBIC, COMP, G>(v, cs, h, bad);
+    G::sync();
+    spass<A, S, 1, D0, D1, D2, CUBIC, COMP, G>(v, cs, h, bad);
+    G::sync();
+    spass<A, S, 2, D0, D1, D2, CUBIC, COMP, G>(v, cs, h, bad);
+    return bad;
+}
+
+template <int A, int S, bool COMP, class G>
+__device__ __forceinline__ bool slevel_dispatch(int sel, float* v, uint8_t* cs, const Hot h)
+{
+    switch (sel) {
+    case 0: return slevel<A, S, 0, 1, 2, false, COMP, G>(v, cs, h);
+    case 1: return slevel<A, S, 0, 1, 2, true, COMP, G>(v, cs, h);
+    case 2: return slevel<A, S, 0, 2, 1, false, COMP, G>(v, cs, h);
+    case 3: return slevel<A, S, 0, 2, 1, true, COMP, G>(v, cs, h);
+    case 4: return slevel<A, S, 1, 0, 2, false, COMP, G>(v, cs, h);
+    case 5: return slevel<A, S, 1, 0, 2, true, COMP, G>(v, cs, h);
+    case 6: return slevel<A, S, 1, 2, 0, false, COMP, G>(v, cs, h);
+    case 7: return slevel<A, S, 1, 2, 0, true, COMP, G>(v, cs, h);
+    case 8: return slevel<A, S, 2, 0, 1, false, COMP, G>(v, cs, h);
+    case 9: return slevel<A, S, 2, 0, 1, true, COMP, G>(v, cs, h);
+    case 10: return slevel<A, S, 2, 1, 0, false, COMP, G>(v, cs, h);
+    case 11: return slevel<A, S, 2, 1, 0, true, COMP, G>(v, cs, h);
+    case 12: return md_full_owned<A, S, false, COMP, G>(v, cs, h);
+    default: return md_full_owned<A, S, true, COMP, G>(v, cs, h);
+    }
+}
+
+// Levels HI .. LO (coarse strides) by a small group, coarsest first.
+template <int A, int HI, int LO, bool COMP, class G>
+__device__ __forceinline__ bool slevels(const int* s_sel, float* v, uint8_t* cs, const Hot h)
+{
+    bool bad = slevel_dispatch<A, (1 << HI), COMP, G>(s_sel[HI], v, cs, h);
+    if constexpr (HI > LO) {
+        G::sync();
+        bad = slevels<A, HI - 1, LO, COMP, G>(s_sel, v, cs, h) || bad;
     }
     return bad;
 }
@@ -524,7 +656,13 @@ __device__ __forceinline__ void fast_hist4(uint32_t w, uint32_t& hacc, uint32_t*
         const uint32_t code = __byte_perm(w, 0u, 0x4440u | (uint32_t)b);
         const uint32_t sh = code * 8u - 8u * kFastHotLo;
         hacc += __funnelshift_lc(0u, 1u, sh);  // 1 << sh; 0 for sh >= 32 (codes outside 126..129)
-        if (sh >= 32u) atomicAdd(&s_hist[code], 1u);
+        // other codes: a predicated shared-memory reduction, no branch
+        asm volatile(
+            "{\n\t.reg .pred pc;\n\t"
+            "setp.ge.u32 pc, %0, 32;\n\t"
+            "@pc red.shared.add.u32 [%1], 1;\n\t}" ::"r"(sh),
+            "r"(smem_addr(s_hist + code))
+            : "memory");
     }
 }
 
@@ -541,15 +679,15 @@ __device__ __forceinline__ void fast_hist_flush(uint32_t& hacc, uint32_t* s_hist
 
 // Owned codes (A^3 box, rows of A bytes) to the field's code array, and
 // their histogram.  vec_ok: rows may be stored as A-byte vectors.
-template <int A, int T>
+template <int A, class G>
 __device__ __forceinline__ void fast_codes_out(const FieldGeo& g, const TileInfo& ti, const uint8_t* cs,
                                                uint8_t* __restrict__ codes, bool vec_ok, bool hist_on,
                                                uint32_t& hacc, uint32_t* s_hist)
 {
     constexpr int NROW = A * A;
 #pragma unroll
-    for (int r0 = 0; r0 < NROW; r0 += T) {
-        const int r = r0 + (int)threadIdx.x;
+    for (int r0 = 0; r0 < NROW; r0 += G::T) {
+        const int r = r0 + G::tid();
         if (r < NROW) {
             const int c0 = r / A, c1 = r - (r / A) * A;
             uint8_t* dst = codes + ((int64_t)(ti.o[0] + c0) * g.n[1] + (ti.o[1] + c1)) * g.n[2] + ti.o[2];
@@ -583,15 +721,15 @@ __device__ __forceinline__ void fast_codes_out(const FieldGeo& g, const TileInfo
 // Outliers of a fast tile (code 0 in the owned box; values from the field,
 // since an outlier's reconstruction is its own value): a row per lane, the
 // warp reserves its slots with one atomic.
-template <int A, int T>
+template <int A, class G>
 __device__ __noinline__ void fast_outliers(const FieldGeo& g, const TileInfo& ti, const uint8_t* cs,
                                            const float* __restrict__ x, hi_header* hdr, uint32_t* out_idx,
                                            float* out_val, uint64_t out_cap)
 {
     constexpr int NROW = A * A, NW = A / 4;
     const int lane = threadIdx.x & 31;
-    for (int r0 = 0; r0 < NROW; r0 += T) {
-        const int r = r0 + (int)threadIdx.x;
+    for (int r0 = 0; r0 < NROW; r0 += G::T) {
+        const int r = r0 + G::tid();
         const bool act = r < NROW;
         uint32_t zm[NW];
         int cnt = 0;
@@ -635,32 +773,6 @@ __device__ __noinline__ void fast_outliers(const FieldGeo& g, const TileInfo& ti
         }
         if (over) set_status(&hdr->status, HI_ECAPACITY);
     }
-}
-
-// Decompression: whether the staged code tile (all (A+1)^3 points) holds an
-// outlier code; such tiles take the scalar passes, which read the outlier
-// values.
-template <int A, int T>
-__device__ __forceinline__ bool tile_has_zero_code(const uint8_t* cs)
-{
-    using Lw = Lay<A>;
-    constexpr int P = A + 1;
-    bool z = false;
-    for (int r = threadIdx.x; r < P * P; r += T) {
-        const int c0 = r / P, c1 = r - (r / P) * P;
-        const uint8_t* row = cs + c0 * Lw::CYD + c1 * Lw::CXD;
-        uint32_t acc = 0;
-        if constexpr (A == 16) {
-            const uint4 q = *reinterpret_cast<const uint4*>(row);
-            acc = ((q.x - 0x01010101u) & ~q.x) | ((q.y - 0x01010101u) & ~q.y) | ((q.z - 0x01010101u) & ~q.z) |
-                  ((q.w - 0x01010101u) & ~q.w);
-        } else {
-            const uint2 q = *reinterpret_cast<const uint2*>(row);
-            acc = ((q.x - 0x01010101u) & ~q.x) | ((q.y - 0x01010101u) & ~q.y);
-        }
-        z = z || (acc & 0x80808080u) != 0 || row[A] == 0;
-    }
-    return z;
 }
 
 }  // namespace hi

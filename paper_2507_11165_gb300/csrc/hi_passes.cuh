@@ -847,6 +847,43 @@ __device__ __forceinline__ void outliers_append_words(const uint32_t* zm, int vi
 // to shared-memory atomics.  Folded into the CTA histogram at kernel end.
 constexpr int kHistLo = 120, kHistBins = 16;
 
+// Histogram of tiles of A <= 16: codes 126..129 (the bulk at practical error
+// bounds) in the four bytes of one register per thread, folded into the CTA
+// histogram at the end of every tile (a thread counts fewer than 256 codes of
+// a tile); other codes by a predicated shared-memory reduction, no branch.
+constexpr uint32_t kHotLo = 126;
+
+__device__ __forceinline__ void hist_hot(uint32_t code, bool valid, uint32_t& hacc, uint32_t* s_hist)
+{
+    const uint32_t sh = code * 8u - 8u * kHotLo;
+    hacc += valid ? __funnelshift_lc(0u, 1u, sh) : 0u;  // 1 << sh; 0 for sh >= 32
+    const uint32_t cold = (valid && sh >= 32u) ? 1u : 0u;
+    asm volatile(
+        "{\n\t.reg .pred pc;\n\t"
+        "setp.ne.u32 pc, %0, 0;\n\t"
+        "@pc red.shared.add.u32 [%1], 1;\n\t}" ::"r"(cold),
+        "r"(smem_addr(s_hist + code))
+        : "memory");
+}
+
+// The four codes of a word.
+__device__ __forceinline__ void hist_hot4(uint32_t w, bool valid, uint32_t& hacc, uint32_t* s_hist)
+{
+#pragma unroll
+    for (int b = 0; b < 4; ++b) hist_hot(__byte_perm(w, 0u, 0x4440u | (uint32_t)b), valid, hacc, s_hist);
+}
+
+// Fold the register counters into the CTA histogram and clear them (whole warps).
+__device__ __forceinline__ void hist_hot_flush(uint32_t& hacc, uint32_t* s_hist)
+{
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const uint32_t n = __reduce_add_sync(0xffffffffu, (hacc >> (8 * b)) & 0xffu);
+        if ((threadIdx.x & 31) == 0 && n) atomicAdd(&s_hist[kHotLo + b], n);
+    }
+    hacc = 0;
+}
+
 __device__ __forceinline__ void hist_count(uint16_t* hc, uint32_t* s_hist, int code, bool valid)
 {
     const unsigned k = (unsigned)(code - kHistLo);
