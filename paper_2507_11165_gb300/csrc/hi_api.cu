@@ -399,9 +399,7 @@ hi_status hi_compress(const hi_params* p, const float* d_x, uint8_t* d_codes, fl
     c.buffers = (int)((p->tuning >> 2) & 3u);
     c.num_sms = num_sms();
     c.max_ctas = 0;
-    // 3D fields that TMA stages, at the default launch shape: the pipelined kernel
-    const bool pipe = tma && (G.A == 8 || G.A == 16) && G.ndim_active == 3 && p->tuning == 0;
-    s = cuda_status(pipe ? launch_compress_pipe(G.A, c, stream) : launch_compress(G.A, c, stream));
+    s = cuda_status(launch_compress(G.A, c, stream));
     stage_event(4, stream);
     return s;
 }

@@ -90,8 +90,6 @@ struct TuneCands {
 };
 
 cudaError_t launch_compress(int A, const CompressLaunch& c, cudaStream_t st);
-// 3D fields staged by TMA with A = 8 or 16: the two-stage pipeline kernel (hi_compress_pipe.cu)
-cudaError_t launch_compress_pipe(int A, const CompressLaunch& c, cudaStream_t st);
 cudaError_t launch_decompress(int A, const DecompressLaunch& c, cudaStream_t st);
 size_t compress_smem_bytes(int A, int b0);
 
