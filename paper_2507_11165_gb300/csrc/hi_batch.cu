@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(kMaxThreads, 5)
     float* const vbuf0 = reinterpret_cast<float*>(smem);
     float* const vbuf1 = reinterpret_cast<float*>(smem + (dbuf ? vb_bytes : 0));
     uint8_t* cs = smem + (dbuf ? 2 : 1) * vb_bytes;
-    uint16_t* hc = reinterpret_cast<uint16_t*>(cs + round128((A + 1) * Lw::P * Lw::CXC));
+    uint16_t* hc = A <= 16 ? nullptr : reinterpret_cast<uint16_t*>(cs + round128((A + 1) * Lw::P * Lw::CXC));
     __shared__ uint32_t s_hist[256];
     __shared__ __align__(8) uint64_t s_mbar[2];
     __shared__ BatchCur s_cur[2];  // the current field's record; the next field's, arriving
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kMaxThreads, 5)
 
     const int tid = threadIdx.x;
     for (int i = tid; i < 256; i += blockDim.x) s_hist[i] = 0;
-    for (int k = 0; k < kHistBins; ++k) hc[k * blockDim.x + tid] = 0;
+    for (int k = 0; hc && k < kHistBins; ++k) hc[k * blockDim.x + tid] = 0;
     if (tid == 0) {
         mbar_init(&s_mbar[0], 1);
         mbar_init(&s_mbar[1], 1);

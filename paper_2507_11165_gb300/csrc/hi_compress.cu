@@ -10,7 +10,7 @@ namespace hi {
 // Predict + quantize
 // ---------------------------------------------------------------------------
 template <int A>
-__global__ void __launch_bounds__(kMaxThreads, 6)
+__global__ void __launch_bounds__(kMaxThreads, 7)
     k_compress(const __grid_constant__ CUtensorMap tmap, const FieldGeo g, const float* __restrict__ x,
                uint8_t* __restrict__ codes, float* __restrict__ anchors, uint32_t* __restrict__ out_idx,
                float* __restrict__ out_val, const uint64_t out_cap, uint32_t* __restrict__ hist_g,
@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
     float* const vbuf0 = reinterpret_cast<float*>(smem);
     float* const vbuf1 = reinterpret_cast<float*>(smem + (dbuf ? vb_bytes : 0));
     uint8_t* cs = smem + (dbuf ? 2 : 1) * vb_bytes;
-    uint16_t* hc = reinterpret_cast<uint16_t*>(cs + round128(g.b0 * Lw::P * Lw::CXC));  // [kHistBins][threads]
+    uint16_t* hc = A <= 16 ? nullptr : reinterpret_cast<uint16_t*>(cs + round128(g.b0 * Lw::P * Lw::CXC));  // [kHistBins][threads]
     __shared__ uint32_t s_hist[256];
     __shared__ __align__(8) uint64_t s_mbar[2];
     __shared__ hi_level s_lv[HI_MAX_LEVELS];
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
 
     for (int i = tid; i < 256; i += blockDim.x) s_hist[i] = 0;
     if (hist_on)
-        for (int k = 0; k < kHistBins; ++k) hc[k * blockDim.x + tid] = 0;
+        for (int k = 0; hc && k < kHistBins; ++k) hc[k * blockDim.x + tid] = 0;
     if (tid < HI_MAX_LEVELS) {
         s_lv[tid] = hdr->level[tid];
         s_sel[tid] = perm_sel(s_lv[tid]);

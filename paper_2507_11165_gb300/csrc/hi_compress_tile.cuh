@@ -215,6 +215,7 @@ constexpr int kHistFoldTiles = 64;
 // Fold the calling thread's counters into s_hist and clear them (whole warps).
 __device__ __forceinline__ void hist_fold(uint16_t* hc, uint32_t* s_hist)
 {
+    if (hc == nullptr) return;  // tiles of A <= 16 count in registers (hist_hot)
     const int tid = threadIdx.x;
     for (int k = 0; k < kHistBins; ++k) {
         const uint32_t c = __reduce_add_sync(0xffffffffu, (uint32_t)hc[k * blockDim.x + tid]);
@@ -232,7 +233,7 @@ __device__ __forceinline__ void hist_fold(uint16_t* hc, uint32_t* s_hist)
 __device__ __forceinline__ void hist_flush_to(uint16_t* hc, uint32_t* s_hist, uint32_t* hist_g)
 {
     const int tid = threadIdx.x;
-    for (int k = 0; k < kHistBins; ++k) {
+    for (int k = 0; hc != nullptr && k < kHistBins; ++k) {
         const uint32_t c = __reduce_add_sync(0xffffffffu, (uint32_t)hc[k * blockDim.x + tid]);
         hc[k * blockDim.x + tid] = 0;
         if ((tid & 31) == 0 && c) atomicAdd(&hist_g[kHistLo + k], c);

@@ -900,8 +900,10 @@ __device__ __forceinline__ void hist_count(uint16_t* hc, uint32_t* s_hist, int c
 template <int A>
 size_t compress_smem_t(int b0, bool dbuf, int threads)
 {
+    // 16-bit per-thread histogram counters only where the register counters
+    // of hist_hot could overflow within a tile (A = 32)
     return (dbuf ? 2 : 1) * (size_t)vbuf_bytes<A>(b0) + (size_t)round128(b0 * Lay<A>::P * Lay<A>::CXC) +
-           (size_t)kHistBins * threads * sizeof(uint16_t);
+           (A > 16 ? (size_t)kHistBins * threads * sizeof(uint16_t) : 0);
 }
 
 template <int A>
