@@ -168,7 +168,9 @@ HI_API hi_status hi_compress(const hi_params* p, const float* d_x, uint8_t* d_co
  *   - Set-up: the first call on each device (the device current at the
  *     call) looks up the scratch array's device address, which may load the
  *     library's device code; make that first call before any stream capture
- *     begins.  A failed look-up returns HI_ECUDA.
+ *     begins.  A failed look-up returns HI_ECUDA.  The address is kept per
+ *     device and context: after a device reset (a new context) the next call
+ *     looks it up again, so make that call before any capture too.
  *   - Zero state: nothing in the scratch has to start at zero; the call's
  *     first kernel resets the counters it uses.
  *   - Races: every call on a device shares that device's one scratch array.
@@ -375,6 +377,38 @@ HI_API hi_status hi_tp_encode(const uint8_t* d_in, uint64_t n, uint8_t* d_out, u
                               void* d_ws, size_t ws_bytes, cudaStream_t stream);
 HI_API hi_status hi_tp_decode(const uint8_t* d_in, uint64_t in_len, uint8_t* d_out, uint64_t n, uint32_t* d_status,
                               void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
+/* The absolute bound and the float32 quantizer constants of Eq. 1 from a
+ * value range, on the host, with the same IEEE double operations the device
+ * uses in hi_compress (Sec. 6.1.4 read as eps = eb * (vmax - vmin); eps = eb
+ * for a zero range or HI_EB_ABS; eb_f = the largest float <= eps, ebx2_f =
+ * fl(2 eps), r_f = fl(1 / (2 eps))).  For a field processed in parts
+ * (out of core, or one part per GPU): combine the parts' vmin / vmax
+ * (hi_value_range), resolve eps here and compress each part at the absolute
+ * bound eps.  Host only, no CUDA call.  HI_EINVAL for a NULL out, a bad mode
+ * or eb, or constants that are not finite and positive. */
+typedef struct {
+    double eps;
+    float eb_f, ebx2_f, r_f;
+    float pad;
+} hi_eps;
+HI_API hi_status hi_resolve_eps(uint32_t eb_mode, double eb, float vmin, float vmax, hi_eps* out);
+
+/* Entropy-estimated compressed size (the record a Huffman-type entropy coder,
+ * Sec. 5.2.2, approaches): H = -sum p_k log2 p_k over the 256-bin code
+ * histogram h_hist (bins in ascending order, IEEE double), est_bytes =
+ * ceil(N_pred H / 8) + 8 n_outliers + 4 n_anchors + header_bytes with N_pred
+ * the histogram total, cr = 4 n_points / est_bytes, bit_rate = 8 est_bytes /
+ * n_points (bits per value).  Host only.  HI_EINVAL for NULL pointers or
+ * n_points = 0. */
+typedef struct {
+    double entropy_bits;
+    uint64_t est_bytes;
+    double cr;
+    double bit_rate;
+} hi_cr_estimate;
+HI_API hi_status hi_estimate_cr(const uint32_t* h_hist, uint64_t n_outliers, uint64_t n_anchors, uint64_t n_points,
+                                uint64_t header_bytes, hi_cr_estimate* out);
 
 /* Copy the device header to the host (synchronises the stream). */
 HI_API hi_status hi_header_read(const hi_header* d_header, hi_header* h_header, cudaStream_t stream);

@@ -240,19 +240,44 @@ int threads_for(const Geometry& G, uint32_t tuning)
 // this library's device image, so that the call allocates nothing.
 static __device__ __align__(256) unsigned char g_static_ws[HI_STATIC_WS_BYTES];
 
+// The current context (driver API, through the runtime's entry-point query);
+// nullptr when it cannot be had.
+using PFN_ctx_get_current = CUresult (*)(CUcontext*);
+CUcontext current_context()
+{
+    static PFN_ctx_get_current fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_ctx_get_current>(ptr);
+    });
+    CUcontext c = nullptr;
+    if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+    return c;
+}
+
 // Device address of g_static_ws on the current device, looked up once per
-// device; nullptr if the look-up fails.
+// device and context: a device reset (or a released and re-created primary
+// context) gives a new context, and the address is looked up again; nullptr
+// if the look-up fails.
 void* static_ws_address()
 {
     static std::mutex mu;
     static void* addr[kMaxDevices] = {};
+    static CUcontext ctx[kMaxDevices] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    const CUcontext c = current_context();
     std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
+    if (!addr[dev] || !c || ctx[dev] != c) {
         void* a = nullptr;
         if (cudaGetSymbolAddress(&a, g_static_ws) != cudaSuccess) return nullptr;
         addr[dev] = a;
+        ctx[dev] = current_context();  // the look-up has made the device's context current
     }
     return addr[dev];
 }
@@ -290,6 +315,53 @@ const char* hi_status_str(int s)
     case HI_ECORRUPT: return "corrupt compressed record";
     default: return "unknown status";
     }
+}
+
+hi_status hi_resolve_eps(uint32_t eb_mode, double eb, float vmin, float vmax, hi_eps* out)
+{
+    if (!out || (eb_mode != HI_EB_ABS && eb_mode != HI_EB_REL) || !(eb > 0.0) || !std::isfinite(eb))
+        return HI_EINVAL;
+    double eps = eb;
+    if (eb_mode == HI_EB_REL) {
+        const double range = (double)vmax - (double)vmin;
+        if (range > 0.0) eps = eb * range;
+    }
+    const double two_eps = 2.0 * eps;
+    float eb_f = (float)eps;  // round to nearest, then down to the largest float <= eps
+    if ((double)eb_f > eps) eb_f = std::nextafter(eb_f, 0.0f);
+    const float ebx2_f = (float)two_eps;
+    const float r_f = (float)(1.0 / two_eps);
+    if (!(eps > 0.0) || !std::isfinite(eps) || !(eb_f > 0.0f) || !std::isfinite(ebx2_f) || !(r_f > 0.0f) ||
+        !std::isfinite(r_f))
+        return HI_EINVAL;
+    out->eps = eps;
+    out->eb_f = eb_f;
+    out->ebx2_f = ebx2_f;
+    out->r_f = r_f;
+    out->pad = 0.0f;
+    return HI_OK;
+}
+
+hi_status hi_estimate_cr(const uint32_t* h_hist, uint64_t n_outliers, uint64_t n_anchors, uint64_t n_points,
+                         uint64_t header_bytes, hi_cr_estimate* out)
+{
+    if (!h_hist || !out || n_points == 0) return HI_EINVAL;
+    double total = 0.0;
+    for (int k = 0; k < 256; ++k) total += (double)h_hist[k];
+    double H = 0.0;
+    if (total > 0.0)
+        for (int k = 0; k < 256; ++k)
+            if (h_hist[k] > 0) {
+                const double q = (double)h_hist[k] / total;
+                H -= q * std::log2(q);
+            }
+    const uint64_t nbytes =
+        (uint64_t)std::ceil(total * H / 8.0) + 8 * n_outliers + 4 * n_anchors + header_bytes;
+    out->entropy_bits = H;
+    out->est_bytes = nbytes;
+    out->cr = nbytes > 0 ? 4.0 * (double)n_points / (double)nbytes : INFINITY;
+    out->bit_rate = 8.0 * (double)nbytes / (double)n_points;
+    return HI_OK;
 }
 
 hi_status hi_query(const hi_params* p, uint64_t* n_points, uint64_t* n_anchors, uint64_t* n_blocks,

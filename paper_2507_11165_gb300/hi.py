@@ -69,10 +69,20 @@ class HiBatchPlan(ctypes.Structure):
                 ("reserved", ctypes.c_uint64 * 4)]
 
 
+class HiEps(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("eb_f", ctypes.c_float), ("ebx2_f", ctypes.c_float),
+                ("r_f", ctypes.c_float), ("pad", ctypes.c_float)]
+
+
+class HiCrEstimate(ctypes.Structure):
+    _fields_ = [("entropy_bits", ctypes.c_double), ("est_bytes", ctypes.c_uint64), ("cr", ctypes.c_double),
+                ("bit_rate", ctypes.c_double)]
+
+
 HEADER_BYTES = ctypes.sizeof(HiHeader)
 SYMBOLS = ("hi_query", "hi_compress", "hi_decompress", "hi_autotune", "hi_autotune_errors", "hi_header_read",
            "hi_status_str", "hi_version", "hi_set_stage_events", "hi_compress_static_ws", "hi_batch_query",
-           "hi_batch_prepare", "hi_compress_batch", "hi_batch_tune_launch")
+           "hi_batch_prepare", "hi_compress_batch", "hi_batch_tune_launch", "hi_resolve_eps", "hi_estimate_cr")
 STATIC_WS_BYTES = 1 << 20  # HI_STATIC_WS_BYTES
 DECOMPRESS_WS_BYTES = 256  # HI_DECOMPRESS_WS_BYTES
 
@@ -116,12 +126,16 @@ def lib():
             L.hi_tp_decode.argtypes = [P, u64, P, u64, P, P, sz, P]
             L.hi_unreorder_codes.argtypes = [ctypes.POINTER(HiParams), P, P, P]
             L.hi_set_stage_events.argtypes = [P, ctypes.c_uint32]
+            L.hi_resolve_eps.argtypes = [ctypes.c_uint32, ctypes.c_double, ctypes.c_float, ctypes.c_float,
+                                         ctypes.POINTER(HiEps)]
+            L.hi_estimate_cr.argtypes = [P, u64, u64, u64, u64, ctypes.POINTER(HiCrEstimate)]
             L.hi_status_str.argtypes = [ctypes.c_int]
             L.hi_status_str.restype = ctypes.c_char_p
             L.hi_version.restype = ctypes.c_uint32
             for f in ("hi_query", "hi_compress", "hi_decompress", "hi_autotune", "hi_autotune_errors",
                       "hi_header_read", "hi_set_stage_events", "hi_compress_static_ws", "hi_batch_query",
-                      "hi_batch_prepare", "hi_compress_batch", "hi_batch_tune_launch"):
+                      "hi_batch_prepare", "hi_compress_batch", "hi_batch_tune_launch", "hi_resolve_eps",
+                      "hi_estimate_cr"):
                 getattr(L, f).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -519,15 +533,24 @@ class Batch:
 
 
 def estimate_cr(hist, n_out, n_anchors, n_points, header_bytes=None):
-    """Entropy-estimated size: ceil(N_pred H / 8) + 8 n_out + 4 n_anchors + header.
-
-    H = order-0 entropy of the code histogram in bits (what an ideal entropy
-    coder such as the Huffman stage of Sec. 5.2.2 approaches)."""
+    """Entropy-estimated size of the record (hi_estimate_cr): ceil(N_pred H / 8)
+    + 8 n_out + 4 n_anchors + header bytes, H the order-0 entropy of the
+    256-bin code histogram in bits (what an entropy coder such as the Huffman
+    stage of Sec. 5.2.2 approaches).  Host only."""
     import numpy as np
-    hb = HEADER_BYTES if header_bytes is None else header_bytes
-    h = np.asarray(hist, dtype=np.float64)
-    tot = float(h.sum())
-    nz = h[h > 0] / tot if tot > 0 else np.zeros(0)
-    H = float(-(nz * np.log2(nz)).sum()) if nz.size else 0.0
-    nbytes = math.ceil(tot * H / 8.0) + 8 * n_out + 4 * n_anchors + hb
-    return dict(entropy_bits=H, est_bytes=int(nbytes), cr=4.0 * n_points / nbytes, bit_rate=32.0 * nbytes / (4.0 * n_points))
+    h = np.ascontiguousarray(np.asarray(hist).astype(np.uint32).reshape(256))
+    out = HiCrEstimate()
+    hb = HEADER_BYTES if header_bytes is None else int(header_bytes)
+    _check(lib().hi_estimate_cr(ctypes.c_void_p(h.ctypes.data), int(n_out), int(n_anchors), int(n_points), hb,
+                                ctypes.byref(out)), "hi_estimate_cr")
+    return dict(entropy_bits=out.entropy_bits, est_bytes=int(out.est_bytes), cr=out.cr, bit_rate=out.bit_rate)
+
+
+def resolve_eps(mode, eb, vmin, vmax):
+    """The absolute bound and float32 constants of Eq. 1 for a value range
+    (hi_resolve_eps): what the device derives in hi_compress, for fields
+    compressed in parts at the combined range."""
+    out = HiEps()
+    m = {"abs": EB_ABS, "rel": EB_REL}[mode] if isinstance(mode, str) else int(mode)
+    _check(lib().hi_resolve_eps(m, float(eb), float(vmin), float(vmax), ctypes.byref(out)), "hi_resolve_eps")
+    return dict(eps=out.eps, eb_f=out.eb_f, ebx2_f=out.ebx2_f, r_f=out.r_f)

@@ -107,9 +107,10 @@ class Server:
     def _retire(self, slot, t_done, status):
         req, h, b, t_admit = self.in_flight.pop(slot)
         self.bytes_in_flight -= b
+        extra = self.ex.extra_bytes(h)  # a capacity re-run's larger outlier arrays stay with the record
         self.ex.release(h)
         if req.op == "compress" and status == 0:
-            self.records[req.id] = self.ex.record_bytes(req)
+            self.records[req.id] = self.ex.record_bytes(req) + extra
             while len(self.records) > self.keep_records:
                 rid, _ = self.records.popitem(last=False)
                 self.ex.drop_record(rid)
@@ -123,6 +124,13 @@ class Server:
             if r is not None:
                 self._retire(slot, r[0], r[1])
                 n += 1
+            else:
+                # a capacity re-run holds more outlier memory: count it in flight
+                grown = device_bytes(req.op, req.side, req.eb) + self.ex.extra_bytes(h)
+                if grown != b:
+                    self.bytes_in_flight += grown - b
+                    self.in_flight[slot] = (req, h, grown, t_admit)
+                    self.peak_bytes = max(self.peak_bytes, self.bytes_in_flight + self._record_bytes())
         return n
 
     def run(self, requests: List[Request], idle_sleep: float = 0.0) -> List[Done]:
@@ -220,6 +228,9 @@ class FakeExecutor:
     def record_bytes(self, req):
         self.records.add(req.id)
         return req.side ** 3 * 2
+
+    def extra_bytes(self, h):
+        return 0
 
     def drop_record(self, rid):
         self.records.discard(rid)
@@ -350,6 +361,7 @@ class GpuExecutor:
                     h["hdr"].copy_(b.header, non_blocking=True)
                     h["ev"] = torch.cuda.Event(enable_timing=True)
                     h["ev"].record(h["st"])
+                h["extra"] = 8 * max(0, int(hd.n_outliers) - int(h["b"].out_cap))
                 h["b"] = b
                 h["cap"] = None  # not a pooled size
                 h["retried"] = True
@@ -396,6 +408,10 @@ class GpuExecutor:
     def record_bytes(self, req):
         n = req.side ** 3
         return n + 8 * outlier_capacity(req.side, req.eb) + 4 * (n // 64 + 1) + 1024
+
+    def extra_bytes(self, h):
+        """Device bytes a request holds beyond device_bytes(): a capacity re-run's larger outlier arrays."""
+        return int(h.get("extra", 0))
 
     def drop_record(self, rid):
         if self.readers.get(rid, 0) > 0:

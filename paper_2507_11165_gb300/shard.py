@@ -40,16 +40,6 @@ def shard_bounds(n0: int, A: int, parts: int) -> List[dict]:
     return out
 
 
-def eps_from_range(eb_mode: str, eb: float, vmin: float, vmax: float) -> float:
-    """The absolute bound (Eq. 1): eb, or eb * (vmax - vmin) for the
-    value-range-relative bound (eb when the range is 0), in IEEE double as
-    the library derives it on the device."""
-    if eb_mode == "abs":
-        return float(eb)
-    r = float(vmax) - float(vmin)
-    return float(eb) * r if r > 0.0 else float(eb)
-
-
 def sample_blocks(shape, A: int) -> List[int]:
     """Row-major ids of the auto-tuner's sample blocks of the whole field
     (Sec. 5.1.3): every (n_blocks / m)-th block, m = max(1, round(0.002 N /
@@ -98,7 +88,7 @@ def compress_in_sequence(x, eb: float, A: int, parts: int, levels, mode: str = "
             vmin, vmax = min(vmin, float(c.h.vmin)), max(vmax, float(c.h.vmax))
     if vmin > vmax:
         vmin = vmax = 0.0
-    eps = eps_from_range(mode, eb, vmin, vmax)
+    eps = hi.resolve_eps(mode, eb, vmin, vmax)["eps"]
     codes, anchors, oidx, oval = [], [], [], []
     hist = torch.zeros(256, dtype=torch.int64, device=x.device)
     cst = None
@@ -192,7 +182,7 @@ def compress_out_of_core(x_host, eb: float, A: int, levels, mode: str = "rel", s
                 vmin, vmax = min(vmin, float(h.vmin)), max(vmax, float(h.vmax))
         if vmin > vmax:
             vmin = vmax = 0.0
-    eps = eps_from_range(mode, eb, vmin, vmax)
+    eps = hi.resolve_eps(mode, eb, vmin, vmax)["eps"]
 
     # pass 2: each shard with its halo plane at the absolute bound eps
     codes = np.empty(n0 * plane, dtype=np.uint8)

@@ -100,3 +100,31 @@ def test_request_stream_recipe():
             assert src.op == "compress" and src.t < r.t and src.side == r.side
     frac = sum(r.op == "decompress" for r in reqs) / len(reqs)
     assert 0.35 < frac < 0.6
+
+
+class _GrowingExecutor(FakeExecutor):
+    """A stand-in whose request 0 re-runs with larger outlier arrays after its first poll."""
+
+    def __init__(self, extra):
+        super().__init__(lambda r: 0.01)
+        self.extra = extra
+        self.polled = set()
+
+    def poll(self, h):
+        self.polled.add(h[0].id)
+        return super().poll(h)
+
+    def extra_bytes(self, h):
+        return self.extra if (h[0].id == 0 and 0 in self.polled) else 0
+
+
+def test_capacity_rerun_counts_in_the_budget():
+    need = serve.device_bytes("compress", 16)
+    extra = 5 * need
+    reqs = [Request(id=0, t=0.0, op="compress", side=16, eb=1e-3)]
+    ex = _GrowingExecutor(extra)
+    sv = Server(ex, slots=2, budget_bytes=10 ** 12, keep_records=4)
+    sv.run(reqs)
+    assert sv.peak_bytes >= need + extra  # the grown request was counted while in flight
+    assert sv.bytes_in_flight == 0
+    assert sv.records[0] == ex.record_bytes(reqs[0]) + extra  # and its kept record holds the larger arrays

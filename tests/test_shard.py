@@ -10,7 +10,7 @@ import torch
 import torch.distributed as dist
 import torch.multiprocessing as mp
 
-from paper_2507_11165_gb300 import fields, shard
+from paper_2507_11165_gb300 import fields, hi, shard
 
 SHAPE = (101, 80, 80)  # 13 blocks along d0 at A = 8, the last one ragged; 3 auto-tune samples
 A = 8
@@ -27,12 +27,6 @@ def test_shard_bounds_cover_the_field():
             assert a["own_lo"] % A_ == 0 and a["own_hi"] % A_ == 0
         sizes = [s["t_hi"] - s["t_lo"] for s in b]
         assert max(sizes) - min(sizes) <= 1 and min(sizes) >= 1
-
-
-def test_eps_from_range():
-    assert shard.eps_from_range("abs", 0.5, 1.0, 2.0) == 0.5
-    assert shard.eps_from_range("rel", 1e-3, -1.0, 3.0) == 1e-3 * 4.0
-    assert shard.eps_from_range("rel", 1e-3, 2.0, 2.0) == 1e-3  # constant field
 
 
 def _free_port():
@@ -74,7 +68,7 @@ def _worker(rank, world, port, outdir):
     dist.all_reduce(mn, op=dist.ReduceOp.MIN)
     dist.all_reduce(mx, op=dist.ReduceOp.MAX)
     cst = oracle.eps_constants(np.array([mn.item(), mx.item()], dtype=np.float32), 1, EB)
-    assert cst["eps"] == shard.eps_from_range("rel", EB, mn.item(), mx.item())
+    assert cst["eps"] == hi.resolve_eps("rel", EB, mn.item(), mx.item())["eps"]
     # auto-tune: the errors of the global sample blocks this rank holds, then
     # every sample's errors on every rank, summed in global sample order
     gids = shard.sample_blocks(SHAPE, A)
