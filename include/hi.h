@@ -410,6 +410,20 @@ typedef struct {
 HI_API hi_status hi_estimate_cr(const uint32_t* h_hist, uint64_t n_outliers, uint64_t n_anchors, uint64_t n_points,
                                 uint64_t header_bytes, hi_cr_estimate* out);
 
+/* The auto-tuner's per-level choice (Sec. 5.1.3) from per-sample error
+ * sums, on the host: h_err holds m * L * ncfg doubles (sample-major, then
+ * level, then candidate, as hi_autotune_errors returns them; m, L, ncfg as
+ * hi_autotune_errors reports for p).  Per (level, candidate) the samples are
+ * summed in the order the device sums them (sample k into partial k mod 32,
+ * ascending k, then the 32 partials by the butterfly j + (j ^ 16), j + (j ^
+ * 8), ..., j + (j ^ 1)); each level takes the smallest sum, ties to the first
+ * candidate of hi_autotune's enumeration.  For a field compressed in parts:
+ * the parts' rows of the whole field's sample blocks, gathered into one
+ * array, give the choice the whole field would make.  Writes level[0 .. L)
+ * of *out and leaves its other fields as they are.  Host only; HI_EINVAL for
+ * bad arguments or a short h_err. */
+HI_API hi_status hi_autotune_select(const hi_params* p, const double* h_err, size_t h_err_len, hi_params* out);
+
 /* Copy the device header to the host (synchronises the stream). */
 HI_API hi_status hi_header_read(const hi_header* d_header, hi_header* h_header, cudaStream_t stream);
 

@@ -552,6 +552,39 @@ hi_status hi_autotune(const hi_params* p, const float* d_x, hi_header* d_header,
     return enqueue_tune(G, d_x, d_header, d_ws, stream);
 }
 
+hi_status hi_autotune_select(const hi_params* p, const double* h_err, size_t h_err_len, hi_params* out)
+{
+    if (!p || !h_err || !out) return HI_EINVAL;
+    Geometry G;
+    hi_params q = *p;
+    if (q.autotune == 0) q.autotune = 1;
+    const hi_status s = make_geometry(&q, &G);
+    if (s != HI_OK) return s;
+    const int m = G.m, L = G.L, nc = G.cands.ncfg;
+    if (h_err_len < (size_t)m * L * nc) return HI_EINVAL;
+    for (int l = 0; l < L; ++l) {
+        int best = 0;
+        double best_sum = 0.0;
+        for (int c = 0; c < nc; ++c) {
+            double part[32];  // the device's lane partials, then its xor butterfly
+            for (int j = 0; j < 32; ++j) {
+                double a = 0.0;
+                for (int k = j; k < m; k += 32) a += h_err[((size_t)k * L + l) * nc + c];
+                part[j] = a;
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                double nxt[32];
+                for (int j = 0; j < 32; ++j) nxt[j] = part[j] + part[j ^ off];
+                for (int j = 0; j < 32; ++j) part[j] = nxt[j];
+            }
+            if (c == 0 || part[0] < best_sum) best = c, best_sum = part[0];
+        }
+        out->level[l].interp = G.cands.interp[best];
+        for (int k = 0; k < 3; ++k) out->level[l].order[k] = G.cands.order[best][k];
+    }
+    return HI_OK;
+}
+
 hi_status hi_autotune_errors(const hi_params* p, const void* d_ws, double* h_err, size_t h_err_len, uint32_t* m,
                              uint32_t* L, uint32_t* ncfg, cudaStream_t stream)
 {

@@ -82,7 +82,8 @@ class HiCrEstimate(ctypes.Structure):
 HEADER_BYTES = ctypes.sizeof(HiHeader)
 SYMBOLS = ("hi_query", "hi_compress", "hi_decompress", "hi_autotune", "hi_autotune_errors", "hi_header_read",
            "hi_status_str", "hi_version", "hi_set_stage_events", "hi_compress_static_ws", "hi_batch_query",
-           "hi_batch_prepare", "hi_compress_batch", "hi_batch_tune_launch", "hi_resolve_eps", "hi_estimate_cr")
+           "hi_batch_prepare", "hi_compress_batch", "hi_batch_tune_launch", "hi_resolve_eps", "hi_estimate_cr",
+           "hi_autotune_select")
 STATIC_WS_BYTES = 1 << 20  # HI_STATIC_WS_BYTES
 DECOMPRESS_WS_BYTES = 256  # HI_DECOMPRESS_WS_BYTES
 
@@ -129,13 +130,14 @@ def lib():
             L.hi_resolve_eps.argtypes = [ctypes.c_uint32, ctypes.c_double, ctypes.c_float, ctypes.c_float,
                                          ctypes.POINTER(HiEps)]
             L.hi_estimate_cr.argtypes = [P, u64, u64, u64, u64, ctypes.POINTER(HiCrEstimate)]
+            L.hi_autotune_select.argtypes = [ctypes.POINTER(HiParams), P, sz, ctypes.POINTER(HiParams)]
             L.hi_status_str.argtypes = [ctypes.c_int]
             L.hi_status_str.restype = ctypes.c_char_p
             L.hi_version.restype = ctypes.c_uint32
             for f in ("hi_query", "hi_compress", "hi_decompress", "hi_autotune", "hi_autotune_errors",
                       "hi_header_read", "hi_set_stage_events", "hi_compress_static_ws", "hi_batch_query",
                       "hi_batch_prepare", "hi_compress_batch", "hi_batch_tune_launch", "hi_resolve_eps",
-                      "hi_estimate_cr"):
+                      "hi_estimate_cr", "hi_autotune_select"):
                 getattr(L, f).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -554,3 +556,38 @@ def resolve_eps(mode, eb, vmin, vmax):
     m = {"abs": EB_ABS, "rel": EB_REL}[mode] if isinstance(mode, str) else int(mode)
     _check(lib().hi_resolve_eps(m, float(eb), float(vmin), float(vmax), ctypes.byref(out)), "hi_resolve_eps")
     return dict(eps=out.eps, eb_f=out.eb_f, ebx2_f=out.ebx2_f, r_f=out.r_f)
+
+
+def tune_errors(x, anchor_stride=16, md=False, stream=None):
+    """Per-sample, per-level, per-candidate auto-tune error sums of a device
+    field (hi_autotune, then hi_autotune_errors): array [m, L, ncfg]."""
+    if not x.is_cuda or x.dtype != torch.float32 or not x.is_contiguous():
+        raise ValueError("x must be a contiguous float32 CUDA tensor")
+    p = make_params(tuple(x.shape), 1.0, "abs", anchor_stride, autotune=2 if md else True)
+    b = alloc(p, tuple(x.shape), x.device, out_cap=0, hist=False, recon=False)
+    _check(lib().hi_autotune(ctypes.byref(p), _ptr(x), _ptr(b.header), _ptr(b.ws), b.ws.numel(), _stream(stream)),
+           "hi_autotune")
+    return autotune_errors(b, stream)
+
+
+def autotune_select(shape, anchor_stride, err, md=False):
+    """The auto-tuner's levels [(interp, order)] for a field of ``shape`` from
+    its per-sample error rows err[m, L, ncfg] (hi_autotune_select): the
+    choice the device makes from the same rows."""
+    import numpy as np
+    p = make_params(tuple(shape), 1.0, "abs", anchor_stride, autotune=2 if md else True)
+    e = np.ascontiguousarray(err, dtype=np.float64).reshape(-1)
+    out = HiParams()
+    _check(lib().hi_autotune_select(ctypes.byref(p), ctypes.c_void_p(e.ctypes.data), e.size, ctypes.byref(out)),
+           "hi_autotune_select")
+    L = int(anchor_stride).bit_length() - 1
+    return [(int(out.level[l].interp), tuple(int(v) for v in out.level[l].order)) for l in range(L)]
+
+
+def autotune_dims(shape, anchor_stride=16, md=False):
+    """(m, L, ncfg): auto-tune samples, levels and candidates of a field of ``shape``."""
+    p = make_params(tuple(shape), 1.0, "abs", anchor_stride, autotune=2 if md else True)
+    m, L, nc = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    _check(lib().hi_autotune_errors(ctypes.byref(p), None, None, 0, ctypes.byref(m), ctypes.byref(L),
+                                    ctypes.byref(nc), None), "hi_autotune_errors")
+    return m.value, L.value, nc.value

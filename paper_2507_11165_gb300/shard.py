@@ -230,3 +230,165 @@ def compress_out_of_core(x_host, eb: float, A: int, levels, mode: str = "rel", s
                 out_idx=np.concatenate(oidx), out_val=np.concatenate(oval), hist=hist, eps=eps,
                 eb_f=cst.eb_f, ebx2_f=cst.ebx2_f, r_f=cst.r_f, vmin=vmin, vmax=vmax)
 
+
+
+# ---------------------------------------------------------------------------
+# One field over several ranks (torch.distributed): each rank holds the read
+# planes of its shard and compresses them; only the three exchanges of the
+# module docstring cross ranks.
+# ---------------------------------------------------------------------------
+def _coll_device(group):
+    import torch
+    import torch.distributed as dist
+    return torch.device("cuda", torch.cuda.current_device()) if dist.get_backend(group) == "nccl" else \
+        torch.device("cpu")
+
+
+def compress_distributed(x_local, shape, eb: float, A: int, executor, group=None, mode: str = "rel",
+                         autotune: bool = True, levels=None, md: bool = False):
+    """Compress one 3D field split over the ranks of ``group`` along d0
+    (shard_bounds(shape[0], A, world), shard k on rank k); ``x_local`` is
+    this rank's read planes [own_lo, read_hi) (empty on ranks past the last
+    shard).  ``executor`` runs the steps on this rank's data (GpuShardExecutor
+    for the library; any object with its five methods).  Exchanged: the
+    min / max of the finite values (one all-reduce), every sample block's
+    auto-tune error row (one all-reduce; each row comes from the one rank
+    that holds the block), nothing else.  Returns this rank's part of the
+    whole-field record: dict(shard, codes [own planes], anchors [its anchor
+    planes], out_idx (global, int64), out_val, hist (of its own non-anchor
+    points), levels, eps, vmin, vmax); merge_parts() of all ranks' parts in
+    rank order is the single-field record."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from . import hi
+
+    if len(shape) != 3:
+        raise ValueError("compress_distributed takes 3D fields")
+    n0, n1, n2 = (int(v) for v in shape)
+    world = dist.get_world_size(group) if dist.is_initialized() else 1
+    rank = dist.get_rank(group) if dist.is_initialized() else 0
+    plan = shard_bounds(n0, A, world)
+    sh = plan[rank] if rank < len(plan) else None
+    cdev = _coll_device(group) if world > 1 else torch.device("cpu")
+    if sh is not None and tuple(x_local.shape) != (sh["read_hi"] - sh["own_lo"], n1, n2):
+        raise ValueError("x_local must hold planes [%d, %d)" % (sh["own_lo"], sh["read_hi"]))
+
+    # 1. the field's value range -> eps (Eq. 1, relative bound)
+    vmin = vmax = 0.0
+    if mode == "rel":
+        r = executor.value_range(x_local[: sh["own_hi"] - sh["own_lo"]]) if sh is not None else None
+        t = torch.tensor([r[0] if r else math.inf, -r[1] if r else math.inf], dtype=torch.float64, device=cdev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MIN, group=group)
+        vmin, vmax = float(t[0]), -float(t[1])
+        if vmin > vmax:  # no finite value anywhere
+            vmin = vmax = 0.0
+    cst = hi.resolve_eps(mode, eb, vmin, vmax)
+
+    # 2. auto-tune over the whole field's sample blocks (Sec. 5.1.3)
+    if autotune:
+        gids = sample_blocks(shape, A)
+        nb12 = ((n1 - 1 + A - 1) // A) * ((n2 - 1 + A - 1) // A)
+        mine = [k for k, g in enumerate(gids) if sh is not None and sh["t_lo"] <= g // nb12 < sh["t_hi"]]
+        L, nc = executor.tune_dims(shape, A, md)
+        full = torch.zeros((len(gids), L, nc), dtype=torch.float64, device=cdev)
+        if mine:
+            rows = executor.block_errors(x_local, A, [local_block(gids[k], shape, A, sh) for k in mine], md)
+            full[mine] = torch.as_tensor(np.asarray(rows, dtype=np.float64), device=cdev)
+        if world > 1:
+            dist.all_reduce(full, op=dist.ReduceOp.SUM, group=group)  # x + 0 = x: every row exact
+        levels = executor.select(shape, A, full.cpu().numpy(), md)
+    elif levels is None:
+        raise ValueError("levels are needed without autotune")
+
+    out = dict(shard=sh, levels=[(int(i), tuple(int(v) for v in o)) for i, o in levels], eps=cst["eps"],
+               vmin=vmin, vmax=vmax)
+    if sh is None:
+        return out
+    # 3. this shard at the field's absolute bound, then its owned part
+    part = executor.compress(x_local, cst, A, out["levels"])
+    nown = sh["own_hi"] - sh["own_lo"]
+    codes = part["codes"].reshape(-1, n1, n2)
+    anchors = part["anchors"].reshape(-1, (n1 - 1) // A + 1, (n2 - 1) // A + 1)
+    idx = torch.as_tensor(part["out_idx"]).to(torch.int64)
+    val = torch.as_tensor(part["out_val"])
+    keep = idx < nown * n1 * n2
+    hist = torch.as_tensor(part["hist"]).to(torch.int64).clone()
+    if not sh["last"]:  # the read-only plane's non-anchor codes belong to the next shard
+        top = torch.as_tensor(codes[nown]).to(torch.int64)
+        amask = torch.zeros((n1, n2), dtype=torch.bool, device=top.device)
+        amask[::A, ::A] = True
+        hist -= torch.bincount(top[~amask], minlength=256).to(hist.device)
+    out.update(codes=codes[:nown], anchors=anchors if sh["last"] else anchors[:-1],
+               out_idx=idx[keep] + sh["own_lo"] * n1 * n2, out_val=val[keep], hist=hist)
+    return out
+
+
+def merge_parts(parts):
+    """The whole-field record from the ranks' parts (rank order)."""
+    import torch
+    parts = [p for p in parts if p.get("shard") is not None]
+    cat = lambda k: torch.cat([torch.as_tensor(p[k]).cpu() for p in parts], 0)
+    return dict(codes=cat("codes"), anchors=cat("anchors").reshape(-1), out_idx=cat("out_idx"),
+                out_val=cat("out_val"), hist=sum(torch.as_tensor(p["hist"]).cpu() for p in parts),
+                levels=parts[0]["levels"], eps=parts[0]["eps"])
+
+
+class GpuShardExecutor:
+    """The steps of compress_distributed on this rank's GPU, through the C ABI."""
+
+    def __init__(self, device=None):
+        import torch
+        self.dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+
+    def value_range(self, x_own):
+        """(vmin, vmax) of the finite values of the owned planes, or None (hi_value_range)."""
+        import torch
+
+        from . import hi
+        x_own = x_own.to(self.dev).contiguous()
+        if x_own.numel() == 0 or not bool(torch.isfinite(x_own).any()):
+            return None
+        p = hi.make_params(tuple(x_own.shape), 1e-3, "rel", 16, autotune=False, levels=[(hi.LINEAR, (0, 1, 2))] * 4)
+        hdr = torch.empty(hi.HEADER_BYTES, dtype=torch.uint8, device=self.dev)
+        ws = torch.empty(max(8, hi.query(p)["ws_bytes"]), dtype=torch.uint8, device=self.dev)
+        hi.value_range_into(x_own, p, hdr, ws)
+        h = hi.read_header(hdr)
+        return float(h.vmin), float(h.vmax)
+
+    def tune_dims(self, shape, A, md):
+        from . import hi
+        e = hi.autotune_dims(shape, A, md)
+        return e[1], e[2]
+
+    def block_errors(self, x_read, A, local_ids, md):
+        """Auto-tune error rows [len(local_ids), L, ncfg] of blocks of the read planes: each block as a field of
+        its own, whose one sample is the whole block (the same rows the whole field's tuner computes)."""
+        import numpy as np
+
+        from . import hi
+        x_read = x_read.to(self.dev)
+        n = x_read.shape
+        nb = [1 if v == 1 else (v - 1 + A - 1) // A for v in n]
+        rows = []
+        for b in local_ids:
+            t0, r = divmod(int(b), nb[1] * nb[2])
+            t1, t2 = divmod(r, nb[2])
+            blk = x_read[t0 * A: min(t0 * A + A, n[0] - 1) + 1, t1 * A: min(t1 * A + A, n[1] - 1) + 1,
+                         t2 * A: min(t2 * A + A, n[2] - 1) + 1].contiguous()
+            rows.append(hi.tune_errors(blk, A, md)[0])
+        return np.stack(rows)
+
+    def select(self, shape, A, err, md):
+        from . import hi
+        return hi.autotune_select(shape, A, err, md)
+
+    def compress(self, x_read, cst, A, levels):
+        """The read planes at the field's absolute bound: codes, anchors, outliers (local), histogram."""
+        from . import hi
+        x_read = x_read.to(self.dev).contiguous()
+        c = hi.compress(x_read, cst["eps"], "abs", A, autotune=False, levels=levels, out_cap=x_read.numel())
+        idx, val = c.outliers
+        return dict(codes=c.codes, anchors=c.anchors[: int(c.h.n_anchors)], out_idx=idx, out_val=val, hist=c.hist)

@@ -81,3 +81,18 @@ def test_resolve_eps_rejects(hi):
     for args in (("rel", 0.0, 0.0, 1.0), ("rel", float("nan"), 0.0, 1.0), (7, 1e-3, 0.0, 1.0)):
         with pytest.raises(hi.HiError):
             hi.resolve_eps(*args)
+
+
+def test_autotune_select_matches_oracle(hi, oracle_mod):
+    rng = np.random.default_rng(11)
+    for shape, A in (((40, 70, 90), 16), ((300, 500), 16), ((5000,), 8), ((65, 65, 65), 8)):
+        m, L, nc = hi.autotune_dims(shape, A)
+        assert nc == len(oracle_mod.tune_configs(shape)) and L == oracle_mod.n_levels(A)
+        for trial in range(6):
+            # integer error sums: every order of summation is exact, so the argmin is the oracle's
+            err = rng.integers(0, 50 if trial % 2 else 4, size=(m, L, nc)).astype(np.float64)
+            got = hi.autotune_select(shape, A, err)
+            interp, order = oracle_mod.tune_select(shape, A, err.sum(axis=0))
+            assert got == [(int(i), tuple(int(v) for v in o)) for i, o in zip(interp, order)]
+    with pytest.raises(hi.HiError):
+        hi.autotune_select((40, 70, 90), 16, np.zeros(3))  # short array

@@ -35,70 +35,59 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _owned(sh, x, ref, col, n1, n2):
-    nown = sh["own_hi"] - sh["own_lo"]
-    codes = ref["codes"][:nown]
-    ash = ((ref["codes"].shape[0] - 1) // A + 1, (n1 - 1) // A + 1, (n2 - 1) // A + 1)
-    an = ref["anchors"].reshape(ash)
-    an = an if sh["last"] else an[:-1]
-    keep = col["out_idx"] < nown * n1 * n2
-    idx = col["out_idx"][keep].astype(np.int64) + sh["own_lo"] * n1 * n2
-    val = col["out_val"][keep]
-    hist = col["hist"].astype(np.int64)
-    if not sh["last"]:  # the read-only plane's non-anchor codes are the next shard's
-        top = ref["codes"][nown].copy()
-        mask = np.ones((n1, n2), dtype=bool)
-        mask[::A, ::A] = False
-        hist -= np.bincount(top[mask].reshape(-1), minlength=256)
-    return codes, an, idx, val, hist
+class OracleExecutor:
+    """compress_distributed's steps on the CPU oracle (test infrastructure)."""
+
+    def __init__(self):
+        import oracle
+        self.o = oracle
+
+    def value_range(self, x_own):
+        fin = np.asarray(x_own)[np.isfinite(x_own)]
+        return (float(fin.min()), float(fin.max())) if fin.size else None
+
+    def tune_dims(self, shape, A_, md):
+        return self.o.n_levels(A_), len(self.o.tune_configs(shape))
+
+    def block_errors(self, x_read, A_, ids, md):
+        return self.o.tune_errors_tiles(np.ascontiguousarray(x_read), A_, ids)
+
+    def select(self, shape, A_, err, md):
+        tot = np.zeros(err.shape[1:], dtype=np.float64)
+        for k in range(err.shape[0]):  # samples summed in global order
+            tot = tot + err[k]
+        interp, order = self.o.tune_select(shape, A_, tot)
+        return [(int(i), tuple(int(v) for v in o)) for i, o in zip(interp, order)]
+
+    def compress(self, x_read, cst, A_, levels):
+        consts = dict(eb_f=np.float32(cst["eb_f"]), ebx2_f=np.float32(cst["ebx2_f"]), r_f=np.float32(cst["r_f"]),
+                      vmin=np.float32(0), vmax=np.float32(0), eps=cst["eps"])
+        interp = np.array([l[0] for l in levels], dtype=np.uint8)
+        order = np.array([l[1] for l in levels], dtype=np.uint8)
+        x = np.ascontiguousarray(x_read)
+        ref = self.o.compress(x, A_, interp, order, consts)
+        col = self.o.collect(x, ref["codes"], A_)
+        return dict(codes=ref["codes"], anchors=ref["anchors"], out_idx=col["out_idx"], out_val=col["out_val"],
+                    hist=col["hist"])
 
 
 def _worker(rank, world, port, outdir):
-    import oracle
-
     dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=world)
     x = fields.lognormal_grf(SHAPE, seed=21)  # every rank makes the same field and keeps its planes
-    n1, n2 = SHAPE[1], SHAPE[2]
     sh = shard.shard_bounds(SHAPE[0], A, world)[rank]
-    xs = np.ascontiguousarray(x[sh["own_lo"]:sh["read_hi"]])
-    own = x[sh["own_lo"]:sh["own_hi"]]
-    fin = own[np.isfinite(own)]
-    mn = torch.tensor([float(fin.min())], dtype=torch.float64)
-    mx = torch.tensor([float(fin.max())], dtype=torch.float64)
-    dist.all_reduce(mn, op=dist.ReduceOp.MIN)
-    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-    cst = oracle.eps_constants(np.array([mn.item(), mx.item()], dtype=np.float32), 1, EB)
-    assert cst["eps"] == hi.resolve_eps("rel", EB, mn.item(), mx.item())["eps"]
-    # auto-tune: the errors of the global sample blocks this rank holds, then
-    # every sample's errors on every rank, summed in global sample order
+    part = shard.compress_distributed(np.ascontiguousarray(x[sh["own_lo"]:sh["read_hi"]]), SHAPE, EB, A,
+                                      OracleExecutor())
     gids = shard.sample_blocks(SHAPE, A)
-    nb12 = ((n1 - 1 + A - 1) // A) * ((n2 - 1 + A - 1) // A)
-    mine = [k for k, g in enumerate(gids) if sh["t_lo"] <= g // nb12 < sh["t_hi"]]
-    L = oracle.n_levels(A)
-    nc = len(oracle.tune_configs(SHAPE))
-    full = torch.zeros((len(gids), L, nc), dtype=torch.float64)
-    if mine:
-        e = oracle.tune_errors_tiles(xs, A, [shard.local_block(gids[k], SHAPE, A, sh) for k in mine])
-        for j, k in enumerate(mine):
-            full[k] = torch.from_numpy(e[j])
-    dist.all_reduce(full, op=dist.ReduceOp.SUM)  # each sample's row is non-zero on one rank only
-    tot = torch.zeros((L, nc), dtype=torch.float64)
-    for k in range(len(gids)):
-        tot = tot + full[k]
-    interp, order = oracle.tune_select(SHAPE, A, tot.numpy())
-    ref = oracle.compress(xs, A, interp, order, cst)
-    col = oracle.collect(xs, ref["codes"], A)
-    part = _owned(sh, x, ref, col, n1, n2)
+    nb12 = ((SHAPE[1] - 1 + A - 1) // A) * ((SHAPE[2] - 1 + A - 1) // A)
+    held = sum(sh["t_lo"] <= g // nb12 < sh["t_hi"] for g in gids)
     parts = [None] * world
-    dist.all_gather_object(parts, (part, interp, order, len(mine)))
+    dist.all_gather_object(parts, (part, held))
     if rank == 0:
-        codes = np.concatenate([p[0][0] for p in parts], 0)
-        anchors = np.concatenate([p[0][1] for p in parts], 0).reshape(-1)
-        idx = np.concatenate([p[0][2] for p in parts])
-        val = np.concatenate([p[0][3] for p in parts])
-        hist = sum(p[0][4] for p in parts)
-        np.savez(os.path.join(outdir, "merged.npz"), codes=codes, anchors=anchors, idx=idx, val=val, hist=hist,
-                 interp=interp, order=order, held=np.array([p[3] for p in parts]))
+        m = shard.merge_parts([p[0] for p in parts])
+        np.savez(os.path.join(outdir, "merged.npz"), codes=m["codes"].numpy(), anchors=m["anchors"].numpy(),
+                 idx=m["out_idx"].numpy(), val=m["out_val"].numpy(), hist=m["hist"].numpy(),
+                 interp=np.array([l[0] for l in m["levels"]]), order=np.array([l[1] for l in m["levels"]]),
+                 held=np.array([p[1] for p in parts]), eps=np.array([p[0]["eps"] for p in parts]))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -115,6 +104,7 @@ def test_two_ranks_reproduce_the_single_field_record(oracle_mod, tmp_path):
     assert len(shard.sample_blocks(SHAPE, A)) == oracle_mod.tune_samples(SHAPE, A) >= 2
     assert all(h >= 1 for h in m["held"])  # both ranks held sample blocks
     assert np.array_equal(m["interp"], interp) and np.array_equal(m["order"], order)
+    assert all(e == cst["eps"] for e in m["eps"])
     assert np.array_equal(m["codes"], ref["codes"])
     assert np.array_equal(m["anchors"].view(np.uint32), ref["anchors"].view(np.uint32))
     o = np.argsort(m["idx"])

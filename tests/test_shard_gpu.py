@@ -1,6 +1,8 @@
 """One GPU compressing a field shard by shard (as separate ranks would, each
 with the global bound) and merging: the same record as compressing the
 field whole."""
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -100,3 +102,55 @@ def test_value_range_matches_oracle(hi, oracle_mod, shape):
     small = torch.empty(hi.RANGE_WS_BYTES - 8, dtype=torch.uint8, device="cuda")
     with pytest.raises(RuntimeError):
         hi.value_range_into(x, p, hdr, small)
+
+
+def _dist_worker(rank, world, port, outdir):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2507_11165_gb300 import fields, shard
+    torch.cuda.set_device(0)  # both ranks on one GPU: their kernels never wait on each other
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=world)
+    shape = (101, 80, 72)
+    x = fields.lognormal_grf(shape, seed=23)
+    sh = shard.shard_bounds(shape[0], 16, world)[rank]
+    xl = torch.from_numpy(np.ascontiguousarray(x[sh["own_lo"]:sh["read_hi"]])).cuda()
+    part = shard.compress_distributed(xl, shape, 1e-3, 16, shard.GpuShardExecutor())
+    part = {k: (v.cpu() if torch.is_tensor(v) else v) for k, v in part.items()}
+    parts = [None] * world
+    dist.all_gather_object(parts, part)
+    if rank == 0:
+        m = shard.merge_parts(parts)
+        torch.save(m, os.path.join(outdir, "merged.pt"))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.gpu
+def test_distributed_ranks_reproduce_hi_compress(tmp_path):
+    import socket
+
+    import numpy as np
+    import torch
+    import torch.multiprocessing as mp
+
+    from paper_2507_11165_gb300 import fields, hi
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    mp.start_processes(_dist_worker, args=(2, port, str(tmp_path)), nprocs=2, start_method="spawn")
+    m = torch.load(os.path.join(str(tmp_path), "merged.pt"))
+    x = torch.from_numpy(fields.lognormal_grf((101, 80, 72), seed=23)).cuda()
+    c = hi.compress(x, 1e-3, "rel", 16, autotune=True, out_cap=x.numel())
+    levels = [(int(c.h.level[l].interp), tuple(int(v) for v in c.h.level[l].order)) for l in range(c.h.n_levels)]
+    assert m["levels"] == levels
+    assert m["eps"] == c.h.eps
+    assert torch.equal(m["codes"].reshape(-1), c.codes.cpu().reshape(-1))
+    assert torch.equal(m["anchors"].reshape(-1).view(torch.int32), c.anchors.cpu().reshape(-1).view(torch.int32))
+    idx, val = c.outliers
+    o1, o2 = torch.argsort(m["out_idx"]), torch.argsort(idx.cpu().to(torch.int64))
+    assert torch.equal(m["out_idx"][o1], idx.cpu().to(torch.int64)[o2])
+    assert torch.equal(m["out_val"][o1].view(torch.int32), val.cpu()[o2].view(torch.int32))
+    assert torch.equal(m["hist"], c.hist.cpu().to(torch.int64))
+    assert len(idx) > 0
