@@ -90,6 +90,11 @@ def _load():
             lib.hi_oracle_tp_bound.restype = i64
             lib.hi_oracle_tp_encode.argtypes = [P, i64, P, i64, P]
             lib.hi_oracle_tp_decode.argtypes = [P, i64, P, i64]
+            lib.hi_oracle_hf_lengths.argtypes = [P, P]
+            lib.hi_oracle_cr_bound.argtypes = [i64]
+            lib.hi_oracle_cr_bound.restype = i64
+            lib.hi_oracle_cr_encode.argtypes = [P, i64, P, i64, P]
+            lib.hi_oracle_cr_decode.argtypes = [P, i64, P, i64]
             _lib = lib
     return _lib
 
@@ -287,6 +292,75 @@ def trace(shape, A, interp, order):
     return lvl, d, k
 
 
+def _slab_tiles(shape, A, workers):
+    """Row-major block ids split into slabs of whole block planes along the
+    slowest dim with more than one block (one slab list per phase: even
+    slabs, then odd slabs), so that slabs that share a face plane never run
+    at the same time."""
+    nb = block_grid(shape, A)
+    d = next((k for k in range(3) if nb[k] > 1), 2)
+    per_plane = int(np.prod(nb[d + 1:], dtype=np.int64))
+    n_slabs = max(1, min(nb[d], 2 * workers))
+    cuts = [nb[d] * k // n_slabs for k in range(n_slabs + 1)]
+    slabs = [np.arange(cuts[k] * per_plane, cuts[k + 1] * per_plane, dtype=np.int64) for k in range(n_slabs)]
+    return [slabs[0::2], slabs[1::2]]
+
+
+def compress_parallel(x, A, interp, order, consts, workers):
+    """:func:`compress` with the independent blocks (Sec. 5.1.1) spread over
+    ``workers`` host threads: the same C routine called on disjoint block
+    lists into shared output arrays (the library call releases the GIL).
+    Blocks that share a face plane are never processed at the same time."""
+    import concurrent.futures as cf
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    dims = _dims3(x.shape)
+    L = n_levels(A)
+    interp = np.ascontiguousarray(interp, dtype=np.uint8).reshape(L)
+    order = np.ascontiguousarray(order, dtype=np.uint8).reshape(L, 3)
+    c = np.array([consts["eb_f"], consts["ebx2_f"], consts["r_f"]], dtype=np.float32)
+    codes = np.zeros(x.shape, dtype=np.uint8)
+    recon = np.zeros(x.shape, dtype=np.float32)
+    anchors = np.zeros(anchor_dims(x.shape, A), dtype=np.float32)
+
+    def run(t):
+        return lib.hi_oracle_compress(_p(dims), int(A), _p(interp), _p(order), _p(c), _p(x), _p(t), t.size,
+                                      _p(codes), _p(anchors), _p(recon))
+
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        for phase in _slab_tiles(x.shape, A, workers):
+            for rc in ex.map(run, phase):
+                _check(rc)
+    return dict(codes=codes, anchors=anchors.reshape(-1), recon=recon)
+
+
+def decompress_parallel(shape, A, interp, order, ebx2_f, codes, anchors, out_idx, out_val, workers):
+    """:func:`decompress` with the blocks spread over host threads as in
+    :func:`compress_parallel`."""
+    import concurrent.futures as cf
+    lib = _load()
+    dims = _dims3(shape)
+    L = n_levels(A)
+    interp = np.ascontiguousarray(interp, dtype=np.uint8).reshape(L)
+    order = np.ascontiguousarray(order, dtype=np.uint8).reshape(L, 3)
+    codes = np.ascontiguousarray(codes, dtype=np.uint8)
+    anchors = np.ascontiguousarray(anchors, dtype=np.float32)
+    out_idx = np.ascontiguousarray(out_idx, dtype=np.uint32)
+    out_val = np.ascontiguousarray(out_val, dtype=np.float32)
+    recon = np.zeros(tuple(shape), dtype=np.float32)
+
+    def run(t):
+        return lib.hi_oracle_decompress(_p(dims), int(A), _p(interp), _p(order), ctypes.c_float(ebx2_f),
+                                        _p(codes), _p(anchors), _p(out_idx), _p(out_val), out_idx.size,
+                                        _p(t), t.size, _p(recon))
+
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        for phase in _slab_tiles(shape, A, workers):
+            for rc in ex.map(run, phase):
+                _check(rc)
+    return recon
+
+
 def full_compress(x, A, interp, order, eb_mode, eb):
     """Convenience: constants + compress + outlier/histogram collection."""
     consts = eps_constants(x, eb_mode, eb)
@@ -356,3 +430,36 @@ def tp_decode(stream, n):
     _check(lib.hi_oracle_tp_decode(_p(stream), stream.size, _p(out), int(n)))
     return out
 
+
+
+# ---------------------------------------------------------------------------
+# Compression-ratio-mode lossless pipeline HF-RRE4-TCMS8-RZE1 (Sec. 5.2.3)
+# ---------------------------------------------------------------------------
+def hf_lengths(freq):
+    """Huffman code lengths (at most 16) of a 256-bin frequency table."""
+    f = np.ascontiguousarray(freq, dtype=np.uint64).reshape(256)
+    ln = np.zeros(256, dtype=np.uint8)
+    _check(_load().hi_oracle_hf_lengths(_p(f), _p(ln)))
+    return ln
+
+
+def cr_bound(n):
+    return int(_load().hi_oracle_cr_bound(int(n)))
+
+
+def cr_encode(data):
+    """The CR-mode stream of a byte array."""
+    lib = _load()
+    data = np.ascontiguousarray(data, dtype=np.uint8).reshape(-1)
+    out = np.zeros(cr_bound(data.size), dtype=np.uint8)
+    ln = np.zeros(1, dtype=np.int64)
+    _check(lib.hi_oracle_cr_encode(_p(data), data.size, _p(out), out.size, _p(ln)))
+    return out[:int(ln[0])].copy()
+
+
+def cr_decode(stream, n):
+    lib = _load()
+    stream = np.ascontiguousarray(stream, dtype=np.uint8)
+    out = np.zeros(max(int(n), 1), dtype=np.uint8)
+    _check(lib.hi_oracle_cr_decode(_p(stream), stream.size, _p(out), int(n)))
+    return out[:int(n)]

@@ -1372,3 +1372,467 @@ int hi_oracle_tp_decode(const uint8_t* in, int64_t len, uint8_t* out, int64_t n)
     for (int r = 0; r < 9; ++r) free(lv[r]);
     return rc;
 }
+
+/* ---------------------------------------------------------------------------
+ * Compression-ratio-mode lossless pipeline HF-RRE4-TCMS8-RZE1 (Sec. 5.2.3)
+ * over a byte sequence (the reordered codes).  The paper names the stages:
+ * Huffman coding, then repeat elimination on 4-byte symbols with a bitmap
+ * compressed recursively, the magnitude-sign transform (w << 1) ^ (w >> 63)
+ * on 8-byte words, and zero elimination on bytes "similar to RRE4".  The
+ * code construction, block sizes and container are not given; readings:
+ *
+ *   HF       frequencies of the n symbols; Huffman code lengths from the
+ *            tree that repeatedly merges the two lowest-ranked live nodes,
+ *            nodes ranked by (weight, creation index) with the leaves
+ *            created first in increasing symbol order and internal nodes
+ *            numbered on from there as they are formed; a symbol's length
+ *            is its leaf's depth (a lone symbol: 1).  While a length exceeds
+ *            16, every nonzero weight w becomes max(1, w >> 1) and the tree
+ *            is built again.  Canonical codes: symbols in (length, symbol)
+ *            order, the first gets 0, each next (prev + 1) << (its length -
+ *            the previous length).  Symbols are coded in blocks of 4096; a
+ *            block's code bits go out most significant first (bit 7 of a
+ *            byte first) and are padded with zero bits to a multiple of 32;
+ *            the HF bytes are the blocks' padded bit strings in order.
+ *   RRE4     on a chunk of m bytes (m a multiple of 4): word bitmap bit i =
+ *            (word i != word i-1), word -1 = 0, LSB first; the bitmap is
+ *            reduced by RRE1 levels (as in the throughput pipeline) until a
+ *            level has at most 64 bytes; output = top level | kept bytes of
+ *            the levels below, top down | kept words.
+ *   TCMS8    every whole little-endian 8-byte word t of that output becomes
+ *            (t << 1) ^ (t >> 63) (arithmetic shift), the tail bytes stay.
+ *   RZE1     on the m1 bytes of that: levels v_0 = the bytes, v_{r+1} = the
+ *            bitmap of (v_r[i] != 0), until a level has at most 64 bytes;
+ *            payload = v_R | nonzero bytes of v_{R-1} | ... | of v_0.  A
+ *            chunk whose payload is longer than m is stored raw.
+ *   stream   u64 n | u32 4096 | u32 nblocks | u64 H (HF bytes) | u32 16384 |
+ *            u32 nchunks | u8 length[256] | u32 words[nblocks] |
+ *            (u32 size, u32 m1)[nchunks] | zero padding to 16 | payloads,
+ *            each padded to 16 (size = padded bytes, bit 31 = raw; m1 = the
+ *            RRE4 output length, 0 for a raw chunk).
+ * ------------------------------------------------------------------------- */
+#define HF_LMAX 16
+#define HF_BLOCK 4096
+#define CR_CHUNK 16384
+
+/* Tree lengths for weights w (0 = absent); returns the longest length. */
+static int hf_tree_lengths(const uint64_t* w, uint8_t* len)
+{
+    uint64_t wt[511];
+    int parent[511], alive[511], sym[256];
+    int k = 0, nodes, i, step;
+    int maxlen = 0;
+    memset(len, 0, 256);
+    for (i = 0; i < 256; ++i)
+        if (w[i] > 0) {
+            wt[k] = w[i];
+            sym[k] = i;
+            alive[k] = 1;
+            parent[k] = -1;
+            ++k;
+        }
+    if (k == 0) return 0;
+    if (k == 1) {
+        len[sym[0]] = 1;
+        return 1;
+    }
+    nodes = k;
+    for (step = 0; step < k - 1; ++step) {
+        int a = -1, b = -1;
+        for (i = 0; i < nodes; ++i) { /* the two lowest (weight, index) live nodes */
+            if (!alive[i]) continue;
+            if (a < 0 || wt[i] < wt[a]) {
+                b = a;
+                a = i;
+            } else if (b < 0 || wt[i] < wt[b]) {
+                b = i;
+            }
+        }
+        wt[nodes] = wt[a] + wt[b];
+        alive[nodes] = 1;
+        parent[nodes] = -1;
+        parent[a] = nodes;
+        parent[b] = nodes;
+        alive[a] = 0;
+        alive[b] = 0;
+        ++nodes;
+    }
+    for (i = 0; i < k; ++i) {
+        int d = 0, j = i;
+        while (parent[j] >= 0) {
+            j = parent[j];
+            ++d;
+        }
+        len[sym[i]] = (uint8_t)d;
+        if (d > maxlen) maxlen = d;
+    }
+    return maxlen;
+}
+
+/* Huffman code lengths (at most 16) of a 256-bin frequency table. */
+int hi_oracle_hf_lengths(const uint64_t* freq, uint8_t* len)
+{
+    uint64_t w[256];
+    int i;
+    memcpy(w, freq, sizeof w);
+    while (hf_tree_lengths(w, len) > HF_LMAX)
+        for (i = 0; i < 256; ++i)
+            if (w[i] > 0) w[i] = (w[i] >> 1) ? (w[i] >> 1) : 1;
+    return 0;
+}
+
+/* Canonical codes from the lengths. */
+static void hf_canonical(const uint8_t* len, uint32_t* code)
+{
+    int l, v, first = 1, pl = 0;
+    uint32_t c = 0;
+    memset(code, 0, 256 * sizeof(uint32_t));
+    for (l = 1; l <= HF_LMAX; ++l)
+        for (v = 0; v < 256; ++v)
+            if (len[v] == l) {
+                c = first ? 0u : ((c + 1u) << (l - pl));
+                first = 0;
+                pl = l;
+                code[v] = c;
+            }
+}
+
+/* Zero-elimination level: bitmap of (v[i] != 0) into bm, nonzero bytes into kept. */
+static int64_t rze_level(const uint8_t* v, int64_t L, uint8_t* bm, uint8_t* kept)
+{
+    int64_t nk = 0;
+    memset(bm, 0, (size_t)((L + 7) / 8));
+    for (int64_t i = 0; i < L; ++i)
+        if (v[i] != 0) {
+            bm[i / 8] |= (uint8_t)(1u << (i % 8));
+            kept[nk++] = v[i];
+        }
+    return nk;
+}
+
+/* Levels of a byte string (zero elimination or repeat elimination) until a
+ * level has at most 64 bytes; writes v_R | kept_{R-1} | ... | kept_0 to out
+ * and returns its length. */
+static int64_t reduce_levels(const uint8_t* s, int64_t L0, int zero, uint8_t* out)
+{
+    const uint8_t* lv[16];
+    uint8_t* own[16];
+    uint8_t* kept[16];
+    int64_t L[16], nk[16], o = 0;
+    int R = 0, r;
+    lv[0] = s;
+    L[0] = L0;
+    while (L[R] > 64) {
+        own[R + 1] = malloc((size_t)((L[R] + 7) / 8));
+        kept[R] = malloc((size_t)L[R]);
+        L[R + 1] = (L[R] + 7) / 8;
+        nk[R] = zero ? rze_level(lv[R], L[R], own[R + 1], kept[R]) : rre_level(lv[R], L[R], own[R + 1], kept[R]);
+        lv[R + 1] = own[R + 1];
+        ++R;
+    }
+    memcpy(out, lv[R], (size_t)L[R]);
+    o = L[R];
+    for (r = R - 1; r >= 0; --r) {
+        memcpy(out + o, kept[r], (size_t)nk[r]);
+        o += nk[r];
+    }
+    for (r = 0; r < R; ++r) {
+        free(own[r + 1]);
+        free(kept[r]);
+    }
+    return o;
+}
+
+/* Inverse of reduce_levels: rebuilds the L0 bytes of level 0 into dst from
+ * p[0..avail); returns the bytes consumed or -1. */
+static int64_t expand_levels(const uint8_t* p, int64_t avail, int64_t L0, int zero, uint8_t* dst)
+{
+    int64_t L[16], q;
+    uint8_t* lv[16];
+    int R = 0, r;
+    L[0] = L0;
+    while (L[R] > 64) {
+        L[R + 1] = (L[R] + 7) / 8;
+        ++R;
+    }
+    if (L[R] > avail) return -1;
+    lv[0] = dst;
+    for (r = 1; r <= R; ++r) lv[r] = malloc((size_t)L[r]);
+    memcpy(lv[R], p, (size_t)L[R]);
+    q = L[R];
+    for (r = R - 1; r >= 0; --r) {
+        uint8_t prev = 0;
+        for (int64_t i = 0; i < L[r]; ++i) {
+            if ((lv[r + 1][i / 8] >> (i % 8)) & 1) {
+                if (q >= avail) {
+                    q = -1;
+                    break;
+                }
+                prev = p[q++];
+                lv[r][i] = prev;
+            } else {
+                lv[r][i] = zero ? 0 : prev;
+            }
+        }
+        if (q < 0) break;
+    }
+    for (r = 1; r <= R; ++r) free(lv[r]);
+    return q;
+}
+
+static uint64_t ld64(const uint8_t* p)
+{
+    uint64_t v = 0;
+    for (int b = 7; b >= 0; --b) v = (v << 8) | p[b];
+    return v;
+}
+
+static void st64(uint8_t* p, uint64_t v)
+{
+    for (int b = 0; b < 8; ++b) p[b] = (uint8_t)(v >> (8 * b));
+}
+
+static uint64_t tcms8(uint64_t t) { return (t << 1) ^ ((t >> 63) ? ~(uint64_t)0 : 0); }
+static uint64_t tcms8_inv(uint64_t u) { return (u >> 1) ^ ((u & 1) ? ~(uint64_t)0 : 0); }
+
+/* One LC chunk: RRE4, TCMS8, RZE1.  out >= 2 m + 256; returns the payload length and m1. */
+static int64_t cr_chunk_encode(const uint8_t* c, int64_t m, uint8_t* out, int64_t* m1_out, int* raw)
+{
+    const int64_t w = m / 4, L0 = (w + 7) / 8;
+    uint8_t* bm = calloc((size_t)L0 + 1, 1);
+    uint8_t* r = malloc((size_t)(2 * m + 256));
+    int64_t nk = 0, m1, j, len;
+    for (int64_t i = 0; i < w; ++i) {
+        const int eq = i > 0 ? memcmp(c + 4 * i, c + 4 * (i - 1), 4) == 0
+                             : (c[0] == 0 && c[1] == 0 && c[2] == 0 && c[3] == 0);
+        if (!eq) {
+            bm[i / 8] |= (uint8_t)(1u << (i % 8));
+            ++nk;
+        }
+    }
+    m1 = reduce_levels(bm, L0, 0, r);
+    for (int64_t i = 0; i < w; ++i)
+        if ((bm[i / 8] >> (i % 8)) & 1) {
+            memcpy(r + m1, c + 4 * i, 4);
+            m1 += 4;
+        }
+    for (j = 0; j + 8 <= m1; j += 8) st64(r + j, tcms8(ld64(r + j)));
+    len = reduce_levels(r, m1, 1, out);
+    if (len > m) {
+        memcpy(out, c, (size_t)m);
+        len = m;
+        *raw = 1;
+        m1 = 0;
+    } else {
+        *raw = 0;
+    }
+    *m1_out = m1;
+    free(bm);
+    free(r);
+    (void)nk;
+    return len;
+}
+
+static int64_t cr_header_bytes(int64_t nb, int64_t nc) { return (288 + 4 * nb + 8 * nc + 15) / 16 * 16; }
+
+/* Upper bound of the stream size for n input bytes. */
+int64_t hi_oracle_cr_bound(int64_t n)
+{
+    const int64_t nb = (n + HF_BLOCK - 1) / HF_BLOCK;
+    const int64_t H = nb * HF_BLOCK * 2 + 4 * nb; /* at most 16 bits a symbol */
+    const int64_t nc = (H + CR_CHUNK - 1) / CR_CHUNK;
+    return cr_header_bytes(nb, nc) + H + 16 * nc + 16;
+}
+
+int hi_oracle_cr_encode(const uint8_t* in, int64_t n, uint8_t* out, int64_t cap, int64_t* out_len)
+{
+    uint64_t freq[256];
+    uint8_t len[256];
+    uint32_t code[256];
+    int64_t nb, nc, H = 0, b, k, o;
+    uint8_t *hf, *buf;
+    uint32_t* words;
+    if (n < 0 || (n && !in) || !out || !out_len || cap < hi_oracle_cr_bound(n)) return 1;
+    memset(freq, 0, sizeof freq);
+    for (int64_t i = 0; i < n; ++i) freq[in[i]]++;
+    hi_oracle_hf_lengths(freq, len);
+    hf_canonical(len, code);
+    nb = (n + HF_BLOCK - 1) / HF_BLOCK;
+    hf = calloc((size_t)(nb * HF_BLOCK * 2 + 16), 1);
+    words = calloc((size_t)nb + 1, sizeof(uint32_t));
+    if (!hf || !words) {
+        free(hf);
+        free(words);
+        return 2;
+    }
+    for (b = 0; b < nb; ++b) { /* Huffman blocks, MSB first, padded to 32 bits */
+        const int64_t s0 = b * HF_BLOCK, s1 = s0 + HF_BLOCK < n ? s0 + HF_BLOCK : n;
+        int64_t p = 8 * H;
+        for (int64_t i = s0; i < s1; ++i) {
+            const int l = len[in[i]];
+            for (int t = l - 1; t >= 0; --t, ++p)
+                if ((code[in[i]] >> t) & 1) hf[p / 8] |= (uint8_t)(0x80u >> (p % 8));
+        }
+        const int64_t bits = p - 8 * H;
+        words[b] = (uint32_t)((bits + 31) / 32);
+        H += 4 * (int64_t)words[b];
+    }
+    nc = (H + CR_CHUNK - 1) / CR_CHUNK;
+    memset(out, 0, (size_t)cr_header_bytes(nb, nc));
+    memcpy(out, &n, 8);
+    {
+        const uint32_t hb = HF_BLOCK, nb32 = (uint32_t)nb, cc = CR_CHUNK, nc32 = (uint32_t)nc;
+        memcpy(out + 8, &hb, 4);
+        memcpy(out + 12, &nb32, 4);
+        memcpy(out + 16, &H, 8);
+        memcpy(out + 24, &cc, 4);
+        memcpy(out + 28, &nc32, 4);
+    }
+    memcpy(out + 32, len, 256);
+    memcpy(out + 288, words, 4 * (size_t)nb);
+    o = cr_header_bytes(nb, nc);
+    buf = malloc(2 * CR_CHUNK + 256);
+    for (k = 0; k < nc; ++k) {
+        const int64_t m = (k + 1) * CR_CHUNK <= H ? CR_CHUNK : H - k * CR_CHUNK;
+        int64_t m1 = 0;
+        int raw = 0;
+        const int64_t l = cr_chunk_encode(hf + k * CR_CHUNK, m, buf, &m1, &raw);
+        const int64_t pad = (l + 15) / 16 * 16;
+        const uint32_t sz = (uint32_t)pad | (raw ? TP_RAW : 0u), m1_32 = (uint32_t)m1;
+        if (o + pad > cap) {
+            free(buf);
+            free(hf);
+            free(words);
+            return 1;
+        }
+        memcpy(out + o, buf, (size_t)l);
+        memset(out + o + l, 0, (size_t)(pad - l));
+        memcpy(out + 288 + 4 * nb + 8 * k, &sz, 4);
+        memcpy(out + 288 + 4 * nb + 8 * k + 4, &m1_32, 4);
+        o += pad;
+    }
+    free(buf);
+    free(hf);
+    free(words);
+    *out_len = o;
+    return 0;
+}
+
+int hi_oracle_cr_decode(const uint8_t* in, int64_t len_in, uint8_t* out, int64_t n)
+{
+    int64_t n_s, H, nb, nc, o, k, b, pos = 0;
+    uint32_t hb, nb32, cc, nc32;
+    uint8_t len[256], sorted[256];
+    uint32_t code[256], cnt[HF_LMAX + 1], first[HF_LMAX + 1], offs[HF_LMAX + 1];
+    uint8_t *hf, *r;
+    int rc = 0;
+    if (len_in < 288 || !in || (n && !out)) return 1;
+    memcpy(&n_s, in, 8);
+    memcpy(&hb, in + 8, 4);
+    memcpy(&nb32, in + 12, 4);
+    memcpy(&H, in + 16, 8);
+    memcpy(&cc, in + 24, 4);
+    memcpy(&nc32, in + 28, 4);
+    nb = nb32;
+    nc = nc32;
+    if (n_s != n || hb != HF_BLOCK || cc != CR_CHUNK || nb != (n + HF_BLOCK - 1) / HF_BLOCK || H < 0 ||
+        H > nb * HF_BLOCK * 2 + 4 * nb || nc != (H + CR_CHUNK - 1) / CR_CHUNK)
+        return 15;
+    o = cr_header_bytes(nb, nc);
+    if (o > len_in) return 15;
+    memcpy(len, in + 32, 256);
+    for (int v = 0; v < 256; ++v)
+        if (len[v] > HF_LMAX) return 15;
+    hf_canonical(len, code);
+    {   /* per length: how many symbols, the first code, where they start in (length, symbol) order */
+        int nsorted = 0;
+        for (int l = 1; l <= HF_LMAX; ++l) {
+            cnt[l] = 0;
+            offs[l] = (uint32_t)nsorted;
+            first[l] = 0;
+            for (int v = 0; v < 256; ++v)
+                if (len[v] == l) {
+                    if (cnt[l] == 0) first[l] = code[v];
+                    sorted[nsorted++] = (uint8_t)v;
+                    cnt[l]++;
+                }
+        }
+    }
+    hf = calloc((size_t)H + 16, 1);
+    r = malloc(2 * CR_CHUNK + 256);
+    for (k = 0; k < nc && !rc; ++k) { /* LC chunks back to HF bytes */
+        uint32_t sz, m1;
+        const int64_t m = (k + 1) * CR_CHUNK <= H ? CR_CHUNK : H - k * CR_CHUNK;
+        memcpy(&sz, in + 288 + 4 * nb + 8 * k, 4);
+        memcpy(&m1, in + 288 + 4 * nb + 8 * k + 4, 4);
+        const int64_t pad = sz & ~TP_RAW;
+        if (o + pad > len_in) {
+            rc = 15;
+            break;
+        }
+        if (sz & TP_RAW) {
+            if (pad < m) rc = 15;
+            else memcpy(hf + k * CR_CHUNK, in + o, (size_t)m);
+        } else {
+            const int64_t w = m / 4, L0 = (w + 7) / 8;
+            int64_t q, j;
+            if ((int64_t)m1 > 2 * CR_CHUNK + 128 || expand_levels(in + o, pad, m1, 1, r) < 0) {
+                rc = 15;
+                break;
+            }
+            for (j = 0; j + 8 <= (int64_t)m1; j += 8) st64(r + j, tcms8_inv(ld64(r + j)));
+            {
+                uint8_t* bm = malloc((size_t)L0 + 1);
+                q = expand_levels(r, m1, L0, 0, bm);
+                if (q < 0) rc = 15;
+                uint8_t prev[4] = {0, 0, 0, 0};
+                for (int64_t i = 0; i < w && !rc; ++i) {
+                    if ((bm[i / 8] >> (i % 8)) & 1) {
+                        if (q + 4 > (int64_t)m1) {
+                            rc = 15;
+                            break;
+                        }
+                        memcpy(prev, r + q, 4);
+                        q += 4;
+                    }
+                    memcpy(hf + k * CR_CHUNK + 4 * i, prev, 4);
+                }
+                free(bm);
+            }
+        }
+        o += pad;
+    }
+    /* Huffman blocks back to symbols (canonical decoding bit by bit) */
+    for (b = 0; b < nb && !rc; ++b) {
+        uint32_t words;
+        const int64_t s0 = b * HF_BLOCK, s1 = s0 + HF_BLOCK < n ? s0 + HF_BLOCK : n;
+        int64_t p = 8 * pos;
+        memcpy(&words, in + 288 + 4 * b, 4);
+        if (pos + 4 * (int64_t)words > H) {
+            rc = 15;
+            break;
+        }
+        for (int64_t i = s0; i < s1 && !rc; ++i) {
+            uint32_t c = 0;
+            int l, found = 0;
+            for (l = 1; l <= HF_LMAX && !found; ++l) {
+                if (p >= 8 * (pos + 4 * (int64_t)words)) {
+                    rc = 15;
+                    break;
+                }
+                c = (c << 1) | (uint32_t)((hf[p / 8] >> (7 - p % 8)) & 1);
+                ++p;
+                /* canonical codes of length l are first[l] .. first[l] + count[l] - 1 */
+                if (cnt[l] > 0 && c >= first[l] && c - first[l] < cnt[l]) {
+                    out[i] = sorted[offs[l] + (c - first[l])];
+                    found = 1;
+                }
+            }
+            if (!found && !rc) rc = 15;
+        }
+        pos += 4 * (int64_t)words;
+    }
+    free(hf);
+    free(r);
+    return rc;
+}

@@ -573,3 +573,23 @@ def test_md_mean_of_two_and_three(oracle_mod):
     x2 = (6.0 * g[0] ** 2 * g[1]).astype(np.float32)
     out = oracle_mod.compress(x2, 2, interp, order, oracle_mod.eps_constants(x2, oracle_mod.ABS, 0.5))
     assert int(out["codes"][1, 1, 0]) - 128 == 6 - 9
+
+
+@pytest.mark.parametrize("shape,A,workers", [((70, 40, 36), 16, 3), ((33, 20, 17), 8, 4), ((1, 90, 70), 16, 2)])
+def test_parallel_oracle_equals_serial(oracle_mod, shape, A, workers):
+    """The multi-threaded oracle leg of the benchmark (blocks split into d0
+    slabs over host threads) gives the serial oracle's codes, anchors and
+    reconstruction bit for bit, and its decompression the same field."""
+    x = fields.lognormal_grf(shape, seed=3)
+    c = oracle_mod.eps_constants(x, oracle_mod.REL, 1e-3)
+    L = oracle_mod.n_levels(A)
+    interp, order = oracle_mod.levels(L, oracle_mod.CUBIC, (0, 1, 2))
+    a = oracle_mod.compress(x, A, interp, order, c)
+    b = oracle_mod.compress_parallel(x, A, interp, order, c, workers)
+    for k in ("codes", "anchors"):
+        assert np.array_equal(a[k], b[k]), k
+    assert np.array_equal(a["recon"].view(np.uint32), b["recon"].view(np.uint32))
+    col = oracle_mod.collect(x, a["codes"], A)
+    y = oracle_mod.decompress_parallel(x.shape, A, interp, order, c["ebx2_f"], a["codes"], a["anchors"],
+                                       col["out_idx"], col["out_val"], workers)
+    assert np.array_equal(y.view(np.uint32), a["recon"].view(np.uint32))
