@@ -378,6 +378,39 @@ HI_API hi_status hi_tp_encode(const uint8_t* d_in, uint64_t n, uint8_t* d_out, u
 HI_API hi_status hi_tp_decode(const uint8_t* d_in, uint64_t in_len, uint8_t* d_out, uint64_t n, uint32_t* d_status,
                               void* d_ws, size_t ws_bytes, cudaStream_t stream);
 
+/* Compression-ratio-mode lossless pipeline HF-RRE4-TCMS8-RZE1 (Sec. 5.2.3)
+ * over a byte sequence (normally the reordered codes): Huffman coding of the
+ * bytes, then per 16 KiB chunk of the Huffman bytes repeat elimination on
+ * 4-byte words with a recursively reduced bitmap, the magnitude-sign
+ * transform (w << 1) ^ (w >> 63) on 8-byte words, zero elimination on
+ * bytes.  Code construction and container are this library's reading:
+ *   Huffman lengths from the tree merging the two lowest (weight, creation
+ *   index) nodes, leaves created first in symbol order; lengths above 16
+ *   halve every nonzero weight (at least 1) and rebuild; canonical codes;
+ *   blocks of 4096 symbols, MSB first, each padded to 32 bits.
+ *   stream = u64 n | u32 4096 | u32 nblocks | u64 H | u32 16384 |
+ *   u32 nchunks | u8 length[256] | u32 words[nblocks] | (u32 size, u32 m1)
+ *   [nchunks] | zero pad to 16 | payloads padded to 16 (size bit 31: raw).
+ * hi_cr_query: *max_stream_bytes = the largest stream for n input bytes,
+ *   *ws_bytes = the workspace both calls need (either pointer may be NULL).
+ * hi_cr_encode: d_in (n bytes, 16-byte aligned) -> d_out (16-byte aligned,
+ *   out_cap >= max_stream_bytes, not overlapping d_in); the stream length
+ *   goes to *d_len (device uint64).  Nine launches and a 1 KiB memset on
+ *   stream, no sync.
+ * hi_cr_decode: d_in (a stream of in_len bytes, 16-byte aligned) -> d_out
+ *   (n bytes, 16-byte aligned).  A stream that does not match n or whose
+ *   tables, payloads or codes are inconsistent sets HI_ECORRUPT in *d_status
+ *   (may be NULL); the affected chunks or blocks are left unwritten.  Three
+ *   launches on stream, no sync.
+ * All three return HI_EINVAL for NULL or misaligned pointers, short buffers,
+ * a too-small workspace or n >= 2^36 (nothing enqueued), HI_ECUDA if a
+ * launch fails.  The caller owns every buffer; the calls allocate nothing. */
+HI_API hi_status hi_cr_query(uint64_t n, uint64_t* max_stream_bytes, size_t* ws_bytes);
+HI_API hi_status hi_cr_encode(const uint8_t* d_in, uint64_t n, uint8_t* d_out, uint64_t out_cap, uint64_t* d_len,
+                              void* d_ws, size_t ws_bytes, cudaStream_t stream);
+HI_API hi_status hi_cr_decode(const uint8_t* d_in, uint64_t in_len, uint8_t* d_out, uint64_t n, uint32_t* d_status,
+                              void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
 /* The absolute bound and the float32 quantizer constants of Eq. 1 from a
  * value range, on the host, with the same IEEE double operations the device
  * uses in hi_compress (Sec. 6.1.4 read as eps = eb * (vmax - vmin); eps = eb

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhi.so")
 ROOT = os.path.dirname(HERE)
 
-SOURCES = ["hi_api.cu", "hi_compress.cu", "hi_decompress.cu", "hi_aux.cu", "hi_batch.cu", "hi_reorder.cu", "hi_tp.cu"]
+SOURCES = ["hi_api.cu", "hi_compress.cu", "hi_decompress.cu", "hi_aux.cu", "hi_batch.cu", "hi_reorder.cu", "hi_tp.cu", "hi_cr.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "--prec-div=true", "--prec-sqrt=true",
               "-ftz=false", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

@@ -21,7 +21,11 @@ __device__ __forceinline__ float anchor_of(const FieldGeo& g, const float* __res
     return anchors[((int64_t)(tn.o[0] / A + a0) * g.na[1] + (tn.o[1] / A + a1)) * g.na[2] + (tn.o[2] / A + a2)];
 }
 
-template <int A>
+// Issue a tile's code copy right after the previous tile's passes (one
+// buffer): the epilogue only reads the float tile.
+constexpr bool kEarlyTmaD = true;
+
+template <int A, bool EARLY>
 __global__ void __launch_bounds__(kMaxThreads, 6)
     k_decompress(const __grid_constant__ CUtensorMap cmap, const FieldGeo g, const uint8_t* __restrict__ codes,
                  const float* __restrict__ anchors, float* out, const hi_header* __restrict__ hdr,
@@ -80,7 +84,7 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
         const TileInfo ti = s_ti[it & 1];
         if (tid == 0) {
             // one buffer: this tile's copy first, before the queue's round trip
-            if (use_tma && !dbuf && it > 0) tma_issue(cs, &cmap, g, tile, A, &s_mbar[0], tma_bytes);
+            if (use_tma && !dbuf && !EARLY && it > 0) tma_issue(cs, &cmap, g, tile, A, &s_mbar[0], tma_bytes);
             const int nx = (int)gridDim.x + (int)atomicAdd(queue, 1u);
             s_next = nx;
             if (nx < g.ntiles) s_ti[(it + 1) & 1] = tile_info<A>(g, nx);
@@ -123,6 +127,13 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
             } else {
                 levels_ragged<A, TileGeom<A>::L - 1, false>(s_lv, v, cs, h, ti);
             }
+        }
+
+        if constexpr (EARLY) {  // launched only with TMA staging and one buffer
+            // order the passes' generic reads of cs before the copy that overwrites it
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0 && next < g.ntiles) tma_issue(cs, &cmap, g, next, A, &s_mbar[0], tma_bytes);
         }
 
         // ---- epilogue: owned reconstructed values
@@ -174,8 +185,9 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
 template <int A>
 static cudaError_t launch_decompress_t(const DecompressLaunch& c, cudaStream_t st)
 {
-    auto kern = k_decompress<A>;
-    const bool dbuf = c.buffers == 2 && fits_double(kern, decompress_smem_t<A>(c.g.b0, true));
+    const bool dbuf = c.buffers == 2 && fits_double(k_decompress<A, false>, decompress_smem_t<A>(c.g.b0, true));
+    const bool early = kEarlyTmaD && (c.flags & kFlagTma) && !dbuf;
+    auto kern = early ? k_decompress<A, true> : k_decompress<A, false>;
     const size_t smem = decompress_smem_t<A>(c.g.b0, dbuf);
     int grid = 0;
     cudaError_t err = persistent_grid(kern, c.threads, smem, c.num_sms, c.g.ntiles, c.max_ctas, &grid);

@@ -99,25 +99,30 @@ __device__ __forceinline__ float predict(bool cubic, bool have_l3, bool have_r, 
 }
 
 // Rounding to an integer without a conversion instruction: for |t| < 2^22,
-// fl(t + 1.5 * 2^23) has unit spacing, so the addition rounds t to the
-// nearest integer, ties to even, exactly as rint; that integer is the sum's
-// low mantissa bits, and fl(sum - 1.5 * 2^23) is it as a float.  (Larger |t|
-// only occur for outliers, whose code and value do not use the result.)
-constexpr float kRoundMagic = 12582912.0f;  // 1.5 * 2^23
+// fl(t + M) with M in [2^23, 2^24) has unit spacing, so the addition rounds t
+// to the nearest integer; with M even the tie goes to the even integer,
+// exactly as rint.  That integer is the sum's low mantissa bits, and
+// fl(sum - M) is it as a float.  The quantizer takes M = 1.5 * 2^23 + 128,
+// whose bit pattern ends in 0x80: the low byte of the sum's bit pattern is
+// then q + 128, the code itself.  (Larger |t| only occur for outliers, whose
+// code and value do not use the result.)
+constexpr float kRoundMagic = 12582912.0f;   // 1.5 * 2^23
+constexpr float kRoundMagicQ = 12583040.0f;  // 1.5 * 2^23 + 128
 constexpr int kRoundMagicBits = 0x4B400000;
 
-// Linear quantization (Sec. 5.2.1): returns the code (0 = outlier) and the
-// reconstructed value.  t = (x - p) * r; q = rint(t) (ties to even);
-// x' = p + q * 2eps; an outlier when !(|t| < 127.5) or !(|x - x'| < eb_f).
+// Linear quantization (Sec. 5.2.1): returns the code in its low byte (0 =
+// outlier) and the reconstructed value.  t = (x - p) * r; q = rint(t) (ties
+// to even); x' = p + q * 2eps; an outlier when !(|t| < 127.5) or
+// !(|x - x'| < eb_f).
 __device__ __forceinline__ int quantize(float x, float p, float eb_f, float ebx2_f, float r_f, float& xr_out)
 {
     const float t = __fmul_rn(__fsub_rn(x, p), r_f);
-    const float m = __fadd_rn(t, kRoundMagic);
-    const float qf = __fsub_rn(m, kRoundMagic);  // rint(t)
+    const float m = __fadd_rn(t, kRoundMagicQ);
+    const float qf = __fsub_rn(m, kRoundMagicQ);  // rint(t)
     const float xr = __fadd_rn(p, __fmul_rn(qf, ebx2_f));
     const bool ok = (fabsf(t) < kQmax) && (fabsf(__fsub_rn(x, xr)) < eb_f);
     xr_out = ok ? xr : x;
-    return ok ? __float_as_int(m) - (kRoundMagicBits - kRadius) : 0;  // q + 128
+    return ok ? __float_as_int(m) : 0;  // low byte: q + 128
 }
 
 __device__ __forceinline__ float dequantize(int code, float p, float ebx2_f)

@@ -38,6 +38,7 @@ struct CompressOut {
     hi_header* hdr;
     bool vec_ok;   // code rows may be stored as vectors
     bool hist_on;  // count the histogram
+    const float* xg = nullptr;  // not null: outlier values and anchors come from the field in global memory
 };
 
 struct CompressLaunch {
@@ -210,6 +211,12 @@ cudaError_t launch_reorder(const ReorderGeo& G, const uint8_t* src, uint8_t* dst
 // Throughput-mode lossless pipeline TCMS1-BIT1-RRE1 (Sec. 5.2.3).
 size_t tp_ws_bytes(uint64_t n);
 uint64_t tp_stream_bound(uint64_t n);
+size_t cr_ws_bytes(uint64_t n);
+uint64_t cr_stream_bound(uint64_t n);
+cudaError_t launch_cr_encode(const uint8_t* in, uint64_t n, uint8_t* out, uint64_t* len, void* ws, int num_sms,
+                             cudaStream_t st);
+cudaError_t launch_cr_decode(const uint8_t* in, uint64_t in_len, uint64_t n, uint8_t* out, uint32_t* status,
+                             void* ws, int num_sms, cudaStream_t st);
 cudaError_t launch_tp_encode(const uint8_t* in, uint64_t n, uint8_t* out, uint64_t* len, void* ws, int num_sms,
                              cudaStream_t st);
 cudaError_t launch_tp_decode(const uint8_t* in, uint64_t in_len, uint64_t n, uint8_t* out, uint32_t* status, void* ws,

@@ -192,7 +192,7 @@ __device__ __forceinline__ void pass_cols(float* __restrict__ v, uint8_t* __rest
             const int vb = cq * VPQ + cr, cb = cq * CPQ + cr;
             float fa = 0.0f, fb = v[vb], fu = v[vb + 2 * VPD], fv = v[vb + 4 * VPD];
             line_point<A, COMP>(v, cs, h, vb + VPD, cb + CPD, predict(CUBIC, false, true, true, 0.0f, fb, fu, fv));
-#pragma unroll 2
+#pragma unroll
             for (int k = 1; k <= NDM - 2; ++k) {
                 fa = fb, fb = fu, fu = fv;
                 fv = v[vb + (2 * k + 4) * VPD];
@@ -776,7 +776,7 @@ __device__ __forceinline__ void tma_issue(void* dst, const CUtensorMap* map, con
 template <int A>
 __device__ __forceinline__ void outlier_append(bool is_out, int vi, const float* v, hi_header* hdr,
                                                uint32_t* out_idx, float* out_val, uint64_t out_cap,
-                                               const FieldGeo& g, const int o[3])
+                                               const FieldGeo& g, const int o[3], const float* xg = nullptr)
 {
     const unsigned m = __ballot_sync(0xffffffffu, is_out);
     if (m == 0) return;
@@ -789,8 +789,9 @@ __device__ __forceinline__ void outlier_append(bool is_out, int vi, const float*
     if (!is_out) return;
     const unsigned long long pos = base + __popc(m & ((1u << lane) - 1u));
     if (pos < out_cap) {
-        out_idx[pos] = (uint32_t)global_index<A>(g, o, vi);
-        out_val[pos] = v[vi];
+        const int64_t gi = global_index<A>(g, o, vi);
+        out_idx[pos] = (uint32_t)gi;
+        out_val[pos] = xg ? xg[gi] : v[vi];  // an outlier keeps its original value
     } else {
         set_status(&hdr->status, HI_ECAPACITY);
     }
@@ -804,7 +805,7 @@ __device__ __forceinline__ void outlier_append(bool is_out, int vi, const float*
 template <int A, int NW>
 __device__ __forceinline__ void outliers_append_words(const uint32_t* zm, int vi0, const float* v, hi_header* hdr,
                                                       uint32_t* out_idx, float* out_val, uint64_t out_cap,
-                                                      const FieldGeo& g, const int o[3])
+                                                      const FieldGeo& g, const int o[3], const float* xg = nullptr)
 {
     const int lane = threadIdx.x & 31;
     int cnt = 0;
@@ -830,8 +831,9 @@ __device__ __forceinline__ void outliers_append_words(const uint32_t* zm, int vi
             m &= m - 1;
             const int vi = vi0 + 4 * j + (bit >> 3);
             if (pos < out_cap) {
-                out_idx[pos] = (uint32_t)global_index<A>(g, o, vi);
-                out_val[pos] = v[vi];
+                const int64_t gi = global_index<A>(g, o, vi);
+                out_idx[pos] = (uint32_t)gi;
+                out_val[pos] = xg ? xg[gi] : v[vi];
             } else {
                 over = true;
             }
@@ -853,24 +855,54 @@ constexpr int kHistLo = 120, kHistBins = 16;
 // a tile); other codes by a predicated shared-memory reduction, no branch.
 constexpr uint32_t kHotLo = 126;
 
+// One code: the hot bins add 1 << 8 (code - 126) to hacc (0 for codes past
+// 129: the funnel shift clamps at 32); codes below 126 wrap to a shift past
+// 32 as well; every code outside the hot bins is added to s_hist by a
+// predicated shared-memory reduction (no branch).  `valid` false counts
+// nothing.
 __device__ __forceinline__ void hist_hot(uint32_t code, bool valid, uint32_t& hacc, uint32_t* s_hist)
 {
     const uint32_t sh = code * 8u - 8u * kHotLo;
     hacc += valid ? __funnelshift_lc(0u, 1u, sh) : 0u;  // 1 << sh; 0 for sh >= 32
-    const uint32_t cold = (valid && sh >= 32u) ? 1u : 0u;
     asm volatile(
-        "{\n\t.reg .pred pc;\n\t"
-        "setp.ne.u32 pc, %0, 0;\n\t"
-        "@pc red.shared.add.u32 [%1], 1;\n\t}" ::"r"(cold),
-        "r"(smem_addr(s_hist + code))
+        "{\n\t.reg .pred pv, pc;\n\t"
+        "setp.ne.u32 pv, %2, 0;\n\t"
+        "setp.ge.and.u32 pc, %0, 32, pv;\n\t"
+        "@pc red.shared.add.u32 [%1], 1;\n\t}" ::"r"(sh),
+        "r"(smem_addr(s_hist) + 4u * code), "r"((uint32_t)valid)
         : "memory");
 }
 
-// The four codes of a word.
+// The four codes of a word (all valid): one shift amount, one hot add and
+// one predicated reduction per code.
+__device__ __forceinline__ void hist_hot4(uint32_t w, uint32_t& hacc, uint32_t s_base)
+{
+    uint32_t sh[4], ad[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const uint32_t c = __byte_perm(w, 0u, 0x4440u | (uint32_t)b);
+        ad[b] = s_base + 4u * c;
+        sh[b] = 8u * c - 8u * kHotLo;
+        hacc += __funnelshift_lc(0u, 1u, sh[b]);
+    }
+    asm volatile(
+        "{\n\t.reg .pred p0, p1, p2, p3;\n\t"
+        "setp.ge.u32 p0, %0, 32;\n\t"
+        "setp.ge.u32 p1, %1, 32;\n\t"
+        "setp.ge.u32 p2, %2, 32;\n\t"
+        "setp.ge.u32 p3, %3, 32;\n\t"
+        "@p0 red.shared.add.u32 [%4], 1;\n\t"
+        "@p1 red.shared.add.u32 [%5], 1;\n\t"
+        "@p2 red.shared.add.u32 [%6], 1;\n\t"
+        "@p3 red.shared.add.u32 [%7], 1;\n\t}" ::"r"(sh[0]),
+        "r"(sh[1]), "r"(sh[2]), "r"(sh[3]), "r"(ad[0]), "r"(ad[1]), "r"(ad[2]), "r"(ad[3])
+        : "memory");
+}
+
+// The four codes of a word, counted only when `valid`.
 __device__ __forceinline__ void hist_hot4(uint32_t w, bool valid, uint32_t& hacc, uint32_t* s_hist)
 {
-#pragma unroll
-    for (int b = 0; b < 4; ++b) hist_hot(__byte_perm(w, 0u, 0x4440u | (uint32_t)b), valid, hacc, s_hist);
+    if (valid) hist_hot4(w, hacc, smem_addr(s_hist));
 }
 
 // Fold the register counters into the CTA histogram and clear them (whole warps).

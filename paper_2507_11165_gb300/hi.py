@@ -83,7 +83,8 @@ HEADER_BYTES = ctypes.sizeof(HiHeader)
 SYMBOLS = ("hi_query", "hi_compress", "hi_decompress", "hi_autotune", "hi_autotune_errors", "hi_header_read",
            "hi_status_str", "hi_version", "hi_set_stage_events", "hi_compress_static_ws", "hi_batch_query",
            "hi_batch_prepare", "hi_compress_batch", "hi_batch_tune_launch", "hi_resolve_eps", "hi_estimate_cr",
-           "hi_autotune_select")
+           "hi_autotune_select", "hi_tp_query", "hi_tp_encode", "hi_tp_decode", "hi_cr_query", "hi_cr_encode",
+           "hi_cr_decode")
 STATIC_WS_BYTES = 1 << 20  # HI_STATIC_WS_BYTES
 DECOMPRESS_WS_BYTES = 256  # HI_DECOMPRESS_WS_BYTES
 
@@ -125,6 +126,9 @@ def lib():
             L.hi_value_range.argtypes = [ctypes.POINTER(HiParams), P, P, P, sz, P]
             L.hi_tp_encode.argtypes = [P, u64, P, u64, P, P, sz, P]
             L.hi_tp_decode.argtypes = [P, u64, P, u64, P, P, sz, P]
+            L.hi_cr_query.argtypes = [u64, ctypes.POINTER(u64), ctypes.POINTER(sz)]
+            L.hi_cr_encode.argtypes = [P, u64, P, u64, P, P, sz, P]
+            L.hi_cr_decode.argtypes = [P, u64, P, u64, P, P, sz, P]
             L.hi_unreorder_codes.argtypes = [ctypes.POINTER(HiParams), P, P, P]
             L.hi_set_stage_events.argtypes = [P, ctypes.c_uint32]
             L.hi_resolve_eps.argtypes = [ctypes.c_uint32, ctypes.c_double, ctypes.c_float, ctypes.c_float,
@@ -341,6 +345,35 @@ def tp_query(n):
     mx, ws = ctypes.c_uint64(), ctypes.c_size_t()
     _check(lib().hi_tp_query(int(n), ctypes.byref(mx), ctypes.byref(ws)), "hi_tp_query")
     return mx.value, ws.value
+
+
+def cr_query(n):
+    """(largest stream bytes, workspace bytes) of the HF-RRE4-TCMS8-RZE1 pipeline for n input bytes."""
+    mx, ws = ctypes.c_uint64(), ctypes.c_size_t()
+    _check(lib().hi_cr_query(int(n), ctypes.byref(mx), ctypes.byref(ws)), "hi_cr_query")
+    return mx.value, ws.value
+
+
+class CrCodec:
+    """Device buffers for hi_cr_encode / hi_cr_decode of n-byte sequences."""
+
+    def __init__(self, n, device):
+        self.n = int(n)
+        mx, ws = cr_query(self.n)
+        self.stream_buf = torch.empty(mx, dtype=torch.uint8, device=device)
+        self.ws = torch.empty(max(ws, 16), dtype=torch.uint8, device=device)
+        self.len = torch.zeros(1, dtype=torch.int64, device=device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+
+    def encode_into(self, data, stream=None):
+        """Enqueue the encoding of ``data`` (n bytes, device) into ``stream_buf``; length in ``self.len``."""
+        _check(lib().hi_cr_encode(_ptr(data), self.n, _ptr(self.stream_buf), self.stream_buf.numel(),
+                                  _ptr(self.len), _ptr(self.ws), self.ws.numel(), _stream(stream)), "hi_cr_encode")
+
+    def decode_into(self, stream_bytes, in_len, out, stream=None):
+        """Enqueue the decoding of a stream of ``in_len`` bytes into ``out`` (n bytes); status in ``self.status``."""
+        _check(lib().hi_cr_decode(_ptr(stream_bytes), int(in_len), _ptr(out), self.n, _ptr(self.status),
+                                  _ptr(self.ws), self.ws.numel(), _stream(stream)), "hi_cr_decode")
 
 
 class TpCodec:

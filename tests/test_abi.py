@@ -87,3 +87,18 @@ def test_batch_host_validation(lib):
     arr[0].p = lib.make_params((40, 50, 60), 1e-3, "rel", 16)
     assert L.hi_batch_prepare(1, arr, 3, None, 0, C.byref(plan), None) == lib.HI_EINVAL  # bad tuning
     assert L.hi_batch_prepare(1, arr, 0, None, 0, C.byref(plan), None) == lib.HI_EINVAL  # no workspace
+
+
+def test_lossless_query_without_gpu(lib):
+    """Sizes of both lossless pipelines are host-only; the stream bounds cover
+    the oracle's streams, from constant to uniformly random bytes."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(0)
+    for n in (0, 1, 4096, 100000):
+        mx, ws = lib.cr_query(n)
+        mt, wt = lib.tp_query(n)
+        assert ws > 0 and wt > 0
+        for d in (np.full(n, 128, dtype=np.uint8), rng.integers(0, 256, size=n, dtype=np.uint8)):
+            assert oracle.cr_encode(d).size <= mx
+            assert oracle.tp_encode(d).size <= mt
