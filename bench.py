@@ -137,59 +137,214 @@ def kernel_source_sha():
 # ---------------------------------------------------------------------------
 # reference arm / CPU baseline: the oracle, as it stands, on host cores
 # ---------------------------------------------------------------------------
-def oracle_roundtrip(x):
+def oracle_roundtrip(x, A=None, eb=None, levels=None, workers=1):
+    """The oracle's compress + decompress of ``x`` (relative bound): range and
+    eps, auto-tune unless ``levels`` (interp[L], order[L,3]) are given,
+    predict-quantize, outlier/histogram collection, reconstruction.  With
+    workers > 1 the block loops of compress and decompress run on that many
+    host threads (same routine, disjoint blocks)."""
     import oracle
-    import numpy as np
-    cst = oracle.eps_constants(x, oracle.REL, EB)
-    err = oracle.tune_errors(x, A)
-    interp, order = oracle.tune_select(x.shape, A, err)
-    out = oracle.compress(x, A, interp, order, cst)
+    A = A or globals()["A"]
+    eb = eb or EB
+    cst = oracle.eps_constants(x, oracle.REL, eb)
+    if levels is None:
+        err = oracle.tune_errors(x, A)
+        interp, order = oracle.tune_select(x.shape, A, err)
+    else:
+        interp, order = levels
+    if workers > 1:
+        out = oracle.compress_parallel(x, A, interp, order, cst, workers)
+    else:
+        out = oracle.compress(x, A, interp, order, cst)
     col = oracle.collect(x, out["codes"], A)
-    y = oracle.decompress(x.shape, A, interp, order, cst["ebx2_f"], out["codes"], out["anchors"], col["out_idx"],
-                          col["out_val"])
+    if workers > 1:
+        y = oracle.decompress_parallel(x.shape, A, interp, order, cst["ebx2_f"], out["codes"], out["anchors"],
+                                       col["out_idx"], col["out_val"], workers)
+    else:
+        y = oracle.decompress(x.shape, A, interp, order, cst["ebx2_f"], out["codes"], out["anchors"],
+                              col["out_idx"], col["out_val"])
     return out, y, (interp, order)
 
 
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
 def cpu_baseline(x, planes):
-    """Oracle compress + decompress of the first ``planes`` planes (bounded sample)."""
+    """Oracle compress + decompress of the first ``planes`` planes (bounded
+    sample), on every host core (blocks over threads) and on one thread."""
     import numpy as np
     sub = np.ascontiguousarray(x[:planes])
+    cores = host_cores()
     t0 = time.perf_counter()
-    out, y, cfg = oracle_roundtrip(sub)
+    out, y, cfg = oracle_roundtrip(sub, workers=cores)
+    dt_all = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    out1, y1, cfg1 = oracle_roundtrip(sub)
     dt = time.perf_counter() - t0
-    return dict(value=4.0 * sub.size / dt / 1e9, unit="GB/s", cores=1, kind="oracle",
-                sample="compress+decompress of planes [0,%d) of the workload field (%d x %d x %d), "
-                       "single-threaded C oracle" % (planes, planes, x.shape[1], x.shape[2]),
-                seconds=dt), out
+    same = bool(np.array_equal(out["codes"], out1["codes"]) and np.array_equal(y.view(np.uint32), y1.view(np.uint32)))
+    what = "compress+decompress of planes [0,%d) of the workload field (%d x %d x %d), C oracle" % (
+        planes, planes, x.shape[1], x.shape[2])
+    return dict(value=4.0 * sub.size / dt_all / 1e9, unit="GB/s", cores=cores, kind="oracle",
+                sample=what + ", blocks of the compress and decompress loops over %d host threads (range, "
+                              "auto-tune and outlier collection on one)" % cores,
+                seconds=dt_all, threads_equal_single=same,
+                single_thread=dict(value=4.0 * sub.size / dt / 1e9, unit="GB/s", cores=1, seconds=dt,
+                                   sample=what + ", one thread")), out1
 
 
 def run_reference(args):
+    """The reference arm: the oracle, as it stands, on every host core (the
+    block loops of compress and decompress over threads), each step one
+    compress + decompress of planes [0, ref_planes) of the workload field
+    (the whole field by default); one single-threaded step is timed beside."""
     ws, rank, _ = dist_env()
     if ws > 1 and rank != 0:
         return
     from paper_2507_11165_gb300 import fields
     import numpy as np
     x = fields.lognormal_grf(SHAPE, seed=SEED)
-    planes = args.ref_planes
+    planes = min(args.ref_planes, SHAPE[0])
     sub = np.ascontiguousarray(x[:planes])
+    cores = host_cores()
     for _ in range(args.warmup):
-        oracle_roundtrip(sub)
+        oracle_roundtrip(sub, workers=cores)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle_roundtrip(sub)
+        oracle_roundtrip(sub, workers=cores)
         times.append(time.perf_counter() - t0)
     t = sum(times) / len(times)
+    t0 = time.perf_counter()
+    oracle_roundtrip(sub)
+    t1 = time.perf_counter() - t0
     v = 4.0 * sub.size / t / 1e9
+    whole = planes == SHAPE[0]
+    what = ("compress+decompress of the whole %d^3 field per step" % SHAPE[0]) if whole else (
+        "compress+decompress of planes [0,%d) (%d x %d x %d) per step" % (planes, planes, SHAPE[1], SHAPE[2]))
     line = dict(metric=METRIC, value=v, unit="GB/s", impl="reference", n_gpus=args.gpus, steps=args.steps,
                 warmup=args.warmup, ms_per_step=t * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f32", data="synthetic",
-                config=dict(workload=WORKLOAD, sample="planes [0,%d) per step" % planes),
-                cpu_baseline=dict(value=v, unit="GB/s", cores=1, kind="oracle",
-                                  sample="compress+decompress of planes [0,%d) (%d x 512 x 512) per step, "
-                                         "single-threaded C oracle" % (planes, planes)),
+                config=dict(workload=WORKLOAD, sample="whole field" if whole else "planes [0,%d) per step" % planes),
+                cpu_baseline=dict(value=v, unit="GB/s", cores=cores, kind="oracle",
+                                  sample=what + ", C oracle with its block loops over %d host threads" % cores,
+                                  single_thread=dict(value=4.0 * sub.size / t1 / 1e9, unit="GB/s", cores=1,
+                                                     seconds=t1, sample=what + ", one thread, one step")),
                 e2e=dict(value=v, unit="GB/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# The other single-GPU workloads, measured in the default run beside the headline
+# ---------------------------------------------------------------------------
+def field_line(x_host, eb, A_, dev, levels=None, reps=20, cpu=True):
+    """One field at a relative bound: compress and decompress through the
+    public calls (every launch of each), CUDA events, median of ``reps``, L2
+    flushed (a 256 MiB write) before every timed call; quality and entropy
+    size estimate; the oracle's result compared bit for bit and the oracle
+    timed on every host core and on one thread.  ``levels``: fixed
+    (interp, order) per level, or None for the auto-tuner."""
+    import numpy as np
+    import torch
+    from paper_2507_11165_gb300 import hi
+    x = torch.from_numpy(x_host).to(dev)
+    N = x_host.size
+    p = hi.make_params(x.shape, eb, "rel", A_, autotune=levels is None, levels=levels)
+    b = hi.alloc(p, x.shape, dev, out_cap=N, hist=True, recon=False)  # every point may be an outlier
+    out = torch.empty_like(x)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        hi.compress_into(x, b)
+        hi.decompress_into(b, out, st)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(reps)]
+    for r in ev:
+        flush.fill_(1)
+        r[0].record(stream)
+        hi.compress_into(x, b)
+        r[1].record(stream)
+        flush.fill_(2)
+        r[2].record(stream)
+        hi.decompress_into(b, out, st)
+        r[3].record(stream)
+    torch.cuda.synchronize()
+    c_ms = statistics.median(r[0].elapsed_time(r[1]) for r in ev)
+    d_ms = statistics.median(r[2].elapsed_time(r[3]) for r in ev)
+    h = hi.read_header(b.header)
+    assert h.status == 0 and int(st.item()) == 0, (h.status, int(st.item()))
+    hist = b.hist.cpu().numpy().view(np.uint32)
+    est = hi.estimate_cr(hist, int(h.n_outliers), int(h.n_anchors), N)
+    err = (out - x).abs().max().item()
+    mse = float(((out.double() - x.double()) ** 2).mean().item())
+    vrange = float(h.vmax) - float(h.vmin)
+    line = dict(shape=list(x_host.shape), eb=eb, anchor_stride=A_,
+                levels=[(int(h.level[l].interp), list(h.level[l].order)) for l in range(h.n_levels)],
+                tuned=levels is None, compress_ms=c_ms, decompress_ms=d_ms,
+                compress_gbs=4.0 * N / (c_ms * 1e-3) / 1e9, decompress_gbs=4.0 * N / (d_ms * 1e-3) / 1e9,
+                n_outliers=int(h.n_outliers), entropy_bits=est["entropy_bits"], cr_est=est["cr"],
+                max_err_over_eps=err / h.eps,
+                psnr_db=20 * math.log10(vrange) - 10 * math.log10(mse) if mse > 0 else None,
+                gpu_launches_per_call={"compress": 3, "decompress": 2},
+                l2="256 MiB written between timed calls")
+    if cpu:
+        import oracle
+        olv = None
+        if levels is not None:
+            olv = (np.array([lv[0] for lv in levels], dtype=np.uint8),
+                   np.array([lv[1] for lv in levels], dtype=np.uint8))
+        cores = host_cores()
+        t0 = time.perf_counter()
+        ref, y, _ = oracle_roundtrip(x_host, A=A_, eb=eb, levels=olv, workers=cores)
+        t_all = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oracle_roundtrip(x_host, A=A_, eb=eb, levels=olv)
+        t_one = time.perf_counter() - t0
+        line["bit_exact_vs_oracle"] = bool(
+            np.array_equal(b.codes.cpu().numpy().reshape(x_host.shape), ref["codes"])
+            and np.array_equal(out.cpu().numpy().view(np.uint32), y.view(np.uint32)))
+        line["oracle"] = dict(kind="oracle", what="compress + decompress of the whole field", unit="GB/s",
+                              all_cores=dict(cores=cores, value=4.0 * N / t_all / 1e9, seconds=t_all),
+                              one_thread=dict(cores=1, value=4.0 * N / t_one / 1e9, seconds=t_one))
+    del b, out, flush, x
+    torch.cuda.empty_cache()
+    return line
+
+
+def other_workloads(args, dev, x512_host):
+    """Config 0 (64^3 bumps, A = 8, cubic, latency), config 2 (the 2D and the
+    stratified 3D field at 1e-3 and 1e-4), the bound sweep of the 512^3 field
+    (1e-2, 1e-4), the batched workload and the serving loop."""
+    import torch
+    from paper_2507_11165_gb300 import fields, hi
+    res = {}
+    x0 = fields.bumps_field((64, 64, 64), seed=0)
+    c0 = field_line(x0, 1e-3, 8, dev, levels=[(hi.CUBIC, (0, 1, 2))] * 3, reps=50)
+    c0["latency_us"] = dict(compress=1e3 * c0["compress_ms"], decompress=1e3 * c0["decompress_ms"])
+    res["config0_64cube_bumps_A8_cubic_rel1e-3"] = c0
+    x2a = fields.fronts_2d((1800, 3600), seed=2)
+    x2b = fields.stratified_3d((100, 500, 500), seed=3)
+    for eb in (1e-3, 1e-4):
+        res["config2a_1800x3600_fronts_rel%g" % eb] = field_line(x2a, eb, 16, dev)
+        res["config2b_100x500x500_stratified_rel%g" % eb] = field_line(x2b, eb, 16, dev)
+    for eb in (1e-2, 1e-4):
+        res["config1_512cube_grf_rel%g" % eb] = field_line(x512_host, eb, 16, dev, reps=10, cpu=False)
+    if not args.no_batch:
+        try:
+            res["batch"] = batch_line(args)
+        except Exception as e:  # keep the headline line even if a side workload fails
+            res["batch"] = dict(error=repr(e))
+        torch.cuda.empty_cache()
+    if not args.no_serve:
+        try:
+            res["serve"] = serve_line(args, base=torch.from_numpy(x512_host).to(dev))
+        except Exception as e:
+            res["serve"] = dict(error=repr(e))
+        torch.cuda.empty_cache()
+    return res
 
 
 # ---------------------------------------------------------------------------
@@ -334,10 +489,37 @@ def run_gpu(args):
                        decode_gbs_of_codes=N / (td_ms * 1e-3) / 1e9, stream_bytes=s_len,
                        codes_ratio=N / s_len, record_bytes=rec_bytes, cr=4.0 * N / rec_bytes,
                        launches_encode=3, launches_decode=2)
-    del seq, back, codec
+    # compression-ratio-mode lossless pipeline HF-RRE4-TCMS8-RZE1 (Sec. 5.2.3) on the same codes
+    crc = hi.CrCodec(N, dev)
+    for _ in range(2):
+        crc.encode_into(seq, stream=stream)
+        torch.cuda.synchronize()
+        c_len = int(crc.len.item())
+        crc.decode_into(crc.stream_buf, c_len, back, stream=stream)
+    cev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(5)]
+    for e in cev:
+        e[0].record(stream)
+        crc.encode_into(seq, stream=stream)
+        e[1].record(stream)
+        crc.decode_into(crc.stream_buf, c_len, back, stream=stream)
+        e[2].record(stream)
+    torch.cuda.synchronize()
+    assert int(crc.status.item()) == 0 and torch.equal(back, seq) and int(crc.len.item()) == c_len
+    ce_ms = statistics.median(e[0].elapsed_time(e[1]) for e in cev)
+    cd_ms = statistics.median(e[1].elapsed_time(e[2]) for e in cev)
+    rec_cr = c_len + 8 * n_out_tp + 4 * int(b.anchors.numel()) + hi.HEADER_BYTES
+    lossless_cr = dict(pipeline="HF-RRE4-TCMS8-RZE1",
+                       kernels=["k_cr_hist", "k_cr_codebook", "k_hf_count", "k_cr_scan_words", "k_hf_encode",
+                                "k_cr_lc_encode", "k_cr_scan_payloads", "k_cr_gather", "k_cr_dec_scan",
+                                "k_cr_lc_decode", "k_hf_decode"],
+                       encode_ms=ce_ms, decode_ms=cd_ms, encode_gbs_of_codes=N / (ce_ms * 1e-3) / 1e9,
+                       decode_gbs_of_codes=N / (cd_ms * 1e-3) / 1e9, stream_bytes=c_len, codes_ratio=N / c_len,
+                       record_bytes=rec_cr, cr=4.0 * N / rec_cr, launches_encode=8, launches_decode=3)
+    del seq, back, codec, crc
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     e2e = None
+    b2 = None
     if not args.no_e2e:
         xh = torch.from_numpy(x_host).pin_memory()
         codes_h = torch.empty(N, dtype=torch.uint8).pin_memory()
@@ -394,6 +576,12 @@ def run_gpu(args):
             ems = float(tt.item())
         e2e = dict(value=ws * bytes_in / (ems * 1e-3) / 1e9, unit="GB/s", ms_per_step=ems,
                    h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h))
+        del b2, xh, codes_h, anch_h, oidx_h, oval_h, hdr_h, y_h, xd
+
+    others = None
+    if rank == 0 and ws == 1 and not args.no_extra:
+        torch.cuda.empty_cache()
+        others = other_workloads(args, dev, x_host)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -429,10 +617,12 @@ def run_gpu(args):
                          levels=[(int(h.level[l].interp), list(h.level[l].order)) for l in range(h.n_levels)]),
             reorder=reorder,
             lossless_tp=lossless_tp,
+            lossless_cr=lossless_cr,
             e2e=e2e,
             gpu_launches=5 * args.steps,  # setup, range + auto-tune (one launch), predict-quantize, scatter, reconstruct
             cpu_baseline=cpu,
             clocks=clocks,
+            other_workloads=others,
         )
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -462,6 +652,10 @@ BATCH_METRIC = "batched compress input GB/s per GB300 (256 fields, rel eb 1e-2/1
 
 
 def run_batch(args):
+    print(json.dumps(batch_line(args)), flush=True)
+
+
+def batch_line(args):
     """Batched workload: 256 fields with sides log-uniform in [32, 256], rel eb
     per field from {1e-2, 1e-3, 1e-4}, auto-tuned levels; one step = one
     hi_compress_batch (four launches for all fields) replayed from a captured
@@ -584,13 +778,17 @@ def run_batch(args):
         gpu_launches=4 * steps,  # setup, range + auto-tune, gather, predict-quantize
         clocks=clk.summary(),
     )
-    print(json.dumps(line), flush=True)
+    return line
 
 
 SERVE_METRIC = "serving: sustained input GB/s with p50/p99 latency (ms), Poisson 200 req/s, 40 GB budget"
 
 
 def run_serve(args):
+    print(json.dumps(serve_line(args)), flush=True)
+
+
+def serve_line(args, base=None):
     """Serving workload: Poisson arrivals (200 / s), half compress of a
     snapshot, half decompress of an earlier record; cubic sides log-uniform
     in [64, 512]; rel eb from {1e-2, 1e-3, 1e-4, 1e-5}; admitted by slot
@@ -605,7 +803,8 @@ def run_serve(args):
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    base = torch.from_numpy(fields.lognormal_grf(SHAPE, seed=SEED)).to(dev)
+    if base is None:
+        base = torch.from_numpy(fields.lognormal_grf(SHAPE, seed=SEED)).to(dev)
     reqs = serve.make_requests(n=args.serve_requests, rate=200.0, seed=5, lo=64, hi=SHAPE[0])
     warm = serve.make_requests(n=16, rate=1e6, seed=6, lo=64, hi=SHAPE[0])
 
@@ -641,7 +840,7 @@ def run_serve(args):
         gpu_launches=main["launches"],  # compress 3 (+3 on a capacity re-run), decompress 2 per request
         clocks=clk.summary(),
     )
-    print(json.dumps(line), flush=True)
+    return line
 
 
 OOC_METRIC = "out-of-core compress: input GB/s of a host-resident field, two shards on the device"
@@ -704,8 +903,11 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="single: only the headline field (no other workloads)")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--cpu-planes", type=int, default=512)
-    ap.add_argument("--ref-planes", type=int, default=64)
+    ap.add_argument("--ref-planes", type=int, default=512)
     ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "ooc"],
                     help="single: the 512^3 field (default); batch: 256 fields in one batched launch per stage; "
                          "serve: a Poisson request stream through the continuous-batching loop")

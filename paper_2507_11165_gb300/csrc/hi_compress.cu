@@ -6,13 +6,10 @@
 
 namespace hi {
 
-// Issue a tile's copy right after the previous tile's passes (one buffer).
-constexpr bool kEarlyTma = false;
-
 // ---------------------------------------------------------------------------
 // Predict + quantize
 // ---------------------------------------------------------------------------
-template <int A, bool EARLY>
+template <int A>
 __global__ void __launch_bounds__(kMaxThreads, 7)
     k_compress(const __grid_constant__ CUtensorMap tmap, const FieldGeo g, const float* __restrict__ x,
                uint8_t* __restrict__ codes, float* __restrict__ anchors, uint32_t* __restrict__ out_idx,
@@ -37,10 +34,6 @@ __global__ void __launch_bounds__(kMaxThreads, 7)
 
     const int tid = threadIdx.x;
     const bool use_tma = flags & kFlagTma;
-    // one buffer: the next tile's copy goes out as soon as the passes are
-    // done, while the epilogue runs (which then reads outlier values and
-    // anchors from x, not from the buffer)
-    constexpr bool early = EARLY;  // launched only with TMA staging and one buffer
     {   // an earlier stage failed (bad range, device-side EINVAL): leave outputs untouched
         const uint32_t st = hdr->status;
         if (__syncthreads_or(st != 0 && st != HI_ECAPACITY)) return;
@@ -84,7 +77,7 @@ __global__ void __launch_bounds__(kMaxThreads, 7)
         if (tid == 0) {
             // one buffer: this tile's copy first (the buffer is free again),
             // before the queue's round trip
-            if (use_tma && !dbuf && !early && it > 0) tma_issue(v, &tmap, g, tile, A, &s_mbar[0], tma_bytes);
+            if (use_tma && !dbuf && it > 0) tma_issue(v, &tmap, g, tile, A, &s_mbar[0], tma_bytes);
             const int nx = (int)gridDim.x + (int)atomicAdd(queue, 1u);
             s_next = nx;
             if (nx < g.ntiles) s_ti[(it + 1) & 1] = tile_info<A>(g, nx);
@@ -115,18 +108,8 @@ __global__ void __launch_bounds__(kMaxThreads, 7)
         const int next = s_next;
         {
             const CompressOut out{codes, anchors, out_idx, out_val, out_cap, recon_g, hdr,
-                                  (flags & kFlagVecCodes) != 0, hist_on, EARLY ? x : nullptr};
-            if constexpr (EARLY) {
-                const auto mid = [&]() {
-                    // order the passes' generic writes of v before the copy that overwrites it
-                    fence_proxy_async_smem();
-                    __syncthreads();
-                    if (threadIdx.x == 0 && s_next < g.ntiles) tma_issue(v, &tmap, g, s_next, A, &s_mbar[0], tma_bytes);
-                };
-                compress_tile<A>(g, ti, v, cs, hc, s_hist, s_sel, s_lv, h, full_ok, out, mid);
-            } else {
-                compress_tile<A>(g, ti, v, cs, hc, s_hist, s_sel, s_lv, h, full_ok, out);
-            }
+                                  (flags & kFlagVecCodes) != 0, hist_on};
+            compress_tile<A>(g, ti, v, cs, hc, s_hist, s_sel, s_lv, h, full_ok, out);
             if (hist_on && ++nslow % kHistFoldTiles == 0) hist_fold(hc, s_hist);
         }
         // keep the buffers until every thread is done; order the generic-proxy
@@ -141,9 +124,8 @@ __global__ void __launch_bounds__(kMaxThreads, 7)
 template <int A>
 static cudaError_t launch_compress_t(const CompressLaunch& c, cudaStream_t st)
 {
-    const bool dbuf = c.buffers == 2 && fits_double(k_compress<A, false>, compress_smem_t<A>(c.g.b0, true, c.threads));
-    const bool early = kEarlyTma && c.recon == nullptr && (c.flags & kFlagTma) && !dbuf;
-    auto kern = early ? k_compress<A, true> : k_compress<A, false>;
+    auto kern = k_compress<A>;
+    const bool dbuf = c.buffers == 2 && fits_double(kern, compress_smem_t<A>(c.g.b0, true, c.threads));
     const size_t smem = compress_smem_t<A>(c.g.b0, dbuf, c.threads);
     int grid = 0;
     cudaError_t err = persistent_grid(kern, c.threads, smem, c.num_sms, c.g.ntiles, c.max_ctas, &grid);

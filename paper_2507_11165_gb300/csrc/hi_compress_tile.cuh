@@ -9,23 +9,14 @@
 
 namespace hi {
 
-struct NoMid {
-    __device__ void operator()() const {}
-};
-
 // The tile's floats are in v (reconstructed in place), its codes are staged
 // in cs; g, ti: the field and the tile; s_sel / s_lv: the level
 // configuration; full_ok: the field may take the compile-time full-tile
 // passes; out: a CompressOut or a reference to one in shared memory.
-// mid() runs between the level passes and the epilogue (all threads, after
-// the passes' last barrier); when out.xg is not null the epilogue reads
-// outlier values and anchors from the field in global memory instead of v,
-// so that mid() may hand the tile buffer to the next tile's copy.
-template <int A, class Out, class Mid = NoMid>
+template <int A, class Out>
 __device__ __forceinline__ void compress_tile(const FieldGeo& g, const TileInfo& ti, float* v, uint8_t* cs,
                                               uint16_t* hc, uint32_t* s_hist, const int* s_sel,
-                                              const hi_level* s_lv, const Hot h, bool full_ok, const Out& out,
-                                              const Mid& mid = Mid())
+                                              const hi_level* s_lv, const Hot h, bool full_ok, const Out& out)
 {
     using Lw = Lay<A>;
     const int tid = threadIdx.x;
@@ -38,9 +29,7 @@ __device__ __forceinline__ void compress_tile(const FieldGeo& g, const TileInfo&
     } else {
         levels_ragged<A, TileGeom<A>::L - 1, true>(s_lv, v, cs, h, ti);
     }
-    mid();
     const bool vec_ok = out.vec_ok, hist_on = out.hist_on;
-    const float* __restrict__ const xg = out.xg;
     uint8_t* __restrict__ const codes = out.codes;
     float* __restrict__ const anchors = out.anchors;
     uint32_t* __restrict__ const out_idx = out.out_idx;
@@ -88,7 +77,7 @@ __device__ __forceinline__ void compress_tile(const FieldGeo& g, const TileInfo&
                 for (int j = 0; j < CH; ++j)
                     zm[j] = act ? ~(((w[j] & 0x7f7f7f7fu) + 0x7f7f7f7fu) | w[j]) & 0x80808080u : 0u;
                 outliers_append_words<A, CH>(zm, c0 * Lw::PY + c1 * Lw::PX + ch * CH * 4, v, hdr, out_idx, out_val,
-                                             out_cap, g, ti.o, xg);
+                                             out_cap, g, ti.o);
             }
             if (hist_on) {
                 if constexpr (kHot) {
@@ -138,7 +127,7 @@ __device__ __forceinline__ void compress_tile(const FieldGeo& g, const TileInfo&
             if (__any_sync(0xffffffffu, act && z != 0)) {
                 uint32_t zm[1];
                 zm[0] = act ? ~(((w & 0x7f7f7f7fu) + 0x7f7f7f7fu) | w) & 0x80808080u : 0u;
-                outliers_append_words<A, 1>(zm, vi, v, hdr, out_idx, out_val, out_cap, g, ti.o, xg);
+                outliers_append_words<A, 1>(zm, vi, v, hdr, out_idx, out_val, out_cap, g, ti.o);
             }
             if (hist_on) {
                 if constexpr (kHot) {
@@ -173,7 +162,7 @@ __device__ __forceinline__ void compress_tile(const FieldGeo& g, const TileInfo&
                     hist_count(hc, s_hist, code, act);
             }
             outlier_append<A>(act && code == 0, c0 * Lw::PY + c1 * Lw::PX + c2, v, hdr, out_idx, out_val, out_cap,
-                              g, ti.o, xg);
+                              g, ti.o);
         }
     } else {
         const int items = rows * own2;
@@ -195,7 +184,7 @@ __device__ __forceinline__ void compress_tile(const FieldGeo& g, const TileInfo&
                     hist_count(hc, s_hist, code, act);
             }
             outlier_append<A>(act && code == 0, c0 * Lw::PY + c1 * Lw::PX + c2, v, hdr, out_idx, out_val, out_cap,
-                              g, ti.o, xg);
+                              g, ti.o);
         }
     }
     if constexpr (kHot) {
@@ -216,8 +205,7 @@ __device__ __forceinline__ void compress_tile(const FieldGeo& g, const TileInfo&
         if (l0 <= ti.own[0] && l1 <= ti.own[1] && l2 <= ti.own[2]) {
             const int64_t ai = ((int64_t)(ti.o[0] / A + a0) * g.na[1] + (ti.o[1] / A + a1)) * g.na[2] +
                                (ti.o[2] / A + a2);
-            anchors[ai] = xg ? xg[((int64_t)(ti.o[0] + l0) * g.n[1] + (ti.o[1] + l1)) * g.n[2] + ti.o[2] + l2]
-                             : v[l0 * Lw::PY + l1 * Lw::PX + l2];
+            anchors[ai] = v[l0 * Lw::PY + l1 * Lw::PX + l2];
             if (hist_on) atomicSub(&s_hist[kRadius], 1u);  // anchors are not predicted
         }
     }

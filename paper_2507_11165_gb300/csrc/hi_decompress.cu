@@ -65,10 +65,11 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
         mbar_init(&s_mbar[0], 1);
         mbar_init(&s_mbar[1], 1);
         fence_mbar_init();
-        if ((int)blockIdx.x < g.ntiles) s_ti[0] = tile_info<A>(g, blockIdx.x);
+        if ((int)blockIdx.x < g.ntiles) s_ti[0] = tile_info<A>(g, shell_first(g, blockIdx.x));
         if (use_tma) {
             prefetch_tmap(&cmap);
-            if ((int)blockIdx.x < g.ntiles) tma_issue(cbuf0, &cmap, g, blockIdx.x, A, &s_mbar[0], tma_bytes);
+            if ((int)blockIdx.x < g.ntiles)
+                tma_issue(cbuf0, &cmap, g, shell_first(g, blockIdx.x), A, &s_mbar[0], tma_bytes);
         }
     }
     __syncthreads();
@@ -84,15 +85,16 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
         const TileInfo ti = s_ti[it & 1];
         if (tid == 0) {
             // one buffer: this tile's copy first, before the queue's round trip
-            if (use_tma && !dbuf && !EARLY && it > 0) tma_issue(cs, &cmap, g, tile, A, &s_mbar[0], tma_bytes);
+            if (use_tma && !dbuf && !EARLY && it > 0)
+                tma_issue(cs, &cmap, g, shell_first(g, tile), A, &s_mbar[0], tma_bytes);
             const int nx = (int)gridDim.x + (int)atomicAdd(queue, 1u);
             s_next = nx;
-            if (nx < g.ntiles) s_ti[(it + 1) & 1] = tile_info<A>(g, nx);
+            if (nx < g.ntiles) s_ti[(it + 1) & 1] = tile_info<A>(g, shell_first(g, nx));
             s_rare.o[0] = ti.o[0], s_rare.o[1] = ti.o[1], s_rare.o[2] = ti.o[2];
             if (use_tma && dbuf && nx < g.ntiles)
-                tma_issue(buf ? cbuf0 : cbuf1, &cmap, g, nx, A, &s_mbar[buf ^ 1], tma_bytes);
+                tma_issue(buf ? cbuf0 : cbuf1, &cmap, g, shell_first(g, nx), A, &s_mbar[buf ^ 1], tma_bytes);
             // one buffer: the next tile waits in L2 until this one is done
-            if (use_tma && !dbuf && nx < g.ntiles) tma_l2_prefetch(&cmap, g, nx, A);
+            if (use_tma && !dbuf && nx < g.ntiles) tma_l2_prefetch(&cmap, g, shell_first(g, nx), A);
         }
         if (tid < 8) {  // seed the anchors
             const int a0 = (tid >> 2) & 1, a1 = (tid >> 1) & 1, a2 = tid & 1;
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(kMaxThreads, 6)
             // order the passes' generic reads of cs before the copy that overwrites it
             fence_proxy_async_smem();
             __syncthreads();
-            if (tid == 0 && next < g.ntiles) tma_issue(cs, &cmap, g, next, A, &s_mbar[0], tma_bytes);
+            if (tid == 0 && next < g.ntiles) tma_issue(cs, &cmap, g, shell_first(g, next), A, &s_mbar[0], tma_bytes);
         }
 
         // ---- epilogue: owned reconstructed values

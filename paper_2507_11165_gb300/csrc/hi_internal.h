@@ -38,7 +38,6 @@ struct CompressOut {
     hi_header* hdr;
     bool vec_ok;   // code rows may be stored as vectors
     bool hist_on;  // count the histogram
-    const float* xg = nullptr;  // not null: outlier values and anchors come from the field in global memory
 };
 
 struct CompressLaunch {

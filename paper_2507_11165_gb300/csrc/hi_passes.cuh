@@ -751,6 +751,15 @@ __device__ __forceinline__ void prefetch_rows_l2(const void* base, int elem, con
     }
 }
 
+// Queue position with the field's shell (its last blocks along each dim,
+// the ragged tiles of most fields) taken first, then the interior: the slow
+// tiles start early instead of forming the launch's tail.
+__device__ __forceinline__ int shell_first(const FieldGeo& g, int pos)
+{
+    const int n_shell = g.ntiles - g.ni[0] * g.ni[1] * g.ni[2];
+    return pos < n_shell ? pos + (g.ntiles - n_shell) : pos - n_shell;
+}
+
 // L2 prefetch of the box of the tile at queue position `tile`.
 __device__ __forceinline__ void tma_l2_prefetch(const CUtensorMap* map, const FieldGeo& g, int tile, int A)
 {
@@ -776,7 +785,7 @@ __device__ __forceinline__ void tma_issue(void* dst, const CUtensorMap* map, con
 template <int A>
 __device__ __forceinline__ void outlier_append(bool is_out, int vi, const float* v, hi_header* hdr,
                                                uint32_t* out_idx, float* out_val, uint64_t out_cap,
-                                               const FieldGeo& g, const int o[3], const float* xg = nullptr)
+                                               const FieldGeo& g, const int o[3])
 {
     const unsigned m = __ballot_sync(0xffffffffu, is_out);
     if (m == 0) return;
@@ -789,9 +798,8 @@ __device__ __forceinline__ void outlier_append(bool is_out, int vi, const float*
     if (!is_out) return;
     const unsigned long long pos = base + __popc(m & ((1u << lane) - 1u));
     if (pos < out_cap) {
-        const int64_t gi = global_index<A>(g, o, vi);
-        out_idx[pos] = (uint32_t)gi;
-        out_val[pos] = xg ? xg[gi] : v[vi];  // an outlier keeps its original value
+        out_idx[pos] = (uint32_t)global_index<A>(g, o, vi);
+        out_val[pos] = v[vi];
     } else {
         set_status(&hdr->status, HI_ECAPACITY);
     }
@@ -805,7 +813,7 @@ __device__ __forceinline__ void outlier_append(bool is_out, int vi, const float*
 template <int A, int NW>
 __device__ __forceinline__ void outliers_append_words(const uint32_t* zm, int vi0, const float* v, hi_header* hdr,
                                                       uint32_t* out_idx, float* out_val, uint64_t out_cap,
-                                                      const FieldGeo& g, const int o[3], const float* xg = nullptr)
+                                                      const FieldGeo& g, const int o[3])
 {
     const int lane = threadIdx.x & 31;
     int cnt = 0;
@@ -831,9 +839,8 @@ __device__ __forceinline__ void outliers_append_words(const uint32_t* zm, int vi
             m &= m - 1;
             const int vi = vi0 + 4 * j + (bit >> 3);
             if (pos < out_cap) {
-                const int64_t gi = global_index<A>(g, o, vi);
-                out_idx[pos] = (uint32_t)gi;
-                out_val[pos] = xg ? xg[gi] : v[vi];
+                out_idx[pos] = (uint32_t)global_index<A>(g, o, vi);
+                out_val[pos] = v[vi];
             } else {
                 over = true;
             }
