@@ -843,6 +843,78 @@ def serve_line(args, base=None):
     return line
 
 
+SHARD_METRIC = "sharded compress: input GB/s of one field split along d0 over the ranks (whole-job, max over ranks)"
+
+
+def run_shard(args):
+    """One field split along d0 over the ranks of the job (torchrun, NCCL):
+    every rank holds its read planes on its GPU and runs
+    shard.compress_distributed (value-range all-reduce, auto-tune rows of the
+    global sample blocks, its owned part with global indices); one step is
+    that whole call (host wall clock between barriers, max over ranks).  At
+    N = 1 the single rank holds the whole field; rank 0 also checks the
+    merged record against hi_compress of the whole field when N = 1."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2507_11165_gb300 import fields, hi, shard
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    x_np = fields.lognormal_grf(SHAPE, seed=SEED)
+    plan = shard.shard_bounds(SHAPE[0], A, ws)
+    sh = plan[rank] if rank < len(plan) else None
+    x_local = torch.from_numpy(np.ascontiguousarray(x_np[sh["own_lo"]:sh["read_hi"]] if sh else x_np[:0])).to(dev)
+    ex = shard.GpuShardExecutor(dev)
+
+    def step():
+        return shard.compress_distributed(x_local, SHAPE, EB, A, ex, mode="rel", autotune=True)
+
+    for _ in range(max(1, args.warmup)):
+        part = step()
+    steps = max(1, min(args.steps, 10))
+    times = []
+    with ClockSampler(local) as clk:
+        for _ in range(steps):
+            if ws > 1:
+                dist.barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            part = step()
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+    t = statistics.median(times)
+    if ws > 1:
+        tt = torch.tensor([t], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    exact = None
+    if ws == 1:
+        c = hi.compress(torch.from_numpy(x_np).to(dev), EB, "rel", A, autotune=True, out_cap=x_np.size // 8)
+        m = shard.merge_parts([part])
+        exact = bool(np.array_equal(m["codes"].numpy().reshape(SHAPE), c.codes.cpu().numpy().reshape(SHAPE)))
+    if rank == 0:
+        line = dict(
+            metric=SHARD_METRIC, value=4.0 * x_np.size / t / 1e9, unit="GB/s", n_gpus=ws, steps=steps,
+            warmup=max(1, args.warmup), ms_per_step=1e3 * t, higher_is_better=True, scaling="strong",
+            vs_baseline=None, dtype="f32", data="synthetic",
+            config=dict(workload=WORKLOAD + ", split along d0 over the ranks", shards=len(plan),
+                        parallelism="shard%d" % ws,
+                        step="shard.compress_distributed: range all-reduce, auto-tune rows all-reduce, own part "
+                             "(host wall clock, results on the device)"),
+            bit_exact_vs_whole_field=exact,
+            gpu_launches=None,
+            clocks=clk.summary(),
+        )
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
 OOC_METRIC = "out-of-core compress: input GB/s of a host-resident field, two shards on the device"
 
 
@@ -908,7 +980,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--cpu-planes", type=int, default=512)
     ap.add_argument("--ref-planes", type=int, default=512)
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "ooc"],
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "ooc", "shard"],
                     help="single: the 512^3 field (default); batch: 256 fields in one batched launch per stage; "
                          "serve: a Poisson request stream through the continuous-batching loop")
     ap.add_argument("--batch-fields", type=int, default=256)
@@ -937,6 +1009,8 @@ def main():
         run_serve(args)
     elif args.workload == "ooc":
         run_ooc(args)
+    elif args.workload == "shard":
+        run_shard(args)
     else:
         run_gpu(args)
 

@@ -403,8 +403,9 @@ HI_API hi_status hi_tp_decode(const uint8_t* d_in, uint64_t in_len, uint8_t* d_o
  *   (may be NULL); the affected chunks or blocks are left unwritten.  Three
  *   launches on stream, no sync.
  * All three return HI_EINVAL for NULL or misaligned pointers, short buffers,
- * a too-small workspace or n >= 2^36 (nothing enqueued), HI_ECUDA if a
- * launch fails.  The caller owns every buffer; the calls allocate nothing. */
+ * a too-small workspace or n >= 2^32 (symbol counts are 32-bit; nothing
+ * enqueued), HI_ECUDA if a launch fails.  The caller owns every buffer; the
+ * calls allocate nothing. */
 HI_API hi_status hi_cr_query(uint64_t n, uint64_t* max_stream_bytes, size_t* ws_bytes);
 HI_API hi_status hi_cr_encode(const uint8_t* d_in, uint64_t n, uint8_t* d_out, uint64_t out_cap, uint64_t* d_len,
                               void* d_ws, size_t ws_bytes, cudaStream_t stream);

@@ -922,7 +922,7 @@ hi_status hi_tp_decode(const uint8_t* d_in, uint64_t in_len, uint8_t* d_out, uin
 
 hi_status hi_cr_query(uint64_t n, uint64_t* max_stream_bytes, size_t* ws_bytes)
 {
-    if (n >= (1ull << 36)) return HI_EINVAL;
+    if (n >= (1ull << 32)) return HI_EINVAL;
     if (max_stream_bytes) *max_stream_bytes = cr_stream_bound(n);
     if (ws_bytes) *ws_bytes = cr_ws_bytes(n);
     return HI_OK;
@@ -931,7 +931,7 @@ hi_status hi_cr_query(uint64_t n, uint64_t* max_stream_bytes, size_t* ws_bytes)
 hi_status hi_cr_encode(const uint8_t* d_in, uint64_t n, uint8_t* d_out, uint64_t out_cap, uint64_t* d_len,
                        void* d_ws, size_t ws_bytes, cudaStream_t stream)
 {
-    if (n >= (1ull << 36) || (n && !d_in) || !d_out || !d_len || !d_ws) return HI_EINVAL;
+    if (n >= (1ull << 32) || (n && !d_in) || !d_out || !d_len || !d_ws) return HI_EINVAL;
     if ((n && !aligned(d_in, 16)) || !aligned(d_out, 16) || !aligned(d_len, 8) || !aligned(d_ws, 16)) return HI_EINVAL;
     if (out_cap < cr_stream_bound(n) || ws_bytes < cr_ws_bytes(n)) return HI_EINVAL;
     const uintptr_t a = reinterpret_cast<uintptr_t>(d_in), b = reinterpret_cast<uintptr_t>(d_out);
@@ -942,7 +942,7 @@ hi_status hi_cr_encode(const uint8_t* d_in, uint64_t n, uint8_t* d_out, uint64_t
 hi_status hi_cr_decode(const uint8_t* d_in, uint64_t in_len, uint8_t* d_out, uint64_t n, uint32_t* d_status,
                        void* d_ws, size_t ws_bytes, cudaStream_t stream)
 {
-    if (n >= (1ull << 36) || !d_in || (n && !d_out) || !d_ws) return HI_EINVAL;
+    if (n >= (1ull << 32) || !d_in || (n && !d_out) || !d_ws) return HI_EINVAL;
     if (!aligned(d_in, 16) || (n && !aligned(d_out, 16)) || !aligned(d_ws, 16) ||
         (d_status && !aligned(d_status, 4)))
         return HI_EINVAL;

@@ -43,7 +43,7 @@ namespace hi {
 
 constexpr uint32_t kHfBlock = 4096;
 constexpr int kHfLmax = 16;
-constexpr int kHfLut = 10;  // decode table bits
+constexpr int kHfLut = 12;  // decode table bits (codes up to this long take one lookup)
 constexpr uint32_t kCrChunk = 16384;
 constexpr uint32_t kCrRaw = 0x80000000u;
 constexpr int kCrThreads = 256;
@@ -257,72 +257,109 @@ __global__ void __launch_bounds__(256) k_cr_hist(const uint8_t* __restrict__ in,
     if (v) atomicAdd(&hist[threadIdx.x], v);
 }
 
-// The code book (one CTA of 256 threads): Huffman lengths by the two-queue
-// construction -- leaves sorted by (weight, symbol) in one queue, internal
-// nodes in creation order in the other (their weights never decrease), the
-// lighter front taken first and a leaf on a tie, which is the (weight,
-// creation index) order -- then canonical codes.  Writes the lengths into the
-// stream header as well.
-__global__ void __launch_bounds__(256) k_cr_codebook(const uint32_t* __restrict__ hist, uint8_t* __restrict__ len_out,
-                                                     uint32_t* __restrict__ code_out, uint8_t* __restrict__ hdr_len)
+// The code book (one CTA of 8 warps).  Halving every weight k times gives
+// max(1, w >> k), so the trees of eight values of k are built at once, one
+// per warp, and the first k whose longest code fits in 16 bits is taken --
+// the same k as halving one step at a time.  In each warp: ranks of the
+// leaves by (weight, symbol), the two-queue Huffman construction by lane 0
+// (leaves sorted in one queue, internal nodes in creation order in the other,
+// whose weights never decrease; the lighter front first, a leaf on a tie:
+// the (weight, creation index) order), then every leaf's depth by walking up
+// to the root.  Canonical codes from the lengths.  Writes the lengths into
+// the stream header as well.
+constexpr int kBookWarps = 8;
+__global__ void __launch_bounds__(32 * kBookWarps) k_cr_codebook(const uint32_t* __restrict__ hist,
+                                                                 uint8_t* __restrict__ len_out,
+                                                                 uint32_t* __restrict__ code_out,
+                                                                 uint8_t* __restrict__ hdr_len)
 {
-    __shared__ uint64_t w[256], lw[256], iw[256];
-    __shared__ int lsym[256], lpar[256], ipar[256], idep[256];
+    __shared__ uint32_t wkv[kBookWarps][256], lw[kBookWarps][256];  // leaf weights fit 32 bits
+    __shared__ uint64_t iw[kBookWarps][256];
+    __shared__ uint8_t lsym[kBookWarps][256], lpar[kBookWarps][256], ipar[kBookWarps][256], wlen[kBookWarps][256];
+    __shared__ uint32_t h[256];
     __shared__ uint8_t len[256];
     __shared__ uint32_t cnt[kHfLmax + 2], first[kHfLmax + 2];
-    __shared__ int s_max;
-    const int t = threadIdx.x;
-    w[t] = hist[t];
-    for (;;) {
-        __syncthreads();
-        const uint64_t wt = w[t];
-        const bool present = wt > 0;
-        int r = 0;
-        for (int s = 0; s < 256; ++s) {
-            const uint64_t ws = w[s];
-            r += (ws > 0 && (ws < wt || (ws == wt && s < t))) ? 1 : 0;
+    __shared__ unsigned s_pick;
+    const int t = threadIdx.x, lane = t & 31, g = t >> 5;
+    h[t] = hist[t];
+    __syncthreads();
+    int k = 0;  // symbols present
+    for (int s = 0; s < 256; ++s) k += h[s] > 0 ? 1 : 0;
+    for (int kb = 0;; kb += kBookWarps) {
+        const int shift = kb + g;  // this warp's number of halvings
+        for (int v = lane; v < 256; v += 32) {
+            const uint32_t hv = h[v];
+            wkv[g][v] = hv == 0 ? 0u : (shift >= 32 ? 1u : ((hv >> shift) ? (hv >> shift) : 1u));
         }
-        const int k = __syncthreads_count(present);
-        if (present) {
-            lw[r] = wt;
-            lsym[r] = t;
-        }
-        len[t] = 0;
-        __syncthreads();
-        if (t == 0) {
-            int mx = 0;
-            if (k == 1) {
-                len[lsym[0]] = 1;
-                mx = 1;
-            } else if (k > 1) {
-                int i1 = 0, i2 = 0, n2 = 0;
-                for (int step = 0; step < k - 1; ++step) {
-                    uint64_t sum = 0;
-                    for (int pick = 0; pick < 2; ++pick) {
-                        if (i1 < k && (i2 >= n2 || lw[i1] <= iw[i2])) {
-                            lpar[i1] = n2;
-                            sum += lw[i1++];
-                        } else {
-                            ipar[i2] = n2;
-                            sum += iw[i2++];
-                        }
-                    }
-                    iw[n2++] = sum;
-                }
-                idep[n2 - 1] = 0;
-                for (int j = n2 - 2; j >= 0; --j) idep[j] = idep[ipar[j]] + 1;
-                for (int i = 0; i < k; ++i) {
-                    const int d = idep[lpar[i]] + 1;
-                    len[lsym[i]] = (uint8_t)d;
-                    mx = d > mx ? d : mx;
-                }
+        __syncwarp();
+        for (int v = lane; v < 256; v += 32) {
+            const uint32_t wt = wkv[g][v];
+            wlen[g][v] = 0;
+            if (wt == 0) continue;
+            int r = 0;
+            for (int s = 0; s < 256; ++s) {
+                const uint32_t ws = wkv[g][s];
+                r += (ws != 0 && (ws < wt || (ws == wt && s < v))) ? 1 : 0;
             }
-            s_max = mx;
+            lw[g][r] = wt;
+            lsym[g][r] = (uint8_t)v;
+        }
+        __syncwarp();
+        int n2 = 0;
+        if (lane == 0 && k > 1) {
+            int i1 = 0, i2 = 0;
+            uint64_t fl = lw[g][0], fi = 0;
+            for (int step = 0; step < k - 1; ++step) {
+                uint64_t sum = 0;
+#pragma unroll
+                for (int pick = 0; pick < 2; ++pick) {
+                    if (i1 < k && (i2 >= n2 || fl <= fi)) {
+                        lpar[g][i1] = (uint8_t)n2;
+                        sum += fl;
+                        ++i1;
+                        fl = i1 < k ? lw[g][i1] : 0;
+                    } else {
+                        ipar[g][i2] = (uint8_t)n2;
+                        sum += fi;
+                        ++i2;
+                        fi = i2 < n2 ? iw[g][i2] : 0;
+                    }
+                }
+                iw[g][n2] = sum;
+                if (i2 == n2) fi = sum;  // the internal queue was empty: this node is its front
+                ++n2;
+            }
+        }
+        n2 = __shfl_sync(0xffffffffu, n2, 0);
+        __syncwarp();
+        int mx = 0;
+        if (k == 1) {
+            if (lane == 0) wlen[g][lsym[g][0]] = 1;
+            mx = 1;
+        } else {
+            for (int i = lane; i < k; i += 32) {
+                int j = lpar[g][i], d = 1;
+                while (j != n2 - 1) {
+                    j = ipar[g][j];
+                    ++d;
+                }
+                wlen[g][lsym[g][i]] = (uint8_t)d;
+                mx = d > mx ? d : mx;
+            }
+        }
+        mx = (int)__reduce_max_sync(0xffffffffu, (unsigned)mx);
+        if (t == 0) s_pick = 0xffffffffu;
+        __syncthreads();
+        if (lane == 0 && mx <= kHfLmax) atomicMin(&s_pick, (unsigned)g);
+        __syncthreads();
+        const unsigned pick = s_pick;
+        if (pick != 0xffffffffu) {
+            len[t] = wlen[pick][t];
+            break;
         }
         __syncthreads();
-        if (s_max <= kHfLmax) break;
-        if (wt > 0) w[t] = (wt >> 1) ? (wt >> 1) : 1;  // halve and rebuild
     }
+    __syncthreads();
     // canonical codes: first code of each length from the counts of the shorter ones
     if (t <= kHfLmax + 1) cnt[t] = 0;
     __syncthreads();
@@ -387,43 +424,43 @@ __global__ void __launch_bounds__(256) k_hf_count(const uint8_t* __restrict__ in
     }
 }
 
-// Exclusive scan of cnt u32 values (one CTA of 1024 threads); returns the
-// total through *total.
+// Exclusive scan of cnt u32 values (one CTA of 1024 threads), each times
+// scale, starting at base; returns the end through *total.  Each thread takes
+// a contiguous run of ceil(cnt / threads) values: one pass for the run sums,
+// one block scan of them, one pass writing the offsets.
 __device__ __forceinline__ void cta_scan_u32(const uint32_t* in, uint32_t* out_or_null, uint64_t* out64_or_null,
                                              uint64_t cnt, uint64_t base, uint64_t* total, uint32_t scale)
 {
     __shared__ uint64_t s_part[32];
-    __shared__ uint64_t s_carry;
+    __shared__ uint64_t s_tot;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_carry = base;
-    __syncthreads();
-    for (uint64_t c0 = 0; c0 < cnt; c0 += blockDim.x) {
-        const uint64_t i = c0 + threadIdx.x;
-        const uint64_t v = i < cnt ? (uint64_t)(in[i] & ~kCrRaw) * scale : 0;
-        uint64_t incl = v;
+    const uint64_t per = (cnt + blockDim.x - 1) / blockDim.x;
+    const uint64_t lo = min(cnt, per * threadIdx.x), hi = min(cnt, lo + per);
+    uint64_t mine = 0;
+    for (uint64_t i = lo; i < hi; ++i) mine += (uint64_t)(in[i] & ~kCrRaw) * scale;
+    uint64_t incl = mine;
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint64_t t = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= (uint32_t)d) incl += t;
-        }
-        if (lane == 31) s_part[warp] = incl;
-        __syncthreads();
-        uint64_t before = 0, tot = 0;
-        for (uint32_t w = 0; w < (blockDim.x >> 5); ++w) {
-            before += (w < warp) ? s_part[w] : 0;
-            tot += s_part[w];
-        }
-        const uint64_t carry = s_carry;
-        if (i < cnt) {
-            const uint64_t ex = carry + before + incl - v;
-            if (out_or_null) out_or_null[i] = (uint32_t)ex;
-            if (out64_or_null) out64_or_null[i] = ex;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) s_carry = carry + tot;
-        __syncthreads();
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint64_t t = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= (uint32_t)d) incl += t;
     }
-    *total = s_carry;
+    if (lane == 31) s_part[warp] = incl;
+    __syncthreads();
+    uint64_t before = 0, tot = 0;
+    for (uint32_t w = 0; w < (blockDim.x >> 5); ++w) {
+        before += (w < warp) ? s_part[w] : 0;
+        tot += s_part[w];
+    }
+    uint64_t run = base + before + incl - mine;
+    for (uint64_t i = lo; i < hi; ++i) {
+        if (out_or_null) out_or_null[i] = (uint32_t)run;
+        if (out64_or_null) out64_or_null[i] = run;
+        run += (uint64_t)(in[i] & ~kCrRaw) * scale;
+    }
+    if (threadIdx.x == 0) s_tot = base + tot;
+    __syncthreads();
+    *total = s_tot;
+    __syncthreads();
 }
 
 // Block word offsets and H; the stream's fixed header.
@@ -465,7 +502,7 @@ __global__ void __launch_bounds__(32 * kHfEncWarps) k_hf_encode(const uint8_t* _
 {
     __shared__ uint8_t len[256];
     __shared__ uint32_t code[256];
-    __shared__ __align__(16) uint8_t s_sym[kHfEncWarps][kHfBlock];
+    __shared__ __align__(16) uint32_t s_sym[kHfEncWarps][kHfBlock / 4 + kHfBlock / 128];  // word w at w + w / 32
     __shared__ __align__(16) uint32_t s_bits[kHfEncWarps][kHfBlock * kHfLmax / 32];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
         len[i] = len_g[i];
@@ -473,7 +510,8 @@ __global__ void __launch_bounds__(32 * kHfEncWarps) k_hf_encode(const uint8_t* _
     }
     __syncthreads();
     const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
-    uint8_t* sym = s_sym[wid];
+    uint32_t* symw = s_sym[wid];
+    const uint8_t* sym = reinterpret_cast<const uint8_t*>(symw);
     uint32_t* bw = s_bits[wid];
     const uint64_t nb = cr_nblocks(n);
     const uint64_t warps = (uint64_t)gridDim.x * kHfEncWarps;
@@ -482,17 +520,36 @@ __global__ void __launch_bounds__(32 * kHfEncWarps) k_hf_encode(const uint8_t* _
         const uint32_t cnt = (uint32_t)min((uint64_t)kHfBlock, n - s0);
         const uint32_t nw = words[b];
         if (cnt == kHfBlock) {
-            for (uint32_t i = lane; i < kHfBlock / 16; i += 32)
-                reinterpret_cast<uint4*>(sym)[i] = __ldg(reinterpret_cast<const uint4*>(in + s0) + i);
+            for (uint32_t i = lane; i < kHfBlock / 16; i += 32) {
+                const uint4 q = __ldg(reinterpret_cast<const uint4*>(in + s0) + i);
+                const uint32_t w0 = 4 * i;  // the 4 words stay within one group of 32
+                uint32_t* d = symw + w0 + w0 / 32;
+                d[0] = q.x, d[1] = q.y, d[2] = q.z, d[3] = q.w;
+            }
         } else {
-            for (uint32_t i = lane; i < cnt; i += 32) sym[i] = in[s0 + i];
+            // a partial block (the last): symbols byte by byte into the skewed words
+            for (uint32_t w = lane; w < kHfBlock / 4; w += 32) {
+                uint32_t v = 0;
+                for (uint32_t bb = 0; bb < 4; ++bb)
+                    if (4 * w + bb < cnt) v |= (uint32_t)in[s0 + 4 * w + bb] << (8 * bb);
+                symw[w + w / 32] = v;
+            }
         }
         for (uint32_t i = lane; i < nw; i += 32) bw[i] = 0;
         __syncwarp();
         const uint32_t a = lane * (kHfBlock / 32);
         const uint32_t e = min(a + kHfBlock / 32, cnt);
+        const bool whole = e == a + kHfBlock / 32;  // 128 symbols: read as words
         uint32_t mybits = 0;
-        for (uint32_t i = a; i < e; ++i) mybits += len[sym[i]];
+        if (whole) {
+#pragma unroll 4
+            for (uint32_t q = a / 4; q < e / 4; ++q) {
+                const uint32_t w4 = symw[q + q / 32];
+                mybits += len[w4 & 0xffu] + len[(w4 >> 8) & 0xffu] + len[(w4 >> 16) & 0xffu] + len[w4 >> 24];
+            }
+        } else {
+            for (uint32_t i = a; i < e; ++i) mybits += len[sym[i + 4 * (i / 128)]];
+        }
         uint32_t incl = mybits;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -503,15 +560,31 @@ __global__ void __launch_bounds__(32 * kHfEncWarps) k_hf_encode(const uint8_t* _
         uint32_t widx = pos >> 5;
         uint32_t nacc = pos & 31u;  // bits already taken in the first word (by earlier lanes)
         uint64_t acc = 0;
-        for (uint32_t i = a; i < e; ++i) {
-            const uint32_t s = sym[i];
-            const uint32_t l = len[s];
-            acc |= (uint64_t)code[s] << (64 - nacc - l);
-            nacc += l;
+        // two codes at a time (at most 32 bits: with fewer than 32 pending the
+        // 64-bit accumulator holds them), one word out whenever 32 are pending
+        auto put = [&](uint32_t c2, uint32_t l2) {
+            acc |= (uint64_t)c2 << (64 - nacc - l2);
+            nacc += l2;
             if (nacc >= 32) {
                 atomicOr(&bw[widx++], (uint32_t)(acc >> 32));
                 acc <<= 32;
                 nacc -= 32;
+            }
+        };
+        if (whole) {
+#pragma unroll 2
+            for (uint32_t q = a / 4; q < e / 4; ++q) {
+                const uint32_t w4 = symw[q + q / 32];
+                const uint32_t s0 = w4 & 0xffu, s1 = (w4 >> 8) & 0xffu, s2 = (w4 >> 16) & 0xffu, s3 = w4 >> 24;
+                const uint32_t l0 = len[s0], l1 = len[s1], l2 = len[s2], l3 = len[s3];
+                const uint32_t c0 = code[s0], c1 = code[s1], c2 = code[s2], c3 = code[s3];
+                put((c0 << l1) | c1, l0 + l1);
+                put((c2 << l3) | c3, l2 + l3);
+            }
+        } else {
+            for (uint32_t i = a; i < e; ++i) {
+                const uint32_t sy = sym[i + 4 * (i / 128)];
+                put(code[sy], len[sy]);
             }
         }
         if (nacc > 0 && mybits > 0) atomicOr(&bw[widx], (uint32_t)(acc >> 32));
@@ -736,15 +809,15 @@ __global__ void __launch_bounds__(1024) k_cr_dec_scan(const uint8_t* __restrict_
     cta_scan_u32(i32 + kCrHdr / 4, woff, nullptr, nb, 0, &wt, 1);
     // payload offsets: the sizes are every other word of the chunk table
     const uint32_t* tab = reinterpret_cast<const uint32_t*>(in + kCrHdr + 4 * nb);
-    __shared__ uint64_t s_part[32];
-    __shared__ uint64_t s_carry;
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_carry = cr_header_bytes(nb, nc);
-    __syncthreads();
-    for (uint64_t c0 = 0; c0 < nc; c0 += blockDim.x) {
-        const uint64_t i = c0 + threadIdx.x;
-        const uint64_t v = i < nc ? (uint64_t)(tab[2 * i] & ~kCrRaw) : 0;
-        uint64_t incl = v;
+    {
+        __shared__ uint64_t s_part[32];
+        __shared__ uint64_t s_end;
+        const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+        const uint64_t per = ((uint64_t)nc + blockDim.x - 1) / blockDim.x;
+        const uint64_t lo = min((uint64_t)nc, per * threadIdx.x), hi = min((uint64_t)nc, lo + per);
+        uint64_t mine = 0;
+        for (uint64_t i = lo; i < hi; ++i) mine += tab[2 * i] & ~kCrRaw;
+        uint64_t incl = mine;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const uint64_t tt = __shfl_up_sync(0xffffffffu, incl, d);
@@ -757,13 +830,16 @@ __global__ void __launch_bounds__(1024) k_cr_dec_scan(const uint8_t* __restrict_
             before += (w < warp) ? s_part[w] : 0;
             tot += s_part[w];
         }
-        const uint64_t carry = s_carry;
-        if (i < nc) poff[i] = carry + before + incl - v;
+        const uint64_t hb = cr_header_bytes(nb, nc);
+        uint64_t run = hb + before + incl - mine;
+        for (uint64_t i = lo; i < hi; ++i) {
+            poff[i] = run;
+            run += tab[2 * i] & ~kCrRaw;
+        }
+        if (threadIdx.x == 0) s_end = hb + tot;
         __syncthreads();
-        if (threadIdx.x == 0) s_carry = carry + tot;
-        __syncthreads();
+        pt = s_end;
     }
-    pt = s_carry;
     if (threadIdx.x == 0) {
         const bool bad = 4 * wt != H || pt > in_len;
         if (bad) set_status(status, HI_ECORRUPT);
@@ -920,48 +996,57 @@ __global__ void __launch_bounds__(kCrThreads) k_cr_lc_decode(const uint8_t* __re
     }
 }
 
-// A thread per HF block: canonical decoding through a 10-bit table (codes
-// up to 10 bits in one lookup), longer codes bit by bit against the first
-// code of each length.
-__global__ void __launch_bounds__(128) k_hf_decode(const uint8_t* __restrict__ in, const uint8_t* __restrict__ hf,
-                                                   const uint32_t* __restrict__ woff, uint64_t n,
-                                                   const uint64_t* __restrict__ hdr_ws, uint8_t* __restrict__ out,
-                                                   uint32_t* __restrict__ status)
+// A thread per HF block: canonical decoding through a 12-bit table (codes
+// up to 12 bits in one lookup); a longer code's length comes from comparing
+// the next 16 bits against the end of each longer length's code range
+// (canonical codes of one length are consecutive), branch-free.  The next
+// stream word is loaded one refill ahead (its latency hides behind a dozen
+// symbols) and the output leaves in 16-byte stores.
+constexpr int kHfDecThreads = 64;
+__global__ void __launch_bounds__(kHfDecThreads) k_hf_decode(const uint8_t* __restrict__ in,
+                                                             const uint8_t* __restrict__ hf,
+                                                             const uint32_t* __restrict__ woff, uint64_t n,
+                                                             const uint64_t* __restrict__ hdr_ws,
+                                                             uint8_t* __restrict__ out, uint32_t* __restrict__ status)
 {
     __shared__ uint16_t lut[1 << kHfLut];  // symbol | length << 8, 0 = longer code
     __shared__ uint8_t len[256], sorted[256];
-    __shared__ uint32_t cnt[kHfLmax + 1], first[kHfLmax + 1], offs[kHfLmax + 1];
+    __shared__ uint32_t cnt[kHfLmax + 1], first[kHfLmax + 1], offs[kHfLmax + 1], lim[kHfLmax + 1];
     if (reinterpret_cast<const uint32_t*>(hdr_ws)[3]) return;  // the header did not check out
     const int t = threadIdx.x;
     for (int i = t; i < 256; i += blockDim.x) len[i] = in[32 + i];
     for (int i = t; i < (1 << kHfLut); i += blockDim.x) lut[i] = 0;
+    if (t <= kHfLmax) cnt[t] = 0;
+    __syncthreads();
+    for (int v = t; v < 256; v += blockDim.x)
+        if (len[v]) atomicAdd(&cnt[len[v]], 1u);
     __syncthreads();
     if (t == 0) {
         uint32_t c = 0, ns = 0, prev = 0;
         for (int l = 1; l <= kHfLmax; ++l) {
-            cnt[l] = 0;
-            for (int v = 0; v < 256; ++v) cnt[l] += (len[v] == l) ? 1u : 0u;
-        }
-        for (int l = 1; l <= kHfLmax; ++l) {
             c = (c + prev) << 1;
             first[l] = c;
             offs[l] = ns;
-            for (int v = 0; v < 256; ++v)
-                if (len[v] == l) sorted[ns++] = (uint8_t)v;
+            ns += cnt[l];
             prev = cnt[l];
+            lim[l] = (c + cnt[l]) << (kHfLmax - l);  // 16-bit windows below this start a code of length <= l
         }
     }
     __syncthreads();
-    for (int v = t; v < 256; v += blockDim.x) {  // table entries of the short codes
+    for (int v = t; v < 256; v += blockDim.x) {  // (length, symbol) order; table entries of the short codes
         const int l = len[v];
-        if (l == 0 || l > kHfLut) continue;
+        if (l == 0) continue;
         uint32_t rank = 0;
         for (int s = 0; s < v; ++s) rank += (len[s] == l) ? 1u : 0u;
-        const uint32_t code = first[l] + rank;
-        const uint32_t base = code << (kHfLut - l);
+        sorted[offs[l] + rank] = (uint8_t)v;
+        if (l > kHfLut) continue;
+        const uint32_t base = (first[l] + rank) << (kHfLut - l);
         for (uint32_t j = 0; j < (1u << (kHfLut - l)); ++j) lut[base + j] = (uint16_t)(v | (l << 8));
     }
     __syncthreads();
+    // lengths 13..16: a window w16 of the next 16 bits starts a code of length
+    // 13 + (w16 >= lim[13]) + (w16 >= lim[14]) + (w16 >= lim[15]); valid when w16 < lim[16]
+    const uint32_t lim13 = lim[13], lim14 = lim[14], lim15 = lim[15], lim16 = lim[16];
     const uint64_t nb = cr_nblocks(n);
     const uint32_t* words = reinterpret_cast<const uint32_t*>(in + kCrHdr);
     for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + t; b < nb; b += (uint64_t)gridDim.x * blockDim.x) {
@@ -969,16 +1054,22 @@ __global__ void __launch_bounds__(128) k_hf_decode(const uint8_t* __restrict__ i
         const uint32_t* src = reinterpret_cast<const uint32_t*>(hf) + woff[b];
         const uint64_t s0 = b * kHfBlock;
         const uint32_t cntb = (uint32_t)min((uint64_t)kHfBlock, n - s0);
-        uint64_t buf = 0;  // upcoming bits, MSB first
-        uint32_t have = 0, next = 0;
+        auto word = [&](uint32_t k) -> uint32_t { return k < nw ? __byte_perm(__ldg(src + k), 0u, 0x0123) : 0u; };
+        uint64_t buf = (uint64_t)word(0) << 32;  // upcoming bits, MSB first
+        uint32_t have = 32;
+        // the next three words, loaded three refills (some 40 symbols) before they are needed
+        uint32_t pre0 = word(1), pre1 = word(2), pre2 = word(3);
+        uint32_t wi = 4;  // next word to load
         bool bad = false;
-        uint32_t pack = 0;
+        uint32_t o0 = 0, o1 = 0, o2 = 0, cur = 0;
         for (uint32_t i = 0; i < cntb; ++i) {
             if (have <= 32) {
-                const uint32_t wv = next < nw ? __byte_perm(src[next], 0u, 0x0123) : 0u;
-                buf |= (uint64_t)wv << (32 - have);
+                buf |= (uint64_t)pre0 << (32 - have);
                 have += 32;
-                ++next;
+                pre0 = pre1;
+                pre1 = pre2;
+                pre2 = word(wi);
+                ++wi;
             }
             const uint32_t e = lut[(uint32_t)(buf >> (64 - kHfLut))];
             uint32_t sym, l;
@@ -986,35 +1077,40 @@ __global__ void __launch_bounds__(128) k_hf_decode(const uint8_t* __restrict__ i
                 sym = e & 0xffu;
                 l = e >> 8;
             } else {
-                uint32_t c = (uint32_t)(buf >> (64 - kHfLut));
-                l = kHfLut;
-                sym = 0;
-                bool found = false;
-                while (++l <= kHfLmax) {
-                    c = (uint32_t)(buf >> (64 - l));
-                    if (cnt[l] && c >= first[l] && c - first[l] < cnt[l]) {
-                        sym = sorted[offs[l] + (c - first[l])];
-                        found = true;
-                        break;
-                    }
-                }
-                if (!found) {
+                const uint32_t w16 = (uint32_t)(buf >> (64 - kHfLmax));
+                l = 13 + (w16 >= lim13 ? 1u : 0u) + (w16 >= lim14 ? 1u : 0u) + (w16 >= lim15 ? 1u : 0u);
+                const uint32_t c = w16 >> (kHfLmax - l);
+                const uint32_t k = c - first[l];
+                if (w16 >= lim16 || k >= cnt[l]) {
                     bad = true;
                     break;
                 }
+                sym = sorted[offs[l] + k];
             }
             buf <<= l;
             have -= l;
-            pack |= sym << (8 * (i & 3));
+            cur |= sym << (8 * (i & 3));
             if ((i & 3) == 3) {
-                *reinterpret_cast<uint32_t*>(out + s0 + i - 3) = pack;
-                pack = 0;
+                if ((i & 15) == 15) {
+                    *reinterpret_cast<uint4*>(out + s0 + i - 15) = make_uint4(o0, o1, o2, cur);
+                } else {
+                    o0 = o1;
+                    o1 = o2;
+                    o2 = cur;
+                }
+                cur = 0;
             }
         }
         if (!bad) {
-            for (uint32_t i = cntb & ~3u; i < cntb; ++i) out[s0 + i] = (uint8_t)(pack >> (8 * (i & 3)));
-            // bits consumed past the block's words: corrupt
-            if (32ull * next - have > 32ull * nw) bad = true;
+            // the symbols after the last 16-byte store: up to three words in o*, then cur
+            const uint32_t done = cntb & ~15u, rem = cntb - done;
+            const uint32_t wds = rem / 4;
+            const uint32_t ow[3] = {wds == 3 ? o0 : (wds == 2 ? o1 : o2), wds == 3 ? o1 : o2, o2};
+            for (uint32_t k = 0; k < wds; ++k)
+                *reinterpret_cast<uint32_t*>(out + s0 + done + 4 * k) = ow[k];
+            for (uint32_t k = done + 4 * wds; k < cntb; ++k) out[s0 + k] = (uint8_t)(cur >> (8 * (k & 3)));
+            // bits consumed past the block's words: corrupt (wi - 3 words have entered buf)
+            if (32ull * (wi - 3) - have > 32ull * nw) bad = true;
         }
         if (bad) set_status(status, HI_ECORRUPT);
     }
@@ -1058,11 +1154,11 @@ cudaError_t launch_cr_encode(const uint8_t* in, uint64_t n, uint8_t* out, uint64
     cudaError_t e = cudaMemsetAsync(hist, 0, 1024, st);
     if (e != cudaSuccess) return e;
     k_cr_hist<<<cr_grid((n / 16 + 255) / 256, 8, num_sms), 256, 0, st>>>(in, n, hist);
-    k_cr_codebook<<<1, 256, 0, st>>>(hist, lens, codes, out + 32);
+    k_cr_codebook<<<1, 32 * kBookWarps, 0, st>>>(hist, lens, codes, out + 32);
     k_hf_count<<<cr_grid((nb + 7) / 8, 8, num_sms), 256, 0, st>>>(in, n, lens, words,
                                                                     reinterpret_cast<uint32_t*>(out + kCrHdr));
     k_cr_scan_words<<<1, 1024, 0, st>>>(words, n, woff, hdr, out);
-    k_hf_encode<<<cr_grid((nb + kHfEncWarps - 1) / kHfEncWarps, 4, num_sms), 32 * kHfEncWarps, 0, st>>>(
+    k_hf_encode<<<cr_grid((nb + kHfEncWarps - 1) / kHfEncWarps, 8, num_sms), 32 * kHfEncWarps, 0, st>>>(
         in, n, lens, codes, words, woff, hf);
     k_cr_lc_encode<<<cr_grid(ncm, 3, num_sms), kCrThreads, kCrSmem, st>>>(hf, hdr, slots, psize, pm1);
     k_cr_scan_payloads<<<1, 1024, 0, st>>>(psize, pm1, n, hdr, poff, out, len);
@@ -1088,7 +1184,8 @@ cudaError_t launch_cr_decode(const uint8_t* in, uint64_t in_len, uint64_t n, uin
     uint8_t* hf = ws + L.hf;
     k_cr_dec_scan<<<1, 1024, 0, st>>>(in, in_len, n, woff, poff, hdr, status);
     k_cr_lc_decode<<<cr_grid(ncm, 3, num_sms), kCrThreads, kCrSmem, st>>>(in, poff, n, hdr, hf, status);
-    k_hf_decode<<<cr_grid((nb + 127) / 128, 4, num_sms), 128, 0, st>>>(in, hf, woff, n, hdr, out, status);
+    k_hf_decode<<<cr_grid((nb + kHfDecThreads - 1) / kHfDecThreads, 16, num_sms), kHfDecThreads, 0, st>>>(
+        in, hf, woff, n, hdr, out, status);
     return cudaGetLastError();
 }
 
