@@ -17,7 +17,7 @@
 //     large field -- also fix the dimension sequence at compile time, so line
 //     counts, stencil cases and shared-memory offsets are constants;
 //   * all other tiles (ragged field edges, 1D/2D fields, other A) take the
-//     extents at run time.
+//     extents at run time (one instantiation per level, dim and spline).
 // Passes along the contiguous dim move whole rows with 16-byte shared-memory
 // accesses (conflict-free at the 16-byte-multiple, odd-word row pitch);
 // passes along the other dims give each thread one line, lanes adjacent along
@@ -166,8 +166,8 @@ __device__ __forceinline__ int line_q(int line, int nr, float inv_nr)
         return line / nr;
 }
 
-// ED: the pass dim's extent when known at compile time (A for a whole tile,
-// A-1 for the usual ragged edge), 0 when it is only known at run time.
+// ED: the pass dim's extent when known at compile time (A for a whole tile),
+// 0 when it is only known at run time (the other tiles).
 template <int A, int S, int D, bool CUBIC, bool COMP, int ED, bool RT>
 __device__ __forceinline__ void pass_cols(float* __restrict__ v, uint8_t* __restrict__ cs, const Hot h, int stq,
                                           int str, int nq, int nr, int ed_rt)
@@ -538,12 +538,10 @@ template <int A, int S, int D, bool COMP>
 __device__ __forceinline__ void pass_dispatch(bool cubic, float* v, uint8_t* cs, const Hot h, int stq, int str,
                                               int nq, int nr, int ed)
 {
-    if (ed == A)  // the pass dim is whole: only the line counts are shorter
-        pass_spline<A, S, D, COMP, A>(cubic, v, cs, h, stq, str, nq, nr, ed);
-    else if (ed == A - 1)  // the usual ragged edge (n - 1 = -1 mod A), stencil cases fixed too
-        pass_spline<A, S, D, COMP, A - 1>(cubic, v, cs, h, stq, str, nq, nr, ed);
-    else
-        pass_spline<A, S, D, COMP, 0>(cubic, v, cs, h, stq, str, nq, nr, ed);
+    // one run-time instantiation for every extent: instantiations for the
+    // common extents A and A - 1 ran the same instruction count and cost
+    // more instruction fetch
+    pass_spline<A, S, D, COMP, 0>(cubic, v, cs, h, stq, str, nq, nr, ed);
 }
 
 template <int A, int LV, bool COMP>
