@@ -675,7 +675,7 @@ def batch_line(args):
     Ns = [a.size for a in arrs]
     N = sum(Ns)
     # outlier capacity = field size: no field can overflow at any bound
-    bat = hi.Batch(xs, ebs, "rel", anchor_stride=A, autotune=True, out_caps=Ns, hist=True, recon=False)
+    bat = hi.Batch(xs, ebs, "rel", anchor_stride=A, autotune=True, out_caps=Ns, hist=True, recon=False, outs=True)
     shape_ms = bat.tune_launch(reps=3)
     # plain path: one hi_compress per field, its own buffers
     plain = []
@@ -730,6 +730,44 @@ def batch_line(args):
     torch.cuda.synchronize()
     ms_plain = ev[2].elapsed_time(ev[3]) / ksteps
 
+    # batched reconstruction (two launches for all fields, replayed from a graph) against one
+    # hi_decompress per field into the same outputs
+    gd = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gd):
+        bat.decompress()
+    pst = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def plain_dstep():
+        for b, y in zip(bat.buffers, bat.outs):
+            hi.decompress_into(b, y, pst)
+
+    for _ in range(max(args.warmup, 3)):
+        gd.replay()
+        plain_dstep()
+    torch.cuda.synchronize()
+    dev_ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    dev_ev[0].record(stream)
+    for _ in range(steps):
+        gd.replay()
+    dev_ev[1].record(stream)
+    for _ in range(ksteps):
+        plain_dstep()
+    dev_ev[2].record(stream)
+    gd.replay()
+    dev_ev[3].record(stream)
+    torch.cuda.synchronize()
+    d_ms = dev_ev[0].elapsed_time(dev_ev[1]) / steps
+    d_ms_plain = dev_ev[1].elapsed_time(dev_ev[2]) / ksteps
+    d_ok = int(bat.dstatus.item()) == 0 and int(pst.item()) == 0
+    d_exact = True
+    refs = [torch.empty_like(y) for y in bat.outs]
+    for b, r in zip(bat.buffers, refs):
+        hi.decompress_into(b, r, pst)
+    torch.cuda.synchronize()
+    for y, r in zip(bat.outs, refs):
+        d_exact = d_exact and torch.equal(y.view(torch.int32), r.view(torch.int32))
+    del refs
+
     # every field: the batch's record equals the plain path's
     g.replay()
     torch.cuda.synchronize()
@@ -769,6 +807,11 @@ def batch_line(args):
                         launches=4 * len(xs), how="one hi_compress per field, same stream"),
         speedup_vs_plain=ms_plain / ms,
         bit_exact_vs_plain=bool(exact),
+        decompress=dict(value=bytes_in / (d_ms * 1e-3) / 1e9, ms_per_step=d_ms, launches=2,
+                        how="hi_decompress_batch (outlier scatter + one persistent reconstruction) from a CUDA graph",
+                        plain_path=dict(value=bytes_in / (d_ms_plain * 1e-3) / 1e9, ms_per_step=d_ms_plain,
+                                        launches=2 * len(xs), how="one hi_decompress per field, same stream"),
+                        speedup_vs_plain=d_ms_plain / d_ms, bit_exact_vs_plain=bool(d_exact), status_ok=bool(d_ok)),
         mismatched_fields=mismatched,
         stage_ms=stage,
         n_outliers=n_out,

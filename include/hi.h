@@ -228,8 +228,10 @@ HI_API hi_status hi_autotune_errors(const hi_params* p, const void* d_ws, double
  * Not in the paper, which compresses one field per call.
  * ------------------------------------------------------------------------ */
 
-/* One field of a batch: its parameters and buffers, as for hi_compress.
- * Every field of a batch has the same anchor_stride, 8 or 16. */
+/* One field of a batch: its parameters and buffers, as for hi_compress
+ * (d_x may be NULL in a batch used only by hi_decompress_batch), and where
+ * hi_decompress_batch writes its reconstruction (d_out).  Every field of a
+ * batch has the same anchor_stride, 8 or 16. */
 typedef struct {
     hi_params p;
     const float* d_x;
@@ -241,6 +243,7 @@ typedef struct {
     uint32_t* d_hist;   /* or NULL */
     float* d_recon;     /* or NULL */
     hi_header* d_header;
+    float* d_out;       /* reconstruction target of hi_decompress_batch, or NULL */
 } hi_batch_field;
 
 /* A prepared batch (host memory, written by hi_batch_prepare).  The
@@ -281,6 +284,25 @@ HI_API hi_status hi_batch_prepare(uint32_t n, const hi_batch_field* h_fields, ui
  * of hi_set_stage_events (0..4) are recorded as for hi_compress.  Calls that
  * share d_ws must not overlap. */
 HI_API hi_status hi_compress_batch(const hi_batch_plan* h_plan, void* d_ws, cudaStream_t stream);
+
+/* Reconstruct every field of a prepared batch from its record (codes,
+ * anchors, outliers and header, as hi_compress or hi_compress_batch left
+ * them) into its d_out (Eq. 1; the level-by-level reconstruction of
+ * Sec. 3.2, as hi_decompress does for one field): two launches for the
+ * whole batch (the outlier values of every field into its output, then one
+ * persistent reconstruction over the (field, tile) work items of all
+ * fields), no host synchronisation, no memory copy; capturable in a CUDA
+ * graph.  Each field's output equals hi_decompress of it alone.  Every field
+ * needs d_out (4-byte aligned, its point count of floats).  A field whose
+ * header is not a valid record, reports an error or holds more outliers than
+ * out_cap is left unwritten and sets HI_ECAPACITY (over capacity) or
+ * HI_ECORRUPT in *d_status (device uint32, may be NULL; first error wins;
+ * cleared by the call); an outlier index past a field's end sets
+ * HI_ECORRUPT.  HI_EINVAL (nothing enqueued) for a plan without d_out on
+ * every field.  Calls that share d_ws must not overlap (with each other or
+ * with hi_compress_batch).  Not in the paper, which reconstructs one field
+ * per call. */
+HI_API hi_status hi_decompress_batch(const hi_batch_plan* h_plan, void* d_ws, uint32_t* d_status, cudaStream_t stream);
 
 /* Launch-shape tuner of a prepared batch: times hi_compress_batch under
  * each candidate shape (128 then 64 threads per CTA, each with one buffer,

@@ -695,9 +695,10 @@ hi_status hi_batch_prepare(uint32_t n, const hi_batch_field* h_fields, uint32_t 
     if (ws_bytes < plan.ws_bytes) return HI_ENOMEM;
     for (uint32_t i = 0; i < n; ++i) {
         const hi_batch_field& f = h_fields[i];
-        if (!f.d_x || !f.d_codes || !f.d_anchors || !f.d_header) return HI_EINVAL;
+        if (!f.d_codes || !f.d_anchors || !f.d_header) return HI_EINVAL;
         if (f.out_cap > 0 && (!f.d_out_idx || !f.d_out_val)) return HI_EINVAL;
-        if (!aligned(f.d_x, 4) || !aligned(f.d_header, 8)) return HI_EINVAL;
+        if ((f.d_x && !aligned(f.d_x, 4)) || !aligned(f.d_header, 8) || (f.d_out && !aligned(f.d_out, 4)))
+            return HI_EINVAL;
     }
     plan.tuning = tuning;
     char* ws = static_cast<char*>(d_ws);
@@ -712,7 +713,7 @@ hi_status hi_batch_prepare(uint32_t n, const hi_batch_field* h_fields, uint32_t 
     uint32_t* pre = reinterpret_cast<uint32_t*>(host.get() + plan.off_prefix);
     uint32_t *ts = pre, *cs = pre + (n + 1), *ss = pre + 2 * (n + 1), *hs = pre + 3 * (n + 1);
     uint64_t tiles = 0, chunks = 0, samples = 0, err = 0, head = 0, shell = 0;
-    bool all_tma = true;
+    bool all_tma = true, all_in = true, all_out = true;
     int PX, CX;
     pitches((int)plan.anchor_stride, &PX, &CX);
     for (uint32_t i = 0; i < n; ++i) {
@@ -720,8 +721,15 @@ hi_status hi_batch_prepare(uint32_t n, const hi_batch_field* h_fields, uint32_t 
         const Geometry& G = geo[i];
         BatchField& B = table[i];
         new (&B) BatchField();
-        const bool tma = encode_box(&B.tmap, f.d_x, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, G.g, PX, G.A + 1);
+        const bool tma = f.d_x && encode_box(&B.tmap, f.d_x, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, G.g, PX, G.A + 1);
         all_tma = all_tma && tma;
+        all_in = all_in && f.d_x != nullptr;
+        all_out = all_out && f.d_out != nullptr;
+        // code boxes for the batched reconstruction (byte-sized: box origins are 16-byte aligned only for A >= 16)
+        const bool ctma = G.A >= 16 && encode_box(&B.cmap, f.d_codes, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, G.g, CX, G.A + 1);
+        B.out = f.d_out;
+        B.ctma_bytes = (uint32_t)(CX * (G.A + 1) * G.g.b0);
+        B.dflags = (ctma ? kFlagTma : 0) | ((G.g.n[2] % 4 == 0 && f.d_out && aligned(f.d_out, 16)) ? kFlagVecOut : 0);
         B.g = G.g;
         B.p = f.p;
         B.x = f.d_x;
@@ -769,6 +777,7 @@ hi_status hi_batch_prepare(uint32_t n, const hi_batch_field* h_fields, uint32_t 
     ss[n] = (uint32_t)samples;
     plan.all_tma = all_tma ? 1u : 0u;
     plan.reserved[0] = head;
+    plan.reserved[1] = (all_in ? 1u : 0u) | (all_out ? 2u : 0u);  // every field has an input / an output
     cudaError_t e = cudaMemcpyAsync(ws, host.get(), host_bytes, cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) return HI_ECUDA;
     e = cudaStreamSynchronize(stream);
@@ -779,7 +788,7 @@ hi_status hi_batch_prepare(uint32_t n, const hi_batch_field* h_fields, uint32_t 
 
 hi_status hi_compress_batch(const hi_batch_plan* h_plan, void* d_ws, cudaStream_t stream)
 {
-    if (!h_plan || !d_ws || h_plan->n_fields == 0) return HI_EINVAL;
+    if (!h_plan || !d_ws || h_plan->n_fields == 0 || !(h_plan->reserved[1] & 1u)) return HI_EINVAL;
     const BatchLaunch b = batch_launch(h_plan, d_ws);
     stage_event(0, stream);
     if (launch_batch_prologue(b, stream) != cudaSuccess) return HI_ECUDA;
@@ -791,6 +800,17 @@ hi_status hi_compress_batch(const hi_batch_plan* h_plan, void* d_ws, cudaStream_
     const hi_status s = cuda_status(launch_batch_compress(b, stream));
     stage_event(4, stream);
     return s;
+}
+
+hi_status hi_decompress_batch(const hi_batch_plan* h_plan, void* d_ws, uint32_t* d_status, cudaStream_t stream)
+{
+    if (!h_plan || !d_ws || h_plan->n_fields == 0 || !(h_plan->reserved[1] & 2u)) return HI_EINVAL;
+    if (d_status && !aligned(d_status, 4)) return HI_EINVAL;
+    const BatchLaunch b = batch_launch(h_plan, d_ws);
+    uint32_t* queue = reinterpret_cast<uint32_t*>(d_ws) + 1;  // the reconstruction's own counter
+    if (d_status && cudaMemsetAsync(d_status, 0, sizeof(uint32_t), stream) != cudaSuccess) return HI_ECUDA;
+    if (launch_batch_scatter(b, d_status, queue, stream) != cudaSuccess) return HI_ECUDA;
+    return cuda_status(launch_decompress_batch(b, d_status, queue, stream));
 }
 
 hi_status hi_batch_tune_launch(hi_batch_plan* h_plan, void* d_ws, uint32_t reps, float* h_ms, cudaStream_t stream)
@@ -963,6 +983,6 @@ hi_status hi_header_read(const hi_header* d_header, hi_header* h_header, cudaStr
 
 static_assert(sizeof(hi_header) == 168, "hi_header layout");
 static_assert(sizeof(hi_params) == 80, "hi_params layout");
-static_assert(sizeof(hi_batch_field) == 152, "hi_batch_field layout");
+static_assert(sizeof(hi_batch_field) == 160, "hi_batch_field layout");
 static_assert(sizeof(hi_batch_plan) == 120, "hi_batch_plan layout");
 static_assert(sizeof(hi::BatchField) % 128 == 0, "field records stay 128-byte aligned");

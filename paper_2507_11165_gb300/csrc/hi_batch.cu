@@ -10,21 +10,6 @@
 
 namespace hi {
 
-// The field whose work items [start[f], start[f+1]) contain w (fields
-// without work items are skipped).
-__device__ __forceinline__ int find_field(const uint32_t* __restrict__ start, int n, uint32_t w)
-{
-    int lo = 0, hi = n;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(start + mid) <= w)
-            lo = mid;
-        else
-            hi = mid;
-    }
-    return lo;
-}
-
 __global__ void k_batch_prologue(const BatchField* __restrict__ fields, uint32_t* queue)
 {
     const BatchField& F = fields[blockIdx.x];
@@ -105,25 +90,6 @@ __global__ void k_batch_gather(BatchField* __restrict__ fields)
         F.cur.lv[tid] = lv;
         F.cur.sel[tid] = perm_sel(lv);
     }
-}
-
-// Work item w -> (field, position in the field's queue order).  The head
-// tiles of every field (its whole 3D tiles) come first, then the rest of
-// every field: the CTAs in flight mostly run one kind of pass code.
-__device__ __forceinline__ int batch_locate(const BatchField* __restrict__ fields,
-                                            const uint32_t* __restrict__ head_start,
-                                            const uint32_t* __restrict__ shell_start, int n, uint32_t total_head,
-                                            uint32_t w, int* pos)
-{
-    if (w < total_head) {
-        const int f = find_field(head_start, n, w);
-        *pos = (int)(w - __ldg(head_start + f));
-        return f;
-    }
-    const uint32_t w2 = w - total_head;
-    const int f = find_field(shell_start, n, w2);
-    *pos = (int)(fields[f].nint + (w2 - __ldg(shell_start + f)));
-    return f;
 }
 
 // Asynchronous copy of a field's record into a shared-memory slot (thread 0).

@@ -145,6 +145,7 @@ struct alignas(16) BatchCur {
 
 struct alignas(128) BatchField {
     CUtensorMap tmap;  // the field as (PX, A+1, b0) float boxes (when flags & kFlagTma)
+    CUtensorMap cmap;  // its codes as (CX, A+1, b0) byte boxes (when dflags & kFlagTma)
     BatchCur cur;
     FieldGeo g;
     hi_params p;
@@ -168,6 +169,9 @@ struct alignas(128) BatchField {
     int m, stride;       // auto-tune samples (m = 0: levels given)
     uint32_t nchunks;    // range work items (0: absolute bound)
     uint32_t nint;       // tiles at the head of the field's queue order (whole 3D tiles first)
+    float* out;          // reconstruction target of the batched decompression
+    uint32_t ctma_bytes; // bytes of a code box
+    int dflags;          // decompression: kFlagTma (code boxes), kFlagVecOut
 };
 
 struct BatchLaunch {
@@ -190,6 +194,8 @@ cudaError_t launch_batch_prologue(const BatchLaunch& b, cudaStream_t st);
 cudaError_t launch_batch_range_tune(const BatchLaunch& b, cudaStream_t st);
 cudaError_t launch_batch_gather(const BatchLaunch& b, cudaStream_t st);
 cudaError_t launch_batch_compress(const BatchLaunch& b, cudaStream_t st);
+cudaError_t launch_batch_scatter(const BatchLaunch& b, uint32_t* status, uint32_t* queue, cudaStream_t st);
+cudaError_t launch_decompress_batch(const BatchLaunch& b, uint32_t* status, uint32_t* queue, cudaStream_t st);
 
 // Quantization-code reordering (Sec. 5.2.2, Eq. 3): per level l = 0..L, the
 // stride-2^l grid's points along d1 and d2 (D), their halves rounded up (H)

@@ -57,7 +57,7 @@ class HiBatchField(ctypes.Structure):
     _fields_ = [("p", HiParams), ("d_x", ctypes.c_void_p), ("d_codes", ctypes.c_void_p),
                 ("d_anchors", ctypes.c_void_p), ("d_out_idx", ctypes.c_void_p), ("d_out_val", ctypes.c_void_p),
                 ("out_cap", ctypes.c_uint64), ("d_hist", ctypes.c_void_p), ("d_recon", ctypes.c_void_p),
-                ("d_header", ctypes.c_void_p)]
+                ("d_header", ctypes.c_void_p), ("d_out", ctypes.c_void_p)]
 
 
 class HiBatchPlan(ctypes.Structure):
@@ -82,7 +82,8 @@ class HiCrEstimate(ctypes.Structure):
 HEADER_BYTES = ctypes.sizeof(HiHeader)
 SYMBOLS = ("hi_query", "hi_compress", "hi_decompress", "hi_autotune", "hi_autotune_errors", "hi_header_read",
            "hi_status_str", "hi_version", "hi_set_stage_events", "hi_compress_static_ws", "hi_batch_query",
-           "hi_batch_prepare", "hi_compress_batch", "hi_batch_tune_launch", "hi_resolve_eps", "hi_estimate_cr",
+           "hi_batch_prepare", "hi_compress_batch", "hi_decompress_batch", "hi_batch_tune_launch", "hi_resolve_eps",
+           "hi_estimate_cr",
            "hi_autotune_select", "hi_tp_query", "hi_tp_encode", "hi_tp_decode", "hi_cr_query", "hi_cr_encode",
            "hi_cr_decode")
 STATIC_WS_BYTES = 1 << 20  # HI_STATIC_WS_BYTES
@@ -116,6 +117,7 @@ def lib():
             L.hi_batch_query.argtypes = [ctypes.c_uint32, BF, ctypes.POINTER(sz)]
             L.hi_batch_prepare.argtypes = [ctypes.c_uint32, BF, ctypes.c_uint32, P, sz, BP, P]
             L.hi_compress_batch.argtypes = [BP, P, P]
+            L.hi_decompress_batch.argtypes = [BP, P, P, P]
             L.hi_batch_tune_launch.argtypes = [BP, P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_float), P]
             L.hi_decompress.argtypes = [ctypes.POINTER(HiParams), P, P, P, P, P, u64, P, P, P, sz, P]
             L.hi_autotune.argtypes = [ctypes.POINTER(HiParams), P, P, P, sz, P]
@@ -140,7 +142,8 @@ def lib():
             L.hi_version.restype = ctypes.c_uint32
             for f in ("hi_query", "hi_compress", "hi_decompress", "hi_autotune", "hi_autotune_errors",
                       "hi_header_read", "hi_set_stage_events", "hi_compress_static_ws", "hi_batch_query",
-                      "hi_batch_prepare", "hi_compress_batch", "hi_batch_tune_launch", "hi_resolve_eps",
+                      "hi_batch_prepare", "hi_compress_batch", "hi_decompress_batch", "hi_batch_tune_launch",
+                      "hi_resolve_eps",
                       "hi_estimate_cr", "hi_autotune_select"):
                 getattr(L, f).restype = ctypes.c_int
             _lib = L
@@ -501,10 +504,12 @@ class Batch:
     ``xs``: contiguous float32 device tensors (shapes may differ); ``ebs``: one
     bound per field (or one for all); the other arguments apply to every
     field.  Buffers of each field are allocated here; ``compress()`` only
-    enqueues kernels, so it can be captured in a CUDA graph."""
+    enqueues kernels, so it can be captured in a CUDA graph.  With
+    ``outs=True`` every field also gets an output tensor (``self.outs``)
+    that ``decompress()`` (hi_decompress_batch) reconstructs it into."""
 
     def __init__(self, xs, ebs, mode="rel", anchor_stride=16, autotune=True, levels=None, out_caps=None,
-                 hist=True, recon=False, tuning=0):
+                 hist=True, recon=False, tuning=0, outs=False):
         n = len(xs)
         if n == 0:
             raise ValueError("empty batch")
@@ -513,6 +518,8 @@ class Batch:
         modes = mode if isinstance(mode, (list, tuple)) else [mode] * n
         self.xs = list(xs)
         self.buffers = []
+        self.outs = [torch.empty_like(x) for x in self.xs] if outs else None
+        self.dstatus = torch.zeros(1, dtype=torch.int32, device=self.xs[0].device)
         arr = (HiBatchField * n)()
         for i, x in enumerate(self.xs):
             if not x.is_cuda or x.dtype != torch.float32 or not x.is_contiguous():
@@ -531,6 +538,7 @@ class Batch:
             arr[i].d_hist = None if b.hist is None else b.hist.data_ptr()
             arr[i].d_recon = None if b.recon is None else b.recon.data_ptr()
             arr[i].d_header = b.header.data_ptr()
+            arr[i].d_out = None if self.outs is None else self.outs[i].data_ptr()
         self.fields = arr
         wsb = ctypes.c_size_t()
         _check(lib().hi_batch_query(n, arr, ctypes.byref(wsb)), "hi_batch_query")
@@ -546,6 +554,12 @@ class Batch:
         """Enqueue the batch's compression (no sync)."""
         _check(lib().hi_compress_batch(ctypes.byref(self.plan), _ptr(self.ws), _stream(stream)),
                "hi_compress_batch")
+
+    def decompress(self, stream=None):
+        """Enqueue the reconstruction of every field into ``self.outs`` (no
+        sync); the first error of any field goes to ``self.dstatus``."""
+        _check(lib().hi_decompress_batch(ctypes.byref(self.plan), _ptr(self.ws), _ptr(self.dstatus),
+                                         _stream(stream)), "hi_decompress_batch")
 
     def tune_launch(self, reps=3, stream=None):
         """Time every launch shape, keep the fastest; returns {shape: ms}."""

@@ -67,7 +67,7 @@ def test_host_calls_without_gpu(lib):
 
 def test_batch_host_validation(lib):
     import ctypes as C
-    assert C.sizeof(lib.HiBatchField) == 152 and C.sizeof(lib.HiBatchPlan) == 120
+    assert C.sizeof(lib.HiBatchField) == 160 and C.sizeof(lib.HiBatchPlan) == 120
     L = lib.lib()
     arr = (lib.HiBatchField * 3)()
     arr[0].p = lib.make_params((40, 50, 60), 1e-3, "rel", 16)

@@ -182,3 +182,88 @@ def test_batch_workload_sample(hi):
     xs = [torch.from_numpy(a).cuda() for a in arrs]
     mix = [(s["shape"], s["eb"], "rel") for s in specs]
     _batch_vs_single(hi, mix, 16, True, xs=xs)
+
+
+def _decompress_single(hi, b, shape):
+    out = torch.empty(shape, dtype=torch.float32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    hi.decompress_into(b, out, st)
+    torch.cuda.synchronize()
+    return out, int(st.item())
+
+
+@pytest.mark.parametrize("A", [16, 8])
+def test_batched_decompress_equals_single(hi, A):
+    """hi_decompress_batch of a batch (1D/2D/3D, ragged and whole tiles,
+    plain loads, a constant field, many outliers) gives every field the
+    output of hi_decompress of it alone, bit for bit, and the compressor's
+    own reconstruction."""
+    xs = _inputs(MIX16)
+    caps = [x.numel() for x in xs]
+    bat = hi.Batch(xs, [m[1] for m in MIX16], [m[2] for m in MIX16], anchor_stride=A, autotune=A == 16,
+                   levels=None if A == 16 else (hi.CUBIC, (0, 1, 2)), out_caps=caps, recon=True, outs=True)
+    bat.compress()
+    bat.decompress()
+    torch.cuda.synchronize()
+    assert int(bat.dstatus.item()) == 0
+    for x, b, y in zip(xs, bat.buffers, bat.outs):
+        ref, st = _decompress_single(hi, b, x.shape)
+        assert st == 0
+        assert torch.equal(y.view(torch.int32), ref.view(torch.int32))
+        assert torch.equal(y.reshape(-1).view(torch.int32), b.recon.reshape(-1).view(torch.int32))
+
+
+def test_batched_decompress_against_oracle(oracle_mod, hi):
+    """Two fields of a batch reconstructed by hi_decompress_batch against the
+    oracle's decompression of the batch's own records."""
+    mix = [((37, 45, 70), 1e-3, "rel"), ((33, 33, 33), 1e-4, "rel")]
+    xs = _inputs(mix)
+    bat = hi.Batch(xs, [m[1] for m in mix], "rel", anchor_stride=16, autotune=True, out_caps=[x.numel() for x in xs],
+                   outs=True)
+    bat.compress()
+    bat.decompress()
+    torch.cuda.synchronize()
+    for x, b, y in zip(xs, bat.buffers, bat.outs):
+        h = hi.read_header(b.header)
+        L = int(h.n_levels)
+        interp = np.array([h.level[l].interp for l in range(L)], dtype=np.uint8)
+        order = np.array([list(h.level[l].order) for l in range(L)], dtype=np.uint8)
+        k = int(h.n_outliers)
+        ref = oracle_mod.decompress(tuple(x.shape), 16, interp, order, float(h.ebx2_f), b.codes.cpu().numpy(),
+                                    b.anchors[: int(h.n_anchors)].cpu().numpy(), b.out_idx[:k].cpu().numpy(),
+                                    b.out_val[:k].cpu().numpy())
+        assert np.array_equal(y.cpu().numpy().view(np.uint32), ref.view(np.uint32))
+
+
+def test_batched_decompress_graph_replay_and_capacity(hi):
+    """The reconstruction replayed from a captured CUDA graph follows new
+    records; a field whose outliers overflow its capacity is left unwritten
+    and reports HI_ECAPACITY while the others are reconstructed."""
+    mix = [((40, 44, 48), 1e-3, "rel"), ((30, 31, 32), 1e-7, "rel"), ((64, 64, 64), 1e-3, "rel")]
+    xs = _inputs(mix, seed0=7)
+    caps = [xs[0].numel(), 64, xs[2].numel()]  # the tight bound overflows 64 slots
+    bat = hi.Batch(xs, [m[1] for m in mix], "rel", anchor_stride=16, autotune=True, out_caps=caps, outs=True)
+    for y in bat.outs:
+        y.fill_(-7.0)
+    bat.compress()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        bat.decompress()
+    g.replay()
+    torch.cuda.synchronize()
+    assert int(bat.dstatus.item()) == hi.HI_ECAPACITY
+    assert bool((bat.outs[1] == -7.0).all())
+    for i in (0, 2):
+        ref, st = _decompress_single(hi, bat.buffers[i], xs[i].shape)
+        assert st == 0 and torch.equal(bat.outs[i].view(torch.int32), ref.view(torch.int32))
+    # new inputs, recompress, replay the captured reconstruction
+    for i in (0, 2):
+        xs[i].copy_(torch.from_numpy(fields.lognormal_grf(tuple(xs[i].shape), seed=40 + i)).cuda())
+    bat.compress()
+    g.replay()
+    torch.cuda.synchronize()
+    for i in (0, 2):
+        ref, st = _decompress_single(hi, bat.buffers[i], xs[i].shape)
+        assert st == 0 and torch.equal(bat.outs[i].view(torch.int32), ref.view(torch.int32))
+        h = hi.read_header(bat.buffers[i].header)
+        assert float((bat.outs[i] - xs[i]).abs().max()) < h.eps
