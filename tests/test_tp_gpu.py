@@ -106,6 +106,29 @@ def test_full_size_field(hi, oracle_mod):
     assert int(codec.status.item()) == 0 and torch.equal(out, seq)
 
 
+@pytest.mark.parametrize("n", [100, 16384 + 640, 50000])
+def test_unaligned_input_and_output(hi, oracle_mod, n):
+    """Input and output at odd byte offsets (the byte-wise load and store
+    paths): the same stream as the oracle's, and the input back."""
+    rng = np.random.default_rng(n)
+    d = _code_like(rng, n)
+    big = torch.zeros(n + 16, dtype=torch.uint8, device="cuda")
+    big[3:3 + n] = torch.from_numpy(d).cuda()
+    codec = hi.TpCodec(n, "cuda")
+    codec.encode_into(big[3:3 + n])
+    torch.cuda.synchronize()
+    ln = int(codec.len.item())
+    s = codec.stream_buf[:ln].cpu().numpy()
+    assert np.array_equal(s, oracle_mod.tp_encode(d))
+    out = torch.zeros(n + 16, dtype=torch.uint8, device="cuda")
+    codec.status.zero_()
+    codec.decode_into(codec.stream_buf, ln, out[5:5 + n])
+    torch.cuda.synchronize()
+    assert int(codec.status.item()) == 0
+    assert np.array_equal(out[5:5 + n].cpu().numpy(), d)
+    assert int(out[:5].sum()) == 0 and int(out[5 + n:].sum()) == 0
+
+
 def test_corrupt_streams(hi, oracle_mod):
     rng = np.random.default_rng(1)
     d = _code_like(rng, 40000)
