@@ -434,7 +434,12 @@ __global__ void __launch_bounds__(kTpThreads, kTpBlocksPerSm) k_tp_encode_chunks
 
 // Exclusive scan of the padded sizes (one CTA): offsets[k] = header +
 // sum of sizes before k; with out != nullptr also writes the stream header
-// and size table, and the stream length to *len.
+// and size table, and the stream length to *len.  A thread takes
+// kTpScanPer consecutive entries (16-byte loads and stores where whole),
+// one block scan of the per-thread sums for every 1024 kTpScanPer entries.
+// sizes, offsets and out are 16-byte aligned.
+constexpr uint32_t kTpScanPer = 16;
+
 __global__ void __launch_bounds__(1024) k_tp_scan(const uint32_t* __restrict__ sizes, uint32_t nchunks, uint64_t n,
                                                   uint64_t* __restrict__ offsets, uint8_t* __restrict__ out,
                                                   uint64_t* __restrict__ len)
@@ -444,29 +449,59 @@ __global__ void __launch_bounds__(1024) k_tp_scan(const uint32_t* __restrict__ s
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) s_base = tp_header_bytes(nchunks);
     __syncthreads();
-    for (uint32_t c0 = 0; c0 < nchunks; c0 += blockDim.x) {
-        const uint32_t k = c0 + threadIdx.x;
-        const uint32_t raw = k < nchunks ? sizes[k] : 0u;
-        const uint64_t v = raw & ~kTpRaw;
-        uint64_t incl = v;
+    uint32_t* table = out ? reinterpret_cast<uint32_t*>(out + 16) : nullptr;
+    for (uint32_t c0 = 0; c0 < nchunks; c0 += blockDim.x * kTpScanPer) {
+        const uint32_t k0 = c0 + threadIdx.x * kTpScanPer;
+        const bool whole = k0 + kTpScanPer <= nchunks;
+        uint32_t v[kTpScanPer];
+        if (whole) {
+#pragma unroll
+            for (uint32_t j = 0; j < kTpScanPer / 4; ++j) {
+                const uint4 q = reinterpret_cast<const uint4*>(sizes + k0)[j];
+                v[4 * j] = q.x, v[4 * j + 1] = q.y, v[4 * j + 2] = q.z, v[4 * j + 3] = q.w;
+            }
+        } else {
+#pragma unroll
+            for (uint32_t j = 0; j < kTpScanPer; ++j) v[j] = k0 + j < nchunks ? sizes[k0 + j] : 0u;
+        }
+        uint64_t sum = 0;
+#pragma unroll
+        for (uint32_t j = 0; j < kTpScanPer; ++j) sum += v[j] & ~kTpRaw;
+        uint64_t incl = sum;
+#pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const uint64_t t = __shfl_up_sync(0xffffffffu, incl, d);
             if (lane >= (uint32_t)d) incl += t;
         }
         if (lane == 31) s_part[warp] = incl;
         __syncthreads();
-        uint64_t before = s_base;
-        for (uint32_t w = 0; w < warp; ++w) before += s_part[w];
-        if (k < nchunks) {
-            offsets[k] = before + incl - v;
-            if (out) reinterpret_cast<uint32_t*>(out + 16)[k] = raw;
+        uint64_t o = s_base + incl - sum;
+        for (uint32_t w = 0; w < warp; ++w) o += s_part[w];
+        if (whole) {
+#pragma unroll
+            for (uint32_t j = 0; j < kTpScanPer; j += 2) {
+                const uint64_t a = o;
+                o += v[j] & ~kTpRaw;
+                reinterpret_cast<ulonglong2*>(offsets + k0)[j / 2] = make_ulonglong2(a, o);
+                o += v[j + 1] & ~kTpRaw;
+            }
+            if (table) {
+#pragma unroll
+                for (uint32_t j = 0; j < kTpScanPer / 4; ++j)
+                    reinterpret_cast<uint4*>(table + k0)[j] = make_uint4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+            }
+        } else {
+#pragma unroll
+            for (uint32_t j = 0; j < kTpScanPer; ++j) {
+                if (k0 + j < nchunks) {
+                    offsets[k0 + j] = o;
+                    if (table) table[k0 + j] = v[j];
+                }
+                o += v[j] & ~kTpRaw;
+            }
         }
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) {
-            uint64_t t = 0;
-            for (uint32_t w = 0; w < blockDim.x / 32; ++w) t += s_part[w];
-            s_base += t;
-        }
+        __syncthreads();  // s_part read; the last thread's running sum is the round's end
+        if (threadIdx.x == blockDim.x - 1) s_base = o;
         __syncthreads();
     }
     if (threadIdx.x == 0 && out) {
