@@ -461,6 +461,30 @@ def run_gpu(args):
                    traffic_inv=traffic_record("k_reorder_rows_inv") if rows_path else None,
                    forward_gbs=2 * N / (f_ms * 1e-3) / 1e9, inverse_gbs=2 * N / (i_ms * 1e-3) / 1e9,
                    forward_frac=2 * N / (f_ms * 1e-3) / 1e9 / peak, inverse_frac=2 * N / (i_ms * 1e-3) / 1e9 / peak)
+    # the forward reordering written by predict-quantize itself (hi_compress_seq: each tile row's codes
+    # also go to their places in the sequence from the kernel's registers), against hi_compress followed
+    # by hi_reorder_codes; both whole compressions (range, auto-tune, predict-quantize)
+    seq2 = torch.empty(N, dtype=torch.uint8, device=dev)
+    fused = hi.compress_seq_fused(p, b.codes.data_ptr(), seq2.data_ptr())
+    for _ in range(3):
+        hi.compress_seq_into(x, b, seq2, stream=stream)
+        hi.compress_into(x, b, stream=stream)
+        hi.reorder_codes(b.codes, p, out=seq, stream=stream)
+    fev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(10)]
+    for e in fev:
+        e[0].record(stream)
+        hi.compress_seq_into(x, b, seq2, stream=stream)
+        e[1].record(stream)
+        hi.compress_into(x, b, stream=stream)
+        hi.reorder_codes(b.codes, p, out=seq, stream=stream)
+        e[2].record(stream)
+    torch.cuda.synchronize()
+    cs_ms = statistics.median(e[0].elapsed_time(e[1]) for e in fev)
+    cr_ms = statistics.median(e[1].elapsed_time(e[2]) for e in fev)
+    reorder["compress_seq"] = dict(api="hi_compress_seq", fused_in_kernel=fused, compress_seq_ms=cs_ms,
+                                   compress_then_reorder_ms=cr_ms, saved_ms=cr_ms - cs_ms,
+                                   bit_exact_vs_separate=bool(torch.equal(seq, seq2)))
+    del seq2
     # throughput-mode lossless pipeline TCMS1-BIT1-RRE1 (Sec. 5.2.3) on the reordered codes: a real
     # compressed size beside the entropy estimate; timed on its own, not part of the step
     hi.reorder_codes(b.codes, p, out=seq, stream=stream)

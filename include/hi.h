@@ -351,6 +351,27 @@ HI_API hi_status hi_reorder_codes(const hi_params* p, const uint8_t* d_codes, ui
 HI_API hi_status hi_unreorder_codes(const hi_params* p, const uint8_t* d_seq, uint8_t* d_codes,
                                     cudaStream_t stream);
 
+/* hi_compress that also writes the codes in the reordered order of
+ * hi_reorder_codes (Sec. 5.2.2, Eq. 3) to d_seq (n_points bytes, not
+ * overlapping d_codes), the input of the lossless pipelines below.  All
+ * other arguments and results are those of hi_compress, and d_codes is
+ * written as there.  Where the field allows it the predict-quantize kernel
+ * stores each tile row's codes to their places in d_seq from the registers
+ * that hold them, one aligned store per run of a level, instead of a
+ * separate pass over the code array: A = 8 or 16, n2 a multiple of A and of
+ * the vector width (16 codes for A = 16, 8 for A = 8), d_codes and d_seq
+ * 16-byte aligned, fewer than 2^32 points, and every run starting at a
+ * multiple of its length (true when each dim is a multiple of 2A, e.g.
+ * 512^3 at A = 16).  Otherwise hi_reorder_codes runs after the kernel on
+ * the same stream.  HI_EINVAL for a NULL d_seq or overlapping code arrays.
+ * hi_compress_seq_fused: 1 when a call with these parameters and pointers
+ * takes the single-kernel form, else 0 (host only, no GPU work). */
+HI_API hi_status hi_compress_seq(const hi_params* p, const float* d_x, uint8_t* d_codes, uint8_t* d_seq,
+                                 float* d_anchors, uint32_t* d_out_idx, float* d_out_val, uint64_t out_cap,
+                                 uint32_t* d_hist, float* d_recon, hi_header* d_header, void* d_ws,
+                                 size_t ws_bytes, cudaStream_t stream);
+HI_API int hi_compress_seq_fused(const hi_params* p, const uint8_t* d_codes, const uint8_t* d_seq);
+
 /* The value range of the value-range-relative bound (Sec. 6.1.4) alone:
  * the min and the max over the finite values of d_x go to d_header->vmin /
  * vmax (0 and 0 when there is none), with the header's eps and float32

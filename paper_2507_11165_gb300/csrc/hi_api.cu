@@ -401,14 +401,38 @@ static hi_status enqueue_tune(const Geometry& G, const float* d_x, hi_header* d_
     return cuda_status(launch_tune(G.A, tune_launch(G, d_x, d_header, d_ws), stream));
 }
 
-hi_status hi_compress(const hi_params* p, const float* d_x, uint8_t* d_codes, float* d_anchors,
-                      uint32_t* d_out_idx, float* d_out_val, uint64_t out_cap, uint32_t* d_hist,
-                      float* d_recon, hi_header* d_header, void* d_ws, size_t ws_bytes, cudaStream_t stream)
+// Whether the predict-quantize kernel can write the reordered sequence from
+// its code registers: A = 8 or 16, every tile row whole (n2 a multiple of A)
+// and stored as vectors, the sequence 16-byte aligned with fewer than 2^32
+// places, and every run of a tile row (A >> l codes on level l, half of
+// them for the odd columns of a row of even subgrid coordinates) starting
+// at a multiple of its length: the terms of its place are multiples of
+// A >> l.
+static bool seq_fusable(const Geometry& G, const ReorderGeo& R, int flags, const uint8_t* d_seq)
+{
+    if ((G.A != 8 && G.A != 16) || !(flags & kFlagVecCodes) || G.g.n[2] % G.A != 0) return false;
+    if (!aligned(d_seq, 16) || G.g.N >= (int64_t(1) << 32)) return false;
+    for (int l = 0; l < G.L; ++l) {
+        const uint64_t c = (uint64_t)(G.A >> l);
+        if (R.prefix[l] % c || R.D2[l] % c || ((uint64_t)R.H1[l] * R.H2[l]) % c || R.H2[l] % c) return false;
+    }
+    return true;
+}
+
+static hi_status compress_impl(const hi_params* p, const float* d_x, uint8_t* d_codes, uint8_t* d_seq,
+                               float* d_anchors, uint32_t* d_out_idx, float* d_out_val, uint64_t out_cap,
+                               uint32_t* d_hist, float* d_recon, hi_header* d_header, void* d_ws, size_t ws_bytes,
+                               cudaStream_t stream)
 {
     Geometry G;
     hi_status s = make_geometry(p, &G);
     if (s != HI_OK) return s;
     if (!d_x || !d_codes || !d_anchors || !d_header || !d_ws) return HI_EINVAL;
+    if (d_seq) {
+        const uintptr_t a = reinterpret_cast<uintptr_t>(d_codes), b = reinterpret_cast<uintptr_t>(d_seq);
+        const uintptr_t n = (uintptr_t)G.g.N;
+        if (a < b + n && b < a + n) return HI_EINVAL;  // overlapping code arrays
+    }
     if (out_cap > 0 && (!d_out_idx || !d_out_val)) return HI_EINVAL;
     if (!aligned(d_x, 4) || !aligned(d_ws, 8) || !aligned(d_header, 8)) return HI_EINVAL;
     if (ws_bytes < workspace_bytes(G)) return HI_ENOMEM;
@@ -471,9 +495,49 @@ hi_status hi_compress(const hi_params* p, const float* d_x, uint8_t* d_codes, fl
     c.buffers = (int)((p->tuning >> 2) & 3u);
     c.num_sms = num_sms();
     c.max_ctas = 0;
+    ReorderGeo R{};
+    if (d_seq) {
+        R = make_reorder_geo(G.g.n, G.L);
+        if (seq_fusable(G, R, c.flags, d_seq)) {
+            c.seq = d_seq;
+            for (int l = 0; l <= G.L; ++l) {
+                c.sg.D1[l] = R.D1[l], c.sg.D2[l] = R.D2[l];
+                c.sg.H12[l] = R.H1[l] * R.H2[l], c.sg.H2[l] = R.H2[l];
+                c.sg.prefix[l] = R.prefix[l];
+            }
+        }
+    }
     s = cuda_status(launch_compress(G.A, c, stream));
     stage_event(4, stream);
+    if (s == HI_OK && d_seq && !c.seq) s = cuda_status(launch_reorder(R, d_codes, d_seq, false, num_sms(), stream));
     return s;
+}
+
+hi_status hi_compress(const hi_params* p, const float* d_x, uint8_t* d_codes, float* d_anchors,
+                      uint32_t* d_out_idx, float* d_out_val, uint64_t out_cap, uint32_t* d_hist,
+                      float* d_recon, hi_header* d_header, void* d_ws, size_t ws_bytes, cudaStream_t stream)
+{
+    return compress_impl(p, d_x, d_codes, nullptr, d_anchors, d_out_idx, d_out_val, out_cap, d_hist, d_recon,
+                         d_header, d_ws, ws_bytes, stream);
+}
+
+hi_status hi_compress_seq(const hi_params* p, const float* d_x, uint8_t* d_codes, uint8_t* d_seq,
+                          float* d_anchors, uint32_t* d_out_idx, float* d_out_val, uint64_t out_cap,
+                          uint32_t* d_hist, float* d_recon, hi_header* d_header, void* d_ws, size_t ws_bytes,
+                          cudaStream_t stream)
+{
+    if (!d_seq) return HI_EINVAL;
+    return compress_impl(p, d_x, d_codes, d_seq, d_anchors, d_out_idx, d_out_val, out_cap, d_hist, d_recon,
+                         d_header, d_ws, ws_bytes, stream);
+}
+
+int hi_compress_seq_fused(const hi_params* p, const uint8_t* d_codes, const uint8_t* d_seq)
+{
+    Geometry G;
+    if (!p || make_geometry(p, &G) != HI_OK) return 0;
+    const int ch = G.A >= 16 ? 16 : 8;
+    const int flags = (G.g.n[2] % ch == 0 && aligned(d_codes, 16)) ? kFlagVecCodes : 0;
+    return seq_fusable(G, make_reorder_geo(G.g.n, G.L), flags, d_seq) ? 1 : 0;
 }
 
 hi_status hi_compress_static_ws(const hi_params* p, const float* d_x, uint8_t* d_codes, float* d_anchors,

@@ -1,7 +1,8 @@
 // hi_compress.cu -- the fused interpolation-predict + quantize kernel of one
 // field (cuSZ-Hi, arXiv 2507.11165, Sec. 3.2, Sec. 5.1.1-5.1.2, Sec. 5.2.1):
 // persistent CTAs take tiles from a queue, stage them with TMA and run
-// compress_tile (hi_compress_tile.cuh) on each.
+// compress_tile (hi_compress_tile.cuh) on each.  With SEQ the codes also go
+// to the reordered sequence of Sec. 5.2.2 (Eq. 3) from the same registers.
 #include "hi_compress_tile.cuh"
 
 namespace hi {
@@ -9,13 +10,14 @@ namespace hi {
 // ---------------------------------------------------------------------------
 // Predict + quantize
 // ---------------------------------------------------------------------------
-template <int A>
+template <int A, bool SEQ>
 __global__ void __launch_bounds__(kMaxThreads, 7)
     k_compress(const __grid_constant__ CUtensorMap tmap, const FieldGeo g, const float* __restrict__ x,
                uint8_t* __restrict__ codes, float* __restrict__ anchors, uint32_t* __restrict__ out_idx,
                float* __restrict__ out_val, const uint64_t out_cap, uint32_t* __restrict__ hist_g,
                float* __restrict__ recon_g, hi_header* __restrict__ hdr, uint32_t* __restrict__ queue,
-               const uint32_t tma_bytes, const int flags)
+               const uint32_t tma_bytes, const int flags, uint8_t* __restrict__ seq,
+               const __grid_constant__ SeqGeo sg)
 {
     using Lw = Lay<A>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -109,7 +111,7 @@ __global__ void __launch_bounds__(kMaxThreads, 7)
         {
             const CompressOut out{codes, anchors, out_idx, out_val, out_cap, recon_g, hdr,
                                   (flags & kFlagVecCodes) != 0, hist_on};
-            compress_tile<A>(g, ti, v, cs, hc, s_hist, s_sel, s_lv, h, full_ok, out);
+            compress_tile<A, SEQ>(g, ti, v, cs, hc, s_hist, s_sel, s_lv, h, full_ok, out, seq, &sg);
             if (hist_on && ++nslow % kHistFoldTiles == 0) hist_fold(hc, s_hist);
         }
         // keep the buffers until every thread is done; order the generic-proxy
@@ -121,10 +123,10 @@ __global__ void __launch_bounds__(kMaxThreads, 7)
     if (hist_on) hist_flush(hc, s_hist, hist_g);
 }
 
-template <int A>
+template <int A, bool SEQ>
 static cudaError_t launch_compress_t(const CompressLaunch& c, cudaStream_t st)
 {
-    auto kern = k_compress<A>;
+    auto kern = k_compress<A, SEQ>;
     const bool dbuf = c.buffers == 2 && fits_double(kern, compress_smem_t<A>(c.g.b0, true, c.threads));
     const size_t smem = compress_smem_t<A>(c.g.b0, dbuf, c.threads);
     int grid = 0;
@@ -132,18 +134,25 @@ static cudaError_t launch_compress_t(const CompressLaunch& c, cudaStream_t st)
     if (err != cudaSuccess) return err;
     kern<<<grid, c.threads, smem, st>>>(c.tmap, c.g, c.x, c.codes, c.anchors, c.out_idx, c.out_val, c.out_cap,
                                         c.hist, c.recon, c.hdr, c.queue, c.tma_bytes,
-                                        c.flags | (dbuf ? kFlagDoubleBuf : 0));
+                                        c.flags | (dbuf ? kFlagDoubleBuf : 0), c.seq, c.sg);
     return cudaGetLastError();
 }
 
 cudaError_t launch_compress(int A, const CompressLaunch& c, cudaStream_t st)
 {
+    if (c.seq) {
+        switch (A) {
+        case 8: return launch_compress_t<8, true>(c, st);
+        case 16: return launch_compress_t<16, true>(c, st);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     switch (A) {
-    case 2: return launch_compress_t<2>(c, st);
-    case 4: return launch_compress_t<4>(c, st);
-    case 8: return launch_compress_t<8>(c, st);
-    case 16: return launch_compress_t<16>(c, st);
-    case 32: return launch_compress_t<32>(c, st);
+    case 2: return launch_compress_t<2, false>(c, st);
+    case 4: return launch_compress_t<4, false>(c, st);
+    case 8: return launch_compress_t<8, false>(c, st);
+    case 16: return launch_compress_t<16, false>(c, st);
+    case 32: return launch_compress_t<32, false>(c, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -9,14 +9,83 @@
 
 namespace hi {
 
+// Reordered-sequence store of one tile row (Sec. 5.2.2, Eq. 3): the A codes
+// of row (x, y), columns z0 .. z0 + A - 1 (z0 a multiple of A), 4 to a word
+// in w.  On the stride-2^l subgrid the row (x >> l, y >> l) holds A >> l of
+// them from column z0 >> l: if x >> l or y >> l is odd all are on level l,
+// at consecutive places; otherwise the odd columns are on level l, at
+// consecutive places, and the even ones go on to level l + 1; on level
+// log2 A the one left is an anchor.  A place is prefix[l] (the coarser
+// points) + the row-major rank on the subgrid - the all-even points before
+// it.  Callers take this path only where every run starts at a multiple of
+// its length, so each run is one aligned store.
+template <int N>
+__device__ __forceinline__ void seq_store_run(uint8_t* p, uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3)
+{
+    if constexpr (N == 16)
+        *reinterpret_cast<uint4*>(p) = make_uint4(v0, v1, v2, v3);
+    else if constexpr (N == 8)
+        *reinterpret_cast<uint2*>(p) = make_uint2(v0, v1);
+    else if constexpr (N == 4)
+        *reinterpret_cast<uint32_t*>(p) = v0;
+    else if constexpr (N == 2)
+        *reinterpret_cast<uint16_t*>(p) = (uint16_t)v0;
+    else
+        *p = (uint8_t)v0;
+}
+
+template <int A, int l>
+__device__ __forceinline__ void seq_store_level(uint8_t* __restrict__ seq, const SeqGeo& sg, uint32_t x, uint32_t y,
+                                                uint32_t z0, uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3)
+{
+    constexpr int L = (A == 16) ? 4 : 3;
+    constexpr int N = A >> l;  // codes of the row on this subgrid
+    const uint32_t xs = x >> l, ys = y >> l, zs = z0 >> l;
+    const uint32_t rank = (xs * sg.D1[l] + ys) * sg.D2[l];
+    if constexpr (l == L) {
+        seq[rank + zs] = (uint8_t)v0;  // the anchors come first: prefix 0
+    } else {
+        uint32_t base = sg.prefix[l] + rank - ((xs + 1u) >> 1) * sg.H12[l];
+        if ((xs & 1u) == 0) base -= ((ys + 1u) >> 1) * sg.H2[l];
+        if ((xs | ys) & 1u) {
+            seq_store_run<N>(seq + base + zs, v0, v1, v2, v3);
+            return;
+        }
+        uint32_t o0, o1 = 0u, e0, e1 = 0u;  // odd and even columns, in order
+        if constexpr (N == 16) {
+            o0 = __byte_perm(v0, v1, 0x7531), o1 = __byte_perm(v2, v3, 0x7531);
+            e0 = __byte_perm(v0, v1, 0x6420), e1 = __byte_perm(v2, v3, 0x6420);
+        } else if constexpr (N == 8) {
+            o0 = __byte_perm(v0, v1, 0x7531), e0 = __byte_perm(v0, v1, 0x6420);
+        } else if constexpr (N == 4) {
+            o0 = __byte_perm(v0, 0u, 0x31), e0 = __byte_perm(v0, 0u, 0x20);
+        } else {
+            o0 = v0 >> 8, e0 = v0;
+        }
+        seq_store_run<N / 2>(seq + base + (zs >> 1), o0, o1, 0u, 0u);
+        seq_store_level<A, l + 1>(seq, sg, x, y, z0, e0, e1, 0u, 0u);
+    }
+}
+
+template <int A>
+__device__ __forceinline__ void seq_store_row(uint8_t* __restrict__ seq, const SeqGeo& sg, uint32_t x, uint32_t y,
+                                              uint32_t z0, const uint32_t* w)
+{
+    static_assert(A == 8 || A == 16, "rows of 8 or 16 codes");
+    seq_store_level<A, 0>(seq, sg, x, y, z0, w[0], w[1], A == 16 ? w[2] : 0u, A == 16 ? w[3] : 0u);
+}
+
 // The tile's floats are in v (reconstructed in place), its codes are staged
 // in cs; g, ti: the field and the tile; s_sel / s_lv: the level
 // configuration; full_ok: the field may take the compile-time full-tile
-// passes; out: a CompressOut or a reference to one in shared memory.
-template <int A, class Out>
+// passes; out: a CompressOut or a reference to one in shared memory.  With
+// SEQ the owned codes also go to the reordered sequence seq (constants sg);
+// the caller takes SEQ only where every tile row is stored as vectors.
+template <int A, bool SEQ = false, class Out>
 __device__ __forceinline__ void compress_tile(const FieldGeo& g, const TileInfo& ti, float* v, uint8_t* cs,
                                               uint16_t* hc, uint32_t* s_hist, const int* s_sel,
-                                              const hi_level* s_lv, const Hot h, bool full_ok, const Out& out)
+                                              const hi_level* s_lv, const Hot h, bool full_ok, const Out& out,
+                                              uint8_t* seq = nullptr, const SeqGeo* sg = nullptr)
 {
     using Lw = Lay<A>;
     const int tid = threadIdx.x;
@@ -70,6 +139,9 @@ __device__ __forceinline__ void compress_tile(const FieldGeo& g, const TileInfo&
                     *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
                 else
                     *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
+                if constexpr (SEQ)
+                    seq_store_row<A>(seq, *sg, (uint32_t)(ti.o[0] + c0), (uint32_t)(ti.o[1] + c1), (uint32_t)ti.o[2],
+                                     w);
             }
             if (__any_sync(0xffffffffu, act && z != 0)) {
                 uint32_t zm[CH];  // 0x80 in each byte that is zero (exact, no borrow between bytes)

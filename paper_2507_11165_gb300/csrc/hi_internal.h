@@ -40,6 +40,16 @@ struct CompressOut {
     bool hist_on;  // count the histogram
 };
 
+// Constants of the reordered sequence (Sec. 5.2.2, Eq. 3) per level l of
+// the stride-2^l subgrid: D1, D2 = its extents along dims 1 and 2, H12 and
+// H2 = the all-even points of a plane and of a row, prefix = the points of
+// the coarser levels.
+struct SeqGeo {
+    uint32_t D1[HI_MAX_LEVELS], D2[HI_MAX_LEVELS];
+    uint32_t H12[HI_MAX_LEVELS], H2[HI_MAX_LEVELS];
+    uint32_t prefix[HI_MAX_LEVELS];
+};
+
 struct CompressLaunch {
     CUtensorMap tmap;
     FieldGeo g;
@@ -59,6 +69,9 @@ struct CompressLaunch {
     int buffers;   // 2: two tile buffers when they fit; otherwise one
     int num_sms;
     int max_ctas;  // 0 = occupancy-limited persistent grid
+    uint8_t* seq;  // non-null: the codes also go to their places in the reordered sequence (A = 8 or 16,
+                   // every row whole and stored as vectors, every run aligned to its length)
+    SeqGeo sg;
 };
 
 struct DecompressLaunch {

@@ -85,7 +85,7 @@ SYMBOLS = ("hi_query", "hi_compress", "hi_decompress", "hi_autotune", "hi_autotu
            "hi_batch_prepare", "hi_compress_batch", "hi_decompress_batch", "hi_batch_tune_launch", "hi_resolve_eps",
            "hi_estimate_cr",
            "hi_autotune_select", "hi_tp_query", "hi_tp_encode", "hi_tp_decode", "hi_cr_query", "hi_cr_encode",
-           "hi_cr_decode")
+           "hi_cr_decode", "hi_compress_seq", "hi_compress_seq_fused", "hi_reorder_codes", "hi_unreorder_codes")
 STATIC_WS_BYTES = 1 << 20  # HI_STATIC_WS_BYTES
 DECOMPRESS_WS_BYTES = 256  # HI_DECOMPRESS_WS_BYTES
 
@@ -113,6 +113,9 @@ def lib():
                                    ctypes.POINTER(u64), ctypes.POINTER(sz)]
             L.hi_compress.argtypes = [ctypes.POINTER(HiParams), P, P, P, P, P, u64, P, P, P, P, sz, P]
             L.hi_compress_static_ws.argtypes = [ctypes.POINTER(HiParams), P, P, P, P, P, u64, P, P, P, P]
+            L.hi_compress_seq.argtypes = [ctypes.POINTER(HiParams), P, P, P, P, P, P, u64, P, P, P, P, sz, P]
+            L.hi_compress_seq_fused.argtypes = [ctypes.POINTER(HiParams), P, P]
+            L.hi_compress_seq_fused.restype = ctypes.c_int
             BF, BP = ctypes.POINTER(HiBatchField), ctypes.POINTER(HiBatchPlan)
             L.hi_batch_query.argtypes = [ctypes.c_uint32, BF, ctypes.POINTER(sz)]
             L.hi_batch_prepare.argtypes = [ctypes.c_uint32, BF, ctypes.c_uint32, P, sz, BP, P]
@@ -285,6 +288,23 @@ def compress_into(x, b: Buffers, stream=None):
                            _ptr(b.out_val), b.out_cap, _ptr(b.hist), _ptr(b.recon), _ptr(b.header), _ptr(b.ws),
                            b.ws.numel(), _stream(stream))
     _check(rc, "hi_compress")
+
+
+def compress_seq_into(x, b: Buffers, seq, stream=None):
+    """Enqueue hi_compress_seq of ``x`` into ``b`` and the reordered codes
+    (Sec. 5.2.2, Eq. 3) into ``seq`` (n_points uint8 device bytes; no sync)."""
+    if not x.is_cuda or x.dtype != torch.float32 or not x.is_contiguous():
+        raise ValueError("x must be a contiguous float32 CUDA tensor")
+    rc = lib().hi_compress_seq(ctypes.byref(b.params), _ptr(x), _ptr(b.codes), _ptr(seq), _ptr(b.anchors),
+                               _ptr(b.out_idx), _ptr(b.out_val), b.out_cap, _ptr(b.hist), _ptr(b.recon),
+                               _ptr(b.header), _ptr(b.ws), b.ws.numel(), _stream(stream))
+    _check(rc, "hi_compress_seq")
+
+
+def compress_seq_fused(p, codes_ptr, seq_ptr):
+    """Whether hi_compress_seq with these parameters and buffer addresses
+    writes the sequence from the predict-quantize kernel (host only)."""
+    return bool(lib().hi_compress_seq_fused(ctypes.byref(p), ctypes.c_void_p(codes_ptr), ctypes.c_void_p(seq_ptr)))
 
 
 def compress_static_ws_into(x, b: Buffers, stream=None):

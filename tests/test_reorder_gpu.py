@@ -130,3 +130,49 @@ def test_rejects_overlap_and_bad_args(hi):
     q.anchor_stride = 12
     with pytest.raises(RuntimeError):
         hi.reorder_codes(buf[:512], q, out=buf[512:])
+
+
+SEQ_CASES = [((64, 64, 64), 16, True), ((32, 48, 64), 16, True), ((24, 40, 32), 8, True), ((1, 64, 128), 16, True),
+             ((1, 1, 4096), 16, True), ((37, 45, 70), 16, False), ((16, 16, 48), 16, False), ((33, 20, 48), 16, False),
+             ((9, 9, 9), 8, False)]
+
+
+@pytest.mark.parametrize("shape,A,fused", SEQ_CASES)
+def test_compress_seq_matches_oracle(hi, oracle_mod, shape, A, fused):
+    """hi_compress_seq: the same record as hi_compress, and the oracle's
+    reordering of its codes in d_seq, whether the predict-quantize kernel
+    writes the sequence itself (fused) or a reordering pass follows it."""
+    x = torch.from_numpy(fields.lognormal_grf(shape, seed=sum(shape) + A)).cuda()
+    p = hi.make_params(shape, 1e-3, "rel", A, autotune=True)
+    a = hi.alloc(p, shape, "cuda", out_cap=x.numel(), hist=True, recon=True)
+    b = hi.alloc(p, shape, "cuda", out_cap=x.numel(), hist=True, recon=True)
+    seq = torch.full((x.numel(),), 7, dtype=torch.uint8, device="cuda")
+    assert hi.compress_seq_fused(p, b.codes.data_ptr(), seq.data_ptr()) == fused
+    hi.compress_into(x, a)
+    hi.compress_seq_into(x, b, seq)
+    torch.cuda.synchronize()
+    assert torch.equal(a.codes, b.codes) and torch.equal(a.hist, b.hist)
+    assert torch.equal(a.recon.view(torch.int32), b.recon.view(torch.int32))
+    assert bytes(hi.read_header(a.header)) == bytes(hi.read_header(b.header))
+    codes = b.codes.cpu().numpy().reshape(shape)
+    assert np.array_equal(seq.cpu().numpy(), oracle_mod.reorder_codes(codes, A))
+
+
+def test_compress_seq_full_size(hi):
+    """The benchmark field (512^3, A = 16), fused: d_seq equals the separate
+    reordering of the kernel's own codes (whose permutation the full-size
+    test above checks), with outliers and a capacity re-run in between."""
+    shape = (512, 512, 512)
+    x = torch.from_numpy(fields.lognormal_grf(shape, seed=1)).cuda()
+    p = hi.make_params(shape, 1e-4, "rel", 16, autotune=True)
+    b = hi.alloc(p, shape, "cuda", out_cap=1 << 16, hist=True, recon=False)
+    seq = torch.empty(x.numel(), dtype=torch.uint8, device="cuda")
+    assert hi.compress_seq_fused(p, b.codes.data_ptr(), seq.data_ptr())
+    hi.compress_seq_into(x, b, seq)
+    torch.cuda.synchronize()
+    h = hi.read_header(b.header)
+    assert h.status == hi.HI_ECAPACITY  # the codes (and the sequence) stay valid
+    ref = hi.reorder_codes(b.codes, p)
+    torch.cuda.synchronize()
+    assert torch.equal(seq, ref)
+    assert int((seq == 0).sum()) == int(h.n_outliers)
