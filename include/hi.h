@@ -356,14 +356,13 @@ HI_API hi_status hi_unreorder_codes(const hi_params* p, const uint8_t* d_seq, ui
  * overlapping d_codes), the input of the lossless pipelines below.  All
  * other arguments and results are those of hi_compress, and d_codes is
  * written as there.  Where the field allows it the predict-quantize kernel
- * stores each tile row's codes to their places in d_seq from the registers
- * that hold them, one aligned store per run of a level, instead of a
- * separate pass over the code array: A = 8 or 16, n2 a multiple of A and of
- * the vector width (16 codes for A = 16, 8 for A = 8), d_codes and d_seq
- * 16-byte aligned, fewer than 2^32 points, and every run starting at a
- * multiple of its length (true when each dim is a multiple of 2A, e.g.
- * 512^3 at A = 16).  Otherwise hi_reorder_codes runs after the kernel on
- * the same stream.  HI_EINVAL for a NULL d_seq or overlapping code arrays.
+ * stores each tile's codes to their places in d_seq from shared memory,
+ * one aligned store per run of consecutive places, instead of a separate
+ * pass over the code array: A = 8 or 16, n2 a multiple of A, d_seq 16-byte
+ * aligned, fewer than 2^32 points, and every run starting at a multiple of
+ * its length (true when each dim is a multiple of 2A, e.g. 512^3 at
+ * A = 16).  Otherwise hi_reorder_codes runs after the kernel on the same
+ * stream.  HI_EINVAL for a NULL d_seq or overlapping code arrays.
  * hi_compress_seq_fused: 1 when a call with these parameters and pointers
  * takes the single-kernel form, else 0 (host only, no GPU work). */
 HI_API hi_status hi_compress_seq(const hi_params* p, const float* d_x, uint8_t* d_codes, uint8_t* d_seq,

@@ -402,15 +402,14 @@ static hi_status enqueue_tune(const Geometry& G, const float* d_x, hi_header* d_
 }
 
 // Whether the predict-quantize kernel can write the reordered sequence from
-// its code registers: A = 8 or 16, every tile row whole (n2 a multiple of A)
-// and stored as vectors, the sequence 16-byte aligned with fewer than 2^32
-// places, and every run of a tile row (A >> l codes on level l, half of
-// them for the odd columns of a row of even subgrid coordinates) starting
-// at a multiple of its length: the terms of its place are multiples of
-// A >> l.
-static bool seq_fusable(const Geometry& G, const ReorderGeo& R, int flags, const uint8_t* d_seq)
+// its staged codes: A = 8 or 16, every tile row whole (n2 a multiple of A),
+// the sequence 16-byte aligned with fewer than 2^32 places, and every run
+// of a tile row (A >> l codes on level l, half of them for the odd columns
+// of a row of even subgrid coordinates) starting at a multiple of its
+// length: the terms of its place are multiples of A >> l.
+static bool seq_fusable(const Geometry& G, const ReorderGeo& R, const uint8_t* d_seq)
 {
-    if ((G.A != 8 && G.A != 16) || !(flags & kFlagVecCodes) || G.g.n[2] % G.A != 0) return false;
+    if ((G.A != 8 && G.A != 16) || G.g.n[2] % G.A != 0) return false;
     if (!aligned(d_seq, 16) || G.g.N >= (int64_t(1) << 32)) return false;
     for (int l = 0; l < G.L; ++l) {
         const uint64_t c = (uint64_t)(G.A >> l);
@@ -498,7 +497,7 @@ static hi_status compress_impl(const hi_params* p, const float* d_x, uint8_t* d_
     ReorderGeo R{};
     if (d_seq) {
         R = make_reorder_geo(G.g.n, G.L);
-        if (seq_fusable(G, R, c.flags, d_seq)) {
+        if (seq_fusable(G, R, d_seq)) {
             c.seq = d_seq;
             for (int l = 0; l <= G.L; ++l) {
                 c.sg.D1[l] = R.D1[l], c.sg.D2[l] = R.D2[l];
@@ -534,10 +533,8 @@ hi_status hi_compress_seq(const hi_params* p, const float* d_x, uint8_t* d_codes
 int hi_compress_seq_fused(const hi_params* p, const uint8_t* d_codes, const uint8_t* d_seq)
 {
     Geometry G;
-    if (!p || make_geometry(p, &G) != HI_OK) return 0;
-    const int ch = G.A >= 16 ? 16 : 8;
-    const int flags = (G.g.n[2] % ch == 0 && aligned(d_codes, 16)) ? kFlagVecCodes : 0;
-    return seq_fusable(G, make_reorder_geo(G.g.n, G.L), flags, d_seq) ? 1 : 0;
+    if (!p || !d_codes || make_geometry(p, &G) != HI_OK) return 0;
+    return seq_fusable(G, make_reorder_geo(G.g.n, G.L), d_seq) ? 1 : 0;
 }
 
 hi_status hi_compress_static_ws(const hi_params* p, const float* d_x, uint8_t* d_codes, float* d_anchors,

@@ -18,7 +18,8 @@ namespace hi {
 // log2 A the one left is an anchor.  A place is prefix[l] (the coarser
 // points) + the row-major rank on the subgrid - the all-even points before
 // it.  Callers take this path only where every run starts at a multiple of
-// its length, so each run is one aligned store.
+// its length, so each run is one aligned store.  (seq_store_tile below runs
+// it for the rows of tiles that are not whole.)
 template <int N>
 __device__ __forceinline__ void seq_store_run(uint8_t* p, uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3)
 {
@@ -75,12 +76,98 @@ __device__ __forceinline__ void seq_store_row(uint8_t* __restrict__ seq, const S
     seq_store_level<A, 0>(seq, sg, x, y, z0, w[0], w[1], A == 16 ? w[2] : 0u, A == 16 ? w[3] : 0u);
 }
 
+// The codes of columns k 2^l of a row (ODD: odd k only), packed 4 to a word.
+template <int A, int l, bool ODD>
+__device__ __forceinline__ void seq_gather(const uint32_t* w, uint32_t* o)
+{
+    constexpr int M = A >> l, K = ODD ? M / 2 : M;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) o[j] = 0u;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int byte = (ODD ? 2 * j + 1 : j) << l;
+        o[j >> 2] |= ((w[byte >> 2] >> (8 * (byte & 3))) & 0xffu) << (8 * (j & 3));
+    }
+}
+
+// Level l of a whole tile's sequence store: the rows whose coordinates are
+// multiples of 2^l, the M = A >> l codes of each at columns k 2^l.  Rows
+// with an odd coordinate on this subgrid are one run each and come first,
+// then the all-even rows, whose odd columns are one run (their even ones
+// are level l + 1's rows): each warp issues one kind of store, save at the
+// boundary.
+template <int A, int l>
+__device__ __forceinline__ void seq_level_pass(uint8_t* __restrict__ seq, const SeqGeo& sg, const TileInfo& ti,
+                                               const uint8_t* cs)
+{
+    using Lw = Lay<A>;
+    constexpr int M = A >> l, H = M / 2;
+    constexpr int n_first = H * M, n_odd = M * M - H * H;
+    const uint32_t zs = (uint32_t)ti.o[2] >> l;
+    for (int r = threadIdx.x; r < M * M; r += blockDim.x) {
+        int a, b;
+        if (r < n_first) {  // odd a, any b
+            a = 2 * (r / M) + 1, b = r - (r / M) * M;
+        } else {
+            const int j = r - (r < n_odd ? n_first : n_odd);
+            a = 2 * (j / H), b = 2 * (j - (j / H) * H) + (r < n_odd ? 1 : 0);
+        }
+        const int c0 = a << l, c1 = b << l;
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(cs + c0 * Lw::CYC + c1 * Lw::CXC);
+        uint32_t w[A / 4];
+#pragma unroll
+        for (int j = 0; j < A / 4; ++j) w[j] = src[j];
+        const uint32_t xs = ((uint32_t)ti.o[0] + c0) >> l, ys = ((uint32_t)ti.o[1] + c1) >> l;
+        uint32_t base = sg.prefix[l] + (xs * sg.D1[l] + ys) * sg.D2[l] - ((xs + 1u) >> 1) * sg.H12[l];
+        if ((xs & 1u) == 0) base -= ((ys + 1u) >> 1) * sg.H2[l];
+        uint32_t o[4];
+        if (r < n_odd) {
+            seq_gather<A, l, false>(w, o);
+            seq_store_run<M>(seq + base + zs, o[0], o[1], o[2], o[3]);
+        } else {
+            seq_gather<A, l, true>(w, o);
+            seq_store_run<H>(seq + base + (zs >> 1), o[0], o[1], o[2], o[3]);
+        }
+    }
+}
+
+// A tile's owned codes (staged in cs) to their places in the sequence.
+// Whole tiles (own0 = own1 = A) level by level; the others row by row.
+template <int A>
+__device__ __forceinline__ void seq_store_tile(uint8_t* __restrict__ seq, const SeqGeo& sg, const TileInfo& ti,
+                                               const uint8_t* cs, int own0, int own1)
+{
+    using Lw = Lay<A>;
+    constexpr int L = (A == 16) ? 4 : 3;
+    if (own0 == A && own1 == A) {
+        seq_level_pass<A, 0>(seq, sg, ti, cs);
+        seq_level_pass<A, 1>(seq, sg, ti, cs);
+        seq_level_pass<A, 2>(seq, sg, ti, cs);
+        if constexpr (L == 4) seq_level_pass<A, 3>(seq, sg, ti, cs);
+        if (threadIdx.x == 0) {  // the anchor row's one code on level log2 A
+            const uint32_t xs = (uint32_t)ti.o[0] >> L, ys = (uint32_t)ti.o[1] >> L, zs = (uint32_t)ti.o[2] >> L;
+            seq[(xs * sg.D1[L] + ys) * sg.D2[L] + zs] = cs[0];
+        }
+    } else {
+        for (int r = threadIdx.x; r < own0 * own1; r += blockDim.x) {
+            const int c0 = r / own1, c1 = r - (r / own1) * own1;
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(cs + c0 * Lw::CYC + c1 * Lw::CXC);
+            uint32_t w[A / 4];
+#pragma unroll
+            for (int j = 0; j < A / 4; ++j) w[j] = src[j];
+            seq_store_row<A>(seq, sg, (uint32_t)(ti.o[0] + c0), (uint32_t)(ti.o[1] + c1), (uint32_t)ti.o[2], w);
+        }
+    }
+}
+
 // The tile's floats are in v (reconstructed in place), its codes are staged
 // in cs; g, ti: the field and the tile; s_sel / s_lv: the level
 // configuration; full_ok: the field may take the compile-time full-tile
 // passes; out: a CompressOut or a reference to one in shared memory.  With
-// SEQ the owned codes also go to the reordered sequence seq (constants sg);
-// the caller takes SEQ only where every tile row is stored as vectors.
+// SEQ the owned codes also go to the reordered sequence seq (constants sg),
+// from cs after the epilogue; the caller takes SEQ only where every tile row
+// is whole (n2 a multiple of A) and every run starts at a multiple of its
+// length.
 template <int A, bool SEQ = false, class Out>
 __device__ __forceinline__ void compress_tile(const FieldGeo& g, const TileInfo& ti, float* v, uint8_t* cs,
                                               uint16_t* hc, uint32_t* s_hist, const int* s_sel,
@@ -139,9 +226,6 @@ __device__ __forceinline__ void compress_tile(const FieldGeo& g, const TileInfo&
                     *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
                 else
                     *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
-                if constexpr (SEQ)
-                    seq_store_row<A>(seq, *sg, (uint32_t)(ti.o[0] + c0), (uint32_t)(ti.o[1] + c1), (uint32_t)ti.o[2],
-                                     w);
             }
             if (__any_sync(0xffffffffu, act && z != 0)) {
                 uint32_t zm[CH];  // 0x80 in each byte that is zero (exact, no borrow between bytes)
@@ -262,6 +346,7 @@ __device__ __forceinline__ void compress_tile(const FieldGeo& g, const TileInfo&
     if constexpr (kHot) {
         if (hist_on) hist_hot_flush(hacc, s_hist);
     }
+    if constexpr (SEQ) seq_store_tile<A>(seq, *sg, ti, cs, own0, own1);
     if (recon_g && vec_codes) {
         const int items = rows * own2;
         for (int i = tid; i < items; i += blockDim.x) {

@@ -107,8 +107,8 @@ def test_lossless_query_without_gpu(lib):
 def test_compress_seq_fused_decision(lib):
     """hi_compress_seq writes the reordered codes from the predict-quantize
     kernel only where every run of a tile row starts at a multiple of its
-    length (A = 8 or 16, n2 a multiple of A and of the vector width, 16-byte
-    aligned code arrays); elsewhere it reorders after the kernel."""
+    length (A = 8 or 16, n2 a multiple of A, a 16-byte aligned sequence);
+    elsewhere it reorders after the kernel."""
     a, b = 0x100000, 0x900000  # addresses only: nothing is dereferenced
     fused = [((512, 512, 512), 16), ((64, 64, 64), 16), ((32, 48, 64), 16), ((24, 40, 32), 8), ((384, 384, 384), 16),
              ((1, 64, 128), 16), ((1, 1, 4096), 16)]
@@ -118,6 +118,6 @@ def test_compress_seq_fused_decision(lib):
         p = lib.make_params(shape, 1e-3, "rel", A)
         assert lib.compress_seq_fused(p, a, b), (shape, A)
         assert not lib.compress_seq_fused(p, a, b + 8), (shape, A)  # sequence off a 16-byte boundary
-        assert not lib.compress_seq_fused(p, a + 4, b), (shape, A)  # codes not stored as vectors
+        assert lib.compress_seq_fused(p, a + 4, b), (shape, A)  # the codes' own alignment does not matter
     for shape, A in separate:
         assert not lib.compress_seq_fused(lib.make_params(shape, 1e-3, "rel", A), a, b), (shape, A)

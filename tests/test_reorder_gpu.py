@@ -133,6 +133,7 @@ def test_rejects_overlap_and_bad_args(hi):
 
 
 SEQ_CASES = [((64, 64, 64), 16, True), ((32, 48, 64), 16, True), ((24, 40, 32), 8, True), ((1, 64, 128), 16, True),
+             ((40, 48, 64), 16, True), ((33, 48, 64), 16, True), ((17, 9, 32), 8, True),
              ((1, 1, 4096), 16, True), ((37, 45, 70), 16, False), ((16, 16, 48), 16, False), ((33, 20, 48), 16, False),
              ((9, 9, 9), 8, False)]
 
