@@ -592,30 +592,30 @@ def run_gpu(args):
         serial_ms = e0.elapsed_time(e1) / ke
         assert torch.equal(y_h.to(dev), out)
 
-        # the same steps with two fields in flight: a field's upload and compression on one stream while
-        # the previous field's record goes to the host and back, is reconstructed and comes back on a
-        # second (uploads and downloads share the link in opposite directions); the host still reads
-        # each record's header before copying its outliers
-        s_c, s_d = torch.cuda.Stream(), torch.cuda.Stream()
-        xds = [xd, torch.empty_like(x)]
-        bbs = [b, hi.alloc(p, SHAPE, dev, out_cap=b.out_cap, hist=True, recon=False)]
-        outs = [out, torch.empty_like(out)]
-        hdr_hs = [hdr_h, torch.empty(hi.HEADER_BYTES, dtype=torch.uint8).pin_memory()]
-        y_hs = [y_h, torch.empty(SHAPE, dtype=torch.float32).pin_memory()]
-        ev_hdr = [torch.cuda.Event(), torch.cuda.Event()]
-        ev_free = [torch.cuda.Event(), torch.cuda.Event()]
+        # the same steps with two fields in flight on three streams: a field's upload and compression;
+        # the previous field's record to the host and back and its reconstruction; the download of the
+        # reconstructed field (uploads and downloads share the link in opposite directions); the host
+        # still reads each record's header before copying its outliers
+        s_c, s_d, s_y = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+        D = 2  # steps in flight (three measured the same)
+        xds = [xd] + [torch.empty_like(x) for _ in range(D - 1)]
+        bbs = [b] + [hi.alloc(p, SHAPE, dev, out_cap=b.out_cap, hist=True, recon=False) for _ in range(D - 1)]
+        outs = [out] + [torch.empty_like(out) for _ in range(D - 1)]
+        hdr_hs = [hdr_h] + [torch.empty(hi.HEADER_BYTES, dtype=torch.uint8).pin_memory() for _ in range(D - 1)]
+        y_hs = [y_h] + [torch.empty(SHAPE, dtype=torch.float32).pin_memory() for _ in range(D - 1)]
+        ev_hdr, ev_free, ev_dec, ev_yfree = ([torch.cuda.Event() for _ in range(D)] for _ in range(4))
 
         def front(k):
-            i = k % 2
+            i = k % D
             with torch.cuda.stream(s_c):
-                s_c.wait_event(ev_free[i])  # the record of two steps back has left these buffers
+                s_c.wait_event(ev_free[i])  # the record of D steps back has left these buffers
                 xds[i].copy_(xh, non_blocking=True)
                 hi.compress_into(xds[i], bbs[i], stream=s_c)
                 hdr_hs[i].copy_(bbs[i].header, non_blocking=True)
                 ev_hdr[i].record(s_c)
 
         def back(k):
-            i = k % 2
+            i = k % D
             ev_hdr[i].synchronize()
             kk = min(int(hi.HiHeader.from_buffer_copy(hdr_hs[i].numpy().tobytes()).n_outliers), bbs[i].out_cap)
             bb = bbs[i]
@@ -633,33 +633,41 @@ def run_gpu(args):
                 if kk:
                     b2.out_idx[:kk].copy_(oidx_h[:kk], non_blocking=True)
                     b2.out_val[:kk].copy_(oval_h[:kk], non_blocking=True)
+                s_d.wait_event(ev_yfree[i])  # the field of D steps back has left outs[i]
                 hi.decompress_into(b2, outs[i], status, stream=s_d)
+                ev_dec[i].record(s_d)
+            with torch.cuda.stream(s_y):
+                s_y.wait_event(ev_dec[i])
                 y_hs[i].copy_(outs[i], non_blocking=True)
+                ev_yfree[i].record(s_y)
             return kk
 
         def pipelined(nsteps, ev_a=None, ev_b=None):
             if ev_a is not None:
                 ev_a.record(s_c)
                 s_d.wait_event(ev_a)
+                s_y.wait_event(ev_a)
             kl = []
-            front(0)
-            for k in range(1, nsteps):
+            for k in range(min(D - 1, nsteps)):
                 front(k)
-                kl.append(back(k - 1))
-            kl.append(back(nsteps - 1))
+            for k in range(D - 1, nsteps):
+                front(k)
+                kl.append(back(k - D + 1))
+            for k in range(max(0, nsteps - D + 1), nsteps):
+                kl.append(back(k))
             if ev_b is not None:
-                ev_b.record(s_d)  # after the last step's download, which waited for its upload
+                ev_b.record(s_y)  # after the last step's download, which waited for all its other work
             return kl
 
         torch.cuda.synchronize()
-        pipelined(2)
+        pipelined(D)
         torch.cuda.synchronize()
         p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ks = pipelined(ke, p0, p1)
         torch.cuda.synchronize()
         ems = p0.elapsed_time(p1) / ke
         assert int(status.item()) == 0
-        assert torch.equal(y_hs[(ke - 1) % 2].to(dev), outs[(ke - 1) % 2])
+        assert torch.equal(y_hs[(ke - 1) % D].to(dev), outs[(ke - 1) % D])
         kmean = sum(ks) / len(ks)
         h2d = 4 * N + (N + 4 * b.anchors.numel() + hi.HEADER_BYTES + 8 * kmean)
         d2h = (N + 4 * b.anchors.numel() + hi.HEADER_BYTES + 8 * kmean) + hi.HEADER_BYTES + 4 * N
@@ -667,11 +675,38 @@ def run_gpu(args):
             tt = torch.tensor([ems, serial_ms], device=dev)
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             ems, serial_ms = float(tt[0].item()), float(tt[1].item())
-        e2e = dict(value=ws * bytes_in / (ems * 1e-3) / 1e9, unit="GB/s", ms_per_step=ems,
+        # the link alone, same pinned buffers: the field up, the field down, and both at once on two
+        # streams (10 repetitions each, median); the step's copies cannot beat these
+        def copy_ms(up, down):
+            ts = []
+            for _ in range(10):
+                a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                a.record(s_c)
+                s_d.wait_event(a)
+                if up:
+                    with torch.cuda.stream(s_c):
+                        xds[0].copy_(xh, non_blocking=True)
+                if down:
+                    with torch.cuda.stream(s_d):
+                        y_hs[0].copy_(outs[0], non_blocking=True)
+                s_c.wait_stream(s_d)
+                z.record(s_c)
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(z))
+            return statistics.median(ts)
+        up_ms, down_ms, both_ms = copy_ms(True, False), copy_ms(False, True), copy_ms(True, True)
+        link = dict(h2d_gbs=4 * N / (up_ms * 1e-3) / 1e9, d2h_gbs=4 * N / (down_ms * 1e-3) / 1e9,
+                    both_gbs=8 * N / (both_ms * 1e-3) / 1e9, bytes=4 * N,
+                    step_copy_bound_ms=(h2d + d2h) / (8 * N / (both_ms * 1e-3)) * 1e3,
+                    how="512 MiB pinned host <-> device with cudaMemcpyAsync (torch copy_), up, down, and both "
+                        "at once on two streams; medians of 10")
+        e2e = dict(value=ws * bytes_in / (ems * 1e-3) / 1e9, unit="GB/s", ms_per_step=ems, link=link,
                    h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h),
                    how="per step: the field from pinned host memory, hi_compress, the record to pinned host "
                        "memory (header read on the host first), back to the device, hi_decompress, the field "
-                       "to the host; two steps in flight on two streams",
+                       "to the host; two steps in flight on three streams (upload + compress, record round trip + "
+                       "reconstruct, download)",
                    serial=dict(value=ws * bytes_in / (serial_ms * 1e-3) / 1e9, ms_per_step=serial_ms,
                                how="the same step one at a time on one stream"))
         del b2, xh, codes_h, anch_h, oidx_h, oval_h, hdr_h, y_h, xd, xds, bbs, outs, hdr_hs, y_hs
