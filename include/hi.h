@@ -431,8 +431,11 @@ HI_API hi_status hi_tp_decode(const uint8_t* d_in, uint64_t in_len, uint8_t* d_o
  *   halve every nonzero weight (at least 1) and rebuild; canonical codes;
  *   blocks of 4096 symbols, MSB first, each padded to 32 bits.
  *   stream = u64 n | u32 4096 | u32 nblocks | u64 H | u32 16384 |
- *   u32 nchunks | u8 length[256] | u32 words[nblocks] | (u32 size, u32 m1)
- *   [nchunks] | zero pad to 16 | payloads padded to 16 (size bit 31: raw).
+ *   u32 nchunks | u8 length[256] | u32 words[nblocks] | u16 sub[3 nblocks]
+ *   | zero pad to 4 | (u32 size, u32 m1)[nchunks] | zero pad to 16 |
+ *   payloads padded to 16 (size bit 31: raw); sub[3 b + j - 1] = the bit
+ *   offset in block b of its symbol 1024 j (its bit count when shorter),
+ *   where a decoder may start: four independent streams a block.
  * hi_cr_query: *max_stream_bytes = the largest stream for n input bytes,
  *   *ws_bytes = the workspace both calls need (either pointer may be NULL).
  * hi_cr_encode: d_in (n bytes, 16-byte aligned) -> d_out (16-byte aligned,

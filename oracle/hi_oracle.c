@@ -1407,9 +1407,13 @@ int hi_oracle_tp_decode(const uint8_t* in, int64_t len, uint8_t* out, int64_t n)
  *            chunk whose payload is longer than m is stored raw.
  *   stream   u64 n | u32 4096 | u32 nblocks | u64 H (HF bytes) | u32 16384 |
  *            u32 nchunks | u8 length[256] | u32 words[nblocks] |
+ *            u16 sub[3 nblocks] | zero padding to 4 |
  *            (u32 size, u32 m1)[nchunks] | zero padding to 16 | payloads,
  *            each padded to 16 (size = padded bytes, bit 31 = raw; m1 = the
- *            RRE4 output length, 0 for a raw chunk).
+ *            RRE4 output length, 0 for a raw chunk).  sub[3 b + j - 1]
+ *            (j = 1, 2, 3) is the bit offset in block b of its symbol
+ *            1024 j, or the block's bit count when it has fewer symbols:
+ *            four independent starting points a block for a decoder.
  * ------------------------------------------------------------------------- */
 #define HF_LMAX 16
 #define HF_BLOCK 4096
@@ -1633,7 +1637,9 @@ static int64_t cr_chunk_encode(const uint8_t* c, int64_t m, uint8_t* out, int64_
     return len;
 }
 
-static int64_t cr_header_bytes(int64_t nb, int64_t nc) { return (288 + 4 * nb + 8 * nc + 15) / 16 * 16; }
+#define HF_SUB 1024 /* symbols between the starting points of a block */
+static int64_t cr_tab_off(int64_t nb) { return 288 + 4 * nb + (6 * nb + 3) / 4 * 4; }
+static int64_t cr_header_bytes(int64_t nb, int64_t nc) { return (cr_tab_off(nb) + 8 * nc + 15) / 16 * 16; }
 
 /* Upper bound of the stream size for n input bytes. */
 int64_t hi_oracle_cr_bound(int64_t n)
@@ -1652,6 +1658,7 @@ int hi_oracle_cr_encode(const uint8_t* in, int64_t n, uint8_t* out, int64_t cap,
     int64_t nb, nc, H = 0, b, k, o;
     uint8_t *hf, *buf;
     uint32_t* words;
+    uint16_t* sub;
     if (n < 0 || (n && !in) || !out || !out_len || cap < hi_oracle_cr_bound(n)) return 1;
     memset(freq, 0, sizeof freq);
     for (int64_t i = 0; i < n; ++i) freq[in[i]]++;
@@ -1660,20 +1667,25 @@ int hi_oracle_cr_encode(const uint8_t* in, int64_t n, uint8_t* out, int64_t cap,
     nb = (n + HF_BLOCK - 1) / HF_BLOCK;
     hf = calloc((size_t)(nb * HF_BLOCK * 2 + 16), 1);
     words = calloc((size_t)nb + 1, sizeof(uint32_t));
-    if (!hf || !words) {
+    sub = calloc(3 * (size_t)nb + 2, sizeof(uint16_t));
+    if (!hf || !words || !sub) {
         free(hf);
         free(words);
+        free(sub);
         return 2;
     }
     for (b = 0; b < nb; ++b) { /* Huffman blocks, MSB first, padded to 32 bits */
         const int64_t s0 = b * HF_BLOCK, s1 = s0 + HF_BLOCK < n ? s0 + HF_BLOCK : n;
         int64_t p = 8 * H;
         for (int64_t i = s0; i < s1; ++i) {
+            if (i > s0 && (i - s0) % HF_SUB == 0) sub[3 * b + (i - s0) / HF_SUB - 1] = (uint16_t)(p - 8 * H);
             const int l = len[in[i]];
             for (int t = l - 1; t >= 0; --t, ++p)
                 if ((code[in[i]] >> t) & 1) hf[p / 8] |= (uint8_t)(0x80u >> (p % 8));
         }
         const int64_t bits = p - 8 * H;
+        for (int j = 1; j <= 3; ++j)
+            if (s0 + (int64_t)j * HF_SUB >= s1) sub[3 * b + j - 1] = (uint16_t)bits;
         words[b] = (uint32_t)((bits + 31) / 32);
         H += 4 * (int64_t)words[b];
     }
@@ -1690,6 +1702,7 @@ int hi_oracle_cr_encode(const uint8_t* in, int64_t n, uint8_t* out, int64_t cap,
     }
     memcpy(out + 32, len, 256);
     memcpy(out + 288, words, 4 * (size_t)nb);
+    memcpy(out + 288 + 4 * nb, sub, 6 * (size_t)nb);
     o = cr_header_bytes(nb, nc);
     buf = malloc(2 * CR_CHUNK + 256);
     for (k = 0; k < nc; ++k) {
@@ -1703,17 +1716,19 @@ int hi_oracle_cr_encode(const uint8_t* in, int64_t n, uint8_t* out, int64_t cap,
             free(buf);
             free(hf);
             free(words);
+            free(sub);
             return 1;
         }
         memcpy(out + o, buf, (size_t)l);
         memset(out + o + l, 0, (size_t)(pad - l));
-        memcpy(out + 288 + 4 * nb + 8 * k, &sz, 4);
-        memcpy(out + 288 + 4 * nb + 8 * k + 4, &m1_32, 4);
+        memcpy(out + cr_tab_off(nb) + 8 * k, &sz, 4);
+        memcpy(out + cr_tab_off(nb) + 8 * k + 4, &m1_32, 4);
         o += pad;
     }
     free(buf);
     free(hf);
     free(words);
+    free(sub);
     *out_len = o;
     return 0;
 }
@@ -1763,8 +1778,8 @@ int hi_oracle_cr_decode(const uint8_t* in, int64_t len_in, uint8_t* out, int64_t
     for (k = 0; k < nc && !rc; ++k) { /* LC chunks back to HF bytes */
         uint32_t sz, m1;
         const int64_t m = (k + 1) * CR_CHUNK <= H ? CR_CHUNK : H - k * CR_CHUNK;
-        memcpy(&sz, in + 288 + 4 * nb + 8 * k, 4);
-        memcpy(&m1, in + 288 + 4 * nb + 8 * k + 4, 4);
+        memcpy(&sz, in + cr_tab_off(nb) + 8 * k, 4);
+        memcpy(&m1, in + cr_tab_off(nb) + 8 * k + 4, 4);
         const int64_t pad = sz & ~TP_RAW;
         if (o + pad > len_in) {
             rc = 15;
@@ -1815,6 +1830,14 @@ int hi_oracle_cr_decode(const uint8_t* in, int64_t len_in, uint8_t* out, int64_t
         for (int64_t i = s0; i < s1 && !rc; ++i) {
             uint32_t c = 0;
             int l, found = 0;
+            if (i > s0 && (i - s0) % HF_SUB == 0) { /* a starting point: the table must agree */
+                uint16_t so;
+                memcpy(&so, in + 288 + 4 * nb + 2 * (3 * b + (i - s0) / HF_SUB - 1), 2);
+                if ((int64_t)so != p - 8 * pos) {
+                    rc = 15;
+                    break;
+                }
+            }
             for (l = 1; l <= HF_LMAX && !found; ++l) {
                 if (p >= 8 * (pos + 4 * (int64_t)words)) {
                     rc = 15;
@@ -1829,6 +1852,11 @@ int hi_oracle_cr_decode(const uint8_t* in, int64_t len_in, uint8_t* out, int64_t
                 }
             }
             if (!found && !rc) rc = 15;
+        }
+        for (int j = 1; j <= 3 && !rc; ++j) { /* starting points past the block's end hold its bit count */
+            uint16_t so;
+            memcpy(&so, in + 288 + 4 * nb + 2 * (3 * b + j - 1), 2);
+            if (s0 + (int64_t)j * HF_SUB >= s1 && (int64_t)so != p - 8 * pos) rc = 15;
         }
         pos += 4 * (int64_t)words;
     }

@@ -24,16 +24,21 @@
 //          nonzero bytes of each level below, top down.  A chunk whose
 //          payload would be longer than the chunk is stored raw.
 //   stream u64 n | u32 4096 | u32 nblocks | u64 H | u32 16384 | u32 nchunks
-//          | u8 length[256] | u32 words[nblocks] | (u32 size, u32 m1)
-//          [nchunks] | zero pad to 16 | payloads, each padded to 16 (size =
-//          padded bytes, bit 31 = raw; m1 = RRE4 output bytes, 0 if raw).
+//          | u8 length[256] | u32 words[nblocks] | u16 sub[3 nblocks] | zero
+//          pad to 4 | (u32 size, u32 m1)[nchunks] | zero pad to 16 |
+//          payloads, each padded to 16 (size = padded bytes, bit 31 = raw;
+//          m1 = RRE4 output bytes, 0 if raw); sub[3 b + j - 1] = the bit
+//          offset in block b of its symbol 1024 j, or its bit count when
+//          the block is shorter.
 // Encoding: a histogram pass; the code book in one CTA; a warp per HF block
 // counting its bits, a scan of the block sizes, a warp per block packing its
 // codes (shared-memory words, OR-ed at the lanes' seams); a CTA per 16 KiB
 // chunk running RRE4 / TCMS8 / RZE1 in shared memory into a scratch slot; a
 // scan of the payload sizes; a gather.  Decoding: a scan of both tables, a
 // CTA per chunk expanding the levels (kept byte of rank popcount(bitmap
-// [0..i])), a thread per HF block decoding its bits through a 10-bit table.
+// [0..i])), a thread per quarter of an HF block decoding its 1024 symbols
+// from the block's starting point through a 12-bit table (longer codes by
+// comparison), checked to end at the next starting point.
 #include <algorithm>
 
 #include "hi_internal.h"
@@ -48,14 +53,18 @@ constexpr uint32_t kCrChunk = 16384;
 constexpr uint32_t kCrRaw = 0x80000000u;
 constexpr int kCrThreads = 256;
 constexpr uint32_t kCrHdr = 288;  // fixed header + length table
+constexpr uint32_t kHfSub = 1024;  // symbols between a block's starting points
 
 __host__ __device__ inline uint64_t cr_nblocks(uint64_t n) { return (n + kHfBlock - 1) / kHfBlock; }
 // HF bytes at most: 16 bits a symbol, plus a padding word a block
 __host__ __device__ inline uint64_t cr_hmax(uint64_t n) { return 2 * n + 4 * cr_nblocks(n); }
 __host__ __device__ inline uint64_t cr_ncmax(uint64_t n) { return (cr_hmax(n) + kCrChunk - 1) / kCrChunk; }
+// The chunk table follows the word table and the starting points (3 u16 a
+// block, padded to 4 bytes).
+__host__ __device__ inline uint64_t cr_tab_off(uint64_t nb) { return kCrHdr + 4 * nb + (6 * nb + 3) / 4 * 4; }
 __host__ __device__ inline uint64_t cr_header_bytes(uint64_t nb, uint64_t nc)
 {
-    return (kCrHdr + 4 * nb + 8 * nc + 15) / 16 * 16;
+    return (cr_tab_off(nb) + 8 * nc + 15) / 16 * 16;
 }
 
 // Workspace layout (byte offsets, 16-byte aligned).
@@ -387,10 +396,12 @@ __global__ void __launch_bounds__(32 * kBookWarps) k_cr_codebook(const uint32_t*
 }
 
 // Bits of each HF block (a warp per block): words[b] = ceil(bits / 32), also
-// written to the stream's table.
+// written to the stream's table, and the block's starting points: the bit
+// offsets of its symbols 1024, 2048, 3072 (the bit count where the block is
+// shorter), from the bits of its four quarters.
 __global__ void __launch_bounds__(256) k_hf_count(const uint8_t* __restrict__ in, uint64_t n,
                                                   const uint8_t* __restrict__ len_g, uint32_t* __restrict__ words,
-                                                  uint32_t* __restrict__ tab)
+                                                  uint32_t* __restrict__ tab, uint16_t* __restrict__ sub_tab)
 {
     __shared__ uint8_t len[256];
     len[threadIdx.x] = len_g[threadIdx.x];
@@ -401,25 +412,41 @@ __global__ void __launch_bounds__(256) k_hf_count(const uint8_t* __restrict__ in
     for (uint64_t b = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < nb; b += warps) {
         const uint64_t s0 = b * kHfBlock;
         const uint32_t cnt = (uint32_t)min((uint64_t)kHfBlock, n - s0);
-        uint32_t bits = 0;
+        uint32_t qb[4] = {0u, 0u, 0u, 0u};  // bits of each quarter
         if (cnt == kHfBlock) {
+            static_assert(kHfBlock == 4 * kHfSub && kHfSub == 16 * 64, "16-symbol vectors, 64 a quarter");
             const uint4* p = reinterpret_cast<const uint4*>(in + s0);
-            for (uint32_t i = lane; i < kHfBlock / 16; i += 32) {
-                const uint4 q = __ldg(p + i);
+#pragma unroll
+            for (uint32_t k = 0; k < kHfBlock / 16 / 32; ++k) {  // vector lane + 32 k is in quarter k / 2
+                const uint4 q = __ldg(p + lane + 32 * k);
                 const uint32_t wv[4] = {q.x, q.y, q.z, q.w};
+                uint32_t s = 0;
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) bits += len[(wv[j] >> (8 * k)) & 0xffu];
+                    for (int e = 0; e < 4; ++e) s += len[(wv[j] >> (8 * e)) & 0xffu];
+                qb[k >> 1] += s;
             }
         } else {
-            for (uint32_t i = lane; i < cnt; i += 32) bits += len[in[s0 + i]];
+            for (uint32_t i = lane; i < cnt; i += 32) {
+                const uint32_t l = len[in[s0 + i]], qi = i / kHfSub;
+                qb[0] += qi == 0 ? l : 0u;
+                qb[1] += qi == 1 ? l : 0u;
+                qb[2] += qi == 2 ? l : 0u;
+                qb[3] += qi == 3 ? l : 0u;
+            }
         }
-        bits = __reduce_add_sync(0xffffffffu, bits);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) qb[j] = __reduce_add_sync(0xffffffffu, qb[j]);
         if (lane == 0) {
+            const uint32_t bits = qb[0] + qb[1] + qb[2] + qb[3];
             const uint32_t wd = (bits + 31) / 32;
             words[b] = wd;
             tab[b] = wd;
+            sub_tab[3 * b] = (uint16_t)qb[0];
+            sub_tab[3 * b + 1] = (uint16_t)(qb[0] + qb[1]);
+            sub_tab[3 * b + 2] = (uint16_t)(qb[0] + qb[1] + qb[2]);
+            if (b == nb - 1 && (nb & 1)) sub_tab[3 * nb] = 0;  // the padding to 4 bytes
         }
     }
 }
@@ -751,12 +778,12 @@ __global__ void __launch_bounds__(1024) k_cr_scan_payloads(const uint32_t* __res
     const uint64_t hb = cr_header_bytes(nb, nc);
     uint64_t tot = 0;
     cta_scan_u32(psize, nullptr, poff, nc, hb, &tot, 1);
-    uint32_t* tab = reinterpret_cast<uint32_t*>(out + kCrHdr + 4 * nb);
+    uint32_t* tab = reinterpret_cast<uint32_t*>(out + cr_tab_off(nb));
     for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) {
         tab[2 * i] = psize[i];
         tab[2 * i + 1] = pm1[i];
     }
-    for (uint64_t i = kCrHdr + 4 * nb + 8 * (uint64_t)nc + threadIdx.x; i < hb; i += blockDim.x) out[i] = 0;
+    for (uint64_t i = cr_tab_off(nb) + 8 * (uint64_t)nc + threadIdx.x; i < hb; i += blockDim.x) out[i] = 0;
     if (threadIdx.x == 0) *len = tot;
 }
 
@@ -808,7 +835,7 @@ __global__ void __launch_bounds__(1024) k_cr_dec_scan(const uint8_t* __restrict_
     uint64_t wt = 0, pt = 0;
     cta_scan_u32(i32 + kCrHdr / 4, woff, nullptr, nb, 0, &wt, 1);
     // payload offsets: the sizes are every other word of the chunk table
-    const uint32_t* tab = reinterpret_cast<const uint32_t*>(in + kCrHdr + 4 * nb);
+    const uint32_t* tab = reinterpret_cast<const uint32_t*>(in + cr_tab_off(nb));
     {
         __shared__ uint64_t s_part[32];
         __shared__ uint64_t s_end;
@@ -905,7 +932,7 @@ __global__ void __launch_bounds__(kCrThreads) k_cr_lc_decode(const uint8_t* __re
     const uint64_t H = hdr_ws[0];
     const uint32_t nc = reinterpret_cast<const uint32_t*>(hdr_ws)[2];
     const uint64_t nb = cr_nblocks(n);
-    const uint32_t* tab = reinterpret_cast<const uint32_t*>(in + kCrHdr + 4 * nb);
+    const uint32_t* tab = reinterpret_cast<const uint32_t*>(in + cr_tab_off(nb));
     for (uint32_t k = blockIdx.x; k < nc; k += gridDim.x) {
         const uint32_t m = (uint32_t)min((uint64_t)kCrChunk, H - (uint64_t)k * kCrChunk);
         const uint32_t sz = tab[2 * k], m1 = tab[2 * k + 1];
@@ -1002,7 +1029,7 @@ __global__ void __launch_bounds__(kCrThreads) k_cr_lc_decode(const uint8_t* __re
 // (canonical codes of one length are consecutive), branch-free.  The next
 // stream word is loaded one refill ahead (its latency hides behind a dozen
 // symbols) and the output leaves in 16-byte stores.
-constexpr int kHfDecThreads = 64;
+constexpr int kHfDecThreads = 256;
 __global__ void __launch_bounds__(kHfDecThreads) k_hf_decode(const uint8_t* __restrict__ in,
                                                              const uint8_t* __restrict__ hf,
                                                              const uint32_t* __restrict__ woff, uint64_t n,
@@ -1049,20 +1076,31 @@ __global__ void __launch_bounds__(kHfDecThreads) k_hf_decode(const uint8_t* __re
     const uint32_t lim13 = lim[13], lim14 = lim[14], lim15 = lim[15], lim16 = lim[16];
     const uint64_t nb = cr_nblocks(n);
     const uint32_t* words = reinterpret_cast<const uint32_t*>(in + kCrHdr);
-    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + t; b < nb; b += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t nw = words[b];
-        const uint32_t* src = reinterpret_cast<const uint32_t*>(hf) + woff[b];
+    const uint16_t* subs = reinterpret_cast<const uint16_t*>(in + kCrHdr + 4 * nb);
+    // a thread per quarter of a block: from its starting point in the table,
+    // its (up to) 1024 symbols; it must end where the next starting point is
+    for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + t; u < 4 * nb; u += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t b = u >> 2;
+        const uint32_t j = (uint32_t)(u & 3u);
         const uint64_t s0 = b * kHfBlock;
-        const uint32_t cntb = (uint32_t)min((uint64_t)kHfBlock, n - s0);
+        const uint32_t cnt_blk = (uint32_t)min((uint64_t)kHfBlock, n - s0);
+        const uint32_t i0 = j * kHfSub;
+        if (i0 >= cnt_blk) continue;
+        const uint32_t cntb = min(kHfSub, cnt_blk - i0);
+        const uint64_t base = s0 + i0;
+        const uint32_t nw = words[b];
+        const uint32_t start = j ? subs[3 * b + j - 1] : 0u;
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(hf) + woff[b];
         auto word = [&](uint32_t k) -> uint32_t { return k < nw ? __byte_perm(__ldg(src + k), 0u, 0x0123) : 0u; };
-        uint64_t buf = (uint64_t)word(0) << 32;  // upcoming bits, MSB first
-        uint32_t have = 32;
+        const uint32_t k0 = start >> 5, sh = start & 31u;
+        uint64_t buf = (((uint64_t)word(k0) << 32) | word(k0 + 1)) << sh;  // upcoming bits, MSB first
+        uint32_t have = 64 - sh;
         // the next three words, loaded three refills (some 40 symbols) before they are needed
-        uint32_t pre0 = word(1), pre1 = word(2), pre2 = word(3);
-        uint32_t wi = 4;  // next word to load
-        bool bad = false;
+        uint32_t pre0 = word(k0 + 2), pre1 = word(k0 + 3), pre2 = word(k0 + 4);
+        uint32_t wi = k0 + 5;  // next word to load
+        bool bad = start > 32u * nw;
         uint32_t o0 = 0, o1 = 0, o2 = 0, cur = 0;
-        for (uint32_t i = 0; i < cntb; ++i) {
+        for (uint32_t i = 0; i < cntb && !bad; ++i) {
             if (have <= 32) {
                 buf |= (uint64_t)pre0 << (32 - have);
                 have += 32;
@@ -1092,7 +1130,7 @@ __global__ void __launch_bounds__(kHfDecThreads) k_hf_decode(const uint8_t* __re
             cur |= sym << (8 * (i & 3));
             if ((i & 3) == 3) {
                 if ((i & 15) == 15) {
-                    *reinterpret_cast<uint4*>(out + s0 + i - 15) = make_uint4(o0, o1, o2, cur);
+                    *reinterpret_cast<uint4*>(out + base + i - 15) = make_uint4(o0, o1, o2, cur);
                 } else {
                     o0 = o1;
                     o1 = o2;
@@ -1107,10 +1145,12 @@ __global__ void __launch_bounds__(kHfDecThreads) k_hf_decode(const uint8_t* __re
             const uint32_t wds = rem / 4;
             const uint32_t ow[3] = {wds == 3 ? o0 : (wds == 2 ? o1 : o2), wds == 3 ? o1 : o2, o2};
             for (uint32_t k = 0; k < wds; ++k)
-                *reinterpret_cast<uint32_t*>(out + s0 + done + 4 * k) = ow[k];
-            for (uint32_t k = done + 4 * wds; k < cntb; ++k) out[s0 + k] = (uint8_t)(cur >> (8 * (k & 3)));
-            // bits consumed past the block's words: corrupt (wi - 3 words have entered buf)
-            if (32ull * (wi - 3) - have > 32ull * nw) bad = true;
+                *reinterpret_cast<uint32_t*>(out + base + done + 4 * k) = ow[k];
+            for (uint32_t k = done + 4 * wds; k < cntb; ++k) out[base + k] = (uint8_t)(cur >> (8 * (k & 3)));
+            // the bit position reached (wi - 3 words have entered buf): the next starting point,
+            // and within the block's words
+            const uint64_t pos = 32ull * (wi - 3) - have;
+            if (pos > 32ull * nw || (j < 3 && pos != subs[3 * b + j])) bad = true;
         }
         if (bad) set_status(status, HI_ECORRUPT);
     }
@@ -1155,8 +1195,8 @@ cudaError_t launch_cr_encode(const uint8_t* in, uint64_t n, uint8_t* out, uint64
     if (e != cudaSuccess) return e;
     k_cr_hist<<<cr_grid((n / 16 + 255) / 256, 8, num_sms), 256, 0, st>>>(in, n, hist);
     k_cr_codebook<<<1, 32 * kBookWarps, 0, st>>>(hist, lens, codes, out + 32);
-    k_hf_count<<<cr_grid((nb + 7) / 8, 8, num_sms), 256, 0, st>>>(in, n, lens, words,
-                                                                    reinterpret_cast<uint32_t*>(out + kCrHdr));
+    k_hf_count<<<cr_grid((nb + 7) / 8, 8, num_sms), 256, 0, st>>>(
+        in, n, lens, words, reinterpret_cast<uint32_t*>(out + kCrHdr), reinterpret_cast<uint16_t*>(out + kCrHdr + 4 * nb));
     k_cr_scan_words<<<1, 1024, 0, st>>>(words, n, woff, hdr, out);
     k_hf_encode<<<cr_grid((nb + kHfEncWarps - 1) / kHfEncWarps, 8, num_sms), 32 * kHfEncWarps, 0, st>>>(
         in, n, lens, codes, words, woff, hf);
@@ -1184,7 +1224,7 @@ cudaError_t launch_cr_decode(const uint8_t* in, uint64_t in_len, uint64_t n, uin
     uint8_t* hf = ws + L.hf;
     k_cr_dec_scan<<<1, 1024, 0, st>>>(in, in_len, n, woff, poff, hdr, status);
     k_cr_lc_decode<<<cr_grid(ncm, 3, num_sms), kCrThreads, kCrSmem, st>>>(in, poff, n, hdr, hf, status);
-    k_hf_decode<<<cr_grid((nb + kHfDecThreads - 1) / kHfDecThreads, 16, num_sms), kHfDecThreads, 0, st>>>(
+    k_hf_decode<<<cr_grid((4 * nb + kHfDecThreads - 1) / kHfDecThreads, 8, num_sms), kHfDecThreads, 0, st>>>(
         in, hf, woff, n, hdr, out, status);
     return cudaGetLastError();
 }

@@ -135,7 +135,7 @@ def test_corrupt_streams(hi, oracle_mod):
     assert st == hi.HI_ECORRUPT
     # a chunk size that points past the end of the stream
     nb = (d.size + 4095) // 4096
-    tab = 288 + 4 * nb
+    tab = 288 + 4 * nb + (6 * nb + 3) // 4 * 4
     bad = s.copy()
     bad[tab:tab + 4] = np.frombuffer(np.uint32(1 << 24).tobytes(), dtype=np.uint8)
     _, st = _gpu_decode(hi, codec, bad, d.size)
@@ -147,6 +147,13 @@ def test_corrupt_streams(hi, oracle_mod):
     assert st == hi.HI_ECORRUPT
     # truncated payloads
     _, st = _gpu_decode(hi, codec, s[: s.size // 2 // 16 * 16], d.size)
+    assert st == hi.HI_ECORRUPT
+    # a starting point of a block that is not where its symbol 1024 begins
+    bad = s.copy()
+    sp = 288 + 4 * nb + 2 * 3 * 5  # block 5's first starting point
+    bad[sp:sp + 2] = np.frombuffer(np.uint16(int(np.frombuffer(bytes(s[sp:sp + 2]), np.uint16)[0]) + 1).tobytes(),
+                                   dtype=np.uint8)
+    _, st = _gpu_decode(hi, codec, bad, d.size)
     assert st == hi.HI_ECORRUPT
 
 

@@ -103,8 +103,9 @@ def test_single_symbol_stream_by_hand():
     s = oracle.cr_encode(np.full(8, 128, dtype=np.uint8))
     ln = bytearray(256)
     ln[128] = 1
-    want = _header(8, 1, 4, 1) + bytes(ln) + struct.pack("<I", 1) + struct.pack("<II", 16, 1)
-    want += bytes(304 - len(want)) + bytes(16)
+    want = _header(8, 1, 4, 1) + bytes(ln) + struct.pack("<I", 1) + struct.pack("<HHH", 8, 8, 8) + bytes(2)
+    want += struct.pack("<II", 16, 1)
+    want += bytes(320 - len(want)) + bytes(16)
     assert bytes(s) == want
     assert np.array_equal(oracle.cr_decode(s, 8), np.full(8, 128, dtype=np.uint8))
 
@@ -127,8 +128,9 @@ def test_two_symbol_stream_by_hand():
     payload = u.to_bytes(8, "little") + r[8:]
     ln = bytearray(256)
     ln[127] = ln[129] = 1
-    want = _header(128, 1, 16, 1) + bytes(ln) + struct.pack("<I", 4) + struct.pack("<II", 16, 9)
-    want += bytes(304 - len(want)) + payload + bytes(16 - len(payload))
+    want = _header(128, 1, 16, 1) + bytes(ln) + struct.pack("<I", 4) + struct.pack("<HHH", 128, 128, 128) + bytes(2)
+    want += struct.pack("<II", 16, 9)
+    want += bytes(320 - len(want)) + payload + bytes(16 - len(payload))
     assert bytes(s) == want
     assert np.array_equal(oracle.cr_decode(s, 128), d)
 
@@ -151,7 +153,8 @@ def test_random_bytes_stored_raw():
     n, hb, nb, H, cc, nc = struct.unpack("<QIIQII", bytes(s[:32]))
     assert (n, nb, H, nc) == (16384, 4, 16384, 1)
     assert all(v == 8 for v in s[32:288])
-    size, m1 = struct.unpack("<II", bytes(s[288 + 16:288 + 24]))
+    assert struct.unpack("<12H", bytes(s[288 + 16:288 + 40])) == (8192, 16384, 24576) * 4
+    size, m1 = struct.unpack("<II", bytes(s[288 + 40:288 + 48]))
     assert size == 0x80000000 | 16384 and m1 == 0
     assert np.array_equal(oracle.cr_decode(s, d.size), d)
 
@@ -175,3 +178,30 @@ def test_reordered_codes_smaller_than_throughput_mode():
     s = oracle.cr_encode(seq)
     assert np.array_equal(oracle.cr_decode(s, seq.size), seq)
     assert s.size < oracle.tp_encode(seq).size
+
+
+@pytest.mark.parametrize("n", [5000, 4096 * 3 + 1500, 4096 + 1024, 4096 + 1023])
+def test_block_starting_points(n):
+    """The table of starting points: for every block, the bit offsets of its
+    symbols 1024, 2048 and 3072 (the running sum of the code lengths), or
+    its bit count where the block is shorter; a wrong entry makes the
+    stream corrupt."""
+    rng = np.random.default_rng(n)
+    d = np.clip(np.round(rng.laplace(128.0, 2.0, n)), 0, 255).astype(np.uint8)
+    s = oracle.cr_encode(d)
+    freq = np.bincount(d, minlength=256).astype(np.uint64)
+    ln = oracle.hf_lengths(freq).astype(np.int64)
+    nb = (n + 4095) // 4096
+    sub = struct.unpack("<%dH" % (3 * nb), bytes(s[288 + 4 * nb:288 + 4 * nb + 6 * nb]))
+    for b in range(nb):
+        blk = d[4096 * b:4096 * (b + 1)].astype(np.int64)
+        cum = np.concatenate([[0], np.cumsum(ln[blk])])
+        for j in (1, 2, 3):
+            want = int(cum[min(1024 * j, blk.size)])
+            assert sub[3 * b + j - 1] == want, (b, j)
+    assert np.array_equal(oracle.cr_decode(s, n), d)
+    bad = s.copy()
+    off = 288 + 4 * nb + 2 * 0
+    bad[off] ^= 1
+    with pytest.raises(Exception):
+        oracle.cr_decode(bad, n)
