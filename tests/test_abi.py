@@ -121,3 +121,38 @@ def test_compress_seq_fused_decision(lib):
         assert lib.compress_seq_fused(p, a + 4, b), (shape, A)  # the codes' own alignment does not matter
     for shape, A in separate:
         assert not lib.compress_seq_fused(lib.make_params(shape, 1e-3, "rel", A), a, b), (shape, A)
+
+
+def test_compress_seq_fused_rule_random_shapes(lib):
+    """The same decision on 300 random shapes against a restatement of the
+    rule: A = 8 or 16, n2 a multiple of A, and on every level l < log2 A
+    the coarser-point count, the fastest-dim extent, the all-even points of a
+    plane and of a row of the stride-2^l subgrid all multiples of A >> l."""
+    import numpy as np
+    rng = np.random.default_rng(3)
+
+    def rule(shape, A):
+        n = (1,) * (3 - len(shape)) + tuple(shape)
+        if A not in (8, 16) or n[2] % A:
+            return False
+        sub = list(n)
+        for l in range(A.bit_length() - 1):
+            c = A >> l
+            h1, h2 = (sub[1] + 1) // 2, (sub[2] + 1) // 2
+            pre = ((sub[0] + 1) // 2) * h1 * h2
+            if pre % c or sub[2] % c or (h1 * h2) % c or h2 % c:
+                return False
+            sub = [(s + 1) // 2 for s in sub]
+        return True
+
+    hits = 0
+    for _ in range(300):
+        A = int(rng.choice([4, 8, 16, 32]))
+        shape = tuple(int(v) for v in rng.choice([1, 2, 3, 5, 8, 16, 24, 32, 40, 48, 64, 96, 100, 128], size=3))
+        if max(shape) < 2:
+            continue
+        p = lib.make_params(shape, 1e-3, "rel", A)
+        want = rule(shape, A)
+        hits += want
+        assert lib.compress_seq_fused(p, 0x100000, 0x900000) == want, (shape, A)
+    assert hits > 20
