@@ -156,3 +156,20 @@ def test_compress_seq_fused_rule_random_shapes(lib):
         hits += want
         assert lib.compress_seq_fused(p, 0x100000, 0x900000) == want, (shape, A)
     assert hits > 20
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/hi.h is a C header: it compiles as strict C99 with no C++ and
+    no torch types (the boundary is plain pointers and sizes)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_hi.c"
+    src.write_text('#include "hi.h"\nint main(void) { return (int)sizeof(hi_header) == 0; }\n')
+    cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                        "-I" + os.path.join(ROOT, "include"), "-I" + cuda_inc, str(src)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
