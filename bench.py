@@ -723,7 +723,7 @@ def run_gpu(args):
         others = other_workloads(args, dev, x_host)
 
     cpu = None
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and ws == 1 and not args.no_cpu:  # the oracle leg: one process on one GPU only
         cpu, ref = cpu_baseline(x_host, args.cpu_planes)
         if args.cpu_planes == SHAPE[0]:
             # same field, same eb: the oracle's codes must equal this run's, bit for bit
